@@ -1,0 +1,169 @@
+"""CPU oracle for the Needleman-Wunsch path -- TEST INFRASTRUCTURE ONLY.
+
+Only ``tests/``, ``__graft_entry__.smoke()`` and the CPU-baseline leg of
+``bench.py`` may import this package.  The library under
+``paper_2412_21103_gb300`` never imports it and shares no code with it.
+
+``nw_oracle.c`` holds the plain full-matrix dynamic programme (Sec. 2.1-2.4 of
+the paper, Eq. 1 read as standard NW) and is compiled here with gcc into
+``oracle/_build/libnw_oracle.so``.  The Python helpers below only marshal
+arguments and run-length encode the op string.
+
+Functions whose result the paper or mathematics pins (see ``tests/``):
+  fill / score / align  -- brute force over all alignments, closed forms,
+                           Levenshtein and LCS special cases, invariants,
+                           hand-worked grids in ``tests/golden``.
+  banded                -- equals full NW for a band covering the grid;
+                           brute force over in-band paths; the bound U is
+                           checked against brute force over out-of-band paths.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import subprocess
+import threading
+from concurrent.futures import ThreadPoolExecutor
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SRC = os.path.join(_HERE, "nw_oracle.c")
+_OUT = os.path.join(_HERE, "_build", "libnw_oracle.so")
+_lock = threading.Lock()
+_lib = None
+
+NEG_INF = -(2 ** 31) // 2   # INT32_MIN / 2, the banded "-inf"
+
+
+def build(force: bool = False) -> str:
+    """Compile the oracle with gcc (plain -O2, no vector extensions)."""
+    os.makedirs(os.path.dirname(_OUT), exist_ok=True)
+    if force or not os.path.exists(_OUT) or os.path.getmtime(_OUT) < os.path.getmtime(_SRC):
+        tmp = _OUT + f".tmp{os.getpid()}"
+        subprocess.check_call(["gcc", "-O2", "-std=c11", "-fPIC", "-shared", "-o", tmp, _SRC])
+        os.replace(tmp, _OUT)
+    return _OUT
+
+
+def _load():
+    global _lib
+    with _lock:
+        if _lib is None:
+            lib = ctypes.CDLL(build())
+            u8p = ctypes.POINTER(ctypes.c_uint8)
+            i32p = ctypes.POINTER(ctypes.c_int32)
+            i64 = ctypes.c_int64
+            i32 = ctypes.c_int32
+            lib.nwo_fill.argtypes = [u8p, i64, u8p, i64, i32, i32, i32, i32p]
+            lib.nwo_align.argtypes = [u8p, i64, u8p, i64, i32, i32, i32, i32p, ctypes.c_char_p,
+                                      ctypes.POINTER(i64)]
+            lib.nwo_score.argtypes = [u8p, i64, u8p, i64, i32, i32, i32, i32p]
+            lib.nwo_banded.argtypes = [u8p, i64, u8p, i64, i32, i32, i32, i64, i32p, i32p, i32p]
+            for f in (lib.nwo_fill, lib.nwo_align, lib.nwo_score, lib.nwo_banded):
+                f.restype = ctypes.c_int
+            _lib = lib
+    return _lib
+
+
+def _codes(x) -> np.ndarray:
+    if isinstance(x, str):
+        lut = {"A": 0, "C": 1, "G": 2, "T": 3}
+        return np.array([lut[c] for c in x.upper()], dtype=np.uint8)
+    arr = np.ascontiguousarray(np.asarray(x, dtype=np.uint8))
+    if arr.size and arr.max() > 3:
+        raise ValueError("base codes must be 0..3")
+    return arr
+
+
+def _ptr(arr: np.ndarray, ctype=ctypes.c_uint8):
+    if arr.size == 0:
+        arr = np.zeros(1, dtype=arr.dtype)
+    return arr.ctypes.data_as(ctypes.POINTER(ctype)), arr
+
+
+def fill(a, b, match: int = 1, mismatch: int = -1, gap: int = -1) -> np.ndarray:
+    """The full (m+1) x (n+1) score grid H."""
+    a, b = _codes(a), _codes(b)
+    H = np.empty((a.size + 1, b.size + 1), dtype=np.int32)
+    pa, ka = _ptr(a)
+    pb, kb = _ptr(b)
+    rc = _load().nwo_fill(pa, a.size, pb, b.size, match, mismatch, gap,
+                          H.ctypes.data_as(ctypes.POINTER(ctypes.c_int32)))
+    assert rc == 0, rc
+    return H
+
+
+def score(a, b, match: int = 1, mismatch: int = -1, gap: int = -1) -> int:
+    a, b = _codes(a), _codes(b)
+    out = ctypes.c_int32(0)
+    pa, ka = _ptr(a)
+    pb, kb = _ptr(b)
+    rc = _load().nwo_score(pa, a.size, pb, b.size, match, mismatch, gap, ctypes.byref(out))
+    assert rc == 0, rc
+    return int(out.value)
+
+
+def align(a, b, match: int = 1, mismatch: int = -1, gap: int = -1) -> tuple[int, str]:
+    """(score, op string over '=XID' in forward order)."""
+    a, b = _codes(a), _codes(b)
+    out = ctypes.c_int32(0)
+    nops = ctypes.c_int64(0)
+    buf = ctypes.create_string_buffer(a.size + b.size + 1)
+    pa, ka = _ptr(a)
+    pb, kb = _ptr(b)
+    rc = _load().nwo_align(pa, a.size, pb, b.size, match, mismatch, gap, ctypes.byref(out), buf,
+                           ctypes.byref(nops))
+    if rc == -2:
+        raise MemoryError("oracle grid does not fit in host memory")
+    assert rc == 0, rc
+    return int(out.value), buf.raw[: nops.value].decode()
+
+
+def banded(a, b, w: int, match: int = 1, mismatch: int = -1, gap: int = -1,
+           want_grid: bool = False):
+    """(S_b, U) for half-width w, plus the banded grid when asked."""
+    a, b = _codes(a), _codes(b)
+    sb = ctypes.c_int32(0)
+    ub = ctypes.c_int32(0)
+    pa, ka = _ptr(a)
+    pb, kb = _ptr(b)
+    H = np.empty((a.size + 1, b.size + 1), dtype=np.int32) if want_grid else None
+    hp = H.ctypes.data_as(ctypes.POINTER(ctypes.c_int32)) if want_grid else None
+    rc = _load().nwo_banded(pa, a.size, pb, b.size, match, mismatch, gap, w, ctypes.byref(sb),
+                            ctypes.byref(ub), hp)
+    assert rc == 0, rc
+    if want_grid:
+        return int(sb.value), int(ub.value), H
+    return int(sb.value), int(ub.value)
+
+
+def rle(ops: str) -> str:
+    """Run-length encode an op string into a CIGAR ('3=1X2I')."""
+    if not ops:
+        return ""
+    out = []
+    prev = ops[0]
+    cnt = 0
+    for c in ops:
+        if c == prev:
+            cnt += 1
+        else:
+            out.append(f"{cnt}{prev}")
+            prev, cnt = c, 1
+    out.append(f"{cnt}{prev}")
+    return "".join(out)
+
+
+def score_many(pairs, match: int = 1, mismatch: int = -1, gap: int = -1, threads: int | None = None):
+    """Scores of many (a, b) pairs on a pool of host threads (the C call
+    releases the GIL)."""
+    threads = threads or os.cpu_count() or 1
+    with ThreadPoolExecutor(threads) as ex:
+        return list(ex.map(lambda p: score(p[0], p[1], match, mismatch, gap), pairs))
+
+
+def align_many(pairs, match: int = 1, mismatch: int = -1, gap: int = -1, threads: int | None = None):
+    threads = threads or os.cpu_count() or 1
+    with ThreadPoolExecutor(threads) as ex:
+        return list(ex.map(lambda p: align(p[0], p[1], match, mismatch, gap), pairs))
