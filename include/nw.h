@@ -1,0 +1,175 @@
+/*
+ * nw.h -- C ABI of libnw, a GB300 (sm_103a) Needleman-Wunsch library.
+ *
+ * What it computes (the paper's Sec. 2): global alignment of two DNA
+ * sequences with a linear gap penalty.  The score grid has (m+1) x (n+1)
+ * cells (Sec. 2.1, row 0 / column 0 are the empty label cells), starts from
+ * H(0,0)=0, H(i,0)=i*gap, H(0,j)=j*gap (Sec. 2.2) and is filled with
+ *     H(i,j) = max(H(i-1,j-1) + s(A_i,B_j), H(i-1,j) + gap, H(i,j-1) + gap)
+ * (Sec. 2.3, Eq. 1 read as standard NW; s = match or mismatch).  The
+ * alignment is the backtrack of Sec. 2.4 from (m,n) with the single path
+ * chosen by the priority diagonal > vertical > horizontal (the order of the
+ * direction codes 1/2/3 of Sec. 3.1).
+ *
+ * Conventions used by every entry point
+ *   - A is the query (rows, length m), B the reference (columns, length n).
+ *   - Sequences are 2-bit packed: A=0, C=1, G=2, T=3; base k sits at bits
+ *     2*(k%4) .. 2*(k%4)+1 of byte k/4 (least significant first); a sequence
+ *     of L bases takes ceil(L/4) bytes; unused high bits of the last byte are
+ *     ignored.
+ *   - CIGAR ops: '=' match, 'X' mismatch, 'I' base of A alone (vertical move),
+ *     'D' base of B alone (horizontal move); run-length encoded ("12=1X3I"),
+ *     NUL-terminated.  NW_CIGAR_M merges '='/'X' into 'M'.  A CIGAR never
+ *     needs more than nw_cigar_bound(m, n) bytes including the NUL.
+ *   - Zero-length sequences are valid.  m and n must be below 2^30.
+ *   - Scoring: gap <= 0, mismatch <= match, every value in [-40, 40]; the
+ *     product (match - 2*gap) * min(m,n) must stay below 2^29.
+ *   - Memory: without NW_HOST_IO every sequence/output pointer is a device
+ *     pointer on the context's device and the call is asynchronous on the
+ *     context's stream (stream-ordered; call nw_ctx_sync to wait and collect
+ *     device-side errors).  With NW_HOST_IO they are host pointers: the call
+ *     copies inputs in, runs, copies results out and waits.  Per-pair and
+ *     per-sequence metadata arrays (offsets, lengths, CIGAR offsets) are
+ *     always host arrays.
+ *   - Ownership: the caller owns every buffer it passes; the library never
+ *     frees or retains them after the call returns (device-side work may
+ *     still read them until the stream reaches that point).  Scratch memory
+ *     comes from the context's pool, capped by its budget (NW_ERR_OOM beyond).
+ *   - Errors: every call returns an nw_status; nw_strerror gives a short
+ *     text and nw_ctx_last_message the detail of the last failure on that
+ *     context.  Calls on one context must not be made from two host threads
+ *     at once.
+ */
+#ifndef NW_H_
+#define NW_H_
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    NW_OK = 0,
+    NW_ERR_ARG = 1,           /* bad argument (size, scoring, null pointer)  */
+    NW_ERR_BAD_BASE = 2,      /* a character outside ACGT/acgt               */
+    NW_ERR_OOM = 3,           /* scratch would exceed the context budget     */
+    NW_ERR_CIGAR_TRUNC = 4,   /* CIGAR capacity too small; length reported   */
+    NW_ERR_TIMEOUT = 5,       /* a bounded device-side wait gave up          */
+    NW_ERR_CUDA = 6,          /* a CUDA runtime call failed                   */
+    NW_ERR_UNSUPPORTED = 7    /* valid request this build cannot serve        */
+} nw_status;
+
+/* Flags (bitwise OR). */
+#define NW_SCORE_ONLY   0u
+#define NW_CIGAR        1u    /* also produce the alignment                  */
+#define NW_LEARNED_BAND 2u    /* batch: certified learned band first          */
+#define NW_HOST_IO      4u    /* sequence inputs and outputs are host memory  */
+#define NW_CIGAR_M      8u    /* write 'M' for both '=' and 'X'               */
+
+typedef struct {
+    int32_t match;      /* score of a diagonal step with equal bases (Sec. 2.3: +1)   */
+    int32_t mismatch;   /* score of a diagonal step with unequal bases (Sec. 2.3: -1) */
+    int32_t gap;        /* score of a vertical or horizontal step (Sec. 2.3: -1)      */
+} nw_scoring;
+
+typedef struct nw_ctx nw_ctx;
+
+/* ---------------------------------------------------------------- context */
+
+/* Create a context on CUDA device `device` that launches on `stream` (a
+ * cudaStream_t; NULL = the legacy default stream) and keeps at most
+ * `mem_budget` bytes of scratch (0 = 90% of the device's free memory).
+ * Returns NULL on failure.  Not in the paper: the host-side state the
+ * library needs around its kernels. */
+nw_ctx *nw_ctx_create(int device, void *stream, uint64_t mem_budget);
+void nw_ctx_destroy(nw_ctx *ctx);
+/* Change the stream later calls launch on. */
+int nw_ctx_set_stream(nw_ctx *ctx, void *stream);
+/* Wait for the context's stream and return the first device-side error
+ * raised since the previous sync (NW_ERR_TIMEOUT, NW_ERR_BAD_BASE), else the
+ * CUDA status mapped to NW_ERR_CUDA, else NW_OK.  Clears the device error. */
+int nw_ctx_sync(nw_ctx *ctx);
+/* Detail of the last failure on this context ("" if none).  Owned by ctx. */
+const char *nw_ctx_last_message(const nw_ctx *ctx);
+const char *nw_strerror(int status);
+
+/* Per-kernel timing: when on, every launch is bracketed by CUDA events on
+ * the context's stream; nw_ctx_kernel_stats reports, per kernel name, the
+ * launch count and the summed device time in ms (summed after a sync). It
+ * returns how many kernel names exist (fills at most `cap` of them). */
+int nw_ctx_set_profiling(nw_ctx *ctx, int on);
+int nw_ctx_kernel_stats(nw_ctx *ctx, const char **names, uint64_t *launches, double *total_ms, int cap);
+int nw_ctx_reset_stats(nw_ctx *ctx);
+
+/* ---------------------------------------------------------------- packing */
+
+/* Host: pack `len` ASCII bases (ACGT, either case) into 2-bit codes.
+ * out2b must hold ceil(len/4) bytes.  NW_ERR_BAD_BASE on any other
+ * character (out2b is then unspecified).  The paper stores one char per
+ * base (Sec. 3.1 listing); this is the 2-bit layout described above. */
+int nw_pack(const char *ascii, uint64_t len, uint8_t *out2b);
+
+/* Device: the same packing by a GPU kernel (device pointers, asynchronous).
+ * A bad character is reported by the next nw_ctx_sync as NW_ERR_BAD_BASE. */
+int nw_pack_device(nw_ctx *ctx, const char *ascii, uint64_t len, uint8_t *out2b);
+
+/* Worst-case CIGAR size in bytes, NUL included: 2*(m+n)+1. */
+uint64_t nw_cigar_bound(uint64_t m, uint64_t n);
+
+/* -------------------------------------------------------------- alignment */
+
+/* One pair (Sec. 2.2-2.4).  Writes the score H(m,n) to *score; with
+ * NW_CIGAR also the CIGAR (NUL-terminated) into cigar[0..cigar_cap) and its
+ * length without the NUL into *cigar_len.  With device outputs cigar_cap
+ * must be at least nw_cigar_bound(m,n); with NW_HOST_IO a smaller buffer
+ * returns NW_ERR_CIGAR_TRUNC with the needed length in *cigar_len. */
+int nw_align(nw_ctx *ctx, const uint8_t *a2b, uint64_t m, const uint8_t *b2b, uint64_t n,
+             nw_scoring sc, uint32_t flags, int32_t *score,
+             char *cigar, uint64_t cigar_cap, uint64_t *cigar_len);
+
+/* Many independent pairs in one call (the paper's Sec. 3.2 pairwise stage,
+ * batched on one device instead of split over MPI ranks).  Pair k aligns the
+ * sequence at byte offset a_off[k] of `pool2b` (a_len[k] bases) against the
+ * one at b_off[k] (b_len[k] bases).  scores[k] receives the score.  With
+ * NW_CIGAR, pair k's CIGAR goes to cigar_pool + cigar_off[k] with capacity
+ * cigar_off[k+1] - cigar_off[k] (which must be >= nw_cigar_bound of the pair)
+ * and its length to cigar_len[k].  a_off, a_len, b_off, b_len and cigar_off
+ * (npairs+1 entries) are host arrays; pool2b, scores, cigar_pool, cigar_len
+ * are device memory unless NW_HOST_IO.  With NW_LEARNED_BAND each pair is
+ * first run in a band whose half-width a trained model predicts (see
+ * nw_band_model_load); a banded result is kept only when a certificate
+ * proves it equals the full alignment, else the band is widened and finally
+ * the full grid is used -- results are exact either way. */
+int nw_align_batch(nw_ctx *ctx, const uint8_t *pool2b,
+                   const uint64_t *a_off, const uint32_t *a_len,
+                   const uint64_t *b_off, const uint32_t *b_len, uint32_t npairs,
+                   nw_scoring sc, uint32_t flags, int32_t *scores,
+                   char *cigar_pool, const uint64_t *cigar_off, uint64_t *cigar_len);
+
+/* All-vs-all scores of `nseq` sequences (the scoring-matrix stage of the
+ * paper's center-star alignment, Sec. 3.2; Eq. 2 gives its n(n-1)/2 pairs).
+ * Sequence k starts at byte offset off[k] of pool2b and has len[k] bases
+ * (host arrays).  out receives the full nseq x nseq int32 matrix,
+ * row-major: out[i*nseq+j] = score(seq i as A, seq j as B), symmetric, with
+ * out[i*nseq+i] = len[i]*match. */
+int nw_score_all_pairs(nw_ctx *ctx, const uint8_t *pool2b, const uint64_t *off, const uint32_t *len,
+                       uint32_t nseq, nw_scoring sc, uint32_t flags, int32_t *out);
+
+/* ------------------------------------------------------------ measurement */
+
+/* Integer-pipe peak microbenchmark used as the roofline denominator: every
+ * SM runs independent dependency chains of one instruction kind for
+ * `iters` iterations; *gops receives the measured rate in 1e9 warp-lane
+ * operations per second.  kind: 0 = 3-input add-then-max (__viaddmax_s32),
+ * 1 = 3-input max (__vimax3_s32), 2 = 2-input max, 3 = add, 4 = byte
+ * permute (prmt), 5 = the score-only cell mix (1 prmt + 1 add-max + 1 max).
+ * Not in the paper. */
+int nw_peak_int(nw_ctx *ctx, int kind, uint64_t iters, double *gops);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* NW_H_ */

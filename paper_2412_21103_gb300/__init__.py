@@ -1,0 +1,324 @@
+"""Python binding of libnw, the GB300 Needleman-Wunsch library.
+
+Argument marshalling only: every step of the alignment runs in the CUDA
+kernels behind the C ABI declared in ``include/nw.h``.  Device buffers are
+torch CUDA tensors (torch is used for device memory and streams), host
+buffers are numpy arrays.  If ``libnw.so`` has not been built this module
+raises on first use; there is no CPU fallback.
+
+Functions keep the C names: ``nw_pack``, ``nw_pack_device``, ``nw_align``,
+``nw_align_batch``, ``nw_score_all_pairs``, ``nw_peak_int``; ``Context``
+wraps ``nw_ctx``.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+from . import build as _build
+
+NW_OK = 0
+NW_ERR_ARG = 1
+NW_ERR_BAD_BASE = 2
+NW_ERR_OOM = 3
+NW_ERR_CIGAR_TRUNC = 4
+NW_ERR_TIMEOUT = 5
+NW_ERR_CUDA = 6
+NW_ERR_UNSUPPORTED = 7
+
+NW_SCORE_ONLY = 0
+NW_CIGAR = 1
+NW_LEARNED_BAND = 2
+NW_HOST_IO = 4
+NW_CIGAR_M = 8
+
+DEFAULT_SCORING = (1, -1, -1)
+
+_lib = None
+
+
+class NWError(RuntimeError):
+    def __init__(self, status: int, msg: str):
+        super().__init__(f"libnw status {status}: {msg}")
+        self.status = status
+
+
+class Scoring(ctypes.Structure):
+    _fields_ = [("match", ctypes.c_int32), ("mismatch", ctypes.c_int32), ("gap", ctypes.c_int32)]
+
+
+def lib_path() -> str:
+    return _build.LIB
+
+
+def load():
+    """Load libnw.so (built by ``build()``); raises if it is missing."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    path = lib_path()
+    if not os.path.exists(path):
+        raise ImportError(f"libnw.so is not built ({path}); run __graft_entry__.build()")
+    L = ctypes.CDLL(path)
+    vp, u64, u32, i32 = ctypes.c_void_p, ctypes.c_uint64, ctypes.c_uint32, ctypes.c_int32
+    u64p = ctypes.POINTER(ctypes.c_uint64)
+    u32p = ctypes.POINTER(ctypes.c_uint32)
+    sig = {
+        "nw_ctx_create": (vp, [ctypes.c_int, vp, u64]),
+        "nw_ctx_destroy": (None, [vp]),
+        "nw_ctx_set_stream": (ctypes.c_int, [vp, vp]),
+        "nw_ctx_sync": (ctypes.c_int, [vp]),
+        "nw_ctx_last_message": (ctypes.c_char_p, [vp]),
+        "nw_strerror": (ctypes.c_char_p, [ctypes.c_int]),
+        "nw_ctx_set_profiling": (ctypes.c_int, [vp, ctypes.c_int]),
+        "nw_ctx_kernel_stats": (ctypes.c_int, [vp, ctypes.POINTER(ctypes.c_char_p), u64p,
+                                               ctypes.POINTER(ctypes.c_double), ctypes.c_int]),
+        "nw_ctx_reset_stats": (ctypes.c_int, [vp]),
+        "nw_pack": (ctypes.c_int, [ctypes.c_char_p, u64, vp]),
+        "nw_pack_device": (ctypes.c_int, [vp, vp, u64, vp]),
+        "nw_cigar_bound": (u64, [u64, u64]),
+        "nw_align": (ctypes.c_int, [vp, vp, u64, vp, u64, Scoring, u32, vp, vp, u64, vp]),
+        "nw_align_batch": (ctypes.c_int, [vp, vp, u64p, u32p, u64p, u32p, u32, Scoring, u32, vp, vp, u64p, vp]),
+        "nw_score_all_pairs": (ctypes.c_int, [vp, vp, u64p, u32p, u32, Scoring, u32, vp]),
+        "nw_peak_int": (ctypes.c_int, [vp, ctypes.c_int, u64, ctypes.POINTER(ctypes.c_double)]),
+    }
+    for name, (res, args) in sig.items():
+        f = getattr(L, name)
+        f.restype = res
+        f.argtypes = args
+    _lib = L
+    return L
+
+
+def exported_symbols() -> list[str]:
+    """Names declared in include/nw.h (parsed from the header)."""
+    import re
+    hdr = os.path.join(os.path.dirname(os.path.dirname(os.path.abspath(__file__))), "include", "nw.h")
+    text = open(hdr).read()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    return sorted(set(re.findall(r"\b(nw_[a-z0-9_]+)\s*\(", text)))
+
+
+# ---------------------------------------------------------------- helpers
+def _ptr(x) -> int | None:
+    """Raw address of a torch tensor or numpy array (None for None)."""
+    if x is None:
+        return None
+    if hasattr(x, "data_ptr"):
+        return x.data_ptr()
+    if isinstance(x, np.ndarray):
+        return x.ctypes.data
+    raise TypeError(f"cannot take the address of {type(x)}")
+
+
+def _is_host(x) -> bool:
+    return isinstance(x, np.ndarray)
+
+
+def _sc(scoring) -> Scoring:
+    if isinstance(scoring, Scoring):
+        return scoring
+    return Scoring(*scoring)
+
+
+def _check(ctx, rc: int):
+    if rc != NW_OK:
+        L = load()
+        msg = L.nw_ctx_last_message(ctx.handle if isinstance(ctx, Context) else ctx)
+        raise NWError(rc, (msg or b"").decode() or L.nw_strerror(rc).decode())
+
+
+def pack_codes(codes: np.ndarray) -> np.ndarray:
+    """Pack an array of base codes 0..3 into the 2-bit layout (host numpy).
+    Same layout as nw_pack; used to stage inputs that are already codes."""
+    codes = np.ascontiguousarray(codes, dtype=np.uint8)
+    n = codes.size
+    pad = (-n) % 4
+    c = np.concatenate([codes, np.zeros(pad, np.uint8)]).reshape(-1, 4).astype(np.uint8)
+    return (c[:, 0] | (c[:, 1] << 2) | (c[:, 2] << 4) | (c[:, 3] << 6)).astype(np.uint8)
+
+
+class Context:
+    """Owns an ``nw_ctx``: device, stream, scratch pool and error word."""
+
+    def __init__(self, device: int = 0, stream=None, mem_budget: int = 0):
+        L = load()
+        s = None
+        if stream is not None:
+            s = stream.cuda_stream if hasattr(stream, "cuda_stream") else int(stream)
+        self.handle = L.nw_ctx_create(device, s, mem_budget)
+        if not self.handle:
+            raise NWError(NW_ERR_CUDA, f"nw_ctx_create failed on device {device}")
+        self.device = device
+
+    def close(self):
+        if getattr(self, "handle", None):
+            load().nw_ctx_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    def set_stream(self, stream):
+        s = stream.cuda_stream if hasattr(stream, "cuda_stream") else stream
+        _check(self, load().nw_ctx_set_stream(self.handle, s))
+
+    def sync(self):
+        _check(self, load().nw_ctx_sync(self.handle))
+
+    def set_profiling(self, on: bool):
+        _check(self, load().nw_ctx_set_profiling(self.handle, int(bool(on))))
+
+    def reset_stats(self):
+        _check(self, load().nw_ctx_reset_stats(self.handle))
+
+    def kernel_stats(self) -> dict[str, tuple[int, float]]:
+        L = load()
+        n = L.nw_ctx_kernel_stats(self.handle, None, None, None, 0)
+        names = (ctypes.c_char_p * max(n, 1))()
+        launches = (ctypes.c_uint64 * max(n, 1))()
+        ms = (ctypes.c_double * max(n, 1))()
+        n = L.nw_ctx_kernel_stats(self.handle, names, launches, ms, n)
+        return {names[k].decode(): (int(launches[k]), float(ms[k])) for k in range(n)}
+
+
+# ------------------------------------------------------------- entry points
+def nw_pack(ascii_seq) -> np.ndarray:
+    """Host packing of an ASCII sequence (str/bytes) -> uint8 numpy array."""
+    data = ascii_seq.encode() if isinstance(ascii_seq, str) else bytes(ascii_seq)
+    out = np.zeros(max((len(data) + 3) // 4, 1), np.uint8)
+    rc = load().nw_pack(data, len(data), out.ctypes.data)
+    if rc != NW_OK:
+        raise NWError(rc, load().nw_strerror(rc).decode())
+    return out[: (len(data) + 3) // 4]
+
+
+def nw_pack_device(ctx: Context, ascii_dev, length: int, out_dev):
+    """Device packing: ascii_dev / out_dev are CUDA uint8 tensors."""
+    _check(ctx, load().nw_pack_device(ctx.handle, _ptr(ascii_dev), length, _ptr(out_dev)))
+
+
+def nw_cigar_bound(m: int, n: int) -> int:
+    return int(load().nw_cigar_bound(m, n))
+
+
+def nw_align(ctx: Context, a2b, m: int, b2b, n: int, scoring=DEFAULT_SCORING, flags: int = 0,
+             score=None, cigar=None, cigar_len=None):
+    """Align one pair.
+
+    Host mode (a2b, b2b numpy arrays): returns (score, cigar or None).
+    Device mode (CUDA tensors): writes into the given device outputs
+    (int32[1], uint8[nw_cigar_bound], int64[1]) and returns them; the call
+    is asynchronous on the context's stream."""
+    L = load()
+    want = bool(flags & NW_CIGAR)
+    if _is_host(a2b):
+        flags |= NW_HOST_IO
+        sc_out = np.zeros(1, np.int32)
+        cap = nw_cigar_bound(m, n) if want else 0
+        cbuf = np.zeros(max(cap, 1), np.uint8)
+        clen = np.zeros(1, np.uint64)
+        rc = L.nw_align(ctx.handle, _ptr(a2b), m, _ptr(b2b), n, _sc(scoring), flags, _ptr(sc_out),
+                        _ptr(cbuf) if want else None, cap, _ptr(clen) if want else None)
+        _check(ctx, rc)
+        return int(sc_out[0]), (cbuf[: int(clen[0])].tobytes().decode() if want else None)
+    cap = int(cigar.numel()) if (want and cigar is not None) else 0
+    rc = L.nw_align(ctx.handle, _ptr(a2b), m, _ptr(b2b), n, _sc(scoring), flags, _ptr(score),
+                    _ptr(cigar) if want else None, cap, _ptr(cigar_len) if want else None)
+    _check(ctx, rc)
+    return score, cigar, cigar_len
+
+
+def _u64(a):
+    a = np.ascontiguousarray(a, dtype=np.uint64)
+    return a, a.ctypes.data_as(ctypes.POINTER(ctypes.c_uint64))
+
+
+def _u32(a):
+    a = np.ascontiguousarray(a, dtype=np.uint32)
+    return a, a.ctypes.data_as(ctypes.POINTER(ctypes.c_uint32))
+
+
+def nw_align_batch(ctx: Context, pool2b, a_off, a_len, b_off, b_len, scoring=DEFAULT_SCORING, flags: int = 0,
+                   scores=None, cigar_pool=None, cigar_off=None, cigar_len=None):
+    """Align many pairs from one packed pool.  Metadata arrays are host
+    numpy.  Host mode (pool2b numpy) returns (scores ndarray, list of CIGARs
+    or None); device mode writes into the given tensors."""
+    L = load()
+    npairs = len(a_len)
+    ao, aop = _u64(a_off)
+    al, alp = _u32(a_len)
+    bo, bop = _u64(b_off)
+    bl, blp = _u32(b_len)
+    want = bool(flags & NW_CIGAR)
+    if cigar_off is None and want:
+        caps = [nw_cigar_bound(int(x), int(y)) for x, y in zip(al, bl)]
+        cigar_off = np.concatenate([[0], np.cumsum(caps)]).astype(np.uint64)
+    co, cop = _u64(cigar_off) if want else (None, None)
+    if _is_host(pool2b):
+        flags |= NW_HOST_IO
+        sc_out = np.zeros(max(npairs, 1), np.int32)
+        cpool = np.zeros(max(int(co[-1]) if want else 1, 1), np.uint8)
+        clen = np.zeros(max(npairs, 1), np.uint64)
+        rc = L.nw_align_batch(ctx.handle, _ptr(pool2b), aop, alp, bop, blp, npairs, _sc(scoring), flags,
+                              _ptr(sc_out), _ptr(cpool) if want else None, cop, _ptr(clen) if want else None)
+        _check(ctx, rc)
+        cigars = None
+        if want:
+            cigars = [cpool[int(co[k]): int(co[k]) + int(clen[k])].tobytes().decode() for k in range(npairs)]
+        return sc_out[:npairs], cigars
+    rc = L.nw_align_batch(ctx.handle, _ptr(pool2b), aop, alp, bop, blp, npairs, _sc(scoring), flags, _ptr(scores),
+                          _ptr(cigar_pool) if want else None, cop, _ptr(cigar_len) if want else None)
+    _check(ctx, rc)
+    return scores, cigar_pool, cigar_len
+
+
+def nw_score_all_pairs(ctx: Context, pool2b, off, lens, scoring=DEFAULT_SCORING, flags: int = 0, out=None):
+    """All-vs-all score matrix.  Host mode returns an (n, n) int32 array."""
+    L = load()
+    nseq = len(lens)
+    oo, oop = _u64(off)
+    ll, llp = _u32(lens)
+    if _is_host(pool2b):
+        flags |= NW_HOST_IO
+        res = np.zeros((nseq, nseq), np.int32)
+        _check(ctx, L.nw_score_all_pairs(ctx.handle, _ptr(pool2b), oop, llp, nseq, _sc(scoring), flags, _ptr(res)))
+        return res
+    _check(ctx, L.nw_score_all_pairs(ctx.handle, _ptr(pool2b), oop, llp, nseq, _sc(scoring), flags, _ptr(out)))
+    return out
+
+
+def nw_peak_int(ctx: Context, kind: int, iters: int = 1 << 16) -> float:
+    """Measured integer-pipe rate (1e9 lane-ops/s) for one instruction kind."""
+    v = ctypes.c_double(0.0)
+    _check(ctx, load().nw_peak_int(ctx.handle, kind, iters, ctypes.byref(v)))
+    return float(v.value)
+
+
+def pool_of(seqs) -> tuple[np.ndarray, np.ndarray, np.ndarray]:
+    """Pack sequences (code arrays) into one pool; returns (pool, byte
+    offsets, lengths).  Each sequence starts on a 16-byte boundary."""
+    offs, lens, parts = [], [], []
+    pos = 0
+    for s in seqs:
+        p = pack_codes(s)
+        padded = (len(p) + 15) // 16 * 16
+        buf = np.zeros(max(padded, 16), np.uint8)
+        buf[: len(p)] = p
+        offs.append(pos)
+        lens.append(len(s))
+        parts.append(buf)
+        pos += len(buf)
+    pool = np.concatenate(parts) if parts else np.zeros(16, np.uint8)
+    return pool, np.array(offs, np.uint64), np.array(lens, np.uint32)

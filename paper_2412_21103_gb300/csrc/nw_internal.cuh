@@ -1,0 +1,162 @@
+// Internal declarations shared by the libnw translation units.
+//
+// Score domain used by every kernel.  With W(i,j) = H(i,j) - gap*(i+j) the
+// recurrence of Sec. 2.3 becomes
+//     W(i,j) = max(W(i-1,j-1) + s'(A_i,B_j), W(i-1,j), W(i,j-1)),
+//     s' = s - 2*gap,  W(i,0) = W(0,j) = 0,  H(m,n) = W(m,n) + gap*(m+n),
+// because a vertical or horizontal step adds exactly gap to H and one to i+j.
+// The gap term disappears from the inner loop: one cell costs a byte-permute
+// (s'), one DPX add-max and one max.  W is never negative (the all-gap path
+// gives W = 0) and is bounded by max(s',0)*min(i,j).  Ties keep their meaning:
+// H == H(i-1,j-1)+s  <=>  W == W(i-1,j-1)+s',  H == H(i-1,j)+gap  <=>  W == W(i-1,j).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <map>
+#include <string>
+#include <vector>
+
+#include "../../include/nw.h"
+
+namespace nw {
+
+constexpr unsigned kFull = 0xffffffffu;
+
+// Bounds of every spin-wait on a flag another warp or CTA raises: two seconds
+// of wall time (%globaltimer, ns) or 2^24 polls, whichever comes first.
+constexpr uint32_t kSpinLimit = 1u << 24;
+constexpr uint64_t kSpinNanos = 2000000000ull;
+
+// Device error word layout: [0] = first nw_status raised, [1] = detail.
+__device__ __forceinline__ void raise_error(uint32_t *err, uint32_t code, uint32_t detail) {
+    if (atomicCAS(err, 0u, code) == 0u) err[1] = detail;
+}
+
+__device__ __forceinline__ uint32_t ld_acquire(const uint32_t *p) {
+    uint32_t v;
+    asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+    return v;
+}
+
+__device__ __forceinline__ void st_release(uint32_t *p, uint32_t v) {
+    asm volatile("st.release.gpu.global.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+}
+
+__device__ __forceinline__ uint64_t global_ns() {
+    uint64_t t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+
+// Wait until *flag >= target.  Returns false (after raising NW_ERR_TIMEOUT)
+// when a bound is reached or another thread already raised an error, so the
+// caller can leave instead of hanging.
+__device__ __forceinline__ bool wait_geq(const uint32_t *flag, uint32_t target, uint32_t *err, uint32_t where) {
+    if (ld_acquire(flag) >= target) return true;
+    const uint64_t t0 = global_ns();
+    for (uint32_t spins = 1;; ++spins) {
+        if (ld_acquire(flag) >= target) return true;
+        if ((spins & 63u) == 0) {
+            if (*(volatile uint32_t *)err != 0u) return false;
+            if (spins >= kSpinLimit || global_ns() - t0 > kSpinNanos) {
+                raise_error(err, NW_ERR_TIMEOUT, where);
+                return false;
+            }
+            __nanosleep(64);
+        }
+    }
+}
+
+// Byte permute: output byte 0 = byte (sel & 7) of {hi:lo}, etc. (PTX prmt).
+__device__ __forceinline__ uint32_t prmt(uint32_t lo, uint32_t hi, uint32_t sel) {
+    uint32_t d;
+    asm("prmt.b32 %0, %1, %2, %3;" : "=r"(d) : "r"(lo), "r"(hi), "r"(sel));
+    return d;
+}
+
+// Selector that reads byte `code` (0..3) of a row profile and sign-extends
+// it to 32 bits: nibble 0 picks the byte, nibbles 1..3 replicate its sign.
+__device__ __forceinline__ uint32_t sext_selector(uint32_t code) { return code * 0x1111u + 0x8880u; }
+
+// 2-bit code of base k of a packed sequence.
+__device__ __forceinline__ uint32_t base_at(const uint8_t *s2b, uint64_t k) {
+    return (s2b[k >> 2] >> ((k & 3) * 2)) & 3u;
+}
+
+// Scoring handed to kernels: prof[c] is the row profile of a query base c,
+// byte d of prof[c] = s'(c, d) as int8.
+struct Profile {
+    uint32_t prof[4];
+    int32_t gap;
+};
+
+Profile make_profile(const nw_scoring &sc);
+
+// ------------------------------------------------------------------ context
+struct KernelStat {
+    uint64_t launches = 0;
+    double ms = 0.0;
+    std::vector<std::pair<cudaEvent_t, cudaEvent_t>> pending;
+};
+
+struct Buf {
+    void *p = nullptr;
+    size_t cap = 0;
+};
+
+}  // namespace nw
+
+struct nw_ctx {
+    int device = 0;
+    cudaStream_t stream = nullptr;
+    uint64_t budget = 0;
+    uint64_t used = 0;
+    int sm_count = 0;
+    int cc_major = 0, cc_minor = 0;
+    uint32_t *d_err = nullptr;  // 2 words
+    std::map<std::string, nw::Buf> bufs;
+    std::string msg;
+    bool profiling = false;
+    std::map<std::string, nw::KernelStat> stats;
+    std::vector<cudaEvent_t> event_pool;
+    // host staging for NW_HOST_IO (pinned, grown on demand)
+    void *pinned = nullptr;
+    size_t pinned_cap = 0;
+};
+
+namespace nw {
+
+// Set ctx->msg and return code.
+int fail(nw_ctx *ctx, int code, const char *fmt, ...);
+int cuda_fail(nw_ctx *ctx, cudaError_t e, const char *what);
+
+// Named scratch buffer of at least `bytes`, reused across calls; grows
+// (stream-ordered) under the context budget.  Returns NW_OK or NW_ERR_OOM /
+// NW_ERR_CUDA.
+int scratch(nw_ctx *ctx, const char *name, size_t bytes, void **out);
+
+// Validate scoring and sizes shared by all entry points.
+int check_scoring(nw_ctx *ctx, const nw_scoring &sc);
+
+// Launch bracket for per-kernel timing.
+struct LaunchTimer {
+    nw_ctx *ctx;
+    const char *name;
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    LaunchTimer(nw_ctx *c, const char *n);
+    ~LaunchTimer();
+};
+
+// Copy helpers for NW_HOST_IO.
+int to_device(nw_ctx *ctx, const void *host, size_t bytes, const char *slot, void **dev);
+
+}  // namespace nw
+
+// Entry points implemented in the other translation units (C++ linkage).
+namespace nw {
+int align_single(nw_ctx *ctx, const uint8_t *a2b, uint64_t m, const uint8_t *b2b, uint64_t n,
+                 const nw_scoring &sc, uint32_t flags, int32_t *score, char *cigar, uint64_t cigar_cap,
+                 uint64_t *cigar_len);
+}

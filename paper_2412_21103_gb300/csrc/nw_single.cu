@@ -1,0 +1,498 @@
+// One pair: score-matrix fill (a3/a4), traceback (a5) and CIGAR assembly.
+//
+// Fill layout.  The query rows are cut into stripes of 32*R rows; one warp
+// owns a stripe and lane k of it owns R consecutive rows, kept in registers.
+// The warp is a systolic array over the anti-diagonal wavefront: at step t
+// lane k works on column t-k+1, receives the bottom W value of lane k-1 (and
+// the column's base code) by one warp shuffle, and updates its R cells with
+// the Sec. 2.3 recurrence in the W domain (one prmt + one DPX add-max + one
+// max per cell).  Lane 0 of stripe s reads stripe s-1's bottom row from a
+// global boundary buffer, 32 columns at a time, double buffered, after an
+// acquire on the producer's progress counter; lane 31 writes its bottom row
+// there and releases the counter every 32 columns.  Every wait is bounded.
+//
+// Pointer layout (with the alignment requested).  For every cell the fill
+// stores two bits: bit0 = the diagonal candidate is the maximum, bit1 = the
+// vertical candidate is not below the horizontal one.  The Sec. 2.4 backtrack
+// with priority diagonal > vertical > horizontal reads: bit0 -> diagonal,
+// else bit1 -> vertical, else horizontal (the 1/2/3 codes of Sec. 3.1 are
+// recovered as 1, 2, 3).  A 32-bit word holds R rows x (16/R) columns of one
+// lane; words are stored [stripe][lane][column group], so one lane's words
+// are contiguous along the row.
+#include <cstdio>
+
+#include "nw_internal.cuh"
+
+namespace nw {
+
+constexpr int kFillWarps = 4;  // warps per CTA of the fill kernel
+
+struct FillArgs {
+    const uint8_t *a;
+    const uint8_t *b;
+    uint32_t m, n;
+    uint32_t prof[4];
+    int32_t gap;
+    uint32_t S;          // stripes
+    uint32_t bstride;    // words per boundary row
+    uint32_t *bnd;       // boundary rows: row s holds stripe s's bottom, packed (W << 2) | b_j at [j]
+    uint32_t *progress;  // progress[s] = columns of row s published
+    uint32_t *ptr;       // pointer words (may be null)
+    uint32_t ncg;        // words per lane row of the pointer layout
+    int32_t *score;      // H(m,n) out
+    uint32_t *err;
+};
+
+// Warp-uniform bounded wait on a progress counter.
+__device__ __forceinline__ bool warp_wait(const uint32_t *flag, uint32_t target, uint32_t *err, uint32_t where) {
+    int ok = 1;
+    if ((threadIdx.x & 31) == 0) ok = wait_geq(flag, target, err, where) ? 1 : 0;
+    ok = __shfl_sync(kFull, ok, 0);
+    if (ok) (void)ld_acquire(flag);  // acquire for every lane's following loads
+    return ok != 0;
+}
+
+template <int R, bool PTR>
+__global__ void __launch_bounds__(kFillWarps * 32) k_fill(FillArgs p) {
+    constexpr uint32_t SH = 32u * R;
+    constexpr uint32_t CPW = PTR ? 16u / R : 1u;
+    const int lane = threadIdx.x & 31;
+    const uint32_t gw = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const uint32_t nwarps = (gridDim.x * blockDim.x) >> 5;
+    const uint32_t m = p.m, n = p.n;
+    const uint32_t sM = (m - 1) / SH, lM = ((m - 1) % SH) / R, rM = (m - 1) % R;
+
+    for (uint32_t s = gw; s < p.S; s += nwarps) {
+        const uint32_t row0 = s * SH + lane * R;
+        uint32_t prof[R];
+#pragma unroll
+        for (int r = 0; r < R; ++r) {
+            const uint32_t i = row0 + r;
+            const uint32_t c = i < m ? base_at(p.a, i) : 0u;
+            prof[r] = c == 0 ? p.prof[0] : c == 1 ? p.prof[1] : c == 2 ? p.prof[2] : p.prof[3];
+        }
+        int32_t Wl[R];
+#pragma unroll
+        for (int r = 0; r < R; ++r) Wl[r] = 0;  // column 0: W(i,0) = 0
+        int32_t dtop = 0;                        // W(top-1, j-1)
+        uint32_t xout = 0;
+        uint32_t bits = 0;
+        const uint32_t *in = s ? p.bnd + (size_t)(s - 1) * p.bstride : nullptr;
+        uint32_t *outb = (s + 1 < p.S) ? p.bnd + (size_t)s * p.bstride : nullptr;
+        uint32_t *prow = PTR ? p.ptr + (size_t)(s * 32u + lane) * p.ncg : nullptr;
+
+        // Lane-0 input chunks: lane l of `stage` holds the word of column c0 + l
+        // (row 0 of the grid: W = 0, only the base code).
+#define NW_LOAD_CHUNK(C0, DST)                                                              \
+    do {                                                                                    \
+        const uint32_t c0_ = (C0);                                                          \
+        if (c0_ <= n) {                                                                     \
+            if (s && !warp_wait(&p.progress[s - 1], min(c0_ + 31u, n), p.err, s)) return;  \
+            const uint32_t cl_ = c0_ + lane;                                                \
+            if (cl_ <= n) (DST) = s ? __ldcg(in + cl_) : base_at(p.b, cl_ - 1);             \
+        }                                                                                   \
+    } while (0)
+        uint32_t stage = 0, stage_next = 0;
+        NW_LOAD_CHUNK(1u, stage_next);
+
+        const uint32_t T = n + 31;
+        for (uint32_t t = 0; t < T; ++t) {
+            if ((t & 31u) == 0) {
+                stage = stage_next;
+                NW_LOAD_CHUNK(t + 33u, stage_next);
+            }
+            uint32_t x = __shfl_up_sync(kFull, xout, 1);
+            uint32_t x0 = __shfl_sync(kFull, stage, t & 31u);
+            if (lane == 0) x = x0;
+            const int32_t c = (int32_t)t - lane;  // 0-based column of this lane
+            if (c >= 0 && c < (int32_t)n) {
+                const int32_t up = (int32_t)(x >> 2);
+                const uint32_t sel = sext_selector(x & 3u);
+                int32_t d = dtop, u = up;
+                uint32_t code = 0;
+#pragma unroll
+                for (int r = 0; r < R; ++r) {
+                    const int32_t sv = (int32_t)prmt(prof[r], 0u, sel);
+                    int32_t w;
+                    if constexpr (PTR) {
+                        bool pu, pd;
+                        const int32_t mx = __vibmax_s32(u, Wl[r], &pu);  // vertical >= horizontal
+                        w = __vibmax_s32(d + sv, mx, &pd);                // diagonal is the max
+                        code |= ((uint32_t)pd | ((uint32_t)pu << 1)) << (2 * r);
+                    } else {
+                        w = max(__viaddmax_s32(d, sv, Wl[r]), u);
+                    }
+                    d = Wl[r];
+                    Wl[r] = w;
+                    u = w;
+                }
+                dtop = up;
+                xout = ((uint32_t)u << 2) | (x & 3u);
+                if constexpr (PTR) {
+                    const uint32_t cc = (uint32_t)c % CPW;
+                    bits |= code << (2u * R * cc);
+                    if (cc == CPW - 1 || c == (int32_t)n - 1) {
+                        prow[(uint32_t)c / CPW] = bits;
+                        bits = 0;
+                    }
+                }
+                if (lane == 31 && outb) {
+                    outb[c + 1] = xout;
+                    if (((c + 1) & 31) == 0 || c + 1 == (int32_t)n) st_release(&p.progress[s], (uint32_t)c + 1);
+                }
+                if (s == sM && (uint32_t)lane == lM && c == (int32_t)n - 1) {
+                    int32_t wmn = 0;
+#pragma unroll
+                    for (int r = 0; r < R; ++r)
+                        if ((uint32_t)r == rM) wmn = Wl[r];
+                    *p.score = wmn + p.gap * (int32_t)(m + n);
+                }
+            }
+        }
+#undef NW_LOAD_CHUNK
+    }
+}
+
+// Zero-length side: score gap*(m+n); CIGAR "<m>I" or "<n>D" or "".
+__global__ void k_trivial(uint32_t m, uint32_t n, int32_t gap, int32_t *score, char *cigar, uint64_t *cigar_len) {
+    *score = gap * (int32_t)(m + n);
+    if (!cigar) return;
+    uint32_t L = m + n;
+    if (L == 0) {
+        cigar[0] = 0;
+        *cigar_len = 0;
+        return;
+    }
+    char tmp[12];
+    int k = 0;
+    while (L) {
+        tmp[k++] = '0' + L % 10;
+        L /= 10;
+    }
+    for (int q = 0; q < k; ++q) cigar[q] = tmp[k - 1 - q];
+    cigar[k] = m ? 'I' : 'D';
+    cigar[k + 1] = 0;
+    *cigar_len = k + 1;
+}
+
+// ---------------------------------------------------------------- traceback
+// One warp.  The walk itself is sequential (lane 0); the warp loads the
+// 8-lane x 32-word pointer tile that holds the current cell into shared
+// memory whenever the walk leaves the previous tile.  Emits move codes in
+// reverse order: 0 diagonal, 1 vertical ('I'), 2 horizontal ('D').
+constexpr uint32_t kTileLanes = 8, kTileWords = 32;
+
+struct TbArgs {
+    const uint32_t *ptr;
+    uint32_t ncg;
+    uint32_t m, n;
+    uint8_t *moves;     // reversed moves, capacity m+n
+    uint64_t *nmoves;
+};
+
+template <int R>
+__global__ void __launch_bounds__(32) k_traceback(TbArgs p) {
+    constexpr uint32_t SH = 32u * R, CPW = 16u / R;
+    __shared__ __align__(16) uint32_t tile[kTileLanes * kTileWords];
+    const uint32_t lane = threadIdx.x;
+    uint32_t i = p.m, j = p.n;
+    uint64_t k = 0;
+    uint32_t cs = 0xffffffffu, ckt = 0, cct = 0;
+    while (i > 0 && j > 0) {
+        const uint32_t i1 = i - 1, j1 = j - 1;
+        const uint32_t s = i1 / SH, kt = ((i1 % SH) / R) / kTileLanes, ct = (j1 / CPW) / kTileWords;
+        if (s != cs || kt != ckt || ct != cct) {
+            __syncwarp();
+            const uint32_t rl = lane >> 2, part = lane & 3u;
+            const size_t base = (size_t)(s * 32u + kt * kTileLanes + rl) * p.ncg + ct * kTileWords + part * 8u;
+            const uint4 v0 = __ldcg(reinterpret_cast<const uint4 *>(p.ptr + base));
+            const uint4 v1 = __ldcg(reinterpret_cast<const uint4 *>(p.ptr + base + 4));
+            uint4 *dst = reinterpret_cast<uint4 *>(tile + rl * kTileWords + part * 8u);
+            dst[0] = v0;
+            dst[1] = v1;
+            __syncwarp();
+            cs = s;
+            ckt = kt;
+            cct = ct;
+        }
+        if (lane == 0) {
+            while (i > 0 && j > 0) {
+                const uint32_t a1 = i - 1, b1 = j - 1;
+                const uint32_t kk = (a1 % SH) / R, cg = b1 / CPW;
+                if (a1 / SH != cs || kk / kTileLanes != ckt || cg / kTileWords != cct) break;
+                const uint32_t word = tile[(kk - ckt * kTileLanes) * kTileWords + (cg - cct * kTileWords)];
+                const uint32_t code = (word >> (2u * ((b1 % CPW) * R + (a1 % R)))) & 3u;
+                const uint32_t mv = (code & 1u) ? 0u : ((code & 2u) ? 1u : 2u);
+                p.moves[k++] = (uint8_t)mv;
+                i -= (mv != 2u);
+                j -= (mv != 1u);
+            }
+        }
+        i = __shfl_sync(kFull, i, 0);
+        j = __shfl_sync(kFull, j, 0);
+        k = __shfl_sync(kFull, k, 0);
+    }
+    // Row 0 / column 0: only horizontal / vertical moves remain.
+    const uint32_t rest = i + j;
+    const uint8_t mv = i ? 1 : 2;
+    for (uint32_t q = lane; q < rest; q += 32) p.moves[k + q] = mv;
+    if (lane == 0) *p.nmoves = k + rest;
+}
+
+// ------------------------------------------------------------------ finish
+// Reverses the move list, resolves diagonal moves into '=' / 'X' (or 'M'),
+// and run-length encodes.  One CTA of 1024 threads loops over chunks of 4096
+// moves; three block scans per chunk give each move its (i,j), each run its
+// start and each run string its output offset.
+constexpr int kFinThreads = 1024, kFinPer = 4;
+
+template <typename T, typename Op>
+__device__ __forceinline__ T block_exscan(T v, Op op, T ident, T *warp_tot, T &total) {
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    T incl = v;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        T y = __shfl_up_sync(kFull, incl, o);
+        if (lane >= o) incl = op(y, incl);
+    }
+    if (lane == 31) warp_tot[wid] = incl;
+    __syncthreads();
+    if (wid == 0) {
+        T w = warp_tot[lane];
+        T wi = w;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            T y = __shfl_up_sync(kFull, wi, o);
+            if (lane >= o) wi = op(y, wi);
+        }
+        warp_tot[lane] = wi;  // inclusive over warps
+    }
+    __syncthreads();
+    T before = wid ? warp_tot[wid - 1] : ident;
+    T ex = __shfl_up_sync(kFull, incl, 1);
+    if (lane == 0) ex = ident;
+    T res = op(before, ex);
+    total = warp_tot[31];
+    __syncthreads();
+    return res;
+}
+
+struct FinArgs {
+    const uint8_t *moves;
+    const uint64_t *nmoves;
+    const uint8_t *a, *b;
+    uint32_t mflag;   // 1: write 'M' for diagonals
+    char *cigar;
+    uint64_t *cigar_len;
+};
+
+__device__ __forceinline__ uint32_t ndigits(uint64_t v) {
+    uint32_t d = 1;
+    while (v >= 10) {
+        v /= 10;
+        ++d;
+    }
+    return d;
+}
+
+__global__ void __launch_bounds__(kFinThreads) k_finish(FinArgs p) {
+    __shared__ unsigned long long sc_u64[32];
+    __shared__ long long sc_i64[32];
+    __shared__ char first_op[kFinThreads + 1];
+    const uint64_t L = *p.nmoves;
+    const int tid = threadIdx.x;
+    uint64_t ci = 0, cj = 0;   // bases of A / B consumed before this chunk
+    long long last_end = -1;   // forward position of the last run end so far
+    uint64_t out = 0;          // chars written so far
+    const uint64_t CH = (uint64_t)kFinThreads * kFinPer;
+    for (uint64_t base = 0; base < L; base += CH) {
+        const uint64_t p0 = base + (uint64_t)tid * kFinPer;
+        uint8_t mv[kFinPer];
+        uint32_t cnt_i = 0, cnt_j = 0;
+#pragma unroll
+        for (int e = 0; e < kFinPer; ++e) {
+            const uint64_t q = p0 + e;
+            mv[e] = q < L ? p.moves[L - 1 - q] : 3;
+            cnt_i += (mv[e] == 0 || mv[e] == 1);
+            cnt_j += (mv[e] == 0 || mv[e] == 2);
+        }
+        unsigned long long tot;
+        const unsigned long long packed = ((unsigned long long)cnt_i << 32) | cnt_j;
+        const unsigned long long ex = block_exscan<unsigned long long>(
+            packed, [](unsigned long long x, unsigned long long y) { return x + y; }, 0ull, sc_u64, tot);
+        uint64_t pi = ci + (ex >> 32), pj = cj + (ex & 0xffffffffull);
+        char op[kFinPer];
+#pragma unroll
+        for (int e = 0; e < kFinPer; ++e) {
+            char o = 0;
+            if (mv[e] == 0) {
+                o = p.mflag ? 'M' : (base_at(p.a, pi) == base_at(p.b, pj) ? '=' : 'X');
+                ++pi;
+                ++pj;
+            } else if (mv[e] == 1) {
+                o = 'I';
+                ++pi;
+            } else if (mv[e] == 2) {
+                o = 'D';
+                ++pj;
+            }
+            op[e] = o;
+        }
+        first_op[tid] = op[0];
+        if (tid == kFinThreads - 1) {
+            // first op of the next chunk (its position is this chunk's end)
+            const uint64_t q = base + CH;
+            char o = 0;
+            if (q < L) {
+                const uint8_t m2 = p.moves[L - 1 - q];
+                if (m2 == 0)
+                    o = p.mflag ? 'M' : (base_at(p.a, pi) == base_at(p.b, pj) ? '=' : 'X');
+                else
+                    o = m2 == 1 ? 'I' : 'D';
+            }
+            first_op[kFinThreads] = o;
+        }
+        __syncthreads();
+        const char next_after = first_op[tid + 1];
+        bool is_end[kFinPer];
+        long long my_last = -1;
+#pragma unroll
+        for (int e = 0; e < kFinPer; ++e) {
+            const uint64_t q = p0 + e;
+            const char nx = e + 1 < kFinPer ? op[e + 1] : next_after;
+            is_end[e] = q < L && (q + 1 == L || nx != op[e]);
+            if (is_end[e]) my_last = (long long)q;
+        }
+        long long tot_max;
+        const long long prev_excl =
+            block_exscan<long long>(my_last, [](long long x, long long y) { return x > y ? x : y; }, -1ll, sc_i64, tot_max);
+        long long prev = prev_excl > last_end ? prev_excl : last_end;
+        uint32_t chars = 0;
+        long long pe = prev;
+#pragma unroll
+        for (int e = 0; e < kFinPer; ++e)
+            if (is_end[e]) {
+                chars += ndigits((uint64_t)((long long)(p0 + e) - pe)) + 1;
+                pe = (long long)(p0 + e);
+            }
+        unsigned long long tot_chars;
+        const unsigned long long off = block_exscan<unsigned long long>(
+            chars, [](unsigned long long x, unsigned long long y) { return x + y; }, 0ull, sc_u64, tot_chars);
+        uint64_t w = out + off;
+        pe = prev;
+#pragma unroll
+        for (int e = 0; e < kFinPer; ++e)
+            if (is_end[e]) {
+                uint64_t len = (uint64_t)((long long)(p0 + e) - pe);
+                const uint32_t nd = ndigits(len);
+                for (uint32_t d = nd; d-- > 0;) {
+                    p.cigar[w + d] = (char)('0' + len % 10);
+                    len /= 10;
+                }
+                p.cigar[w + nd] = op[e];
+                w += nd + 1;
+                pe = (long long)(p0 + e);
+            }
+        ci += tot >> 32;
+        cj += tot & 0xffffffffull;
+        if (tot_max > last_end) last_end = tot_max;
+        out += tot_chars;
+        __syncthreads();
+    }
+    if (tid == 0) {
+        p.cigar[out] = 0;
+        *p.cigar_len = out;
+    }
+}
+
+// ----------------------------------------------------------------- dispatch
+template <int R, bool PTR>
+static int launch_fill(nw_ctx *ctx, FillArgs &fa) {
+    int occ = 0;
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_fill<R, PTR>, kFillWarps * 32, 0);
+    if (occ < 1) occ = 1;
+    uint32_t blocks = (fa.S + kFillWarps - 1) / kFillWarps;
+    const uint32_t cap = (uint32_t)occ * (uint32_t)ctx->sm_count;  // all CTAs co-resident
+    if (blocks > cap) blocks = cap;
+    LaunchTimer t(ctx, PTR ? "fill_ptr" : "fill_score");
+    k_fill<R, PTR><<<blocks, kFillWarps * 32, 0, ctx->stream>>>(fa);
+    return NW_OK;
+}
+
+template <int R>
+static int run_pair(nw_ctx *ctx, const uint8_t *a2b, uint32_t m, const uint8_t *b2b, uint32_t n, const Profile &pf,
+                    uint32_t flags, int32_t *score, char *cigar, uint64_t *cigar_len) {
+    const bool want = flags & NW_CIGAR;
+    const uint32_t SH = 32u * R;
+    FillArgs fa{};
+    fa.a = a2b;
+    fa.b = b2b;
+    fa.m = m;
+    fa.n = n;
+    for (int c = 0; c < 4; ++c) fa.prof[c] = pf.prof[c];
+    fa.gap = pf.gap;
+    fa.S = (m + SH - 1) / SH;
+    fa.bstride = ((n + 1 + 31) / 32) * 32;
+    fa.score = score;
+    fa.err = ctx->d_err;
+    int rc;
+    void *v = nullptr;
+    if (fa.S > 1) {
+        if ((rc = scratch(ctx, "fill_bnd", (size_t)(fa.S - 1) * fa.bstride * 4, &v))) return rc;
+        fa.bnd = (uint32_t *)v;
+    }
+    if ((rc = scratch(ctx, "fill_progress", (size_t)fa.S * 4, &v))) return rc;
+    fa.progress = (uint32_t *)v;
+    cudaMemsetAsync(fa.progress, 0, (size_t)fa.S * 4, ctx->stream);
+    if (!want) return launch_fill<R, false>(ctx, fa);
+
+    const uint32_t CPW = 16u / R;
+    fa.ncg = (((n + CPW - 1) / CPW + kTileWords - 1) / kTileWords) * kTileWords;
+    const size_t ptr_bytes = (size_t)fa.S * 32u * fa.ncg * 4u;
+    if ((rc = scratch(ctx, "ptr", ptr_bytes, &v))) return rc;
+    fa.ptr = (uint32_t *)v;
+    if ((rc = launch_fill<R, true>(ctx, fa))) return rc;
+
+    void *mv = nullptr, *nm = nullptr;
+    if ((rc = scratch(ctx, "moves", (size_t)m + n + 16, &mv))) return rc;
+    if ((rc = scratch(ctx, "nmoves", 16, &nm))) return rc;
+    TbArgs ta{fa.ptr, fa.ncg, m, n, (uint8_t *)mv, (uint64_t *)nm};
+    {
+        LaunchTimer t(ctx, "traceback");
+        k_traceback<R><<<1, 32, 0, ctx->stream>>>(ta);
+    }
+    FinArgs fin{(const uint8_t *)mv, (const uint64_t *)nm, a2b, b2b, (flags & NW_CIGAR_M) ? 1u : 0u, cigar, cigar_len};
+    {
+        LaunchTimer t(ctx, "finish");
+        k_finish<<<1, kFinThreads, 0, ctx->stream>>>(fin);
+    }
+    return NW_OK;
+}
+
+int align_single(nw_ctx *ctx, const uint8_t *a2b, uint64_t m, const uint8_t *b2b, uint64_t n, const nw_scoring &sc,
+                 uint32_t flags, int32_t *score, char *cigar, uint64_t cigar_cap, uint64_t *cigar_len) {
+    (void)cigar_cap;
+    const Profile pf = make_profile(sc);
+    const bool want = flags & NW_CIGAR;
+    if (m == 0 || n == 0) {
+        LaunchTimer t(ctx, "trivial");
+        k_trivial<<<1, 1, 0, ctx->stream>>>((uint32_t)m, (uint32_t)n, sc.gap, score, want ? cigar : nullptr,
+                                            want ? cigar_len : nullptr);
+    } else {
+        // Rows per lane: enough stripes to spread over the SMs, but at least
+        // 4 rows so shuffles stay a small share of the work.
+        int rc;
+        const uint64_t warps_wanted = (uint64_t)ctx->sm_count * 2;
+        if (m >= warps_wanted * 32 * 16)
+            rc = run_pair<16>(ctx, a2b, (uint32_t)m, b2b, (uint32_t)n, pf, flags, score, cigar, cigar_len);
+        else if (m >= warps_wanted * 32 * 8 / 4)
+            rc = run_pair<8>(ctx, a2b, (uint32_t)m, b2b, (uint32_t)n, pf, flags, score, cigar, cigar_len);
+        else
+            rc = run_pair<4>(ctx, a2b, (uint32_t)m, b2b, (uint32_t)n, pf, flags, score, cigar, cigar_len);
+        if (rc) return rc;
+    }
+    cudaError_t e = cudaGetLastError();
+    return e == cudaSuccess ? NW_OK : cuda_fail(ctx, e, "single-pair launch");
+}
+
+}  // namespace nw

@@ -1,0 +1,53 @@
+"""The C-ABI library builds for sm_103a, loads without a GPU and exports
+every entry point include/nw.h declares (no compute calls here)."""
+import ctypes
+
+import numpy as np
+import pytest
+
+import paper_2412_21103_gb300 as nw
+from paper_2412_21103_gb300 import build as nwbuild
+
+
+@pytest.fixture(scope="module")
+def lib():
+    nwbuild.build()
+    return nw.load()
+
+
+def test_header_declares_the_boundary():
+    names = nw.exported_symbols()
+    for required in ["nw_align", "nw_align_batch", "nw_score_all_pairs", "nw_pack", "nw_ctx_create",
+                     "nw_ctx_destroy", "nw_strerror"]:
+        assert required in names
+
+
+def test_every_declared_symbol_is_exported(lib):
+    missing = [s for s in nw.exported_symbols() if not hasattr(lib, s)]
+    assert not missing, missing
+
+
+def test_host_pack_layout(lib):
+    out = nw.nw_pack("ACGTacgtA")
+    # base k at bits 2*(k%4) of byte k/4: ACGT -> 0b11100100
+    assert out.tolist() == [0b11100100, 0b11100100, 0b00000000]
+    codes = np.array([0, 1, 2, 3, 0, 1, 2, 3, 0], np.uint8)
+    assert nw.pack_codes(codes).tolist() == out.tolist()
+
+
+def test_host_pack_rejects_bad_base(lib):
+    with pytest.raises(nw.NWError) as e:
+        nw.nw_pack("ACGN")
+    assert e.value.status == nw.NW_ERR_BAD_BASE
+
+
+def test_strerror_and_bound(lib):
+    assert lib.nw_strerror(nw.NW_ERR_TIMEOUT) == b"device-side wait timed out"
+    assert nw.nw_cigar_bound(3, 4) == 15
+
+
+def test_context_without_gpu_fails_cleanly(lib):
+    import torch
+    if torch.cuda.is_available():
+        pytest.skip("a GPU is present")
+    assert lib.nw_ctx_create(0, None, 0) in (None, 0)
