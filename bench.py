@@ -55,6 +55,10 @@ def dist_env():
 
 
 def workload(name: str):
+    if name == "allpairs":
+        seqs = seqgen.all_vs_all_family(1003)
+        return seqs, ("all-vs-all scores of 512 mutants of one random 1,500-base root (lengths U{500..1500}, "
+                      "divergence U[0.05,0.30], 20% of mutations 1-bp indels), 130,816 pairs, int32 matrix (seed 1003)")
     if name == "pair1k":
         p = seqgen.random_pair(1001, 1000, 1000)
         return p, "single pair 1,000 x 1,000 i.i.d. uniform ACGT, score + CIGAR (seed 1001)"
@@ -140,18 +144,38 @@ def oracle_gcups(pair, budget_s: float = 12.0, threads: int | None = None):
                                    f"of the pair ({cells:.3g} cells, {dt:.1f} s)"
 
 
+def allpairs_oracle_gcups(seqs, budget_s: float = 12.0):
+    """The CPU oracle, as it stands, on random pairs of the family (score
+    only), spread over the host threads."""
+    import oracle
+    threads = len(os.sched_getaffinity(0))
+    rs = seqgen.Stream(4242)
+    idx = rs.integers(0, len(seqs) - 1, 4000).reshape(-1, 2)
+    pairs = [(seqs[int(i)], seqs[int(j)]) for i, j in idx if i != j]
+    t0 = time.perf_counter()
+    done, cells = 0, 0
+    while time.perf_counter() - t0 < budget_s and done < len(pairs):
+        chunk = pairs[done: done + 64]
+        oracle.score_many(chunk, *SCORING, threads=threads)
+        cells += sum(a.size * b.size for a, b in chunk)
+        done += len(chunk)
+    dt = time.perf_counter() - t0
+    return cells / dt / 1e9, threads, f"{done} random pairs of the family, score only ({cells:.3g} cells, {dt:.1f} s)"
+
+
 def run_reference(args):
     rank, world, _ = dist_env()
     if rank != 0:
         return
-    pair, desc = workload(args.workload)
+    data, desc = workload(args.workload)
     import oracle
     oracle.build()
+    sample_fn = allpairs_oracle_gcups if args.workload == "allpairs" else oracle_gcups
     vals = []
     for _ in range(args.warmup):
-        oracle_gcups(pair, budget_s=1.0)
+        sample_fn(data, budget_s=1.0)
     for _ in range(args.steps):
-        g, cores, sample = oracle_gcups(pair, budget_s=max(2.0, 60.0 / max(args.steps, 1)))
+        g, cores, sample = sample_fn(data, budget_s=max(2.0, 60.0 / max(args.steps, 1)))
         vals.append(g)
     v = statistics.mean(vals)
     line = {"impl": "reference", "metric": METRIC, "value": v, "unit": "GCUPS", "n_gpus": args.gpus,
@@ -164,6 +188,80 @@ def run_reference(args):
 
 
 # ------------------------------------------------------------------ our arm
+class PairWork:
+    """One pair: pack both sequences on the device, fill with pointers,
+    trace back, build the CIGAR."""
+    dominant = "fill_ptr"
+
+    def __init__(self, nw, ctx, dev, name):
+        import torch
+        self.nw, self.ctx = nw, ctx
+        pair, self.desc = workload(name)
+        self.pair = pair
+        m, n = pair.a.size, pair.b.size
+        self.m, self.n, self.cells = m, n, m * n
+        self.a_ascii = torch.tensor(np.frombuffer(seqgen.to_ascii(pair.a).encode(), np.uint8), device=dev)
+        self.b_ascii = torch.tensor(np.frombuffer(seqgen.to_ascii(pair.b).encode(), np.uint8), device=dev)
+        self.a2b = torch.zeros((m + 3) // 4, dtype=torch.uint8, device=dev)
+        self.b2b = torch.zeros((n + 3) // 4, dtype=torch.uint8, device=dev)
+        self.score = torch.zeros(1, dtype=torch.int32, device=dev)
+        self.cigar = torch.zeros(nw.nw_cigar_bound(m, n), dtype=torch.uint8, device=dev)
+        self.clen = torch.zeros(1, dtype=torch.int64, device=dev)
+        self.a_host = torch.from_numpy(nw.pack_codes(pair.a)).pin_memory().numpy()
+        self.b_host = torch.from_numpy(nw.pack_codes(pair.b)).pin_memory().numpy()
+        self.config = {"m": m, "n": n}
+
+    def step(self):
+        nw = self.nw
+        nw.nw_pack_device(self.ctx, self.a_ascii, self.m, self.a2b)
+        nw.nw_pack_device(self.ctx, self.b_ascii, self.n, self.b2b)
+        nw.nw_align(self.ctx, self.a2b, self.m, self.b2b, self.n, SCORING, nw.NW_CIGAR, self.score, self.cigar,
+                    self.clen)
+
+    def e2e(self):
+        res = self.nw.nw_align(self.ctx, self.a_host, self.m, self.b_host, self.n, SCORING, self.nw.NW_CIGAR)
+        return self.a_host.nbytes + self.b_host.nbytes, 16 + len(res[1]) + 1
+
+    def result(self):
+        return {"score": int(self.score.item())}
+
+    def oracle_sample(self):
+        return oracle_gcups(self.pair, budget_s=12.0)
+
+
+class AllPairsWork:
+    """All-vs-all int32 score matrix of 512 sequences (130,816 pairs)."""
+    dominant = "batch_score"
+
+    def __init__(self, nw, ctx, dev, name):
+        import torch
+        self.nw, self.ctx = nw, ctx
+        seqs, self.desc = workload(name)
+        self.seqs = seqs
+        pool, off, lens = nw.pool_of(seqs)
+        self.pool_host = torch.from_numpy(pool).pin_memory().numpy()
+        self.off, self.lens = off, lens
+        self.pool = torch.from_numpy(pool).to(dev)
+        n = len(seqs)
+        self.out = torch.zeros((n, n), dtype=torch.int32, device=dev)
+        L = lens.astype(np.float64)
+        self.cells = int((np.outer(L, L).sum() - (L * L).sum()) / 2)
+        self.config = {"nseq": n, "pairs": n * (n - 1) // 2}
+
+    def step(self):
+        self.nw.nw_score_all_pairs(self.ctx, self.pool, self.off, self.lens, SCORING, 0, self.out)
+
+    def e2e(self):
+        res = self.nw.nw_score_all_pairs(self.ctx, self.pool_host, self.off, self.lens, SCORING)
+        return self.pool_host.nbytes, res.nbytes
+
+    def result(self):
+        return {"matrix_checksum": int(self.out.sum().item())}
+
+    def oracle_sample(self):
+        return allpairs_oracle_gcups(self.seqs)
+
+
 def run_ours(args):
     import torch
     import torch.distributed as dist
@@ -177,31 +275,16 @@ def run_ours(args):
     dev = torch.device("cuda", local)
     stream = torch.cuda.current_stream(dev)
     ctx = nw.Context(local, stream)
-
-    pair, desc = workload(args.workload)
-    m, n = pair.a.size, pair.b.size
-    cells = m * n
-    a_ascii = torch.tensor(np.frombuffer(seqgen.to_ascii(pair.a).encode(), np.uint8), device=dev)
-    b_ascii = torch.tensor(np.frombuffer(seqgen.to_ascii(pair.b).encode(), np.uint8), device=dev)
-    a2b = torch.zeros((m + 3) // 4, dtype=torch.uint8, device=dev)
-    b2b = torch.zeros((n + 3) // 4, dtype=torch.uint8, device=dev)
-    score = torch.zeros(1, dtype=torch.int32, device=dev)
-    cap = nw.nw_cigar_bound(m, n)
-    cigar = torch.zeros(cap, dtype=torch.uint8, device=dev)
-    clen = torch.zeros(1, dtype=torch.int64, device=dev)
+    work = (AllPairsWork if args.workload == "allpairs" else PairWork)(nw, ctx, dev, args.workload)
     flush = torch.empty(L2_FLUSH_BYTES, dtype=torch.uint8, device=dev)
 
-    def step():
-        nw.nw_pack_device(ctx, a_ascii, m, a2b)
-        nw.nw_pack_device(ctx, b_ascii, n, b2b)
-        nw.nw_align(ctx, a2b, m, b2b, n, SCORING, nw.NW_CIGAR, score, cigar, clen)
-
     for _ in range(max(args.warmup, 3)):
-        step()
+        work.step()
     ctx.sync()
 
-    # integer-pipe peak (roofline denominator), measured live
-    peak_mix = nw.nw_peak_int(ctx, 5, 1 << 15)
+    # integer-pipe peak (roofline denominator), measured live: lane-ops/s of
+    # the score-only cell mix (3 ALU-pipe instructions per cell)
+    peak_ops = nw.nw_peak_int(ctx, 5, 1 << 15) * OPS_PER_CELL
 
     ctx.reset_stats()
     ctx.set_profiling(True)
@@ -214,13 +297,12 @@ def run_ours(args):
         for k in range(args.steps):
             flush.zero_()                       # evict L2 between timed steps
             evs[k][0].record(stream)
-            step()
+            work.step()
             evs[k][1].record(stream)
         torch.cuda.synchronize(dev)
     wall = time.perf_counter() - wall0
     ctx.set_profiling(False)
-    step_ms = [e0.elapsed_time(e1) for e0, e1 in evs]
-    ms = statistics.mean(step_ms)
+    ms = statistics.mean(e0.elapsed_time(e1) for e0, e1 in evs)
     ctx.sync()
     stats = ctx.kernel_stats()
     if world > 1:
@@ -229,53 +311,45 @@ def run_ours(args):
         ms = float(t.item())
         dist.barrier()
 
-    # correctness of the timed result (score from the device)
-    got_score = int(score.item())
-
-    # end to end through the public API with host buffers (pinned), copies inside
-    a_host = torch.from_numpy(nw.pack_codes(pair.a)).pin_memory().numpy()
-    b_host = torch.from_numpy(nw.pack_codes(pair.b)).pin_memory().numpy()
+    # end to end through the public API with host buffers, copies inside
     e2e_ms = []
-    last = None
-    for k in range(max(2, min(args.steps, 5)) + 1):
+    h2d = d2h = 0
+    for k in range(4):
         flush.zero_()
         torch.cuda.synchronize(dev)
         t0 = time.perf_counter()
-        last = nw.nw_align(ctx, a_host, m, b_host, n, SCORING, nw.NW_CIGAR)
+        h2d, d2h = work.e2e()
         t1 = time.perf_counter()
         if k:
             e2e_ms.append((t1 - t0) * 1e3)
-    e2e_gcups = world * cells / (statistics.mean(e2e_ms) * 1e-3) / 1e9
-    h2d = a_host.nbytes + b_host.nbytes
-    d2h = 16 + len(last[1]) + 1
+    e2e_val = world * work.cells / (statistics.mean(e2e_ms) * 1e-3) / 1e9
 
-    fill_name = "fill_ptr"
-    fl, fms = stats.get(fill_name, (0, 0.0))
-    fill_avg_ms = fms / max(fl, 1)
-    achieved_gops = cells * OPS_PER_CELL / (fill_avg_ms * 1e-3) / 1e9 if fill_avg_ms else None
+    dl, dms = stats.get(work.dominant, (0, 0.0))
+    dom_avg_ms = dms / max(dl, 1)
+    achieved = work.cells * OPS_PER_CELL / (dom_avg_ms * 1e-3) / 1e9 if dom_avg_ms else None
     launches = sum(v[0] for k_, v in stats.items() if k_ != "peak")
 
     line = {
-        "metric": METRIC, "value": world * cells / (ms * 1e-3) / 1e9, "unit": "GCUPS", "n_gpus": world,
+        "metric": METRIC, "value": world * work.cells / (ms * 1e-3) / 1e9, "unit": "GCUPS", "n_gpus": world,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "int32", "data": "synthetic",
-        "config": {"workload": desc, "m": m, "n": n, "scoring": list(SCORING), "parallelism": f"replicas{world}",
-                   "l2": "flushed between timed steps (256 MB device write)", "score": got_score},
-        "roofline": {"bound": "alu", "kernel": fill_name, "achieved": achieved_gops, "peak": peak_mix,
-                     "unit": "Gop/s", "frac": (achieved_gops / peak_mix) if achieved_gops else None,
-                     "traffic": None, "ops_per_cell": OPS_PER_CELL,
-                     "kernel_ms": fill_avg_ms,
-                     "peak_source": "measured live: nw_peak_int kind 5 (score-only cell mix, all SMs)"},
+        "config": dict(workload=work.desc, scoring=list(SCORING), parallelism=f"replicas{world}",
+                       l2="flushed between timed steps (256 MB device write)", cells=work.cells,
+                       **work.config, **work.result()),
+        "roofline": {"bound": "alu", "kernel": work.dominant, "achieved": achieved, "peak": peak_ops,
+                     "unit": "Gop/s", "frac": (achieved / peak_ops) if achieved else None, "traffic": None,
+                     "ops_per_cell": OPS_PER_CELL, "kernel_ms": dom_avg_ms,
+                     "peak_source": "measured live by nw_peak_int kind 5 (score-only cell mix on every SM) x 3"},
         "kernels": {k_: {"launches": v[0], "ms_total": v[1]} for k_, v in stats.items()},
         "gpu_launches": launches,
-        "e2e": {"value": e2e_gcups, "unit": "GCUPS", "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
+        "e2e": {"value": e2e_val, "unit": "GCUPS", "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
                 "ms_per_step": statistics.mean(e2e_ms)},
         "wall_s_timed": wall,
     }
     if not args.no_clocks:
         line["clocks"] = clk.summary()
     if rank == 0 and world == 1:
-        g, cores, sample = oracle_gcups(pair, budget_s=12.0)
+        g, cores, sample = work.oracle_sample()
         line["cpu_baseline"] = {"value": g, "unit": "GCUPS", "cores": cores, "kind": "oracle", "sample": sample}
     if rank == 0:
         print(json.dumps(line), flush=True)

@@ -156,6 +156,29 @@ int to_device(nw_ctx *ctx, const void *host, size_t bytes, const char *slot, voi
 
 // Entry points implemented in the other translation units (C++ linkage).
 namespace nw {
+// Pointer-tile geometry shared by the fill kernels and the traceback: the
+// walk stages 8 lanes x 32 words of one stripe at a time, so every lane row
+// of pointer words is padded to a multiple of 32 words.
+constexpr uint32_t kTileLanes = 8, kTileWords = 32;
+inline uint32_t ptr_words_per_lane_row(uint32_t n, int R) {
+    const uint32_t cpw = 16u / (uint32_t)R;
+    return (((n + cpw - 1) / cpw + kTileWords - 1) / kTileWords) * kTileWords;
+}
+
+// One traceback + CIGAR job (see nw_trace.cu).
+struct TraceTask {
+    const uint32_t *ptr;   // pointer words of the pair
+    uint32_t ncg;          // words per lane row
+    uint32_t m, n;
+    uint8_t *moves;        // scratch, m+n bytes (reversed move codes)
+    uint64_t *nmoves;      // scratch, 1 word
+    const uint8_t *a, *b;  // packed sequences
+    char *cigar;           // output
+    uint64_t *cigar_len;   // output
+};
+// Launch traceback + finish for one task (by value, many == nullptr) or for
+// `ntasks` tasks in a device array.
+int launch_trace(nw_ctx *ctx, int R, const TraceTask &one, const TraceTask *many, uint32_t ntasks, uint32_t mflag);
 int align_single(nw_ctx *ctx, const uint8_t *a2b, uint64_t m, const uint8_t *b2b, uint64_t n,
                  const nw_scoring &sc, uint32_t flags, int32_t *score, char *cigar, uint64_t cigar_cap,
                  uint64_t *cigar_len);

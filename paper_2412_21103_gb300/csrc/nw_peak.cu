@@ -11,6 +11,9 @@ namespace nw {
 constexpr int kChains = 8;
 constexpr int kPeakThreads = 256;
 
+// Kinds 0-4, 8, 9 time one instruction; 5-7 time one score-only cell in
+// three formulations.  Every chain reads a neighbouring chain so the
+// compiler cannot fold or strength-reduce the loop.
 template <int KIND>
 __global__ void __launch_bounds__(kPeakThreads) k_peak(uint64_t iters, int32_t seed, int32_t *sink) {
     int32_t x[kChains], y[kChains];
@@ -19,29 +22,45 @@ __global__ void __launch_bounds__(kPeakThreads) k_peak(uint64_t iters, int32_t s
         x[c] = (int32_t)threadIdx.x * 3 + c + seed;
         y[c] = (int32_t)threadIdx.x - c;
     }
-    const int32_t k1 = seed & 3, k2 = (seed >> 2) & 3;
+    const int32_t k1 = (seed & 3) + 1;
     const uint32_t sel = sext_selector((uint32_t)seed & 3u);
     const uint32_t prof = 0x01030103u + (uint32_t)seed;
     for (uint64_t it = 0; it < iters; ++it) {
 #pragma unroll
         for (int c = 0; c < kChains; ++c) {
+            const int c1 = (c + 1) % kChains, c2 = (c + 2) % kChains;
             if constexpr (KIND == 0) {
-                x[c] = __viaddmax_s32(x[c], k1, y[c]);
+                x[c] = __viaddmax_s32(x[c], k1, x[c1]);
             } else if constexpr (KIND == 1) {
-                x[c] = __vimax3_s32(x[c], y[c], k1);
+                x[c] = __vimax3_s32(x[c], x[c1], x[c2]);
             } else if constexpr (KIND == 2) {
-                x[c] = max(x[c], y[c]) ;
-                y[c] = y[c] ^ k2;  // keep the max from being hoisted (extra op not counted)
+                x[c] = max(x[c], x[c1]);
             } else if constexpr (KIND == 3) {
-                x[c] = x[c] + y[c];
+                x[c] = (int32_t)((uint32_t)x[c] + (uint32_t)x[c1] + (uint32_t)k1);
             } else if constexpr (KIND == 4) {
-                x[c] = (int32_t)prmt((uint32_t)x[c], prof, sel);
-            } else {
-                // score-only cell: s' = prmt(profile), t = addmax(diag, s', left), w = max(t, up)
-                const int32_t s = (int32_t)prmt(prof + (uint32_t)x[c], 0u, sel);
+                x[c] = (int32_t)prmt((uint32_t)x[c], (uint32_t)x[c1], sel);
+            } else if constexpr (KIND == 5) {
+                // prmt + DPX add-max + max
+                const int32_t s = (int32_t)prmt(prof ^ (uint32_t)y[c], 0u, sel);
                 const int32_t t = __viaddmax_s32(y[c], s, x[c]);
                 y[c] = x[c];
-                x[c] = max(t, x[(c + 1) % kChains]);
+                x[c] = max(t, x[c1]);
+            } else if constexpr (KIND == 6) {
+                // prmt + add + 3-input max
+                const int32_t s = (int32_t)prmt(prof ^ (uint32_t)y[c], 0u, sel);
+                const int32_t t = y[c] + s;
+                y[c] = x[c];
+                x[c] = __vimax3_s32(t, x[c], x[c1]);
+            } else if constexpr (KIND == 7) {
+                // prmt + add + two 2-input max
+                const int32_t s = (int32_t)prmt(prof ^ (uint32_t)y[c], 0u, sel);
+                const int32_t t = y[c] + s;
+                y[c] = x[c];
+                x[c] = max(max(t, x[c]), x[c1]);
+            } else if constexpr (KIND == 8) {
+                x[c] = (x[c] ^ x[c1]) & (x[c2] | k1);  // one LOP3
+            } else {
+                x[c] = (int32_t)((uint32_t)x[c] * (uint32_t)k1 + (uint32_t)x[c1]);  // IMAD
             }
         }
     }
@@ -77,7 +96,7 @@ static float run_peak(nw_ctx *ctx, uint64_t iters, int32_t *sink) {
 using namespace nw;
 
 extern "C" int nw_peak_int(nw_ctx *ctx, int kind, uint64_t iters, double *gops) {
-    if (!ctx || !gops || kind < 0 || kind > 5 || iters == 0) return NW_ERR_ARG;
+    if (!ctx || !gops || kind < 0 || kind > 9 || iters == 0) return NW_ERR_ARG;
     cudaSetDevice(ctx->device);
     void *sink = nullptr;
     int rc = scratch(ctx, "peak_sink", 16, &sink);
@@ -89,12 +108,16 @@ extern "C" int nw_peak_int(nw_ctx *ctx, int kind, uint64_t iters, double *gops) 
         case 2: ms = run_peak<2>(ctx, iters, (int32_t *)sink); break;
         case 3: ms = run_peak<3>(ctx, iters, (int32_t *)sink); break;
         case 4: ms = run_peak<4>(ctx, iters, (int32_t *)sink); break;
-        default: ms = run_peak<5>(ctx, iters, (int32_t *)sink); break;
+        case 5: ms = run_peak<5>(ctx, iters, (int32_t *)sink); break;
+        case 6: ms = run_peak<6>(ctx, iters, (int32_t *)sink); break;
+        case 7: ms = run_peak<7>(ctx, iters, (int32_t *)sink); break;
+        case 8: ms = run_peak<8>(ctx, iters, (int32_t *)sink); break;
+        default: ms = run_peak<9>(ctx, iters, (int32_t *)sink); break;
     }
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return cuda_fail(ctx, e, "peak kernel");
-    const double ops_per_iter = (kind == 5) ? 3.0 : 1.0;
-    const double ops = (double)ctx->sm_count * 8 * kPeakThreads * kChains * (double)iters * ops_per_iter;
+    // kinds 5-7 count cells, the others instructions (per lane)
+    const double ops = (double)ctx->sm_count * 8 * kPeakThreads * kChains * (double)iters;
     *gops = ms > 0 ? ops / (ms * 1e-3) / 1e9 : 0.0;
     return NW_OK;
 }

@@ -1,0 +1,132 @@
+"""GPU parity of the batched paths (nw_align_batch, nw_score_all_pairs)
+against the CPU oracle: scores and CIGARs bit-exact."""
+import numpy as np
+import pytest
+
+import oracle
+import seqgen
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def ctx():
+    import torch
+    import paper_2412_21103_gb300 as nw
+    c = nw.Context(0, torch.cuda.current_stream())
+    yield c
+    c.close()
+
+
+def _pairs_pool(pairs):
+    import paper_2412_21103_gb300 as nw
+    seqs = []
+    for a, b in pairs:
+        seqs += [a, b]
+    pool, off, lens = nw.pool_of(seqs)
+    return pool, off[0::2], lens[0::2], off[1::2], lens[1::2]
+
+
+def _mixed_pairs(seed, count, lengths):
+    rs = seqgen.Stream(seed)
+    out = []
+    for k in range(count):
+        m = lengths[int(rs.integers(0, len(lengths) - 1, 1)[0])]
+        n = lengths[int(rs.integers(0, len(lengths) - 1, 1)[0])]
+        if k % 3 == 0 and m and n:
+            p = seqgen.long_mutated_pair(seed * 1000 + k, m=max(m, 2))
+            out.append((p.a, p.b))
+        else:
+            out.append((rs.bases(m), rs.bases(n)))
+    return out
+
+
+LENGTHS = [0, 1, 2, 31, 32, 33, 95, 96, 97, 127, 128, 129, 255, 256, 257, 300, 513, 1000, 1500]
+
+
+@pytest.mark.parametrize("sc", [(1, -1, -1), (2, -1, -2), (1, -3, -1)])
+def test_batch_scores(ctx, sc):
+    import paper_2412_21103_gb300 as nw
+    pairs = _mixed_pairs(11 + sc[0], 120, LENGTHS)
+    pool, ao, al, bo, bl = _pairs_pool(pairs)
+    scores, _ = nw.nw_align_batch(ctx, pool, ao, al, bo, bl, sc, 0)
+    want = oracle.score_many(pairs, *sc)
+    assert scores.tolist() == want
+
+
+@pytest.mark.parametrize("sc", [(1, -1, -1), (3, -2, -1)])
+def test_batch_cigars(ctx, sc):
+    import paper_2412_21103_gb300 as nw
+    pairs = _mixed_pairs(21 + sc[0], 90, LENGTHS)
+    pool, ao, al, bo, bl = _pairs_pool(pairs)
+    scores, cigars = nw.nw_align_batch(ctx, pool, ao, al, bo, bl, sc, nw.NW_CIGAR)
+    want = oracle.align_many(pairs, *sc)
+    for k, (s, ops) in enumerate(want):
+        assert scores[k] == s, k
+        assert cigars[k] == oracle.rle(ops), k
+
+
+def test_batch_cigar_waves_small_budget():
+    """A small scratch budget forces several pointer waves."""
+    import torch
+    import paper_2412_21103_gb300 as nw
+    c = nw.Context(0, torch.cuda.current_stream(), mem_budget=96 << 20)
+    pairs = [(p.a, p.b) for p in (seqgen.long_mutated_pair(300 + k, m=3000 + 500 * k) for k in range(12))]
+    pool, ao, al, bo, bl = _pairs_pool(pairs)
+    scores, cigars = nw.nw_align_batch(c, pool, ao, al, bo, bl, (1, -1, -1), nw.NW_CIGAR)
+    want = oracle.align_many(pairs)
+    for k, (s, ops) in enumerate(want):
+        assert scores[k] == s
+        assert cigars[k] == oracle.rle(ops)
+    c.close()
+
+
+def test_all_pairs_small_family(ctx):
+    import paper_2412_21103_gb300 as nw
+    seqs = seqgen.all_vs_all_family(7, nseq=40, root_len=420, lmin=60, lmax=400)
+    pool, off, lens = nw.pool_of(seqs)
+    mat = nw.nw_score_all_pairs(ctx, pool, off, lens)
+    n = len(seqs)
+    for i in range(n):
+        assert mat[i, i] == len(seqs[i])
+        for j in range(i + 1, n):
+            s = oracle.score(seqs[i], seqs[j])
+            assert mat[i, j] == s and mat[j, i] == s, (i, j)
+
+
+def test_all_pairs_full_size_sampled(ctx):
+    """The 512-sequence family (130,816 pairs, Eq. 2): symmetric, exact
+    diagonal, and 400 sampled entries equal to the oracle."""
+    import paper_2412_21103_gb300 as nw
+    seqs = seqgen.all_vs_all_family(1003)
+    pool, off, lens = nw.pool_of(seqs)
+    mat = nw.nw_score_all_pairs(ctx, pool, off, lens)
+    assert (mat == mat.T).all()
+    assert (np.diag(mat) == np.array([len(s) for s in seqs])).all()
+    rs = seqgen.Stream(99)
+    idx = rs.integers(0, 511, 800).reshape(-1, 2)
+    idx = [(int(i), int(j)) for i, j in idx if i != j][:400]
+    want = oracle.score_many([(seqs[i], seqs[j]) for i, j in idx])
+    got = [int(mat[i, j]) for i, j in idx]
+    assert got == want
+
+
+def test_batch_device_io(ctx):
+    import torch
+    import paper_2412_21103_gb300 as nw
+    pairs = _mixed_pairs(5, 40, [50, 200, 700, 1200])
+    pool, ao, al, bo, bl = _pairs_pool(pairs)
+    dpool = torch.from_numpy(pool).cuda()
+    scores = torch.zeros(len(pairs), dtype=torch.int32, device="cuda")
+    caps = [nw.nw_cigar_bound(int(x), int(y)) for x, y in zip(al, bl)]
+    coff = np.concatenate([[0], np.cumsum(caps)]).astype(np.uint64)
+    cpool = torch.zeros(int(coff[-1]), dtype=torch.uint8, device="cuda")
+    clen = torch.zeros(len(pairs), dtype=torch.int64, device="cuda")
+    nw.nw_align_batch(ctx, dpool, ao, al, bo, bl, (1, -1, -1), nw.NW_CIGAR, scores, cpool, coff, clen)
+    ctx.sync()
+    want = oracle.align_many(pairs)
+    cp = cpool.cpu().numpy()
+    cl = clen.cpu().numpy()
+    for k, (s, ops) in enumerate(want):
+        assert int(scores[k]) == s
+        assert cp[int(coff[k]): int(coff[k]) + int(cl[k])].tobytes().decode() == oracle.rle(ops)
