@@ -129,6 +129,26 @@ int nw_align(nw_ctx *ctx, const uint8_t *a2b, uint64_t m, const uint8_t *b2b, ui
              nw_scoring sc, uint32_t flags, int32_t *score,
              char *cigar, uint64_t cigar_cap, uint64_t *cigar_len);
 
+/* Score of one pair without allocating anything.  The paper has no
+ * counterpart; this exists for callers that cannot allocate device memory
+ * when they align -- a server that reserved all device memory for its own
+ * pool up front, a plug-in inside a runtime that owns the allocator, or a
+ * latency-critical path where cudaMalloc/cudaFree would synchronize the
+ * device.  No context is needed: the fill's scratch lives in a 12 MiB
+ * static device array that every GPU loading the library reserves until
+ * the process exits.  a2b, b2b and score are device pointers on the current
+ * device; the kernel runs on `stream` (a cudaStream_t, NULL = legacy
+ * default) and the call waits for it before returning, so a device-side
+ * timeout comes back as NW_ERR_TIMEOUT.  The first call on each device
+ * looks up the array's device address (do it before any stream capture).
+ * Sizes: ceil(m/512) <= 4096 and (ceil(m/512)-1) * 32*ceil((n+1)/32) <=
+ * 3,141,568 words (for example m = n = 32,768 fits); larger inputs return
+ * NW_ERR_ARG.  Calls share the array, so calls that overlap on the GPU
+ * (two host threads, or two streams) race; serialize them.  Same scoring
+ * and length rules as nw_align; score only. */
+int nw_align_score_noalloc(const uint8_t *a2b, uint64_t m, const uint8_t *b2b, uint64_t n, nw_scoring sc,
+                           int32_t *score, void *stream);
+
 /* Many independent pairs in one call (the paper's Sec. 3.2 pairwise stage,
  * batched on one device instead of split over MPI ranks).  Pair k aligns the
  * sequence at byte offset a_off[k] of `pool2b` (a_len[k] bases) against the

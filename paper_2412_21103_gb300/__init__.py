@@ -83,6 +83,7 @@ def load():
         "nw_align_batch": (ctypes.c_int, [vp, vp, u64p, u32p, u64p, u32p, u32, Scoring, u32, vp, vp, u64p, vp]),
         "nw_score_all_pairs": (ctypes.c_int, [vp, vp, u64p, u32p, u32, Scoring, u32, vp]),
         "nw_peak_int": (ctypes.c_int, [vp, ctypes.c_int, u64, ctypes.POINTER(ctypes.c_double)]),
+        "nw_align_score_noalloc": (ctypes.c_int, [vp, u64, vp, u64, Scoring, vp, vp]),
     }
     for name, (res, args) in sig.items():
         f = getattr(L, name)
@@ -297,6 +298,16 @@ def nw_score_all_pairs(ctx: Context, pool2b, off, lens, scoring=DEFAULT_SCORING,
         return res
     _check(ctx, L.nw_score_all_pairs(ctx.handle, _ptr(pool2b), oop, llp, nseq, _sc(scoring), flags, _ptr(out)))
     return out
+
+
+def nw_align_score_noalloc(a2b, m: int, b2b, n: int, scoring=DEFAULT_SCORING, score=None, stream=None) -> int:
+    """Score of one pair with no allocation inside the library (device
+    tensors in, device int32[1] out; waits for completion).  Returns the
+    status code (NW_OK, NW_ERR_ARG beyond the static scratch, ...)."""
+    s = None
+    if stream is not None:
+        s = stream.cuda_stream if hasattr(stream, "cuda_stream") else int(stream)
+    return int(load().nw_align_score_noalloc(_ptr(a2b), m, _ptr(b2b), n, _sc(scoring), _ptr(score), s))
 
 
 def nw_peak_int(ctx: Context, kind: int, iters: int = 1 << 16) -> float:

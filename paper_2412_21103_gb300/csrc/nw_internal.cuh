@@ -182,4 +182,7 @@ int launch_trace(nw_ctx *ctx, int R, const TraceTask &one, const TraceTask *many
 int align_single(nw_ctx *ctx, const uint8_t *a2b, uint64_t m, const uint8_t *b2b, uint64_t n,
                  const nw_scoring &sc, uint32_t flags, int32_t *score, char *cigar, uint64_t cigar_cap,
                  uint64_t *cigar_len);
+cudaError_t fill_score_with_scratch(const uint8_t *a2b, uint32_t m, const uint8_t *b2b, uint32_t n,
+                                    const nw_scoring &sc, int32_t *score, uint32_t *bnd, uint32_t *progress,
+                                    uint32_t *err, cudaStream_t stream, int sm_count);
 }

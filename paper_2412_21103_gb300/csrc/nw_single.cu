@@ -230,6 +230,39 @@ static int run_pair(nw_ctx *ctx, const uint8_t *a2b, uint32_t m, const uint8_t *
     return NW_OK;
 }
 
+// Score-only fill with 16 rows per lane on `stream`, using scratch the
+// caller provides (no context, no allocation): `bnd` holds
+// (S-1) * bstride words and `progress` S words that must be zero, where
+// S = ceil(m / 512) and bstride = 32 * ceil((n + 1) / 32).  m, n >= 1.
+cudaError_t fill_score_with_scratch(const uint8_t *a2b, uint32_t m, const uint8_t *b2b, uint32_t n,
+                                    const nw_scoring &sc, int32_t *score, uint32_t *bnd, uint32_t *progress,
+                                    uint32_t *err, cudaStream_t stream, int sm_count) {
+    constexpr int R = 16;
+    const Profile pf = make_profile(sc);
+    FillArgs fa{};
+    fa.a = a2b;
+    fa.b = b2b;
+    fa.m = m;
+    fa.n = n;
+    for (int c = 0; c < 4; ++c) fa.prof[c] = pf.prof[c];
+    fa.gap = pf.gap;
+    fa.S = (m + 32u * R - 1) / (32u * R);
+    fa.bstride = ((n + 1 + 31) / 32) * 32;
+    fa.bnd = bnd;
+    fa.progress = progress;
+    fa.score = score;
+    fa.err = err;
+    int occ = 0;
+    cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_fill<R, false>, kFillWarps * 32, 0);
+    if (e != cudaSuccess) return e;
+    if (occ < 1) occ = 1;
+    uint32_t blocks = (fa.S + kFillWarps - 1) / kFillWarps;
+    const uint32_t cap = (uint32_t)occ * (uint32_t)sm_count;  // all CTAs co-resident
+    if (blocks > cap) blocks = cap;
+    k_fill<R, false><<<blocks, kFillWarps * 32, 0, stream>>>(fa);
+    return cudaGetLastError();
+}
+
 int align_single(nw_ctx *ctx, const uint8_t *a2b, uint64_t m, const uint8_t *b2b, uint64_t n, const nw_scoring &sc,
                  uint32_t flags, int32_t *score, char *cigar, uint64_t cigar_cap, uint64_t *cigar_len) {
     (void)cigar_cap;
