@@ -44,6 +44,8 @@ def parse():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="pair32k", choices=["pair32k", "pair1k", "allpairs"])
     ap.add_argument("--no-clocks", action="store_true")
+    ap.add_argument("--nseq", type=int, default=512, help="allpairs: number of sequences (512 = the full workload)")
+    ap.add_argument("--m", type=int, default=32768, help="pair32k: query length (32,768 = the full workload)")
     return ap.parse_args()
 
 
@@ -54,15 +56,20 @@ def dist_env():
     return rank, world, local
 
 
+WL_ARGS = {"nseq": 512, "m": 32768}
+
+
 def workload(name: str):
     if name == "allpairs":
-        seqs = seqgen.all_vs_all_family(1003)
-        return seqs, ("all-vs-all scores of 512 mutants of one random 1,500-base root (lengths U{500..1500}, "
-                      "divergence U[0.05,0.30], 20% of mutations 1-bp indels), 130,816 pairs, int32 matrix (seed 1003)")
+        nseq = WL_ARGS["nseq"]
+        seqs = seqgen.all_vs_all_family(1003, nseq=nseq)
+        return seqs, (f"all-vs-all scores of {nseq} mutants of one random 1,500-base root (lengths U{{500..1500}}, "
+                      f"divergence U[0.05,0.30], 20% of mutations 1-bp indels), {nseq * (nseq - 1) // 2:,} pairs, int32 matrix "
+                      "(seed 1003)")
     if name == "pair1k":
         p = seqgen.random_pair(1001, 1000, 1000)
         return p, "single pair 1,000 x 1,000 i.i.d. uniform ACGT, score + CIGAR (seed 1001)"
-    p = seqgen.long_mutated_pair(1002)
+    p = seqgen.long_mutated_pair(1002, m=WL_ARGS["m"])
     return p, (f"single long pair {p.a.size:,} x {p.b.size:,}: B = A with 10% substitutions and 2% geometric "
                f"indels (mean 3), score + CIGAR (seed 1002)")
 
@@ -371,6 +378,7 @@ class _Null:
 
 def main():
     args = parse()
+    WL_ARGS.update(nseq=args.nseq, m=args.m)
     if args.impl == "reference":
         run_reference(args)
     else:

@@ -12,7 +12,8 @@
 // processing time first), which balances uneven lengths.
 //
 // The cell update is the one of nw_single.cu (W domain, prmt + DPX add-max
-// + max; with pointers: prmt + add + two DPX max-with-predicate).
+// + max; with pointers: prmt + add + two max, the pointer bits taken from
+// differences).
 #include <algorithm>
 #include <cstring>
 #include <numeric>
@@ -143,10 +144,14 @@ __global__ void __launch_bounds__(kBatchWarps * 32) k_batch(BatchArgs p) {
                     const int32_t sv = (int32_t)prmt(prof[r], 0u, sel);
                     int32_t w;
                     if constexpr (PTR) {
-                        bool pu, pd;
-                        const int32_t mx = __vibmax_s32(u, Wl[r], &pu);
-                        w = __vibmax_s32(d + sv, mx, &pd);
-                        code |= ((uint32_t)pd | ((uint32_t)pu << 1)) << (2 * r);
+                        // bit0: diagonal is the maximum; bit1: W == up (the
+                        // vertical candidate wins over the horizontal one
+                        // whenever the diagonal loses) -- from differences,
+                        // off the dependency chain
+                        const int32_t t1 = d + sv;
+                        w = max(t1, max(u, Wl[r]));
+                        const uint32_t bits = 3u - (uint32_t)min(w - t1, 1) - (uint32_t)min(2 * (w - u), 2);
+                        code |= bits << (2 * r);
                     } else {
                         w = max(__viaddmax_s32(d, sv, Wl[r]), u);
                     }

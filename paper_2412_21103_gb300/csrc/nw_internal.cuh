@@ -185,4 +185,6 @@ int align_single(nw_ctx *ctx, const uint8_t *a2b, uint64_t m, const uint8_t *b2b
 cudaError_t fill_score_with_scratch(const uint8_t *a2b, uint32_t m, const uint8_t *b2b, uint32_t n,
                                     const nw_scoring &sc, int32_t *score, uint32_t *bnd, uint32_t *progress,
                                     uint32_t *err, cudaStream_t stream, int sm_count);
+int launch_pair_fill(nw_ctx *ctx, int R, bool ptr, const uint8_t *a2b, uint32_t m, const uint8_t *b2b, uint32_t n,
+                     const Profile &pf, int32_t *score, uint32_t *ptr_words, uint32_t ncg, int nw);
 }

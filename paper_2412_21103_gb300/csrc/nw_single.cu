@@ -20,6 +20,7 @@
 // lane; words are stored [stripe][lane][column group], so one lane's words
 // are contiguous along the row.
 #include <cstdio>
+#include <cstdlib>
 
 #include "nw_internal.cuh"
 
@@ -189,45 +190,35 @@ static int launch_fill(nw_ctx *ctx, FillArgs &fa) {
     return NW_OK;
 }
 
-template <int R>
+// Rows per lane and warps per CTA for the single-pair fill (tunable at run
+// time through NW_PAIR_R / NW_PAIR_WARPS for sweeps).
+static void pair_shape(nw_ctx *ctx, uint64_t m, int &R, int &nw) {
+    (void)ctx;
+    R = m >= 32u * 4 * 8 ? 4 : 2;
+    nw = 4;
+    if (const char *e = getenv("NW_PAIR_R")) R = atoi(e);
+    if (const char *e = getenv("NW_PAIR_WARPS")) nw = atoi(e);
+}
+
 static int run_pair(nw_ctx *ctx, const uint8_t *a2b, uint32_t m, const uint8_t *b2b, uint32_t n, const Profile &pf,
                     uint32_t flags, int32_t *score, char *cigar, uint64_t *cigar_len) {
     const bool want = flags & NW_CIGAR;
-    const uint32_t SH = 32u * R;
-    FillArgs fa{};
-    fa.a = a2b;
-    fa.b = b2b;
-    fa.m = m;
-    fa.n = n;
-    for (int c = 0; c < 4; ++c) fa.prof[c] = pf.prof[c];
-    fa.gap = pf.gap;
-    fa.S = (m + SH - 1) / SH;
-    fa.bstride = ((n + 1 + 31) / 32) * 32;
-    fa.score = score;
-    fa.err = ctx->d_err;
+    int R, nw;
+    pair_shape(ctx, m, R, nw);
     int rc;
+    if (!want) return launch_pair_fill(ctx, R, false, a2b, m, b2b, n, pf, score, nullptr, 0, nw);
+    const uint32_t SH = 32u * R;
+    const uint32_t S = (m + SH - 1) / SH;
+    const uint32_t ncg = ptr_words_per_lane_row(n, R);
     void *v = nullptr;
-    if (fa.S > 1) {
-        if ((rc = scratch(ctx, "fill_bnd", (size_t)(fa.S - 1) * fa.bstride * 4, &v))) return rc;
-        fa.bnd = (uint32_t *)v;
-    }
-    if ((rc = scratch(ctx, "fill_progress", (size_t)fa.S * 4, &v))) return rc;
-    fa.progress = (uint32_t *)v;
-    cudaMemsetAsync(fa.progress, 0, (size_t)fa.S * 4, ctx->stream);
-    if (!want) return launch_fill<R, false>(ctx, fa);
-
-    fa.ncg = ptr_words_per_lane_row(n, R);
-    const size_t ptr_bytes = (size_t)fa.S * 32u * fa.ncg * 4u;
-    if ((rc = scratch(ctx, "ptr", ptr_bytes, &v))) return rc;
-    fa.ptr = (uint32_t *)v;
-    if ((rc = launch_fill<R, true>(ctx, fa))) return rc;
-
+    if ((rc = scratch(ctx, "ptr", (size_t)S * 32u * ncg * 4u, &v))) return rc;
+    uint32_t *ptr = (uint32_t *)v;
+    if ((rc = launch_pair_fill(ctx, R, true, a2b, m, b2b, n, pf, score, ptr, ncg, nw))) return rc;
     void *mv = nullptr, *nm = nullptr;
     if ((rc = scratch(ctx, "moves", (size_t)m + n + 16, &mv))) return rc;
     if ((rc = scratch(ctx, "nmoves", 16, &nm))) return rc;
-    TraceTask tt{fa.ptr, fa.ncg, m, n, (uint8_t *)mv, (uint64_t *)nm, a2b, b2b, cigar, cigar_len};
-    if ((rc = launch_trace(ctx, R, tt, nullptr, 1, (flags & NW_CIGAR_M) ? 1u : 0u))) return rc;
-    return NW_OK;
+    TraceTask tt{ptr, ncg, m, n, (uint8_t *)mv, (uint64_t *)nm, a2b, b2b, cigar, cigar_len};
+    return launch_trace(ctx, R, tt, nullptr, 1, (flags & NW_CIGAR_M) ? 1u : 0u);
 }
 
 // Score-only fill with 16 rows per lane on `stream`, using scratch the
@@ -273,16 +264,7 @@ int align_single(nw_ctx *ctx, const uint8_t *a2b, uint64_t m, const uint8_t *b2b
         k_trivial<<<1, 1, 0, ctx->stream>>>((uint32_t)m, (uint32_t)n, sc.gap, score, want ? cigar : nullptr,
                                             want ? cigar_len : nullptr);
     } else {
-        // Rows per lane: enough stripes to spread over the SMs, but at least
-        // 4 rows so shuffles stay a small share of the work.
-        int rc;
-        const uint64_t warps_wanted = (uint64_t)ctx->sm_count * 2;
-        if (m >= warps_wanted * 32 * 16)
-            rc = run_pair<16>(ctx, a2b, (uint32_t)m, b2b, (uint32_t)n, pf, flags, score, cigar, cigar_len);
-        else if (m >= warps_wanted * 32 * 8 / 4)
-            rc = run_pair<8>(ctx, a2b, (uint32_t)m, b2b, (uint32_t)n, pf, flags, score, cigar, cigar_len);
-        else
-            rc = run_pair<4>(ctx, a2b, (uint32_t)m, b2b, (uint32_t)n, pf, flags, score, cigar, cigar_len);
+        const int rc = run_pair(ctx, a2b, (uint32_t)m, b2b, (uint32_t)n, pf, flags, score, cigar, cigar_len);
         if (rc) return rc;
     }
     cudaError_t e = cudaGetLastError();

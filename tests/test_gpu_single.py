@@ -157,3 +157,16 @@ def test_cigar_m_flag(ctx):
     s, cig = nw.nw_align(ctx, nw.pack_codes(p.a), 200, nw.pack_codes(p.b), 180, (1, -1, -1),
                          nw.NW_CIGAR | nw.NW_CIGAR_M)
     assert cig == oracle.rle(ops.replace("=", "M").replace("X", "M"))
+
+
+@pytest.mark.parametrize("R", [2, 4, 8])
+@pytest.mark.parametrize("nwarps", [1, 2, 4, 8])
+def test_pair_kernel_shapes(ctx, R, nwarps, monkeypatch):
+    """Every rows-per-lane / warps-per-CTA shape of the single-pair fill:
+    several CTA stripes (global handoffs) and several warps per CTA (shared
+    memory handoffs), ragged last stripe."""
+    monkeypatch.setenv("NW_PAIR_R", str(R))
+    monkeypatch.setenv("NW_PAIR_WARPS", str(nwarps))
+    for seed, m, n in [(1, 32 * R * nwarps * 3 + 17, 700), (2, 5000, 301), (3, 64, 2000), (4, 2 * 32 * R + 1, 31)]:
+        p = seqgen.long_mutated_pair(seed, m=m)
+        _check(ctx, p.a, p.b[:n] if n < p.b.size else p.b)
