@@ -67,6 +67,9 @@ typedef enum {
 #define NW_LEARNED_BAND 2u    /* batch: certified learned band first          */
 #define NW_HOST_IO      4u    /* sequence inputs and outputs are host memory  */
 #define NW_CIGAR_M      8u    /* write 'M' for both '=' and 'X'               */
+#define NW_BAND_RAW     16u   /* nw_align_batch_banded: one banded round, the
+                                 banded score itself, no certificate or
+                                 fallback (score only; for inspection)      */
 
 typedef struct {
     int32_t match;      /* score of a diagonal step with equal bases (Sec. 2.3: +1)   */
@@ -167,6 +170,59 @@ int nw_align_batch(nw_ctx *ctx, const uint8_t *pool2b,
                    const uint64_t *b_off, const uint32_t *b_len, uint32_t npairs,
                    nw_scoring sc, uint32_t flags, int32_t *scores,
                    char *cigar_pool, const uint64_t *cigar_off, uint64_t *cigar_len);
+
+/* The certified band with explicit starting half-widths (host array
+ * band_w, one per pair): each pair is first aligned in the band of diagonals
+ * d = j - i in [min(0,n-m) - w, max(0,n-m) + w].  The banded score S_b is
+ * kept only when a certificate proves it is the full-grid score: every path
+ * that leaves the band makes at least G gap moves (G from the band
+ * geometry), so it scores at most U0 = match*floor((m+n-G)/2) + gap*(m+n-2*
+ * floor((m+n-G)/2)); S_b >= U0 certifies the score and S_b > U0 also the
+ * alignment (no out-of-band path can tie).  Rejected pairs retry at 2w and
+ * 4w, then go to the full kernel, so results always equal nw_align_batch.
+ * Needs match >= 0.  Arguments otherwise as nw_align_batch.  Not in the
+ * paper. */
+int nw_align_batch_banded(nw_ctx *ctx, const uint8_t *pool2b, const uint64_t *a_off, const uint32_t *a_len,
+                          const uint64_t *b_off, const uint32_t *b_len, uint32_t npairs, const uint32_t *band_w,
+                          nw_scoring sc, uint32_t flags, int32_t *scores, char *cigar_pool, const uint64_t *cigar_off,
+                          uint64_t *cigar_len);
+/* Counters of the certified band since the context was created: [0] pairs
+ * tried in a band, [1..3] certified in round 1..3, [4] unused, [5] sent to
+ * the full kernel, [6] cells the banded kernels computed, [7] full-grid
+ * cells of every pair handed to the banded path.  Returns 8 (fills at most
+ * `cap`). */
+int nw_ctx_band_stats(nw_ctx *ctx, uint64_t *out, int cap);
+
+/* ------------------------------------------------------------ learned band
+ * Not in the paper.  A pair's features (65 floats): a 64-bin histogram of
+ * exact 4-mer hits around the pair's expected diagonal (256 anchors in A,
+ * hits within +-max(m,n)/8 of the anchor's expected column, bins over that
+ * window, log1p(count)/log1p(anchors)) and (n-m)/max(m,n).  The model is a
+ * 65-128-128-1 ReLU network with BF16 weights and activations and FP32
+ * accumulation whose output is log of the band half-width; with
+ * NW_LEARNED_BAND, nw_align_batch runs the certified band from
+ * ceil(1.25 * exp(output)) (at least 8), or from 64 without a model. */
+
+/* Features of npairs pairs into feat (device, npairs x 65 floats, row per
+ * pair); pool2b device, metadata host arrays; B <= 200,000 bases. */
+int nw_band_features(nw_ctx *ctx, const uint8_t *pool2b, const uint64_t *a_off, const uint32_t *a_len,
+                     const uint64_t *b_off, const uint32_t *b_len, uint32_t npairs, float *feat);
+/* Number of model parameters (FP32 masters, flat: W1[128][65], b1[128],
+ * W2[128][128], b2[128], W3[128], b3). */
+uint64_t nw_band_model_size(void);
+/* Fresh parameters (uniform He initialisation from a counter-based
+ * SplitMix64 stream keyed by seed), Adam state cleared. */
+int nw_band_model_init(nw_ctx *ctx, uint64_t seed);
+/* Copy parameters in / out (host arrays of nw_band_model_size() floats). */
+int nw_band_model_set(nw_ctx *ctx, const float *params, uint64_t count);
+int nw_band_model_get(nw_ctx *ctx, float *params, uint64_t count);
+/* Network outputs for n feature rows (device in, device out). */
+int nw_band_model_forward(nw_ctx *ctx, const float *feat, uint32_t n, float *out);
+/* Gradient of 0.5*mean((y - target)^2) w.r.t. the parameters (device
+ * arrays: grad has nw_band_model_size() floats, loss one float). */
+int nw_band_model_grad(nw_ctx *ctx, const float *feat, const float *target, uint32_t n, float *grad, float *loss);
+/* One Adam step (lr; beta 0.9/0.999, eps 1e-8) on that loss. */
+int nw_band_model_train_step(nw_ctx *ctx, const float *feat, const float *target, uint32_t n, float lr, float *loss);
 
 /* All-vs-all scores of `nseq` sequences (the scoring-matrix stage of the
  * paper's center-star alignment, Sec. 3.2; Eq. 2 gives its n(n-1)/2 pairs).

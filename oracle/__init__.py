@@ -16,6 +16,7 @@ Functions whose result the paper or mathematics pins (see ``tests/``):
   banded                -- equals full NW for a band covering the grid;
                            brute force over in-band paths; the bound U is
                            checked against brute force over out-of-band paths.
+  exit_bound (U0)       -- brute force over every path that leaves the band.
 """
 from __future__ import annotations
 
@@ -136,6 +137,37 @@ def banded(a, b, w: int, match: int = 1, mismatch: int = -1, gap: int = -1,
     if want_grid:
         return int(sb.value), int(ub.value), H
     return int(sb.value), int(ub.value)
+
+
+def band_limits(m: int, n: int, w: int) -> tuple[int, int]:
+    """Diagonals d = j - i of the band of half-width w: [min(0,n-m)-w, max(0,n-m)+w]."""
+    delta = n - m
+    return min(0, delta) - w, max(0, delta) + w
+
+
+def exit_bound(m: int, n: int, w: int, match: int = 1, gap: int = -1) -> int | None:
+    """Closed-form bound U0 on the score of any path that leaves the band
+    (None when no path can leave it).  A path from diagonal 0 to diagonal
+    n-m that visits diagonal hi+1 needs at least (hi+1) + (hi+1-(n-m)) gap
+    moves; one that visits lo-1 needs (1-lo) + ((n-m)-lo+1).  A path with G
+    gap moves has (m+n-G)/2 diagonal moves, each worth at most `match`, so
+    its score is at most match*(m+n-G)/2 + gap*G, which falls as G grows
+    (match >= 0 >= gap); the parity of m+n-G is kept exact."""
+    lo, hi = band_limits(m, n, w)
+    delta = n - m
+    best = None
+    for g_min in ((hi + 1) + (hi + 1 - delta), (1 - lo) + (delta - lo + 1)):
+        if g_min > m + n:
+            continue
+        # paths need both ends inside the grid: the excursion must fit
+        if g_min == (hi + 1) + (hi + 1 - delta) and hi + 1 > n:
+            continue
+        if g_min == (1 - lo) + (delta - lo + 1) and 1 - lo > m:
+            continue
+        k = (m + n - g_min) // 2
+        val = match * k + gap * (m + n - 2 * k)
+        best = val if best is None else max(best, val)
+    return best
 
 
 def rle(ops: str) -> str:

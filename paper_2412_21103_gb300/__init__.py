@@ -33,6 +33,7 @@ NW_CIGAR = 1
 NW_LEARNED_BAND = 2
 NW_HOST_IO = 4
 NW_CIGAR_M = 8
+NW_BAND_RAW = 16
 
 DEFAULT_SCORING = (1, -1, -1)
 
@@ -84,6 +85,17 @@ def load():
         "nw_score_all_pairs": (ctypes.c_int, [vp, vp, u64p, u32p, u32, Scoring, u32, vp]),
         "nw_peak_int": (ctypes.c_int, [vp, ctypes.c_int, u64, ctypes.POINTER(ctypes.c_double)]),
         "nw_align_score_noalloc": (ctypes.c_int, [vp, u64, vp, u64, Scoring, vp, vp]),
+        "nw_align_batch_banded": (ctypes.c_int, [vp, vp, u64p, u32p, u64p, u32p, u32, u32p, Scoring, u32, vp, vp,
+                                                 u64p, vp]),
+        "nw_ctx_band_stats": (ctypes.c_int, [vp, u64p, ctypes.c_int]),
+        "nw_band_features": (ctypes.c_int, [vp, vp, u64p, u32p, u64p, u32p, u32, vp]),
+        "nw_band_model_size": (u64, []),
+        "nw_band_model_init": (ctypes.c_int, [vp, u64]),
+        "nw_band_model_set": (ctypes.c_int, [vp, vp, u64]),
+        "nw_band_model_get": (ctypes.c_int, [vp, vp, u64]),
+        "nw_band_model_forward": (ctypes.c_int, [vp, vp, u32, vp]),
+        "nw_band_model_grad": (ctypes.c_int, [vp, vp, vp, u32, vp, vp]),
+        "nw_band_model_train_step": (ctypes.c_int, [vp, vp, vp, u32, ctypes.c_float, vp]),
     }
     for name, (res, args) in sig.items():
         f = getattr(L, name)
@@ -283,6 +295,109 @@ def nw_align_batch(ctx: Context, pool2b, a_off, a_len, b_off, b_len, scoring=DEF
                           _ptr(cigar_pool) if want else None, cop, _ptr(cigar_len) if want else None)
     _check(ctx, rc)
     return scores, cigar_pool, cigar_len
+
+
+def nw_align_batch_banded(ctx: Context, pool2b, a_off, a_len, b_off, b_len, band_w, scoring=DEFAULT_SCORING,
+                          flags: int = 0, scores=None, cigar_pool=None, cigar_off=None, cigar_len=None):
+    """Certified banded batch with explicit starting half-widths (host
+    array band_w).  Same marshalling as nw_align_batch."""
+    L = load()
+    npairs = len(a_len)
+    ao, aop = _u64(a_off)
+    al, alp = _u32(a_len)
+    bo, bop = _u64(b_off)
+    bl, blp = _u32(b_len)
+    ww, wwp = _u32(band_w)
+    want = bool(flags & NW_CIGAR)
+    if cigar_off is None and want:
+        caps = [nw_cigar_bound(int(x), int(y)) for x, y in zip(al, bl)]
+        cigar_off = np.concatenate([[0], np.cumsum(caps)]).astype(np.uint64)
+    co, cop = _u64(cigar_off) if want else (None, None)
+    if _is_host(pool2b):
+        flags |= NW_HOST_IO
+        sc_out = np.zeros(max(npairs, 1), np.int32)
+        cpool = np.zeros(max(int(co[-1]) if want else 1, 1), np.uint8)
+        clen = np.zeros(max(npairs, 1), np.uint64)
+        rc = L.nw_align_batch_banded(ctx.handle, _ptr(pool2b), aop, alp, bop, blp, npairs, wwp, _sc(scoring), flags,
+                                     _ptr(sc_out), _ptr(cpool) if want else None, cop, _ptr(clen) if want else None)
+        _check(ctx, rc)
+        cigars = None
+        if want:
+            cigars = [cpool[int(co[k]): int(co[k]) + int(clen[k])].tobytes().decode() for k in range(npairs)]
+        return sc_out[:npairs], cigars
+    rc = L.nw_align_batch_banded(ctx.handle, _ptr(pool2b), aop, alp, bop, blp, npairs, wwp, _sc(scoring), flags,
+                                 _ptr(scores), _ptr(cigar_pool) if want else None, cop,
+                                 _ptr(cigar_len) if want else None)
+    _check(ctx, rc)
+    return scores, cigar_pool, cigar_len
+
+
+def nw_ctx_band_stats(ctx: Context) -> dict:
+    out = (ctypes.c_uint64 * 8)()
+    load().nw_ctx_band_stats(ctx.handle, out, 8)
+    v = [int(x) for x in out]
+    return {"tried": v[0], "certified_round": v[1:4], "full_fallback": v[5], "band_cells": v[6],
+            "full_cells": v[7]}
+
+
+def nw_band_features(ctx: Context, pool_dev, a_off, a_len, b_off, b_len, out=None):
+    """Features of the pairs (device pool) -> CUDA float32 tensor (n, 65)."""
+    import torch
+    n = len(a_len)
+    if out is None:
+        out = torch.zeros((n, 65), dtype=torch.float32, device=pool_dev.device)
+    ao, aop = _u64(a_off)
+    al, alp = _u32(a_len)
+    bo, bop = _u64(b_off)
+    bl, blp = _u32(b_len)
+    _check(ctx, load().nw_band_features(ctx.handle, _ptr(pool_dev), aop, alp, bop, blp, n, _ptr(out)))
+    return out
+
+
+def nw_band_model_size() -> int:
+    return int(load().nw_band_model_size())
+
+
+def nw_band_model_init(ctx: Context, seed: int = 0):
+    _check(ctx, load().nw_band_model_init(ctx.handle, seed))
+
+
+def nw_band_model_set(ctx: Context, params: np.ndarray):
+    p = np.ascontiguousarray(params, dtype=np.float32)
+    _check(ctx, load().nw_band_model_set(ctx.handle, _ptr(p), p.size))
+
+
+def nw_band_model_get(ctx: Context) -> np.ndarray:
+    p = np.zeros(nw_band_model_size(), np.float32)
+    _check(ctx, load().nw_band_model_get(ctx.handle, _ptr(p), p.size))
+    return p
+
+
+def nw_band_model_forward(ctx: Context, feat, out=None):
+    import torch
+    n = int(feat.shape[0])
+    if out is None:
+        out = torch.zeros(n, dtype=torch.float32, device=feat.device)
+    _check(ctx, load().nw_band_model_forward(ctx.handle, _ptr(feat), n, _ptr(out)))
+    return out
+
+
+def nw_band_model_grad(ctx: Context, feat, target):
+    import torch
+    grad = torch.zeros(nw_band_model_size(), dtype=torch.float32, device=feat.device)
+    loss = torch.zeros(1, dtype=torch.float32, device=feat.device)
+    _check(ctx, load().nw_band_model_grad(ctx.handle, _ptr(feat), _ptr(target), int(feat.shape[0]), _ptr(grad),
+                                          _ptr(loss)))
+    return grad, loss
+
+
+def nw_band_model_train_step(ctx: Context, feat, target, lr: float, loss=None):
+    import torch
+    if loss is None:
+        loss = torch.zeros(1, dtype=torch.float32, device=feat.device)
+    _check(ctx, load().nw_band_model_train_step(ctx.handle, _ptr(feat), _ptr(target), int(feat.shape[0]), lr,
+                                                _ptr(loss)))
+    return loss
 
 
 def nw_score_all_pairs(ctx: Context, pool2b, off, lens, scoring=DEFAULT_SCORING, flags: int = 0, out=None):

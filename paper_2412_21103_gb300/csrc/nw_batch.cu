@@ -32,7 +32,8 @@ struct BatchTask {
     uint32_t out0, out1;    // score destinations (out1 == ~0u: none)
     uint64_t ptr_off;       // word offset of the pair's pointer words
     uint32_t ncg;           // pointer words per lane row
-    uint32_t pad;
+    uint32_t period;        // steps per stripe (banded: fixed band width)
+    int32_t lo, hi;         // banded: diagonals j - i kept, [lo, hi]
 };
 
 struct BatchArgs {
@@ -65,7 +66,17 @@ __device__ __forceinline__ uint32_t load_rows(const uint8_t *s, uint32_t i0, uin
     return w;
 }
 
-template <int R, bool PTR>
+// Out-of-band cells of the banded variant take this value: far below any
+// reachable W (>= 0) and far enough from INT32_MIN that adding scores never
+// wraps.
+constexpr int32_t kNegW = -(1 << 27);
+
+// BAND: only the diagonals d = j - i in [lo, hi] are computed.  Stripe s
+// runs over its band columns [cbeg(s), cend(s)] (0-based) only, cells of the
+// stripe rectangle outside the band are forced to kNegW (which stops every
+// path through them), and the boundary row/column cells outside the band
+// are kNegW too.  The stripe period is the task's fixed `period`.
+template <int R, bool PTR, bool BAND>
 __global__ void __launch_bounds__(kBatchWarps * 32) k_batch(BatchArgs p) {
     constexpr uint32_t SH = 32u * R;
     constexpr uint32_t CPW = PTR ? 16u / R : 1u;
@@ -92,35 +103,54 @@ __global__ void __launch_bounds__(kBatchWarps * 32) k_batch(BatchArgs p) {
             continue;
         }
         const uint32_t S = (m + SH - 1) / SH;
-        const uint32_t P = max(n, kMinPeriod);
+        const int32_t lo = BAND ? tk.lo : 0, hi = BAND ? tk.hi : 0;
+        const uint32_t P = BAND ? tk.period : max(n, kMinPeriod);
         const uint32_t T = S * P + 31;
         const uint32_t sM = (m - 1) / SH, lM = ((m - 1) % SH) / R, rM = (m - 1) % R;
         uint32_t *pbase = PTR ? p.ptr + tk.ptr_off : nullptr;
+        // first / last 0-based column of stripe s
+        auto cbeg = [&](uint32_t st) -> int32_t { return BAND ? max(0, (int32_t)(st * SH) + lo) : 0; };
+        auto cend = [&](uint32_t st) -> int32_t {
+            return BAND ? min((int32_t)n - 1, (int32_t)(st * SH + SH - 1) + hi) : (int32_t)n - 1;
+        };
 
         uint32_t prof[R];
         int32_t Wl[R];
         int32_t dtop = 0;
         uint32_t xout = 0, bits = 0;
-        auto init_rows = [&](uint32_t codes) {
+        int32_t cb = cbeg(0), ce = cend(0);   // this lane's stripe columns
+        auto init_rows = [&](uint32_t codes, uint32_t st) {
+            const uint32_t i0 = st * SH + (uint32_t)lane * R;  // 1-based row above the lane's first row
+            const bool col0 = cbeg(st) == 0;
 #pragma unroll
             for (int r = 0; r < R; ++r) {
                 const uint32_t c = (codes >> (2 * r)) & 3u;
                 prof[r] = c == 0 ? P0 : c == 1 ? P1 : c == 2 ? P2 : P3;
-                Wl[r] = 0;
+                // left boundary (column cbeg-1): grid column 0 if the band
+                // reaches it (row i in band iff i <= -lo), else out of band
+                Wl[r] = (!BAND || (col0 && (int32_t)(i0 + r + 1) <= -lo)) ? 0 : kNegW;
             }
-            dtop = 0;
+            dtop = (!BAND || (col0 && (int32_t)i0 <= -lo)) ? 0 : kNegW;
+            cb = cbeg(st);
+            ce = cend(st);
         };
-        init_rows(load_rows<R>(A, (uint32_t)lane * R, m));
+        init_rows(load_rows<R>(A, (uint32_t)lane * R, m), 0);
         uint32_t next_rows = S > 1 ? load_rows<R>(A, SH + (uint32_t)lane * R, m) : 0u;
-        int32_t c = -lane;   // column of this lane at step t (negative: not started)
+        int32_t c = -lane;   // step within this lane's stripe (negative: not started)
         uint32_t s = 0;      // stripe of this lane
 
-        // Lane-0 input for global index g: stripe 0 reads B (W = 0), later
-        // stripes read the row buffer.
+        // Lane-0 input for global index g: stripe 0 reads B (W = 0 on the
+        // grid's row 0, kNegW beyond the band), later stripes read the row
+        // buffer (kNegW where the previous stripe computed nothing).
         auto chunk_word = [&](uint32_t g) -> uint32_t {
-            const uint32_t sg = g / P, cg = g - sg * P;
-            if (sg >= S || cg >= n) return 0u;
-            return sg == 0 ? base_at(B, cg) : __ldcg(ring + cg);
+            const uint32_t sg = g / P, tg = g - sg * P;
+            if (sg >= S) return 0u;
+            const int32_t col = cbeg(sg) + (int32_t)tg;
+            if (col > cend(sg)) return 0u;
+            const uint32_t bc = base_at(B, (uint32_t)col);
+            if (sg == 0) return BAND && col + 1 > hi ? (((uint32_t)kNegW << 2) | bc) : bc;
+            if (BAND && col > cend(sg - 1)) return ((uint32_t)kNegW << 2) | bc;
+            return __ldcg(ring + col);
         };
         uint32_t stage = 0, stage_next = chunk_word((uint32_t)lane);
 
@@ -134,11 +164,13 @@ __global__ void __launch_bounds__(kBatchWarps * 32) k_batch(BatchArgs p) {
             uint32_t x = __shfl_up_sync(kFull, xout, 1);
             const uint32_t x0 = __shfl_sync(kFull, stage, t & 31u);
             if (lane == 0) x = x0;
-            if (c >= 0 && c < (int32_t)n && s < S) {
-                const int32_t up = (int32_t)(x >> 2);
+            const int32_t col = cb + c;
+            if (c >= 0 && col <= ce && s < S) {
+                const int32_t up = (int32_t)x >> 2;
                 const uint32_t sel = sext_selector(x & 3u);
                 int32_t d = dtop, u = up;
                 uint32_t code = 0;
+                const int32_t D0 = col - (int32_t)(s * SH + (uint32_t)lane * R);  // j - i of row 0 of the lane
 #pragma unroll
                 for (int r = 0; r < R; ++r) {
                     const int32_t sv = (int32_t)prmt(prof[r], 0u, sel);
@@ -150,10 +182,12 @@ __global__ void __launch_bounds__(kBatchWarps * 32) k_batch(BatchArgs p) {
                         // off the dependency chain
                         const int32_t t1 = d + sv;
                         w = max(t1, max(u, Wl[r]));
+                        if (BAND && (uint32_t)(D0 - r - lo) > (uint32_t)(hi - lo)) w = kNegW;
                         const uint32_t bits = 3u - (uint32_t)min(w - t1, 1) - (uint32_t)min(2 * (w - u), 2);
                         code |= bits << (2 * r);
                     } else {
                         w = max(__viaddmax_s32(d, sv, Wl[r]), u);
+                        if (BAND && (uint32_t)(D0 - r - lo) > (uint32_t)(hi - lo)) w = kNegW;
                     }
                     d = Wl[r];
                     Wl[r] = w;
@@ -164,13 +198,13 @@ __global__ void __launch_bounds__(kBatchWarps * 32) k_batch(BatchArgs p) {
                 if constexpr (PTR) {
                     const uint32_t cc = (uint32_t)c % CPW;
                     bits |= code << (2u * R * cc);
-                    if (cc == CPW - 1 || c == (int32_t)n - 1) {
+                    if (cc == CPW - 1 || col == ce) {
                         pbase[(size_t)(s * 32u + lane) * tk.ncg + (uint32_t)c / CPW] = bits;
                         bits = 0;
                     }
                 }
-                if (lane == 31 && s + 1 < S) ring[c] = xout;
-                if (s == sM && (uint32_t)lane == lM && c == (int32_t)n - 1) {
+                if (lane == 31 && s + 1 < S) ring[col] = xout;
+                if (s == sM && (uint32_t)lane == lM && col == (int32_t)n - 1) {
                     int32_t wmn = 0;
 #pragma unroll
                     for (int r = 0; r < R; ++r)
@@ -184,8 +218,13 @@ __global__ void __launch_bounds__(kBatchWarps * 32) k_batch(BatchArgs p) {
                 c = 0;
                 ++s;
                 if (s < S) {
-                    init_rows(next_rows);
+                    init_rows(next_rows, s);
                     next_rows = s + 1 < S ? load_rows<R>(A, (s + 1) * SH + (uint32_t)lane * R, m) : 0u;
+                    // Banded: lane 0's first cell has its diagonal neighbour on
+                    // diagonal lo, inside the band -- the previous stripe's
+                    // bottom row at column cb-1 (written by lane 31 at least
+                    // P-SH-32 >= 64 steps ago, past two fences).
+                    if (BAND && lane == 0 && cb > 0) dtop = (int32_t)__ldcg(ring + cb - 1) >> 2;
                 }
             }
         }
@@ -200,10 +239,10 @@ __global__ void k_diag(const uint32_t *len, uint32_t nseq, int32_t match, int32_
 }
 
 // ------------------------------------------------------------------- host
-template <int R, bool PTR>
+template <int R, bool PTR, bool BAND>
 static int launch_batch_R(nw_ctx *ctx, BatchArgs &ba, uint32_t max_n) {
     int occ = 0;
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_batch<R, PTR>, kBatchWarps * 32, 0);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_batch<R, PTR, BAND>, kBatchWarps * 32, 0);
     if (occ < 1) occ = 1;
     uint32_t blocks = (uint32_t)occ * (uint32_t)ctx->sm_count;
     const uint32_t need = (ba.ntasks + kBatchWarps - 1) / kBatchWarps;
@@ -217,24 +256,25 @@ static int launch_batch_R(nw_ctx *ctx, BatchArgs &ba, uint32_t max_n) {
     if ((rc = scratch(ctx, "batch_counter", 16, &v))) return rc;
     ba.counter = (uint32_t *)v;
     cudaMemsetAsync(ba.counter, 0, 4, ctx->stream);
-    LaunchTimer t(ctx, PTR ? "batch_fill_ptr" : "batch_score");
-    k_batch<R, PTR><<<blocks, kBatchWarps * 32, 0, ctx->stream>>>(ba);
+    LaunchTimer t(ctx, BAND ? (PTR ? "band_fill_ptr" : "band_score") : (PTR ? "batch_fill_ptr" : "batch_score"));
+    k_batch<R, PTR, BAND><<<blocks, kBatchWarps * 32, 0, ctx->stream>>>(ba);
     return NW_OK;
 }
 
-static int launch_batch(nw_ctx *ctx, int R, bool ptr, BatchArgs &ba, uint32_t max_n) {
-    if (ptr) {
-        switch (R) {
-            case 4: return launch_batch_R<4, true>(ctx, ba, max_n);
-            case 8: return launch_batch_R<8, true>(ctx, ba, max_n);
-            default: return launch_batch_R<16, true>(ctx, ba, max_n);
-        }
+static int launch_batch(nw_ctx *ctx, int R, bool ptr, BatchArgs &ba, uint32_t max_n, bool band = false) {
+#define NW_BATCH_CASES(PTRV, BANDV)                                         \
+    switch (R) {                                                           \
+        case 4: return launch_batch_R<4, PTRV, BANDV>(ctx, ba, max_n);     \
+        case 8: return launch_batch_R<8, PTRV, BANDV>(ctx, ba, max_n);     \
+        default: return launch_batch_R<16, PTRV, BANDV>(ctx, ba, max_n);   \
     }
-    switch (R) {
-        case 4: return launch_batch_R<4, false>(ctx, ba, max_n);
-        case 8: return launch_batch_R<8, false>(ctx, ba, max_n);
-        default: return launch_batch_R<16, false>(ctx, ba, max_n);
+    if (band) {
+        if (ptr) NW_BATCH_CASES(true, true)
+        NW_BATCH_CASES(false, true)
     }
+    if (ptr) NW_BATCH_CASES(true, false)
+    NW_BATCH_CASES(false, false)
+#undef NW_BATCH_CASES
 }
 
 // Rows per lane for a set of pairs: the one that wastes the fewest padded
@@ -295,22 +335,282 @@ static int check_len(nw_ctx *ctx, const nw_scoring &sc, uint64_t m, uint64_t n) 
     return NW_OK;
 }
 
+// ------------------------------------------------------- certified band
+// Closed-form bound on the score of any path that leaves the band of
+// half-width w: such a path reaches diagonal hi+1 (then needs at least
+// (hi+1) + (hi+1-delta) horizontal/vertical moves) or lo-1 (at least
+// (1-lo) + (delta-lo+1)); with G gap moves it has (m+n-G)/2 diagonal moves
+// worth at most `match` each, and match >= 0 >= gap makes fewer gaps better.
+// Returns false when no path can leave the band (no bound needed).
+bool band_exit_bound(int64_t m, int64_t n, int64_t w, int32_t match, int32_t gap, int64_t *bound) {
+    const int64_t delta = n - m;
+    const int64_t lo = std::min<int64_t>(0, delta) - w, hi = std::max<int64_t>(0, delta) + w;
+    bool any = false;
+    int64_t best = 0;
+    const int64_t g_up = (hi + 1) + (hi + 1 - delta);   // visits diagonal hi+1
+    const int64_t g_dn = (1 - lo) + (delta - lo + 1);   // visits diagonal lo-1
+    const bool up_ok = hi + 1 <= n && g_up <= m + n;
+    const bool dn_ok = 1 - lo <= m && g_dn <= m + n;
+    for (int side = 0; side < 2; ++side) {
+        if (side == 0 ? !up_ok : !dn_ok) continue;
+        const int64_t g = side == 0 ? g_up : g_dn;
+        const int64_t k = (m + n - g) / 2;
+        const int64_t v = (int64_t)match * k + (int64_t)gap * (m + n - 2 * k);
+        best = any ? std::max(best, v) : v;
+        any = true;
+    }
+    *bound = best;
+    return any;
+}
+
+// Band of half-width w for an m x n pair: diagonals and the stripe period.
+static void band_task(BatchTask &t, int R, uint32_t w) {
+    const int64_t delta = (int64_t)t.n - t.m;
+    t.lo = (int32_t)(std::min<int64_t>(0, delta) - w);
+    t.hi = (int32_t)(std::max<int64_t>(0, delta) + w);
+    const uint32_t SH = 32u * R;
+    const uint64_t width = std::min<uint64_t>((uint64_t)t.n, (uint64_t)SH + (uint64_t)(t.hi - t.lo));
+    t.period = (uint32_t)std::max<uint64_t>(width, SH + kMinPeriod);
+}
+
+static uint64_t band_cells(const BatchTask &t, int R) {
+    const uint32_t SH = 32u * R;
+    return (uint64_t)((t.m + SH - 1) / SH) * SH * t.period;
+}
+
+static uint64_t full_cells(const BatchTask &t, int R) {
+    const uint32_t SH = 32u * R;
+    return (uint64_t)((t.m + SH - 1) / SH) * SH * std::max(t.n, kMinPeriod);
+}
+
 }  // namespace nw
 
 using namespace nw;
 
+// Full-grid batch over the pairs ids[0..count) (ids == nullptr: 0..count-1)
+// of the caller's arrays; results go to the caller's slots of those ids.
+int batch_device_impl(nw_ctx *ctx, const uint8_t *pool, const uint64_t *a_off, const uint32_t *a_len,
+                      const uint64_t *b_off, const uint32_t *b_len, const uint32_t *ids, uint32_t count,
+                      const nw_scoring &sc, uint32_t flags, int32_t *scores, char *cigar_pool,
+                      const uint64_t *cigar_off, uint64_t *cigar_len);
+
+// Banded rounds for the pairs in `ids` with starting half-widths w0[k]; the
+// pairs no round certifies are appended to `rest` for the full kernel.
+static int band_rounds(nw_ctx *ctx, const uint8_t *pool, const uint64_t *a_off, const uint32_t *a_len,
+                       const uint64_t *b_off, const uint32_t *b_len, const std::vector<uint32_t> &ids,
+                       const std::vector<uint32_t> &w0, const nw_scoring &sc, uint32_t flags, int32_t *scores,
+                       char *cigar_pool, const uint64_t *cigar_off, uint64_t *cigar_len, std::vector<uint32_t> &rest) {
+    const Profile pf = make_profile(sc);
+    const bool want = flags & NW_CIGAR;
+    constexpr int R = 4;  // 128-row stripes keep the band overhead small
+    constexpr int kRounds = 3;
+    int rc;
+    std::vector<uint32_t> pending(ids), width(w0);
+    std::vector<int32_t> hs;
+    for (int round = 0; round < kRounds && !pending.empty(); ++round) {
+        // pairs whose band would cover most of the grid go straight to full
+        std::vector<BatchTask> tasks;
+        std::vector<uint32_t> tw;  // width used per task
+        std::vector<uint32_t> next;
+        for (size_t q = 0; q < pending.size(); ++q) {
+            const uint32_t id = pending[q];
+            BatchTask t{};
+            t.a_off = a_off[id];
+            t.b_off = b_off[id];
+            t.m = a_len[id];
+            t.n = b_len[id];
+            t.out0 = id;
+            t.out1 = ~0u;
+            const uint32_t w = width[q] << round;
+            if (t.m == 0 || t.n == 0) {
+                rest.push_back(id);
+                continue;
+            }
+            band_task(t, R, w);
+            if (band_cells(t, R) * 10 >= full_cells(t, R) * 6) {
+                rest.push_back(id);
+                continue;
+            }
+            tasks.push_back(t);
+            tw.push_back(width[q]);
+        }
+        if (tasks.empty()) break;
+        ctx->band_stats[0] += round == 0 ? tasks.size() : 0;
+        // waves bounded by pointer memory (score-only: one wave)
+        const uint64_t wave_budget = (ctx->budget - std::min(ctx->budget, ctx->used)) / 2;
+        size_t k0 = 0;
+        while (k0 < tasks.size()) {
+            std::vector<BatchTask> wave;
+            uint64_t words = 0, mvbytes = 0;
+            uint32_t max_n = 1;
+            size_t k = k0;
+            for (; k < tasks.size(); ++k) {
+                BatchTask t = tasks[k];
+                if (want) {
+                    const uint32_t SH = 32u * R;
+                    t.ncg = ptr_words_per_lane_row(t.period, R);
+                    const uint64_t wds = (uint64_t)((t.m + SH - 1) / SH) * 32u * t.ncg;
+                    if (!wave.empty() && (words + wds) * 4 > wave_budget) break;
+                    t.ptr_off = words;
+                    words += wds;
+                    mvbytes += (uint64_t)t.m + t.n + 16;
+                }
+                max_n = std::max(max_n, t.n);
+                ctx->band_stats[6] += band_cells(t, R);
+                wave.push_back(t);
+            }
+            void *pv = nullptr, *mv = nullptr, *nm = nullptr;
+            if (want) {
+                if ((rc = scratch(ctx, "band_ptr", words * 4 + 16, &pv))) return rc;
+                if ((rc = scratch(ctx, "band_moves", mvbytes + 16, &mv))) return rc;
+                if ((rc = scratch(ctx, "band_nmoves", wave.size() * 8 + 16, &nm))) return rc;
+            }
+            std::vector<BatchTask> fill = wave;
+            sort_lpt(fill);
+            BatchTask *dt = nullptr;
+            if ((rc = upload(ctx, "band_tasks", fill, &dt))) return rc;
+            BatchArgs ba{};
+            ba.pool = pool;
+            for (int c = 0; c < 4; ++c) ba.prof[c] = pf.prof[c];
+            ba.gap = pf.gap;
+            ba.scores = scores;
+            ba.err = ctx->d_err;
+            ba.tasks = dt;
+            ba.ntasks = (uint32_t)fill.size();
+            ba.ptr = (uint32_t *)pv;
+            if ((rc = launch_batch(ctx, R, want, ba, max_n, true))) return rc;
+            // certificate on the banded scores
+            hs.resize(wave.size());
+            for (size_t q = 0; q < wave.size(); ++q) {
+                cudaError_t e = cudaMemcpyAsync(&hs[q], scores + wave[q].out0, 4, cudaMemcpyDeviceToHost, ctx->stream);
+                if (e != cudaSuccess) return cuda_fail(ctx, e, "banded score D2H");
+            }
+            if ((rc = nw_ctx_sync(ctx))) return rc;
+            std::vector<TraceTask> tt;
+            for (size_t q = 0; q < wave.size(); ++q) {
+                const BatchTask &t = wave[q];
+                const uint32_t w = tw[k0 + q] << round;
+                int64_t U = 0;
+                const bool can_leave = band_exit_bound(t.m, t.n, w, sc.match, sc.gap, &U);
+                // score: S_b >= U suffices; the alignment needs S_b > U (a
+                // tie outside the band could win the diagonal-first order)
+                const bool ok = !can_leave || (want ? (int64_t)hs[q] > U : (int64_t)hs[q] >= U);
+                if (!ok) {
+                    next.push_back(t.out0);
+                    continue;
+                }
+                ctx->band_stats[1 + round] += 1;
+                if (want) {
+                    const uint32_t id = t.out0;
+                    tt.push_back(TraceTask{(const uint32_t *)pv + t.ptr_off, t.ncg, t.m, t.n,
+                                           (uint8_t *)mv + 0, (uint64_t *)nm + tt.size(), pool + t.a_off,
+                                           pool + t.b_off, cigar_pool + cigar_off[id], cigar_len + id, t.lo});
+                }
+            }
+            if (want && !tt.empty()) {
+                uint64_t mpos = 0;
+                for (auto &x : tt) {
+                    x.moves = (uint8_t *)mv + mpos;
+                    mpos += (uint64_t)x.m + x.n + 16;
+                }
+                TraceTask *dtt = nullptr;
+                if ((rc = upload(ctx, "band_trace_tasks", tt, &dtt))) return rc;
+                if ((rc = launch_trace(ctx, R, tt[0], dtt, (uint32_t)tt.size(), (flags & NW_CIGAR_M) ? 1u : 0u)))
+                    return rc;
+            }
+            k0 = k;
+        }
+        // widen: pairs rejected this round keep their starting width
+        std::vector<uint32_t> nw_width;
+        for (uint32_t id : next)
+            for (size_t q = 0; q < pending.size(); ++q)
+                if (pending[q] == id) {
+                    nw_width.push_back(width[q]);
+                    break;
+                }
+        if (round + 1 < kRounds) {
+            pending.swap(next);
+            width.swap(nw_width);
+        } else {
+            for (uint32_t id : next) rest.push_back(id);
+            pending.clear();
+        }
+    }
+    for (uint32_t id : pending) rest.push_back(id);
+    return NW_OK;
+}
+
+// One banded round with the given half-widths, banded scores as they are
+// (the inspection mode NW_BAND_RAW).
+static int band_raw(nw_ctx *ctx, const uint8_t *pool, const uint64_t *a_off, const uint32_t *a_len,
+                    const uint64_t *b_off, const uint32_t *b_len, uint32_t npairs, const uint32_t *w,
+                    const nw_scoring &sc, int32_t *scores) {
+    const Profile pf = make_profile(sc);
+    constexpr int R = 4;
+    std::vector<BatchTask> tasks;
+    uint32_t max_n = 1;
+    for (uint32_t k = 0; k < npairs; ++k) {
+        BatchTask t{};
+        t.a_off = a_off[k];
+        t.b_off = b_off[k];
+        t.m = a_len[k];
+        t.n = b_len[k];
+        t.out0 = k;
+        t.out1 = ~0u;
+        band_task(t, R, std::max<uint32_t>(w[k], 0));
+        max_n = std::max(max_n, t.n);
+        tasks.push_back(t);
+    }
+    sort_lpt(tasks);
+    BatchTask *dt = nullptr;
+    int rc = upload(ctx, "band_tasks", tasks, &dt);
+    if (rc) return rc;
+    BatchArgs ba{};
+    ba.pool = pool;
+    for (int c = 0; c < 4; ++c) ba.prof[c] = pf.prof[c];
+    ba.gap = pf.gap;
+    ba.scores = scores;
+    ba.err = ctx->d_err;
+    ba.tasks = dt;
+    ba.ntasks = npairs;
+    return launch_batch(ctx, R, false, ba, max_n, true);
+}
+
+// Certified band for every pair with the given starting half-widths, then
+// the full kernel for whatever no band certified.
+static int band_batch(nw_ctx *ctx, const uint8_t *pool, const uint64_t *a_off, const uint32_t *a_len,
+                      const uint64_t *b_off, const uint32_t *b_len, uint32_t npairs, const uint32_t *w0,
+                      const nw_scoring &sc, uint32_t flags, int32_t *scores, char *cigar_pool,
+                      const uint64_t *cigar_off, uint64_t *cigar_len) {
+    std::vector<uint32_t> ids(npairs), width(npairs), rest;
+    for (uint32_t k = 0; k < npairs; ++k) {
+        ids[k] = k;
+        width[k] = std::max<uint32_t>(w0[k], 1);
+        const BatchTask t{a_off[k], b_off[k], a_len[k], b_len[k]};
+        ctx->band_stats[7] += full_cells(t, 4);
+    }
+    int rc = band_rounds(ctx, pool, a_off, a_len, b_off, b_len, ids, width, sc, flags, scores, cigar_pool, cigar_off,
+                         cigar_len, rest);
+    if (rc || rest.empty()) return rc;
+    ctx->band_stats[5] += rest.size();
+    return batch_device_impl(ctx, pool, a_off, a_len, b_off, b_len, rest.data(), (uint32_t)rest.size(), sc, flags,
+                             scores, cigar_pool, cigar_off, cigar_len);
+    return NW_OK;
+}
+
 // Score-only or CIGAR batch on device buffers (the C entry point stages
 // host buffers around this).
-static int batch_device(nw_ctx *ctx, const uint8_t *pool, const uint64_t *a_off, const uint32_t *a_len,
-                        const uint64_t *b_off, const uint32_t *b_len, uint32_t npairs, const nw_scoring &sc,
-                        uint32_t flags, int32_t *scores, char *cigar_pool, const uint64_t *cigar_off,
-                        uint64_t *cigar_len) {
+int batch_device_impl(nw_ctx *ctx, const uint8_t *pool, const uint64_t *a_off, const uint32_t *a_len,
+                      const uint64_t *b_off, const uint32_t *b_len, const uint32_t *ids, uint32_t npairs,
+                      const nw_scoring &sc, uint32_t flags, int32_t *scores, char *cigar_pool,
+                      const uint64_t *cigar_off, uint64_t *cigar_len) {
     const Profile pf = make_profile(sc);
     const bool want = flags & NW_CIGAR;
     int rc;
     std::vector<BatchTask> tasks(npairs);
     uint32_t max_n = 1;
-    for (uint32_t k = 0; k < npairs; ++k) {
+    for (uint32_t q = 0; q < npairs; ++q) {
+        const uint32_t k = ids ? ids[q] : q;
         if ((rc = check_len(ctx, sc, a_len[k], b_len[k]))) return rc;
         if (want && cigar_off[k + 1] - cigar_off[k] < nw_cigar_bound(a_len[k], b_len[k]))
             return fail(ctx, NW_ERR_ARG, "CIGAR capacity of pair %u below its bound", k);
@@ -332,7 +632,7 @@ static int batch_device(nw_ctx *ctx, const uint8_t *pool, const uint64_t *a_off,
         t.out0 = k;
         t.out1 = ~0u;
         max_n = std::max(max_n, t.n);
-        tasks[k] = t;
+        tasks[q] = t;
     }
     const int R = pick_rows(tasks);
     BatchArgs ba{};
@@ -354,15 +654,15 @@ static int batch_device(nw_ctx *ctx, const uint8_t *pool, const uint64_t *a_off,
     // even that does not fit)
     const uint64_t wave_budget = (ctx->budget - std::min(ctx->budget, ctx->used)) / 2;
     std::vector<uint32_t> order(npairs);
-    std::iota(order.begin(), order.end(), 0u);
+    std::iota(order.begin(), order.end(), 0u);  // positions in `tasks`
     size_t k0 = 0;
     while (k0 < npairs) {
         std::vector<BatchTask> wave;
-        std::vector<uint32_t> ids;
+        std::vector<uint32_t> ids_w;
         uint64_t words = 0, mvbytes = 0;
         size_t k = k0;
         for (; k < npairs; ++k) {
-            BatchTask t = tasks[order[k]];
+            BatchTask t = tasks[order[k]];  // t.out0 is the caller's pair id
             const uint32_t SH = 32u * R;
             t.ncg = ptr_words_per_lane_row(std::max(t.n, 1u), R);
             const uint64_t w = (uint64_t)((t.m + SH - 1) / SH) * 32u * t.ncg;
@@ -371,7 +671,7 @@ static int batch_device(nw_ctx *ctx, const uint8_t *pool, const uint64_t *a_off,
             words += w;
             mvbytes += (uint64_t)t.m + t.n + 16;
             wave.push_back(t);
-            ids.push_back(order[k]);
+            ids_w.push_back(t.out0);
         }
         void *pv = nullptr, *mv = nullptr, *nm = nullptr;
         if ((rc = scratch(ctx, "batch_ptr", words * 4 + 16, &pv))) return rc;
@@ -381,10 +681,10 @@ static int batch_device(nw_ctx *ctx, const uint8_t *pool, const uint64_t *a_off,
         uint64_t mpos = 0;
         for (size_t q = 0; q < wave.size(); ++q) {
             const BatchTask &t = wave[q];
-            const uint32_t id = ids[q];
+            const uint32_t id = ids_w[q];
             tt[q] = TraceTask{(const uint32_t *)pv + t.ptr_off, t.ncg, t.m, t.n, (uint8_t *)mv + mpos,
                               (uint64_t *)nm + q, pool + t.a_off, pool + t.b_off, cigar_pool + cigar_off[id],
-                              cigar_len + id};
+                              cigar_len + id, kNoBand};
             mpos += (uint64_t)t.m + t.n + 16;
         }
         // order the fill by cell count; ptr_off stays attached to each task
@@ -406,21 +706,14 @@ static int batch_device(nw_ctx *ctx, const uint8_t *pool, const uint64_t *a_off,
     return NW_OK;
 }
 
-extern "C" int nw_align_batch(nw_ctx *ctx, const uint8_t *pool2b, const uint64_t *a_off, const uint32_t *a_len,
-                              const uint64_t *b_off, const uint32_t *b_len, uint32_t npairs, nw_scoring sc,
-                              uint32_t flags, int32_t *scores, char *cigar_pool, const uint64_t *cigar_off,
-                              uint64_t *cigar_len) {
-    int rc = check_common(ctx, sc);
-    if (rc) return rc;
-    if (npairs == 0) return NW_OK;
-    if (!a_off || !a_len || !b_off || !b_len || !scores || !pool2b) return fail(ctx, NW_ERR_ARG, "null argument");
+// Host-I/O staging shared by the batch entry points: copy the pool in, run
+// `body` on device buffers, copy scores (and CIGARs) out, wait.
+template <typename F>
+static int with_host_io(nw_ctx *ctx, const uint8_t *pool2b, const uint64_t *a_off, const uint32_t *a_len,
+                        const uint64_t *b_off, const uint32_t *b_len, uint32_t npairs, uint32_t flags,
+                        int32_t *scores, char *cigar_pool, const uint64_t *cigar_off, uint64_t *cigar_len, F body) {
     const bool want = flags & NW_CIGAR;
-    if (want && (!cigar_pool || !cigar_off || !cigar_len)) return fail(ctx, NW_ERR_ARG, "CIGAR buffers are null");
-    if (flags & NW_LEARNED_BAND) return fail(ctx, NW_ERR_UNSUPPORTED, "learned band is not built yet");
-    if (!(flags & NW_HOST_IO))
-        return batch_device(ctx, pool2b, a_off, a_len, b_off, b_len, npairs, sc, flags, scores, cigar_pool,
-                            cigar_off, cigar_len);
-    // host buffers: the pool spans up to the furthest sequence end
+    int rc;
     uint64_t pool_bytes = 16;
     for (uint32_t k = 0; k < npairs; ++k) {
         pool_bytes = std::max<uint64_t>(pool_bytes, a_off[k] + (a_len[k] + 3) / 4);
@@ -433,8 +726,7 @@ extern "C" int nw_align_batch(nw_ctx *ctx, const uint8_t *pool2b, const uint64_t
         if ((rc = scratch(ctx, "hio_cigar", cigar_off[npairs] + 16, &dcig))) return rc;
         if ((rc = scratch(ctx, "hio_cigar_len", (size_t)npairs * 8, &dlen))) return rc;
     }
-    rc = batch_device(ctx, (const uint8_t *)dpool, a_off, a_len, b_off, b_len, npairs, sc, flags & ~NW_HOST_IO,
-                      (int32_t *)dsc, (char *)dcig, cigar_off, (uint64_t *)dlen);
+    rc = body((const uint8_t *)dpool, (int32_t *)dsc, (char *)dcig, (uint64_t *)dlen);
     if (rc) return rc;
     cudaMemcpyAsync(scores, dsc, (size_t)npairs * 4, cudaMemcpyDeviceToHost, ctx->stream);
     if (want) {
@@ -442,6 +734,75 @@ extern "C" int nw_align_batch(nw_ctx *ctx, const uint8_t *pool2b, const uint64_t
         cudaMemcpyAsync(cigar_pool, dcig, cigar_off[npairs], cudaMemcpyDeviceToHost, ctx->stream);
     }
     return nw_ctx_sync(ctx);
+}
+
+static int check_batch_args(nw_ctx *ctx, const nw_scoring &sc, const uint8_t *pool2b, const uint64_t *a_off,
+                            const uint32_t *a_len, const uint64_t *b_off, const uint32_t *b_len, uint32_t flags,
+                            int32_t *scores, char *cigar_pool, const uint64_t *cigar_off, uint64_t *cigar_len) {
+    int rc = check_common(ctx, sc);
+    if (rc) return rc;
+    if (!a_off || !a_len || !b_off || !b_len || !scores || !pool2b) return fail(ctx, NW_ERR_ARG, "null argument");
+    if ((flags & NW_CIGAR) && (!cigar_pool || !cigar_off || !cigar_len))
+        return fail(ctx, NW_ERR_ARG, "CIGAR buffers are null");
+    return NW_OK;
+}
+
+int learned_band_widths(nw_ctx *ctx, const uint8_t *pool, const uint64_t *a_off, const uint32_t *a_len,
+                        const uint64_t *b_off, const uint32_t *b_len, uint32_t npairs, std::vector<uint32_t> &w);
+
+extern "C" int nw_align_batch(nw_ctx *ctx, const uint8_t *pool2b, const uint64_t *a_off, const uint32_t *a_len,
+                              const uint64_t *b_off, const uint32_t *b_len, uint32_t npairs, nw_scoring sc,
+                              uint32_t flags, int32_t *scores, char *cigar_pool, const uint64_t *cigar_off,
+                              uint64_t *cigar_len) {
+    if (!ctx) return NW_ERR_ARG;
+    if (npairs == 0) return check_common(ctx, sc);
+    int rc = check_batch_args(ctx, sc, pool2b, a_off, a_len, b_off, b_len, flags, scores, cigar_pool, cigar_off,
+                              cigar_len);
+    if (rc) return rc;
+    auto body = [&](const uint8_t *pool, int32_t *sc_out, char *cig, uint64_t *clen) -> int {
+        const uint32_t fl = flags & ~NW_HOST_IO;
+        if (!(flags & NW_LEARNED_BAND))
+            return batch_device_impl(ctx, pool, a_off, a_len, b_off, b_len, nullptr, npairs, sc, fl, sc_out, cig,
+                                     cigar_off, clen);
+        std::vector<uint32_t> w;
+        int r = learned_band_widths(ctx, pool, a_off, a_len, b_off, b_len, npairs, w);
+        if (r) return r;
+        return band_batch(ctx, pool, a_off, a_len, b_off, b_len, npairs, w.data(), sc, fl, sc_out, cig, cigar_off,
+                          clen);
+    };
+    if (!(flags & NW_HOST_IO)) return body(pool2b, scores, cigar_pool, cigar_len);
+    return with_host_io(ctx, pool2b, a_off, a_len, b_off, b_len, npairs, flags, scores, cigar_pool, cigar_off,
+                        cigar_len, body);
+}
+
+extern "C" int nw_align_batch_banded(nw_ctx *ctx, const uint8_t *pool2b, const uint64_t *a_off,
+                                     const uint32_t *a_len, const uint64_t *b_off, const uint32_t *b_len,
+                                     uint32_t npairs, const uint32_t *band_w, nw_scoring sc, uint32_t flags,
+                                     int32_t *scores, char *cigar_pool, const uint64_t *cigar_off,
+                                     uint64_t *cigar_len) {
+    if (!ctx) return NW_ERR_ARG;
+    if (npairs == 0) return check_common(ctx, sc);
+    int rc = check_batch_args(ctx, sc, pool2b, a_off, a_len, b_off, b_len, flags, scores, cigar_pool, cigar_off,
+                              cigar_len);
+    if (rc) return rc;
+    if (!band_w) return fail(ctx, NW_ERR_ARG, "band widths are null");
+    for (uint32_t k = 0; k < npairs; ++k)
+        if ((rc = check_len(ctx, sc, a_len[k], b_len[k]))) return rc;
+    if ((flags & NW_BAND_RAW) && (flags & NW_CIGAR)) return fail(ctx, NW_ERR_ARG, "NW_BAND_RAW is score only");
+    auto body = [&](const uint8_t *pool, int32_t *sc_out, char *cig, uint64_t *clen) -> int {
+        if (flags & NW_BAND_RAW) return band_raw(ctx, pool, a_off, a_len, b_off, b_len, npairs, band_w, sc, sc_out);
+        return band_batch(ctx, pool, a_off, a_len, b_off, b_len, npairs, band_w, sc, flags & ~NW_HOST_IO, sc_out, cig,
+                          cigar_off, clen);
+    };
+    if (!(flags & NW_HOST_IO)) return body(pool2b, scores, cigar_pool, cigar_len);
+    return with_host_io(ctx, pool2b, a_off, a_len, b_off, b_len, npairs, flags, scores, cigar_pool, cigar_off,
+                        cigar_len, body);
+}
+
+extern "C" int nw_ctx_band_stats(nw_ctx *ctx, uint64_t *out, int cap) {
+    if (!ctx) return -NW_ERR_ARG;
+    for (int k = 0; k < cap && k < 8; ++k) out[k] = ctx->band_stats[k];
+    return 8;
 }
 
 extern "C" int nw_score_all_pairs(nw_ctx *ctx, const uint8_t *pool2b, const uint64_t *off, const uint32_t *len,

@@ -121,6 +121,12 @@ struct nw_ctx {
     bool profiling = false;
     std::map<std::string, nw::KernelStat> stats;
     std::vector<cudaEvent_t> event_pool;
+    // certified-band statistics: [0] pairs tried banded, [1..4] accepted in
+    // round 0..3, [5] sent to the full kernel, [6] banded cells computed,
+    // [7] full-grid cells of all pairs
+    uint64_t band_stats[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+    // learned band model (device parameters, see nw_mlp.cu)
+    void *band_model = nullptr;
     // host staging for NW_HOST_IO (pinned, grown on demand)
     void *pinned = nullptr;
     size_t pinned_cap = 0;
@@ -175,7 +181,10 @@ struct TraceTask {
     const uint8_t *a, *b;  // packed sequences
     char *cigar;           // output
     uint64_t *cigar_len;   // output
+    int32_t band_lo;       // banded layout: stripe s keeps columns from max(0, s*32R + band_lo);
+                           // kNoBand for the full layout
 };
+constexpr int32_t kNoBand = INT32_MIN;
 // Launch traceback + finish for one task (by value, many == nullptr) or for
 // `ntasks` tasks in a device array.
 int launch_trace(nw_ctx *ctx, int R, const TraceTask &one, const TraceTask *many, uint32_t ntasks, uint32_t mflag);
@@ -187,4 +196,5 @@ cudaError_t fill_score_with_scratch(const uint8_t *a2b, uint32_t m, const uint8_
                                     uint32_t *err, cudaStream_t stream, int sm_count);
 int launch_pair_fill(nw_ctx *ctx, int R, bool ptr, const uint8_t *a2b, uint32_t m, const uint8_t *b2b, uint32_t n,
                      const Profile &pf, int32_t *score, uint32_t *ptr_words, uint32_t ncg, int nw);
+void free_band_model(nw_ctx *ctx);
 }

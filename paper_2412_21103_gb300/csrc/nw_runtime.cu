@@ -201,6 +201,7 @@ void nw_ctx_destroy(nw_ctx *ctx) {
             cudaEventDestroy(pr.second);
         }
     for (auto e : ctx->event_pool) cudaEventDestroy(e);
+    free_band_model(ctx);
     if (ctx->d_err) cudaFree(ctx->d_err);
     if (ctx->pinned) cudaFreeHost(ctx->pinned);
     delete ctx;

@@ -217,7 +217,7 @@ static int run_pair(nw_ctx *ctx, const uint8_t *a2b, uint32_t m, const uint8_t *
     void *mv = nullptr, *nm = nullptr;
     if ((rc = scratch(ctx, "moves", (size_t)m + n + 16, &mv))) return rc;
     if ((rc = scratch(ctx, "nmoves", 16, &nm))) return rc;
-    TraceTask tt{ptr, ncg, m, n, (uint8_t *)mv, (uint64_t *)nm, a2b, b2b, cigar, cigar_len};
+    TraceTask tt{ptr, ncg, m, n, (uint8_t *)mv, (uint64_t *)nm, a2b, b2b, cigar, cigar_len, kNoBand};
     return launch_trace(ctx, R, tt, nullptr, 1, (flags & NW_CIGAR_M) ? 1u : 0u);
 }
 

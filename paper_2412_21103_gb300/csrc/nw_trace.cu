@@ -22,9 +22,15 @@ __global__ void __launch_bounds__(32) k_traceback(TraceTask one, const TraceTask
     uint32_t i = p.m, j = p.n;
     uint64_t k = 0;
     uint32_t cs = 0xffffffffu, ckt = 0, cct = 0;
+    // first stored column of stripe s (banded layout) or 0
+    auto cbeg = [&](uint32_t s) -> uint32_t {
+        if (p.band_lo == kNoBand) return 0u;
+        const int64_t v = (int64_t)s * SH + p.band_lo;
+        return v > 0 ? (uint32_t)v : 0u;
+    };
     while (i > 0 && j > 0) {
         const uint32_t i1 = i - 1, j1 = j - 1;
-        const uint32_t s = i1 / SH, kt = ((i1 % SH) / R) / kTileLanes, ct = (j1 / CPW) / kTileWords;
+        const uint32_t s = i1 / SH, kt = ((i1 % SH) / R) / kTileLanes, ct = ((j1 - cbeg(s)) / CPW) / kTileWords;
         if (s != cs || kt != ckt || ct != cct) {
             __syncwarp();
             const uint32_t rl = lane >> 2, part = lane & 3u;
@@ -40,12 +46,15 @@ __global__ void __launch_bounds__(32) k_traceback(TraceTask one, const TraceTask
             cct = ct;
         }
         if (lane == 0) {
+            const uint32_t cb = cbeg(cs);
             while (i > 0 && j > 0) {
                 const uint32_t a1 = i - 1, b1 = j - 1;
-                const uint32_t kk = (a1 % SH) / R, cg = b1 / CPW;
-                if (a1 / SH != cs || kk / kTileLanes != ckt || cg / kTileWords != cct) break;
+                const uint32_t kk = (a1 % SH) / R;
+                if (a1 / SH != cs || b1 < cb) break;
+                const uint32_t cg = (b1 - cb) / CPW;
+                if (kk / kTileLanes != ckt || cg / kTileWords != cct) break;
                 const uint32_t word = tile[(kk - ckt * kTileLanes) * kTileWords + (cg - cct * kTileWords)];
-                const uint32_t code = (word >> (2u * ((b1 % CPW) * R + (a1 % R)))) & 3u;
+                const uint32_t code = (word >> (2u * (((b1 - cb) % CPW) * R + (a1 % R)))) & 3u;
                 const uint32_t mv = (code & 1u) ? 0u : ((code & 2u) ? 1u : 2u);
                 p.moves[k++] = (uint8_t)mv;
                 i -= (mv != 2u);

@@ -201,3 +201,59 @@ def test_rle_roundtrip():
     for ops in ["", "=", "==X", "IIDD=X", "X" * 17]:
         assert parse_cigar(oracle.rle(ops)) == ops
     assert ascii_of(codes("GATTACA")) == "GATTACA"
+
+
+@pytest.mark.parametrize("seed", range(40))
+def test_exit_bound_brute_force(seed):
+    """U0 bounds every band-leaving path and is attained when a path with
+    the minimal gap count exists with all-match diagonals (A == B here for
+    the attainment check is not required: only the bound is asserted, plus
+    None exactly when no path leaves the band)."""
+    rs = seqgen.Stream(900 + seed)
+    m, n = (int(x) for x in rs.integers(0, 6, 2))
+    a, b = rs.bases(m), rs.bases(n)
+    ma, mm, g = [(1, -1, -1), (2, -1, -2), (3, 1, -1), (0, -1, -1)][seed % 4]
+    w = int(rs.integers(0, 3, 1)[0])
+    lo, hi = oracle.band_limits(m, n, w)
+
+    def leaves(path):
+        i = j = 0
+        for mv in path:
+            i += mv in "du"
+            j += mv in "dl"
+            if not (lo <= j - i <= hi):
+                return True
+        return False
+    out = [path_score(p, a, b, ma, mm, g) for p in all_paths(m, n) if leaves(p)]
+    U0 = oracle.exit_bound(m, n, w, ma, g)
+    if not out:
+        assert U0 is None
+    else:
+        assert U0 is not None and U0 >= max(out)
+    # certificate soundness: S_b > U0 implies the banded score is the full one
+    sb, _ = oracle.banded(a, b, w, ma, mm, g)
+    if U0 is None or sb > U0:
+        assert sb == oracle.score(a, b, ma, mm, g)
+
+
+def test_exit_bound_is_attained_by_identical_sequences():
+    """With A == B (all diagonals match) the best band-leaving path makes
+    exactly the minimal number of gap moves, so U0 is attained."""
+    for L in range(1, 7):
+        a = np.arange(L, dtype=np.uint8) % 4
+        for w in range(0, 3):
+            lo, hi = oracle.band_limits(L, L, w)
+
+            def leaves(path):
+                i = j = 0
+                for mv in path:
+                    i += mv in "du"
+                    j += mv in "dl"
+                    if not (lo <= j - i <= hi):
+                        return True
+                return False
+            out = [path_score(p, a, a, 1, -1, -1) for p in all_paths(L, L) if leaves(p)]
+            U0 = oracle.exit_bound(L, L, w, 1, -1)
+            assert (U0 is None) == (not out)
+            if out:
+                assert U0 == max(out)
