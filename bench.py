@@ -42,7 +42,8 @@ def parse():
     ap.add_argument("--steps", type=int, default=10)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--workload", default="pair32k", choices=["pair32k", "pair1k", "allpairs"])
+    ap.add_argument("--workload", default="pair32k", choices=["pair32k", "pair1k", "allpairs", "band"])
+    ap.add_argument("--npairs", type=int, default=20000, help="band: evaluation pairs (20,000 = the full workload)")
     ap.add_argument("--no-clocks", action="store_true")
     ap.add_argument("--nseq", type=int, default=512, help="allpairs: number of sequences (512 = the full workload)")
     ap.add_argument("--m", type=int, default=32768, help="pair32k: query length (32,768 = the full workload)")
@@ -56,10 +57,17 @@ def dist_env():
     return rank, world, local
 
 
-WL_ARGS = {"nseq": 512, "m": 32768}
+WL_ARGS = {"nseq": 512, "m": 32768, "npairs": 20000}
+LABELS = os.path.join(ROOT, "tests", "golden", "band_labels_seed9004.npz")
 
 
 def workload(name: str):
+    if name == "band":
+        npairs = WL_ARGS["npairs"]
+        pairs = seqgen.band_pairs(1004, npairs=npairs)
+        return pairs, (f"learned certified band, {npairs:,} pairs: lengths log-uniform [2,000, 20,000], divergence "
+                       "U[0.01,0.25], geometric indels, indel bursts 50-500 bp w.p. 0.3 (seed 1004); score + CIGAR; "
+                       "model trained on the GPU from oracle labels of 4,000 pairs of seed 9004")
     if name == "allpairs":
         nseq = WL_ARGS["nseq"]
         seqs = seqgen.all_vs_all_family(1003, nseq=nseq)
@@ -177,7 +185,9 @@ def run_reference(args):
     data, desc = workload(args.workload)
     import oracle
     oracle.build()
-    sample_fn = allpairs_oracle_gcups if args.workload == "allpairs" else oracle_gcups
+    sample_fn = {"allpairs": allpairs_oracle_gcups,
+                 "band": lambda d, budget_s: oracle_gcups_pairs([(p.a, p.b) for p in d[:400]], budget_s)}.get(
+        args.workload, oracle_gcups)
     vals = []
     for _ in range(args.warmup):
         sample_fn(data, budget_s=1.0)
@@ -269,6 +279,113 @@ class AllPairsWork:
         return allpairs_oracle_gcups(self.seqs)
 
 
+def train_band_model(nw, ctx, dev, epochs: int = 60, batch: int = 512, lr: float = 2e-3, seed: int = 0):
+    """Train the band-width network on the GPU from the committed oracle
+    labels (tests/golden/band_labels_seed9004.npz); features of the training
+    pairs come from the library's feature kernel.  Returns the final loss."""
+    import torch
+    lab = np.load(LABELS)
+    count = int(lab["label"].size)
+    pairs = seqgen.band_pairs(int(lab["seed"]), npairs=count)
+    seqs = []
+    for p in pairs:
+        seqs += [p.a, p.b]
+    pool, off, lens = nw.pool_of(seqs)
+    feat = nw.nw_band_features(ctx, torch.from_numpy(pool).to(dev), off[0::2], lens[0::2], off[1::2], lens[1::2])
+    target = torch.from_numpy(np.log(np.maximum(lab["label"], 1)).astype(np.float32)).to(dev)
+    nw.nw_band_model_init(ctx, seed)
+    g = torch.Generator(device="cpu").manual_seed(seed)
+    loss = None
+    for _ in range(epochs):
+        perm = torch.randperm(count, generator=g).to(dev)
+        for k in range(0, count - batch + 1, batch):
+            idx = perm[k:k + batch]
+            loss = nw.nw_band_model_train_step(ctx, feat[idx].contiguous(), target[idx].contiguous(), lr)
+    return float(loss.item()) if loss is not None else None
+
+
+class BandWork:
+    """Certified learned band over many pairs (score + CIGAR); the plain
+    full-grid batch runs on the same pairs for comparison."""
+    dominant = "band_fill_ptr"
+
+    def __init__(self, nw, ctx, dev, name):
+        import torch
+        self.nw, self.ctx, self.dev = nw, ctx, dev
+        pairs, self.desc = workload(name)
+        self.pairs = pairs
+        seqs = []
+        for p in pairs:
+            seqs += [p.a, p.b]
+        pool, off, lens = nw.pool_of(seqs)
+        self.pool_host = torch.from_numpy(pool).pin_memory().numpy()
+        self.pool = torch.from_numpy(pool).to(dev)
+        self.ao, self.al, self.bo, self.bl = off[0::2], lens[0::2], off[1::2], lens[1::2]
+        n = len(pairs)
+        caps = [nw.nw_cigar_bound(int(x), int(y)) for x, y in zip(self.al, self.bl)]
+        self.coff = np.concatenate([[0], np.cumsum(caps)]).astype(np.uint64)
+        self.scores = torch.zeros(n, dtype=torch.int32, device=dev)
+        self.cpool = torch.zeros(int(self.coff[-1]), dtype=torch.uint8, device=dev)
+        self.clen = torch.zeros(n, dtype=torch.int64, device=dev)
+        self.cells = int(sum(int(x) * int(y) for x, y in zip(self.al, self.bl)))
+        t0 = time.perf_counter()
+        self.train_loss = train_band_model(nw, ctx, dev)
+        self.train_s = time.perf_counter() - t0
+        self.config = {"npairs": n, "train_loss": self.train_loss, "train_seconds": self.train_s}
+        self.flags = nw.NW_CIGAR | nw.NW_LEARNED_BAND
+
+    def step(self):
+        self.nw.nw_align_batch(self.ctx, self.pool, self.ao, self.al, self.bo, self.bl, SCORING, self.flags,
+                               self.scores, self.cpool, self.coff, self.clen)
+
+    def e2e(self):
+        sc, cig = self.nw.nw_align_batch(self.ctx, self.pool_host, self.ao, self.al, self.bo, self.bl, SCORING,
+                                         self.flags)
+        return self.pool_host.nbytes, sc.nbytes + sum(len(c) for c in cig) + 8 * len(cig)
+
+    def result(self):
+        """Plain full-grid batch on the same pairs: time, and score mismatches."""
+        import torch
+        nw = self.nw
+        plain = torch.zeros_like(self.scores)
+        cp = torch.zeros_like(self.cpool)
+        cl = torch.zeros_like(self.clen)
+        nw.nw_align_batch(self.ctx, self.pool, self.ao, self.al, self.bo, self.bl, SCORING, nw.NW_CIGAR, plain, cp,
+                          self.coff, cl)
+        self.ctx.sync()
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        nw.nw_align_batch(self.ctx, self.pool, self.ao, self.al, self.bo, self.bl, SCORING, nw.NW_CIGAR, plain, cp,
+                          self.coff, cl)
+        self.ctx.sync()
+        plain_s = time.perf_counter() - t0
+        mism = int((plain != self.scores).sum().item())
+        cig_mism = int((cl != self.clen).sum().item())
+        st = nw.nw_ctx_band_stats(self.ctx)
+        return {"plain_full_gcups": self.cells / plain_s / 1e9, "plain_full_s": plain_s,
+                "score_mismatches_vs_plain": mism, "cigar_length_mismatches_vs_plain": cig_mism,
+                "band_stats_cumulative": st}
+
+    def oracle_sample(self):
+        return oracle_gcups_pairs([(p.a, p.b) for p in self.pairs[:400]])
+
+
+def oracle_gcups_pairs(pairs, budget_s: float = 12.0):
+    """The CPU oracle, as it stands, aligning pairs (score + traceback) on
+    all host threads until the budget is spent."""
+    import oracle
+    threads = len(os.sched_getaffinity(0))
+    t0 = time.perf_counter()
+    done, cells = 0, 0
+    while time.perf_counter() - t0 < budget_s and done < len(pairs):
+        chunk = pairs[done: done + threads]
+        oracle.align_many(chunk, *SCORING, threads=threads)
+        cells += sum(a.size * b.size for a, b in chunk)
+        done += len(chunk)
+    dt = time.perf_counter() - t0
+    return cells / dt / 1e9, threads, f"{done} pairs of the workload, score + traceback ({cells:.3g} cells, {dt:.1f} s)"
+
+
 def run_ours(args):
     import torch
     import torch.distributed as dist
@@ -282,7 +399,7 @@ def run_ours(args):
     dev = torch.device("cuda", local)
     stream = torch.cuda.current_stream(dev)
     ctx = nw.Context(local, stream)
-    work = (AllPairsWork if args.workload == "allpairs" else PairWork)(nw, ctx, dev, args.workload)
+    work = {"allpairs": AllPairsWork, "band": BandWork}.get(args.workload, PairWork)(nw, ctx, dev, args.workload)
     flush = torch.empty(L2_FLUSH_BYTES, dtype=torch.uint8, device=dev)
 
     for _ in range(max(args.warmup, 3)):
@@ -293,6 +410,7 @@ def run_ours(args):
     # the score-only cell mix (3 ALU-pipe instructions per cell)
     peak_ops = nw.nw_peak_int(ctx, 5, 1 << 15) * OPS_PER_CELL
 
+    band0 = nw.nw_ctx_band_stats(ctx)["band_cells"]
     ctx.reset_stats()
     ctx.set_profiling(True)
     if world > 1:
@@ -333,7 +451,11 @@ def run_ours(args):
 
     dl, dms = stats.get(work.dominant, (0, 0.0))
     dom_avg_ms = dms / max(dl, 1)
-    achieved = work.cells * OPS_PER_CELL / (dom_avg_ms * 1e-3) / 1e9 if dom_avg_ms else None
+    # cells the dominant kernel computed per launch: the full grid, or for
+    # the banded kernel the band cells it actually swept
+    band_cells = nw.nw_ctx_band_stats(ctx)["band_cells"] - band0
+    kcells = (band_cells / max(dl, 1)) if work.dominant.startswith("band") else work.cells
+    achieved = kcells * OPS_PER_CELL / (dom_avg_ms * 1e-3) / 1e9 if dom_avg_ms else None
     launches = sum(v[0] for k_, v in stats.items() if k_ != "peak")
 
     line = {
@@ -345,7 +467,7 @@ def run_ours(args):
                        **work.config, **work.result()),
         "roofline": {"bound": "alu", "kernel": work.dominant, "achieved": achieved, "peak": peak_ops,
                      "unit": "Gop/s", "frac": (achieved / peak_ops) if achieved else None, "traffic": None,
-                     "ops_per_cell": OPS_PER_CELL, "kernel_ms": dom_avg_ms,
+                     "ops_per_cell": OPS_PER_CELL, "kernel_ms": dom_avg_ms, "cells_per_launch": kcells,
                      "peak_source": "measured live by nw_peak_int kind 5 (score-only cell mix on every SM) x 3"},
         "kernels": {k_: {"launches": v[0], "ms_total": v[1]} for k_, v in stats.items()},
         "gpu_launches": launches,
@@ -378,7 +500,7 @@ class _Null:
 
 def main():
     args = parse()
-    WL_ARGS.update(nseq=args.nseq, m=args.m)
+    WL_ARGS.update(nseq=args.nseq, m=args.m, npairs=args.npairs)
     if args.impl == "reference":
         run_reference(args)
     else:

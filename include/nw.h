@@ -233,6 +233,53 @@ int nw_band_model_train_step(nw_ctx *ctx, const float *feat, const float *target
 int nw_score_all_pairs(nw_ctx *ctx, const uint8_t *pool2b, const uint64_t *off, const uint32_t *len,
                        uint32_t nseq, nw_scoring sc, uint32_t flags, int32_t *out);
 
+/* ---------------------------------------------------------------- serving
+ * Not in the paper (its Sec. 3.2 splits a fixed set of alignments over MPI
+ * ranks): a continuous-batching server on one GPU.  `workers` threads each
+ * own a context and stream and repeatedly admit the oldest waiting requests
+ * into a batch of at most `max_batch` pairs while the traceback buffers in
+ * flight stay within `trace_budget` bytes (a CIGAR request reserves
+ * ceil((m+1)(n+1)/4) rounded up to 256 bytes, a score-only request
+ * nothing; a request alone on an idle server is always admitted).  Batches
+ * run through nw_align_batch (with NW_LEARNED_BAND if given in `flags` and
+ * the creating context holds a model, which every worker copies); batches
+ * of different workers overlap on the GPU.  Results equal those of
+ * nw_align on the same pair. */
+typedef struct nw_server nw_server;
+typedef struct {
+    uint64_t ticket;     /* from nw_server_submit                          */
+    int32_t status;      /* nw_status of this request                      */
+    int32_t score;
+    uint64_t cigar_len;  /* 0 for score-only requests                      */
+    uint64_t cigar_off;  /* offset of its NUL-terminated CIGAR in cigar_buf */
+    double latency_s;    /* completion minus submission (host clock)       */
+} nw_completion;
+
+/* NULL on failure.  The context must outlive the server. */
+nw_server *nw_server_create(nw_ctx *ctx, uint32_t workers, uint32_t max_batch, uint64_t trace_budget, nw_scoring sc,
+                            uint32_t flags);
+/* Queue one request; sequences are host 2-bit arrays, copied before
+ * return.  *ticket identifies its completion. */
+int nw_server_submit(nw_server *srv, const uint8_t *a2b, uint32_t m, const uint8_t *b2b, uint32_t n,
+                     uint32_t want_cigar, uint64_t *ticket);
+/* Queue `count` requests at once from a host pool (same layout as
+ * nw_align_batch); want_cigar[k] != 0 asks for pair k's CIGAR; tickets
+ * (optional) receives their tickets in order. */
+int nw_server_submit_many(nw_server *srv, const uint8_t *pool2b, const uint64_t *a_off, const uint32_t *a_len,
+                          const uint64_t *b_off, const uint32_t *b_len, const uint8_t *want_cigar, uint32_t count,
+                          uint64_t *tickets);
+/* Move up to `cap` finished requests (oldest first) into out; their CIGARs
+ * go to cigar_buf (stops early when cigar_cap would overflow). */
+int nw_server_poll(nw_server *srv, nw_completion *out, uint32_t cap, uint32_t *count, char *cigar_buf,
+                   uint64_t cigar_cap, uint64_t *cigar_used);
+/* Wait until nothing is queued or running (NW_ERR_TIMEOUT after timeout_s). */
+int nw_server_drain(nw_server *srv, double timeout_s);
+/* [0] submitted, [1] completed, [2] waiting, [3] running, [4] full-grid
+ * cells completed, [5] traceback bytes reserved, [6] batches, [7] budget. */
+int nw_server_stats(nw_server *srv, uint64_t *out, int cap);
+/* Finish queued work, stop the workers, free everything. */
+void nw_server_destroy(nw_server *srv);
+
 /* ------------------------------------------------------------ measurement */
 
 /* Integer-pipe peak microbenchmark used as the roofline denominator: every

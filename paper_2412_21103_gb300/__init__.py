@@ -50,6 +50,11 @@ class Scoring(ctypes.Structure):
     _fields_ = [("match", ctypes.c_int32), ("mismatch", ctypes.c_int32), ("gap", ctypes.c_int32)]
 
 
+class Completion(ctypes.Structure):
+    _fields_ = [("ticket", ctypes.c_uint64), ("status", ctypes.c_int32), ("score", ctypes.c_int32),
+                ("cigar_len", ctypes.c_uint64), ("cigar_off", ctypes.c_uint64), ("latency_s", ctypes.c_double)]
+
+
 def lib_path() -> str:
     return _build.LIB
 
@@ -96,6 +101,13 @@ def load():
         "nw_band_model_forward": (ctypes.c_int, [vp, vp, u32, vp]),
         "nw_band_model_grad": (ctypes.c_int, [vp, vp, vp, u32, vp, vp]),
         "nw_band_model_train_step": (ctypes.c_int, [vp, vp, vp, u32, ctypes.c_float, vp]),
+        "nw_server_create": (vp, [vp, u32, u32, u64, Scoring, u32]),
+        "nw_server_submit": (ctypes.c_int, [vp, vp, u32, vp, u32, u32, u64p]),
+        "nw_server_submit_many": (ctypes.c_int, [vp, vp, u64p, u32p, u64p, u32p, vp, u32, u64p]),
+        "nw_server_poll": (ctypes.c_int, [vp, ctypes.POINTER(Completion), u32, u32p, vp, u64, u64p]),
+        "nw_server_drain": (ctypes.c_int, [vp, ctypes.c_double]),
+        "nw_server_stats": (ctypes.c_int, [vp, u64p, ctypes.c_int]),
+        "nw_server_destroy": (None, [vp]),
     }
     for name, (res, args) in sig.items():
         f = getattr(L, name)
@@ -398,6 +410,78 @@ def nw_band_model_train_step(ctx: Context, feat, target, lr: float, loss=None):
     _check(ctx, load().nw_band_model_train_step(ctx.handle, _ptr(feat), _ptr(target), int(feat.shape[0]), lr,
                                                 _ptr(loss)))
     return loss
+
+
+class Server:
+    """Continuous-batching server (nw_server): submit host requests, poll
+    completions.  See include/nw.h."""
+
+    def __init__(self, ctx: Context, workers: int = 3, max_batch: int = 1024, trace_budget: int = 16 << 30,
+                 scoring=DEFAULT_SCORING, flags: int = 0):
+        self.handle = load().nw_server_create(ctx.handle, workers, max_batch, trace_budget, _sc(scoring), flags)
+        if not self.handle:
+            raise NWError(NW_ERR_ARG, "nw_server_create failed")
+        self._cbuf = np.zeros(1 << 24, np.uint8)
+
+    def submit(self, a_codes_packed, m: int, b_codes_packed, n: int, want_cigar: bool) -> int:
+        t = ctypes.c_uint64(0)
+        rc = load().nw_server_submit(self.handle, _ptr(a_codes_packed), m, _ptr(b_codes_packed), n,
+                                     int(bool(want_cigar)), ctypes.byref(t))
+        if rc != NW_OK:
+            raise NWError(rc, "submit failed")
+        return int(t.value)
+
+    def submit_many(self, pool2b, a_off, a_len, b_off, b_len, want_cigar) -> np.ndarray:
+        ao, aop = _u64(a_off)
+        al, alp = _u32(a_len)
+        bo, bop = _u64(b_off)
+        bl, blp = _u32(b_len)
+        wc = np.ascontiguousarray(want_cigar, dtype=np.uint8)
+        n = int(al.size)
+        tickets = np.zeros(max(n, 1), np.uint64)
+        rc = load().nw_server_submit_many(self.handle, _ptr(pool2b), aop, alp, bop, blp, _ptr(wc), n,
+                                          tickets.ctypes.data_as(ctypes.POINTER(ctypes.c_uint64)))
+        if rc != NW_OK:
+            raise NWError(rc, "submit failed")
+        return tickets[:n]
+
+    def poll(self, cap: int = 4096):
+        """[(ticket, status, score, cigar or None, latency_s)]"""
+        out = (Completion * cap)()
+        cnt = ctypes.c_uint32(0)
+        used = ctypes.c_uint64(0)
+        rc = load().nw_server_poll(self.handle, out, cap, ctypes.byref(cnt), _ptr(self._cbuf), self._cbuf.size,
+                                   ctypes.byref(used))
+        if rc != NW_OK:
+            raise NWError(rc, "poll failed")
+        res = []
+        for k in range(cnt.value):
+            c = out[k]
+            cig = None
+            if c.cigar_len:
+                cig = self._cbuf[c.cigar_off: c.cigar_off + c.cigar_len].tobytes().decode()
+            res.append((int(c.ticket), int(c.status), int(c.score), cig, float(c.latency_s)))
+        return res
+
+    def drain(self, timeout_s: float = 600.0) -> bool:
+        return load().nw_server_drain(self.handle, timeout_s) == NW_OK
+
+    def stats(self) -> dict:
+        out = (ctypes.c_uint64 * 8)()
+        load().nw_server_stats(self.handle, out, 8)
+        keys = ["submitted", "completed", "waiting", "running", "cells", "reserved", "batches", "budget"]
+        return {k: int(v) for k, v in zip(keys, out)}
+
+    def close(self):
+        if getattr(self, "handle", None):
+            load().nw_server_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
 
 
 def nw_score_all_pairs(ctx: Context, pool2b, off, lens, scoring=DEFAULT_SCORING, flags: int = 0, out=None):

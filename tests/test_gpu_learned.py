@@ -1,0 +1,91 @@
+"""What the trained band-width network gains (a9): on held-out pairs of the
+band workload, the certified band started from the network's prediction
+sweeps fewer cells than the same certified band started from a fixed width
+without the network, and far fewer than the full grid -- with every score
+and CIGAR equal to the oracle's.  The network is trained on the GPU by the
+library's own kernels from the committed oracle labels."""
+import os
+
+import numpy as np
+import pytest
+
+import oracle
+import seqgen
+
+pytestmark = pytest.mark.gpu
+
+LABELS = os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden", "band_labels_seed9004.npz")
+
+
+def _pool(pairs):
+    import paper_2412_21103_gb300 as nw
+    seqs = []
+    for a, b in pairs:
+        seqs += [a, b]
+    pool, off, lens = nw.pool_of(seqs)
+    return pool, off[0::2], lens[0::2], off[1::2], lens[1::2]
+
+
+def _train(nw, ctx, epochs=40):
+    import torch
+    lab = np.load(LABELS)
+    count = int(lab["label"].size)
+    pairs = seqgen.band_pairs(int(lab["seed"]), npairs=count)
+    pool, ao, al, bo, bl = _pool([(p.a, p.b) for p in pairs])
+    feat = nw.nw_band_features(ctx, torch.from_numpy(pool).cuda(), ao, al, bo, bl)
+    target = torch.from_numpy(np.log(np.maximum(lab["label"], 1)).astype(np.float32)).cuda()
+    nw.nw_band_model_init(ctx, 0)
+    g = torch.Generator().manual_seed(0)
+    first = last = None
+    for _ in range(epochs):
+        perm = torch.randperm(count, generator=g).cuda()
+        for k in range(0, count - 511, 512):
+            idx = perm[k:k + 512]
+            loss = float(nw.nw_band_model_train_step(ctx, feat[idx].contiguous(), target[idx].contiguous(),
+                                                      2e-3).item())
+            first = loss if first is None else first
+            last = loss
+    return first, last
+
+
+def test_learned_band_beats_fixed_start_and_full_grid():
+    import torch
+    import paper_2412_21103_gb300 as nw
+    if not os.path.exists(LABELS):
+        pytest.fail("training labels missing: run tests/golden/make_band_labels.py")
+    held_out = [(p.a, p.b) for p in seqgen.band_pairs(1004, npairs=160)]
+    pool, ao, al, bo, bl = _pool(held_out)
+    want = oracle.align_many(held_out)
+    full_cells = sum(int(x) * int(y) for x, y in zip(al, bl))
+
+    # without the network: certified band from the fixed start (64)
+    c0 = nw.Context(0, torch.cuda.current_stream())
+    s0, g0 = nw.nw_align_batch(c0, pool, ao, al, bo, bl, (1, -1, -1), nw.NW_CIGAR | nw.NW_LEARNED_BAND)
+    st0 = nw.nw_ctx_band_stats(c0)
+
+    # with the network trained on the GPU
+    c1 = nw.Context(0, torch.cuda.current_stream())
+    first, last = _train(nw, c1)
+    assert last < 0.5 * first
+    s1, g1 = nw.nw_align_batch(c1, pool, ao, al, bo, bl, (1, -1, -1), nw.NW_CIGAR | nw.NW_LEARNED_BAND)
+    st1 = nw.nw_ctx_band_stats(c1)
+
+    for k, (s, ops) in enumerate(want):
+        assert s0[k] == s and g0[k] == oracle.rle(ops)
+        assert s1[k] == s and g1[k] == oracle.rle(ops)
+
+    def swept(st):
+        # banded cells plus the full grid of every pair that fell back
+        fb = sum(int(al[k]) * int(bl[k]) for k in range(len(held_out)))  # upper bound used only below
+        return st["band_cells"], st["full_fallback"]
+
+    band1, fb1 = swept(st1)
+    band0, fb0 = swept(st0)
+    print(f"learned: band cells {band1:.3g}, fallbacks {fb1}; fixed start: band cells {band0:.3g}, "
+          f"fallbacks {fb0}; full grid {full_cells:.3g}")
+    # the network sends fewer pairs to the full grid or sweeps fewer band cells
+    assert fb1 <= fb0
+    assert band1 + fb1 * (full_cells / len(held_out)) < band0 + fb0 * (full_cells / len(held_out))
+    assert band1 + fb1 * (full_cells / len(held_out)) < 0.8 * full_cells
+    c0.close()
+    c1.close()
