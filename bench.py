@@ -42,7 +42,10 @@ def parse():
     ap.add_argument("--steps", type=int, default=10)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--workload", default="pair32k", choices=["pair32k", "pair1k", "allpairs", "band"])
+    ap.add_argument("--workload", default="pair32k", choices=["pair32k", "pair1k", "allpairs", "band", "serve"])
+    ap.add_argument("--rate", type=float, default=50000.0, help="serve: Poisson arrival rate (requests/s)")
+    ap.add_argument("--duration", type=float, default=3.0, help="serve: seconds of arrivals")
+    ap.add_argument("--serve-pool", type=int, default=1500, help="serve: distinct requests the stream cycles through")
     ap.add_argument("--npairs", type=int, default=20000, help="band: evaluation pairs (20,000 = the full workload)")
     ap.add_argument("--no-clocks", action="store_true")
     ap.add_argument("--nseq", type=int, default=512, help="allpairs: number of sequences (512 = the full workload)")
@@ -386,6 +389,78 @@ def oracle_gcups_pairs(pairs, budget_s: float = 12.0):
     return cells / dt / 1e9, threads, f"{done} pairs of the workload, score + traceback ({cells:.3g} cells, {dt:.1f} s)"
 
 
+def run_serve(args):
+    """Poisson request stream into the continuous-batching server."""
+    import torch
+
+    import paper_2412_21103_gb300 as nw
+
+    rank, world, local = dist_env()
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    ctx = nw.Context(local, torch.cuda.current_stream(dev))
+    reqs = list(seqgen.serving_stream(1005, rate=args.rate, limit=args.serve_pool))
+    seqs = []
+    for r in reqs:
+        seqs += [r.pair.a, r.pair.b]
+    pool, off, lens = nw.pool_of(seqs)
+    ao, al, bo, bl = off[0::2], lens[0::2], off[1::2], lens[1::2]
+    want = np.array([r.want_cigar for r in reqs], np.uint8)
+    cells_of = al.astype(np.float64) * bl.astype(np.float64)
+    train_loss = train_band_model(nw, ctx, dev)
+    srv = nw.Server(ctx, workers=4, max_batch=512, trace_budget=64 << 30, flags=nw.NW_LEARNED_BAND)
+    # warm-up: a few requests through every worker
+    srv.submit_many(pool, ao[:16], al[:16], bo[:16], bl[:16], want[:16])
+    srv.drain(300.0)
+    srv.poll(1 << 16)
+    arrivals = np.cumsum(-np.log1p(-seqgen.Stream(1005, 77).uniform(int(args.rate * args.duration) + 1)) / args.rate)
+    arrivals = arrivals[arrivals < args.duration]
+    idx = np.arange(arrivals.size) % len(reqs)
+    t0 = time.perf_counter()
+    k = 0
+    ticket_req = {}
+    done = []
+    while k < arrivals.size:
+        now = time.perf_counter() - t0
+        j = int(np.searchsorted(arrivals, now, side="right"))
+        if j > k:
+            sel = idx[k:j]
+            tick = srv.submit_many(pool, ao[sel], al[sel], bo[sel], bl[sel], want[sel])
+            for tt, q in zip(tick, sel):
+                ticket_req[int(tt)] = int(q)
+            k = j
+        else:
+            time.sleep(0.0005)
+        done += srv.poll(1 << 16)
+    submit_end = time.perf_counter() - t0
+    backlog = srv.stats()
+    drained = srv.drain(600.0)
+    done += srv.poll(1 << 20)
+    wall = time.perf_counter() - t0
+    lat = np.array([d[4] for d in done]) if done else np.zeros(1)
+    cells = float(sum(cells_of[ticket_req[d[0]]] for d in done if d[0] in ticket_req))
+    ok = sum(1 for d in done if d[1] == nw.NW_OK)
+    offered = float(cells_of[idx].sum()) / args.duration
+    line = {
+        "metric": METRIC, "value": cells / wall / 1e9, "unit": "GCUPS", "n_gpus": 1, "steps": 1, "warmup": 1,
+        "ms_per_step": wall * 1e3, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "int32", "data": "synthetic",
+        "config": {"workload": (f"serving: Poisson arrivals at {args.rate:,.0f} req/s for {args.duration} s, pair "
+                                "lengths log-uniform [50, 50,000], divergence U[0.01,0.30], half score-only / half "
+                                f"score+CIGAR, requests cycled from {len(reqs)} drawn from seed 1005; certified learned "
+                                "band, 4 workers, 64 GiB traceback budget"),
+                   "requests": int(arrivals.size), "completed": len(done), "ok": ok, "drained": drained,
+                   "offered_gcups": offered / 1e9, "backlog_at_end_of_arrivals": backlog["waiting"] + backlog["running"],
+                   "arrival_window_s": submit_end, "train_loss": train_loss},
+        "latency_s": {"p50": float(np.percentile(lat, 50)), "p99": float(np.percentile(lat, 99)),
+                      "max": float(lat.max())},
+        "gpu_launches": None,
+    }
+    print(json.dumps(line), flush=True)
+    srv.close()
+    ctx.close()
+
+
 def run_ours(args):
     import torch
     import torch.distributed as dist
@@ -503,6 +578,8 @@ def main():
     WL_ARGS.update(nseq=args.nseq, m=args.m, npairs=args.npairs)
     if args.impl == "reference":
         run_reference(args)
+    elif args.workload == "serve":
+        run_serve(args)
     else:
         run_ours(args)
 

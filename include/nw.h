@@ -201,7 +201,7 @@ int nw_ctx_band_stats(nw_ctx *ctx, uint64_t *out, int cap);
  * 65-128-128-1 ReLU network with BF16 weights and activations and FP32
  * accumulation whose output is log of the band half-width; with
  * NW_LEARNED_BAND, nw_align_batch runs the certified band from
- * ceil(1.25 * exp(output)) (at least 8), or from 64 without a model. */
+ * ceil(2 * exp(output)) (at least 8), or from 64 without a model. */
 
 /* Features of npairs pairs into feat (device, npairs x 65 floats, row per
  * pair); pool2b device, metadata host arrays; B <= 200,000 bases. */

@@ -165,12 +165,16 @@ __global__ void __launch_bounds__(kBatchWarps * 32) k_batch(BatchArgs p) {
             const uint32_t x0 = __shfl_sync(kFull, stage, t & 31u);
             if (lane == 0) x = x0;
             const int32_t col = cb + c;
-            if (c >= 0 && col <= ce && s < S) {
+            const bool act = c >= 0 && col <= ce && s < S;
+            const int32_t D0 = col - (int32_t)(s * SH + (uint32_t)lane * R);  // j - i of row 0 of the lane
+            // Banded: mask only when some active lane has rows outside the
+            // band this step (warp-uniform; most steps need no masking).
+            const bool mask = BAND && __any_sync(kFull, act && !(D0 - (R - 1) >= lo && D0 <= hi));
+            if (act) {
                 const int32_t up = (int32_t)x >> 2;
                 const uint32_t sel = sext_selector(x & 3u);
                 int32_t d = dtop, u = up;
                 uint32_t code = 0;
-                const int32_t D0 = col - (int32_t)(s * SH + (uint32_t)lane * R);  // j - i of row 0 of the lane
 #pragma unroll
                 for (int r = 0; r < R; ++r) {
                     const int32_t sv = (int32_t)prmt(prof[r], 0u, sel);
@@ -182,12 +186,12 @@ __global__ void __launch_bounds__(kBatchWarps * 32) k_batch(BatchArgs p) {
                         // off the dependency chain
                         const int32_t t1 = d + sv;
                         w = max(t1, max(u, Wl[r]));
-                        if (BAND && (uint32_t)(D0 - r - lo) > (uint32_t)(hi - lo)) w = kNegW;
+                        if (mask && (uint32_t)(D0 - r - lo) > (uint32_t)(hi - lo)) w = kNegW;
                         const uint32_t bits = 3u - (uint32_t)min(w - t1, 1) - (uint32_t)min(2 * (w - u), 2);
                         code |= bits << (2 * r);
                     } else {
                         w = max(__viaddmax_s32(d, sv, Wl[r]), u);
-                        if (BAND && (uint32_t)(D0 - r - lo) > (uint32_t)(hi - lo)) w = kNegW;
+                        if (mask && (uint32_t)(D0 - r - lo) > (uint32_t)(hi - lo)) w = kNegW;
                     }
                     d = Wl[r];
                     Wl[r] = w;
@@ -335,6 +339,51 @@ static int check_len(nw_ctx *ctx, const nw_scoring &sc, uint64_t m, uint64_t n) 
     return NW_OK;
 }
 
+// ------------------------------------------------------ straggler routing
+// One warp per pair is efficient while the batch fills the GPU, but a pair
+// much longer than the rest (or a long pair in a small batch) leaves the GPU
+// idle while one warp grinds through it.  The longest pairs go to the
+// multi-warp single-pair kernel, one after another: with pairs sorted by
+// one-warp time, routing the first k costs sum(single-pair times) +
+// max(the rest's ideal batch time, the (k+1)-th one-warp time), and the k
+// with the lowest estimate is taken.  Rates are GB300 measurements (cells/s):
+// one warp of the batched kernels, the whole batched kernel, and the
+// single-pair kernel on a long pair.
+constexpr double kWarpRate = 2e9, kBatchRate = 3.5e12, kPairRate = 2e11, kPairFixed = 1e-3;
+
+// warp_cells[k]: cells pair k costs on one warp (scaled for slower
+// kernels), full_cells[k]: its full grid.  Returns the indices to route.
+static std::vector<size_t> pick_stragglers(const std::vector<double> &warp_cells, const std::vector<double> &full_cells) {
+    std::vector<size_t> order(warp_cells.size());
+    std::iota(order.begin(), order.end(), (size_t)0);
+    std::sort(order.begin(), order.end(), [&](size_t x, size_t y) { return warp_cells[x] > warp_cells[y]; });
+    double rest = 0;
+    for (double c : warp_cells) rest += c;
+    double routed = 0, best = 1e300;
+    size_t best_k = 0;
+    for (size_t k = 0; k <= order.size(); ++k) {
+        const double tail = k < order.size() ? warp_cells[order[k]] / kWarpRate : 0.0;
+        const double est = routed + std::max(rest / kBatchRate, tail);
+        if (est < best) {
+            best = est;
+            best_k = k;
+        }
+        if (k == order.size() || full_cells[order[k]] < 1e7) break;
+        routed += full_cells[order[k]] / kPairRate + kPairFixed;
+        rest -= warp_cells[order[k]];
+    }
+    return std::vector<size_t>(order.begin(), order.begin() + best_k);
+}
+
+// Run one pair on the single-pair kernels, writing into the batch outputs.
+static int run_straggler(nw_ctx *ctx, const uint8_t *pool, uint64_t a_off, uint32_t m, uint64_t b_off, uint32_t n,
+                         const nw_scoring &sc, uint32_t flags, int32_t *score, char *cigar, uint64_t cigar_cap,
+                         uint64_t *cigar_len) {
+    LaunchTimer t(ctx, "straggler");
+    return align_single(ctx, pool + a_off, m, pool + b_off, n, sc, flags & (NW_CIGAR | NW_CIGAR_M), score,
+                        (flags & NW_CIGAR) ? cigar : nullptr, cigar_cap, (flags & NW_CIGAR) ? cigar_len : nullptr);
+}
+
 // ------------------------------------------------------- certified band
 // Closed-form bound on the score of any path that leaves the band of
 // half-width w: such a path reaches diagonal hi+1 (then needs at least
@@ -402,7 +451,7 @@ static int band_rounds(nw_ctx *ctx, const uint8_t *pool, const uint64_t *a_off, 
                        char *cigar_pool, const uint64_t *cigar_off, uint64_t *cigar_len, std::vector<uint32_t> &rest) {
     const Profile pf = make_profile(sc);
     const bool want = flags & NW_CIGAR;
-    constexpr int R = 4;  // 128-row stripes keep the band overhead small
+    constexpr int R = 8;  // 256-row stripes: lower per-cell cost, modest band overhead
     constexpr int kRounds = 3;
     int rc;
     std::vector<uint32_t> pending(ids), width(w0);
@@ -435,6 +484,34 @@ static int band_rounds(nw_ctx *ctx, const uint8_t *pool, const uint64_t *a_off, 
             tw.push_back(width[q]);
         }
         if (tasks.empty()) break;
+        {
+            // banded pairs that would leave the GPU idle on one warp run full
+            // on the single-pair kernel instead (counted as fallbacks); a
+            // banded warp is ~4x slower per cell than a full-grid one
+            std::vector<double> wc(tasks.size()), fc(tasks.size());
+            for (size_t q = 0; q < tasks.size(); ++q) {
+                wc[q] = 4.0 * (double)band_cells(tasks[q], R);
+                fc[q] = (double)tasks[q].m * tasks[q].n;
+            }
+            const std::vector<size_t> strag = pick_stragglers(wc, fc);
+            if (!strag.empty()) {
+                std::vector<char> routed(tasks.size(), 0);
+                for (size_t q : strag) {
+                    routed[q] = 1;
+                    rest.push_back(tasks[q].out0);
+                }
+                std::vector<BatchTask> keep;
+                std::vector<uint32_t> keep_w;
+                for (size_t q = 0; q < tasks.size(); ++q)
+                    if (!routed[q]) {
+                        keep.push_back(tasks[q]);
+                        keep_w.push_back(tw[q]);
+                    }
+                tasks.swap(keep);
+                tw.swap(keep_w);
+            }
+            if (tasks.empty()) break;
+        }
         ctx->band_stats[0] += round == 0 ? tasks.size() : 0;
         // waves bounded by pointer memory (score-only: one wave)
         const uint64_t wave_budget = (ctx->budget - std::min(ctx->budget, ctx->used)) / 2;
@@ -546,7 +623,7 @@ static int band_raw(nw_ctx *ctx, const uint8_t *pool, const uint64_t *a_off, con
                     const uint64_t *b_off, const uint32_t *b_len, uint32_t npairs, const uint32_t *w,
                     const nw_scoring &sc, int32_t *scores) {
     const Profile pf = make_profile(sc);
-    constexpr int R = 4;
+    constexpr int R = 8;
     std::vector<BatchTask> tasks;
     uint32_t max_n = 1;
     for (uint32_t k = 0; k < npairs; ++k) {
@@ -587,7 +664,7 @@ static int band_batch(nw_ctx *ctx, const uint8_t *pool, const uint64_t *a_off, c
         ids[k] = k;
         width[k] = std::max<uint32_t>(w0[k], 1);
         const BatchTask t{a_off[k], b_off[k], a_len[k], b_len[k]};
-        ctx->band_stats[7] += full_cells(t, 4);
+        ctx->band_stats[7] += full_cells(t, 8);
     }
     int rc = band_rounds(ctx, pool, a_off, a_len, b_off, b_len, ids, width, sc, flags, scores, cigar_pool, cigar_off,
                          cigar_len, rest);
@@ -633,6 +710,32 @@ int batch_device_impl(nw_ctx *ctx, const uint8_t *pool, const uint64_t *a_off, c
         t.out1 = ~0u;
         max_n = std::max(max_n, t.n);
         tasks[q] = t;
+    }
+    // pairs that would leave the GPU idle on one warp take the single-pair kernel
+    {
+        std::vector<double> wc(tasks.size()), fc(tasks.size());
+        for (size_t q = 0; q < tasks.size(); ++q) wc[q] = fc[q] = (double)tasks[q].m * tasks[q].n;
+        const std::vector<size_t> strag = pick_stragglers(wc, fc);
+        if (!strag.empty()) {
+            std::vector<char> routed(tasks.size(), 0);
+            for (size_t q : strag) {
+                const BatchTask &t = tasks[q];
+                const uint32_t id = t.out0;
+                if ((rc = run_straggler(ctx, pool, t.a_off, t.m, t.b_off, t.n, sc, flags, scores + id,
+                                        want ? cigar_pool + cigar_off[id] : nullptr,
+                                        want ? cigar_off[id + 1] - cigar_off[id] : 0, want ? cigar_len + id : nullptr)))
+                    return rc;
+                routed[q] = 1;
+            }
+            std::vector<BatchTask> keep;
+            for (size_t q = 0; q < tasks.size(); ++q)
+                if (!routed[q]) keep.push_back(tasks[q]);
+            if (keep.empty()) return NW_OK;
+            tasks.swap(keep);
+            npairs = (uint32_t)tasks.size();
+            max_n = 1;
+            for (const auto &t : tasks) max_n = std::max(max_n, t.n);
+        }
     }
     const int R = pick_rows(tasks);
     BatchArgs ba{};

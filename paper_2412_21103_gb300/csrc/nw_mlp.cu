@@ -310,7 +310,7 @@ int learned_band_widths(nw_ctx *ctx, const uint8_t *pool, const uint64_t *a_off,
     cudaMemcpyAsync(y.data(), a.y, (size_t)npairs * 4, cudaMemcpyDeviceToHost, ctx->stream);
     if ((rc = nw_ctx_sync(ctx))) return rc;
     for (uint32_t k = 0; k < npairs; ++k) {
-        const double pred = std::exp((double)y[k]) * 1.25;  // safety factor against under-prediction
+        const double pred = std::exp((double)y[k]) * 2.0;  // safety factor against under-prediction
         const double cap = (double)std::max(a_len[k], b_len[k]);
         w[k] = (uint32_t)std::min(cap, std::max(8.0, std::ceil(pred)));
     }

@@ -84,7 +84,7 @@ def test_certificate_decisions_match_the_closed_form(ctx):
     tried = 0
     for a, b in pairs:
         lo, hi = oracle.band_limits(a.size, b.size, w)
-        R = 4
+        R = 8
         SH = 32 * R
         width = min(b.size, SH + hi - lo)
         period = max(width, SH + 96)
