@@ -70,6 +70,9 @@ typedef enum {
 #define NW_BAND_RAW     16u   /* nw_align_batch_banded: one banded round, the
                                  banded score itself, no certificate or
                                  fallback (score only; for inspection)      */
+#define NW_RECOMPUTE    32u   /* nw_align with NW_CIGAR: take the stripe-
+                                 checkpoint recompute path even when the
+                                 pointer matrix fits (see nw_align)         */
 
 typedef struct {
     int32_t match;      /* score of a diagonal step with equal bases (Sec. 2.3: +1)   */
@@ -127,7 +130,18 @@ uint64_t nw_cigar_bound(uint64_t m, uint64_t n);
  * NW_CIGAR also the CIGAR (NUL-terminated) into cigar[0..cigar_cap) and its
  * length without the NUL into *cigar_len.  With device outputs cigar_cap
  * must be at least nw_cigar_bound(m,n); with NW_HOST_IO a smaller buffer
- * returns NW_ERR_CIGAR_TRUNC with the needed length in *cigar_len. */
+ * returns NW_ERR_CIGAR_TRUNC with the needed length in *cigar_len.
+ *
+ * Memory.  The CIGAR normally comes from a full matrix of 2-bit pointers,
+ * about m*n/4 bytes of scratch.  When that does not fit the context budget
+ * (or with NW_RECOMPUTE) the call switches to stripe-checkpoint recompute:
+ * a score-only fill keeps one W row per 32*R*4 rows (R = 4 rows per lane
+ * from m >= 1024, else 2; about 8*(n+128) bytes per kept row), then the
+ * pointers are filled again wave by wave from the bottom, each wave as many
+ * row groups as the remaining budget holds, and the traceback walks each
+ * wave before the next is computed.  Same result, at most twice the fill
+ * work; NW_ERR_OOM only if one group of 32*R*4 rows of pointers does not
+ * fit.  Sec. 2 keeps the whole matrix; this path is not in the paper. */
 int nw_align(nw_ctx *ctx, const uint8_t *a2b, uint64_t m, const uint8_t *b2b, uint64_t n,
              nw_scoring sc, uint32_t flags, int32_t *score,
              char *cigar, uint64_t cigar_cap, uint64_t *cigar_len);

@@ -34,6 +34,7 @@ NW_LEARNED_BAND = 2
 NW_HOST_IO = 4
 NW_CIGAR_M = 8
 NW_BAND_RAW = 16
+NW_RECOMPUTE = 32
 
 DEFAULT_SCORING = (1, -1, -1)
 

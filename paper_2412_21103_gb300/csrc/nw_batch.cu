@@ -380,7 +380,7 @@ static int run_straggler(nw_ctx *ctx, const uint8_t *pool, uint64_t a_off, uint3
                          const nw_scoring &sc, uint32_t flags, int32_t *score, char *cigar, uint64_t cigar_cap,
                          uint64_t *cigar_len) {
     LaunchTimer t(ctx, "straggler");
-    return align_single(ctx, pool + a_off, m, pool + b_off, n, sc, flags & (NW_CIGAR | NW_CIGAR_M), score,
+    return align_single(ctx, pool + a_off, m, pool + b_off, n, sc, flags & (NW_CIGAR | NW_CIGAR_M | NW_RECOMPUTE), score,
                         (flags & NW_CIGAR) ? cigar : nullptr, cigar_cap, (flags & NW_CIGAR) ? cigar_len : nullptr);
 }
 
@@ -476,7 +476,8 @@ static int band_rounds(nw_ctx *ctx, const uint8_t *pool, const uint64_t *a_off, 
                 continue;
             }
             band_task(t, R, w);
-            if (band_cells(t, R) * 10 >= full_cells(t, R) * 6) {
+            if (band_cells(t, R) * 10 >= full_cells(t, R) * 6 ||
+                (want && band_cells(t, R) / 4 > (ctx->budget - std::min(ctx->budget, ctx->used)) / 2)) {
                 rest.push_back(id);
                 continue;
             }
@@ -711,11 +712,20 @@ int batch_device_impl(nw_ctx *ctx, const uint8_t *pool, const uint64_t *a_off, c
         max_n = std::max(max_n, t.n);
         tasks[q] = t;
     }
-    // pairs that would leave the GPU idle on one warp take the single-pair kernel
+    // pairs that would leave the GPU idle on one warp take the single-pair
+    // kernel, and so do pairs whose pointer matrix alone exceeds half the
+    // remaining budget (the single-pair path recomputes from checkpoints)
     {
         std::vector<double> wc(tasks.size()), fc(tasks.size());
         for (size_t q = 0; q < tasks.size(); ++q) wc[q] = fc[q] = (double)tasks[q].m * tasks[q].n;
-        const std::vector<size_t> strag = pick_stragglers(wc, fc);
+        std::vector<size_t> strag = pick_stragglers(wc, fc);
+        if (want) {
+            const uint64_t room = (ctx->budget - std::min(ctx->budget, ctx->used)) / 2;
+            std::vector<char> in(tasks.size(), 0);
+            for (size_t q : strag) in[q] = 1;
+            for (size_t q = 0; q < tasks.size(); ++q)
+                if (!in[q] && ((uint64_t)tasks[q].m + 512) * ((uint64_t)tasks[q].n + 128) / 4 > room) strag.push_back(q);
+        }
         if (!strag.empty()) {
             std::vector<char> routed(tasks.size(), 0);
             for (size_t q : strag) {

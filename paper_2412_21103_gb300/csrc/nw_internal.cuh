@@ -183,18 +183,41 @@ struct TraceTask {
     uint64_t *cigar_len;   // output
     int32_t band_lo;       // banded layout: stripe s keeps columns from max(0, s*32R + band_lo);
                            // kNoBand for the full layout
+    uint32_t s_lo;         // first stripe whose words `ptr` holds (0: all of them)
+    uint32_t *state;       // null: walk from (m, n) to the end; else a walk resumed and
+                           // paused in device memory: {i, j, k lo, k hi, done}
 };
 constexpr int32_t kNoBand = INT32_MIN;
 // Launch traceback + finish for one task (by value, many == nullptr) or for
 // `ntasks` tasks in a device array.
 int launch_trace(nw_ctx *ctx, int R, const TraceTask &one, const TraceTask *many, uint32_t ntasks, uint32_t mflag);
+// The two halves of launch_trace: the walk (resumable through `state`) and
+// the CIGAR assembly from the finished move list.
+int launch_traceback(nw_ctx *ctx, int R, const TraceTask &one, const TraceTask *many, uint32_t ntasks);
+int launch_finish(nw_ctx *ctx, const TraceTask &one, const TraceTask *many, uint32_t ntasks, uint32_t mflag);
 int align_single(nw_ctx *ctx, const uint8_t *a2b, uint64_t m, const uint8_t *b2b, uint64_t n,
                  const nw_scoring &sc, uint32_t flags, int32_t *score, char *cigar, uint64_t cigar_cap,
                  uint64_t *cigar_len);
 cudaError_t fill_score_with_scratch(const uint8_t *a2b, uint32_t m, const uint8_t *b2b, uint32_t n,
                                     const nw_scoring &sc, int32_t *score, uint32_t *bnd, uint32_t *progress,
                                     uint32_t *err, cudaStream_t stream, int sm_count);
-int launch_pair_fill(nw_ctx *ctx, int R, bool ptr, const uint8_t *a2b, uint32_t m, const uint8_t *b2b, uint32_t n,
-                     const Profile &pf, int32_t *score, uint32_t *ptr_words, uint32_t ncg, int nw);
+// Single-pair fill (nw_pair.cu).  Stripes of 32*R rows, `nw` of them per
+// CTA ("group"); the bottom W row of every group but the last is kept in
+// `bnd` (the checkpoints of the recompute traceback).
+struct PairFill {
+    int R = 4, nw = 4;
+    bool ptr = false;              // write 2-bit pointers
+    uint32_t *ptr_words = nullptr; // pointer words of stripes [cs_lo*nw, ...)
+    uint32_t ncg = 0;              // pointer words per lane row
+    int32_t *score = nullptr;      // null: no score
+    uint32_t *bnd = nullptr;       // group rows (null: scratch)
+    uint32_t *progress = nullptr;  // per-group progress words (null: scratch; zeroed unless recompute)
+    uint32_t cs_lo = 0, cs_hi = 0xffffffffu;  // groups to run
+    const uint32_t *ncols = nullptr;          // device word: columns needed (null: all)
+    bool recompute = false;        // groups start from kept checkpoints, write none
+};
+uint32_t pair_bstride(uint32_t n);
+int launch_pair_fill(nw_ctx *ctx, const uint8_t *a2b, uint32_t m, const uint8_t *b2b, uint32_t n, const Profile &pf,
+                     const PairFill &f);
 void free_band_model(nw_ctx *ctx);
 }

@@ -29,6 +29,8 @@
 // with bit 2*(c*R + r) for block row r, column c is the one the traceback
 // reads.  The step loop runs in three phases (lanes starting, all lanes busy,
 // lanes finishing) so the busy phase has no per-lane tests.
+#include <algorithm>
+
 #include "nw_internal.cuh"
 
 namespace nw {
@@ -46,11 +48,15 @@ struct PairArgs {
     int32_t gap;
     uint32_t S;          // stripes
     uint32_t bstride;    // words per global boundary row (>= NB*C, multiple of 64)
-    uint32_t *bnd;       // global boundary rows: row s = bottom of stripe s (0-based columns)
-    uint32_t *progress;  // per stripe: columns of its global row released
-    uint32_t *ptr;       // pointer words (null: score only)
+    uint32_t *bnd;       // global boundary rows: row g = bottom of group g (0-based columns)
+    uint32_t *progress;  // per group: columns of its global row released
+    uint32_t *ptr;       // pointer words of stripes s_ptr0.. (null: score only)
     uint32_t ncg;        // pointer words per lane row (>= NB)
-    int32_t *score;
+    uint32_t s_ptr0;     // first stripe with pointer words in `ptr`
+    uint32_t cs_lo, cs_hi;   // groups (CTA-stripes) to run
+    const uint32_t *ncols;   // null, or a device word: only columns [0, *ncols) are needed
+    uint32_t recompute;      // groups start from kept rows and write none
+    int32_t *score;          // null: no score
     uint32_t *err;
 };
 
@@ -181,7 +187,7 @@ __device__ __forceinline__ void pair_block(LaneState<R, C> &st, const uint32_t (
 }
 
 template <int R, bool PTR>
-__global__ void __launch_bounds__(kPairMaxWarps * 32) k_pair(PairArgs p) {
+__global__ void __launch_bounds__(kPairMaxWarps * 32, 1) k_pair(PairArgs p) {
     constexpr int C = 16 / R;
     constexpr uint32_t SH = 32u * R;
     constexpr uint32_t QB = kPairQ / C;   // ring capacity in blocks
@@ -195,14 +201,18 @@ __global__ void __launch_bounds__(kPairMaxWarps * 32) k_pair(PairArgs p) {
     const int w = threadIdx.x >> 5;
     const int NW = blockDim.x >> 5;
     const int src = (lane + 31) & 31;  // rotation: lane 0 hears lane 31
-    const uint32_t n = p.n, m = p.m;
+    const uint32_t m = p.m;
+    // recompute passes need only the columns left of the traceback's entry
+    const uint32_t n = p.ncols ? min(p.n, *p.ncols) : p.n;
+    if (n == 0) return;
     const uint32_t NB = (n + C - 1) / C;
     const uint32_t NBC = NB * C;
     const uint32_t CS = (p.S + NW - 1) / NW;
     const uint32_t sM = (m - 1) / SH, lM = ((m - 1) % SH) / R, rM = (m - 1) % R;
     const uint32_t qL = NB - 1, cL = (n - 1) % C;
 
-    for (uint32_t cs = blockIdx.x; cs < CS; cs += gridDim.x) {
+    const uint32_t cs_end = min(CS, p.cs_hi);
+    for (uint32_t cs = p.cs_lo + blockIdx.x; cs < cs_end; cs += gridDim.x) {
         if (lane == 0) {
             head[w] = 0;
             tail[w] = 0;
@@ -231,12 +241,12 @@ __global__ void __launch_bounds__(kPairMaxWarps * 32) k_pair(PairArgs p) {
             const bool self_fill = w == 0;
             const bool has_next = s + 1 < p.S;
             const bool out_ring = has_next && w + 1 < NW;
-            const bool out_glob = has_next && w + 1 == NW;
-            const uint32_t *ginW = (self_fill && s > 0) ? p.bnd + (size_t)(s - 1) * 2 * p.bstride : nullptr;
+            const bool out_glob = has_next && w + 1 == NW && !p.recompute;
+            const uint32_t *ginW = (self_fill && cs > 0) ? p.bnd + (size_t)(cs - 1) * 2 * p.bstride : nullptr;
             const uint32_t *ginS = ginW ? ginW + p.bstride : nullptr;
-            uint32_t *goutW = out_glob ? p.bnd + (size_t)s * 2 * p.bstride : nullptr;
+            uint32_t *goutW = out_glob ? p.bnd + (size_t)cs * 2 * p.bstride : nullptr;
             uint32_t *goutS = goutW ? goutW + p.bstride : nullptr;
-            uint32_t *prow = PTR ? p.ptr + (size_t)(s * 32u + lane) * p.ncg : nullptr;
+            uint32_t *prow = PTR ? p.ptr + (size_t)((s - p.s_ptr0) * 32u + lane) * p.ncg : nullptr;
             const int nx = w + 1 < NW ? w + 1 : w;
             volatile uint32_t *my_head = head + w;
             volatile uint32_t *my_tail = tail + w;
@@ -253,10 +263,10 @@ __global__ void __launch_bounds__(kPairMaxWarps * 32) k_pair(PairArgs p) {
                 if (32u * k >= NBC) return true;
                 if (ginW) {
                     int good = 1;
-                    if (lane == 0) good = wait_geq(&p.progress[s - 1], min(32u * k + 32u, NBC), p.err, s) ? 1 : 0;
+                    if (lane == 0) good = wait_geq(&p.progress[cs - 1], min(32u * k + 32u, NBC), p.err, s) ? 1 : 0;
                     good = __shfl_sync(kFull, good, 0);
                     if (!good) return false;
-                    (void)ld_acquire(&p.progress[s - 1]);
+                    (void)ld_acquire(&p.progress[cs - 1]);
                     stW = __ldcg(ginW + col);
                     stS = __ldcg(ginS + col);
                 } else {
@@ -307,7 +317,7 @@ __global__ void __launch_bounds__(kPairMaxWarps * 32) k_pair(PairArgs p) {
                             __threadfence_block();
                             *nx_head = (uint32_t)done;
                         } else if (out_glob) {
-                            st_release(&p.progress[s], (uint32_t)done * C);
+                            st_release(&p.progress[cs], (uint32_t)done * C);
                         }
                     }
                 }
@@ -371,7 +381,7 @@ __global__ void __launch_bounds__(kPairMaxWarps * 32) k_pair(PairArgs p) {
                 chunk_end(t);
                 t += KB;
             }
-            if (ok && s == sM && (uint32_t)lane == lM) {
+            if (ok && p.score && s == sM && (uint32_t)lane == lM) {
                 int32_t wmn = 0;
 #pragma unroll
                 for (int r = 0; r < R; ++r)
@@ -389,16 +399,20 @@ static int launch_pair_R(nw_ctx *ctx, PairArgs &pa, int nw) {
     cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_pair<R, PTR>, nw * 32, 0);
     if (occ < 1) occ = 1;
     const uint32_t CS = (pa.S + nw - 1) / nw;
-    uint32_t blocks = CS;
+    const uint32_t hi = std::min(CS, pa.cs_hi);
+    if (pa.cs_lo >= hi) return NW_OK;
+    uint32_t blocks = hi - pa.cs_lo;
     const uint32_t cap = (uint32_t)occ * (uint32_t)ctx->sm_count;  // co-resident
     if (blocks > cap) blocks = cap;
-    LaunchTimer t(ctx, PTR ? "fill_ptr" : "fill_score");
+    LaunchTimer t(ctx, pa.recompute ? "fill_recompute" : PTR ? "fill_ptr" : "fill_score");
     k_pair<R, PTR><<<blocks, nw * 32, 0, ctx->stream>>>(pa);
     return NW_OK;
 }
 
-int launch_pair_fill(nw_ctx *ctx, int R, bool ptr, const uint8_t *a2b, uint32_t m, const uint8_t *b2b, uint32_t n,
-                     const Profile &pf, int32_t *score, uint32_t *ptr_words, uint32_t ncg, int nw) {
+uint32_t pair_bstride(uint32_t n) { return ((n + 64 + 63) / 64) * 64; }  // W row then selector row
+
+int launch_pair_fill(nw_ctx *ctx, const uint8_t *a2b, uint32_t m, const uint8_t *b2b, uint32_t n, const Profile &pf,
+                     const PairFill &f) {
     PairArgs pa{};
     pa.a = a2b;
     pa.b = b2b;
@@ -406,25 +420,34 @@ int launch_pair_fill(nw_ctx *ctx, int R, bool ptr, const uint8_t *a2b, uint32_t 
     pa.n = n;
     for (int c = 0; c < 4; ++c) pa.prof[c] = pf.prof[c];
     pa.gap = pf.gap;
+    const int R = f.R;
+    const int nw = std::max(1, std::min(f.nw, kPairMaxWarps));
     pa.S = (m + 32u * R - 1) / (32u * R);
-    pa.bstride = ((n + 64 + 63) / 64) * 64;  // W row then selector row per stripe
-    pa.ptr = ptr_words;
-    pa.ncg = ncg;
-    pa.score = score;
+    pa.bstride = pair_bstride(n);
+    pa.ptr = f.ptr ? f.ptr_words : nullptr;
+    pa.ncg = f.ncg;
+    pa.cs_lo = f.cs_lo;
+    pa.cs_hi = f.cs_hi;
+    pa.s_ptr0 = f.cs_lo * (uint32_t)nw;
+    pa.ncols = f.ncols;
+    pa.recompute = f.recompute ? 1u : 0u;
+    pa.score = f.score;
     pa.err = ctx->d_err;
-    if (nw < 1) nw = 1;
-    if (nw > kPairMaxWarps) nw = kPairMaxWarps;
     int rc;
     void *v = nullptr;
     const uint32_t CS = (pa.S + nw - 1) / nw;
-    if (CS > 1) {
-        if ((rc = scratch(ctx, "pair_bnd", (size_t)pa.S * 2 * pa.bstride * 4, &v))) return rc;
+    pa.bnd = f.bnd;
+    if (!pa.bnd && CS > 1) {
+        if ((rc = scratch(ctx, "pair_bnd", (size_t)(CS - 1) * 2 * pa.bstride * 4, &v))) return rc;
         pa.bnd = (uint32_t *)v;
     }
-    if ((rc = scratch(ctx, "pair_progress", (size_t)pa.S * 4 + 16, &v))) return rc;
-    pa.progress = (uint32_t *)v;
-    cudaMemsetAsync(pa.progress, 0, (size_t)pa.S * 4, ctx->stream);
-    switch (R * 2 + (ptr ? 1 : 0)) {
+    pa.progress = f.progress;
+    if (!pa.progress) {
+        if ((rc = scratch(ctx, "pair_progress", (size_t)CS * 4 + 16, &v))) return rc;
+        pa.progress = (uint32_t *)v;
+    }
+    if (!f.recompute) cudaMemsetAsync(pa.progress, 0, (size_t)CS * 4, ctx->stream);
+    switch (R * 2 + (f.ptr ? 1 : 0)) {
         case 4: return launch_pair_R<2, false>(ctx, pa, nw);
         case 5: return launch_pair_R<2, true>(ctx, pa, nw);
         case 8: return launch_pair_R<4, false>(ctx, pa, nw);

@@ -19,6 +19,7 @@
 // recovered as 1, 2, 3).  A 32-bit word holds R rows x (16/R) columns of one
 // lane; words are stored [stripe][lane][column group], so one lane's words
 // are contiguous along the row.
+#include <algorithm>
 #include <cstdio>
 #include <cstdlib>
 
@@ -200,24 +201,121 @@ static void pair_shape(nw_ctx *ctx, uint64_t m, int &R, int &nw) {
     if (const char *e = getenv("NW_PAIR_WARPS")) nw = atoi(e);
 }
 
+__global__ void k_walk_init(uint32_t *state, uint32_t m, uint32_t n) {
+    state[0] = m;
+    state[1] = n;
+    state[2] = 0;
+    state[3] = 0;
+    state[4] = 0;
+}
+
+// Bytes a scratch slot may still grow to under the budget.
+static uint64_t headroom(nw_ctx *ctx, const char *slot) {
+    const auto it = ctx->bufs.find(slot);
+    const uint64_t mine = it == ctx->bufs.end() ? 0 : it->second.cap;
+    const uint64_t others = ctx->used - mine;
+    return ctx->budget > others ? ctx->budget - others : 0;
+}
+
+// Stripe-checkpoint recompute (a6), for pairs whose pointer matrix exceeds
+// the memory budget.  A score-only fill keeps the bottom W row of every
+// group of nw stripes (one CTA's rows); then, from the bottom up, waves of
+// groups are filled again with pointers -- each group starts from its own
+// kept row, so the groups of a wave run side by side -- and the traceback
+// walks through the wave and pauses at its top.  Each wave computes only the
+// columns left of the walk's current cell (read on the device: no host round
+// trip).  Memory: (groups-1) rows of 8(n+128) bytes plus one wave of
+// pointers; work: at most twice the fill.  Decisions depend only on the
+// pointers, which the second pass reproduces exactly, so the alignment is
+// the one the full pointer matrix gives.
+static int run_pair_recompute(nw_ctx *ctx, const uint8_t *a2b, uint32_t m, const uint8_t *b2b, uint32_t n,
+                              const Profile &pf, uint32_t flags, int R, int nw, int32_t *score, char *cigar,
+                              uint64_t *cigar_len, uint8_t *moves, uint64_t *nmoves) {
+    const uint32_t SH = 32u * R;
+    const uint32_t S = (m + SH - 1) / SH;
+    const uint32_t CS = (S + nw - 1) / nw;
+    const uint32_t ncg = ptr_words_per_lane_row(n, R);
+    int rc;
+    void *v = nullptr;
+    uint32_t *bnd = nullptr;
+    if (CS > 1) {
+        if ((rc = scratch(ctx, "ckpt_rows", (size_t)(CS - 1) * 2 * pair_bstride(n) * 4, &v))) return rc;
+        bnd = (uint32_t *)v;
+    }
+    if ((rc = scratch(ctx, "ckpt_progress", (size_t)CS * 4 + 16, &v))) return rc;
+    uint32_t *progress = (uint32_t *)v;
+    if ((rc = scratch(ctx, "ckpt_walk", 64, &v))) return rc;
+    uint32_t *state = (uint32_t *)v;
+    PairFill f;
+    f.R = R;
+    f.nw = nw;
+    f.score = score;
+    f.bnd = bnd;
+    f.progress = progress;
+    if ((rc = launch_pair_fill(ctx, a2b, m, b2b, n, pf, f))) return rc;  // checkpoints + score
+    {
+        LaunchTimer t(ctx, "walk_init");
+        k_walk_init<<<1, 1, 0, ctx->stream>>>(state, m, n);
+    }
+    const uint64_t group_bytes = (uint64_t)nw * 32u * ncg * 4u;
+    const uint64_t room = headroom(ctx, "ckpt_wave");
+    uint64_t G = room / (group_bytes + group_bytes / 8 + 256);
+    if (G == 0) return fail(ctx, NW_ERR_OOM, "one group of pointers (%llu bytes) exceeds the budget",
+                            (unsigned long long)group_bytes);
+    if (G > CS) G = CS;
+    if ((rc = scratch(ctx, "ckpt_wave", G * group_bytes, &v))) return rc;
+    uint32_t *wave = (uint32_t *)v;
+    TraceTask tt{wave, ncg, m, n, moves, nmoves, a2b, b2b, cigar, cigar_len, kNoBand, 0, state};
+    for (int64_t g1 = CS; g1 > 0; g1 -= (int64_t)G) {
+        const uint32_t g0 = (uint32_t)std::max<int64_t>(0, g1 - (int64_t)G);
+        PairFill r = f;
+        r.ptr = true;
+        r.ptr_words = wave;
+        r.ncg = ncg;
+        r.score = nullptr;
+        r.cs_lo = g0;
+        r.cs_hi = (uint32_t)g1;
+        r.ncols = state + 1;
+        r.recompute = true;
+        if ((rc = launch_pair_fill(ctx, a2b, m, b2b, n, pf, r))) return rc;
+        tt.s_lo = g0 * (uint32_t)nw;
+        if ((rc = launch_traceback(ctx, R, tt, nullptr, 1))) return rc;
+    }
+    return launch_finish(ctx, tt, nullptr, 1, (flags & NW_CIGAR_M) ? 1u : 0u);
+}
+
 static int run_pair(nw_ctx *ctx, const uint8_t *a2b, uint32_t m, const uint8_t *b2b, uint32_t n, const Profile &pf,
                     uint32_t flags, int32_t *score, char *cigar, uint64_t *cigar_len) {
     const bool want = flags & NW_CIGAR;
     int R, nw;
     pair_shape(ctx, m, R, nw);
+    PairFill f;
+    f.R = R;
+    f.nw = nw;
+    f.score = score;
+    if (!want) return launch_pair_fill(ctx, a2b, m, b2b, n, pf, f);
     int rc;
-    if (!want) return launch_pair_fill(ctx, R, false, a2b, m, b2b, n, pf, score, nullptr, 0, nw);
-    const uint32_t SH = 32u * R;
-    const uint32_t S = (m + SH - 1) / SH;
-    const uint32_t ncg = ptr_words_per_lane_row(n, R);
-    void *v = nullptr;
-    if ((rc = scratch(ctx, "ptr", (size_t)S * 32u * ncg * 4u, &v))) return rc;
-    uint32_t *ptr = (uint32_t *)v;
-    if ((rc = launch_pair_fill(ctx, R, true, a2b, m, b2b, n, pf, score, ptr, ncg, nw))) return rc;
     void *mv = nullptr, *nm = nullptr;
     if ((rc = scratch(ctx, "moves", (size_t)m + n + 16, &mv))) return rc;
     if ((rc = scratch(ctx, "nmoves", 16, &nm))) return rc;
-    TraceTask tt{ptr, ncg, m, n, (uint8_t *)mv, (uint64_t *)nm, a2b, b2b, cigar, cigar_len, kNoBand};
+    const uint32_t SH = 32u * R;
+    const uint32_t S = (m + SH - 1) / SH;
+    const uint32_t ncg = ptr_words_per_lane_row(n, R);
+    const uint64_t ptr_bytes = (uint64_t)S * 32u * ncg * 4u;
+    const uint64_t CS = (S + nw - 1) / nw;
+    const uint64_t rows_bytes = (CS > 1 ? (CS - 1) * 2 * pair_bstride(n) * 4 : 0) + CS * 4 + 1024;
+    // the full pointer matrix, unless it (with the fill's rows) exceeds the budget
+    if ((flags & NW_RECOMPUTE) || ptr_bytes + ptr_bytes / 8 + rows_bytes > headroom(ctx, "ptr"))
+        return run_pair_recompute(ctx, a2b, m, b2b, n, pf, flags, R, nw, score, cigar, cigar_len, (uint8_t *)mv,
+                                  (uint64_t *)nm);
+    void *v = nullptr;
+    if ((rc = scratch(ctx, "ptr", ptr_bytes, &v))) return rc;
+    f.ptr = true;
+    f.ptr_words = (uint32_t *)v;
+    f.ncg = ncg;
+    if ((rc = launch_pair_fill(ctx, a2b, m, b2b, n, pf, f))) return rc;
+    TraceTask tt{f.ptr_words, ncg, m, n, (uint8_t *)mv, (uint64_t *)nm, a2b, b2b, cigar, cigar_len, kNoBand, 0,
+                 nullptr};
     return launch_trace(ctx, R, tt, nullptr, 1, (flags & NW_CIGAR_M) ? 1u : 0u);
 }
 

@@ -21,6 +21,14 @@ __global__ void __launch_bounds__(32) k_traceback(TraceTask one, const TraceTask
     const uint32_t lane = threadIdx.x;
     uint32_t i = p.m, j = p.n;
     uint64_t k = 0;
+    if (p.state) {
+        // resumed walk: the pointer words of stripes [s_lo, ...) are present
+        if (p.state[4]) return;
+        i = p.state[0];
+        j = p.state[1];
+        k = (uint64_t)p.state[2] | ((uint64_t)p.state[3] << 32);
+    }
+    const uint32_t s_lo = p.s_lo;
     uint32_t cs = 0xffffffffu, ckt = 0, cct = 0;
     // first stored column of stripe s (banded layout) or 0
     auto cbeg = [&](uint32_t s) -> uint32_t {
@@ -28,13 +36,14 @@ __global__ void __launch_bounds__(32) k_traceback(TraceTask one, const TraceTask
         const int64_t v = (int64_t)s * SH + p.band_lo;
         return v > 0 ? (uint32_t)v : 0u;
     };
-    while (i > 0 && j > 0) {
+    while (i > 0 && j > 0 && (i - 1) / SH >= s_lo) {
         const uint32_t i1 = i - 1, j1 = j - 1;
         const uint32_t s = i1 / SH, kt = ((i1 % SH) / R) / kTileLanes, ct = ((j1 - cbeg(s)) / CPW) / kTileWords;
         if (s != cs || kt != ckt || ct != cct) {
             __syncwarp();
             const uint32_t rl = lane >> 2, part = lane & 3u;
-            const size_t base = (size_t)(s * 32u + kt * kTileLanes + rl) * p.ncg + ct * kTileWords + part * 8u;
+            const size_t base =
+                (size_t)((s - s_lo) * 32u + kt * kTileLanes + rl) * p.ncg + ct * kTileWords + part * 8u;
             const uint4 v0 = __ldcg(reinterpret_cast<const uint4 *>(p.ptr + base));
             const uint4 v1 = __ldcg(reinterpret_cast<const uint4 *>(p.ptr + base + 4));
             uint4 *dst = reinterpret_cast<uint4 *>(tile + rl * kTileWords + part * 8u);
@@ -65,11 +74,29 @@ __global__ void __launch_bounds__(32) k_traceback(TraceTask one, const TraceTask
         j = __shfl_sync(kFull, j, 0);
         k = __shfl_sync(kFull, k, 0);
     }
+    if (i > 0 && j > 0) {
+        // paused at the top of the stripes present (resumable walks only)
+        __syncwarp();
+        if (lane == 0) {
+            p.state[0] = i;
+            p.state[1] = j;
+            p.state[2] = (uint32_t)k;
+            p.state[3] = (uint32_t)(k >> 32);
+        }
+        return;
+    }
     // Row 0 / column 0: only horizontal / vertical moves remain.
     const uint32_t rest = i + j;
     const uint8_t mv = i ? 1 : 2;
     for (uint32_t q = lane; q < rest; q += 32) p.moves[k + q] = mv;
-    if (lane == 0) *p.nmoves = k + rest;
+    if (lane == 0) {
+        *p.nmoves = k + rest;
+        if (p.state) {
+            p.state[0] = 0;
+            p.state[1] = 0;  // no columns left for the passes above
+            p.state[4] = 1;
+        }
+    }
 }
 
 // ------------------------------------------------------------------ finish
@@ -237,7 +264,7 @@ static void launch_tb(nw_ctx *ctx, const TraceTask &one, const TraceTask *many, 
     k_traceback<R><<<ntasks, 32, 0, ctx->stream>>>(one, many);
 }
 
-int launch_trace(nw_ctx *ctx, int R, const TraceTask &one, const TraceTask *many, uint32_t ntasks, uint32_t mflag) {
+int launch_traceback(nw_ctx *ctx, int R, const TraceTask &one, const TraceTask *many, uint32_t ntasks) {
     if (ntasks == 0) return NW_OK;
     {
         LaunchTimer t(ctx, "traceback");
@@ -249,12 +276,23 @@ int launch_trace(nw_ctx *ctx, int R, const TraceTask &one, const TraceTask *many
             default: return fail(ctx, NW_ERR_ARG, "unsupported rows per lane %d", R);
         }
     }
+    cudaError_t e = cudaGetLastError();
+    return e == cudaSuccess ? NW_OK : cuda_fail(ctx, e, "traceback launch");
+}
+
+int launch_finish(nw_ctx *ctx, const TraceTask &one, const TraceTask *many, uint32_t ntasks, uint32_t mflag) {
+    if (ntasks == 0) return NW_OK;
     {
         LaunchTimer t(ctx, "finish");
         k_finish<<<ntasks, kFinThreads, 0, ctx->stream>>>(one, many, mflag);
     }
     cudaError_t e = cudaGetLastError();
-    return e == cudaSuccess ? NW_OK : cuda_fail(ctx, e, "traceback launch");
+    return e == cudaSuccess ? NW_OK : cuda_fail(ctx, e, "CIGAR launch");
+}
+
+int launch_trace(nw_ctx *ctx, int R, const TraceTask &one, const TraceTask *many, uint32_t ntasks, uint32_t mflag) {
+    const int rc = launch_traceback(ctx, R, one, many, ntasks);
+    return rc ? rc : launch_finish(ctx, one, many, ntasks, mflag);
 }
 
 }  // namespace nw
