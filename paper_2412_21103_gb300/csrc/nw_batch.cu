@@ -593,7 +593,7 @@ static int band_rounds(nw_ctx *ctx, const uint8_t *pool, const uint64_t *a_off, 
                 }
                 TraceTask *dtt = nullptr;
                 if ((rc = upload(ctx, "band_trace_tasks", tt, &dtt))) return rc;
-                if ((rc = launch_trace(ctx, R, tt[0], dtt, (uint32_t)tt.size(), (flags & NW_CIGAR_M) ? 1u : 0u)))
+                if ((rc = launch_trace(ctx, R, tt.data(), dtt, (uint32_t)tt.size(), (flags & NW_CIGAR_M) ? 1u : 0u)))
                     return rc;
             }
             k0 = k;
@@ -813,7 +813,7 @@ int batch_device_impl(nw_ctx *ctx, const uint8_t *pool, const uint64_t *a_off, c
         uint32_t wave_max_n = 1;
         for (const auto &t : wave) wave_max_n = std::max(wave_max_n, t.n);
         if ((rc = launch_batch(ctx, R, true, ba, wave_max_n))) return rc;
-        if ((rc = launch_trace(ctx, R, tt[0], dtt, (uint32_t)tt.size(), (flags & NW_CIGAR_M) ? 1u : 0u))) return rc;
+        if ((rc = launch_trace(ctx, R, tt.data(), dtt, (uint32_t)tt.size(), (flags & NW_CIGAR_M) ? 1u : 0u))) return rc;
         k0 = k;
     }
     return NW_OK;

@@ -188,9 +188,11 @@ struct TraceTask {
                            // paused in device memory: {i, j, k lo, k hi, done}
 };
 constexpr int32_t kNoBand = INT32_MIN;
-// Launch traceback + finish for one task (by value, many == nullptr) or for
-// `ntasks` tasks in a device array.
-int launch_trace(nw_ctx *ctx, int R, const TraceTask &one, const TraceTask *many, uint32_t ntasks, uint32_t mflag);
+// Traceback + CIGAR for `ntasks` tasks: `host` describes them on the host
+// (always), `dev` is the same array in device memory (null: one task,
+// passed by value).  Pairs of kParMinStripes stripes or more walk their
+// stripes in parallel (see nw_trace.cu).
+int launch_trace(nw_ctx *ctx, int R, const TraceTask *host, const TraceTask *dev, uint32_t ntasks, uint32_t mflag);
 // The two halves of launch_trace: the walk (resumable through `state`) and
 // the CIGAR assembly from the finished move list.
 int launch_traceback(nw_ctx *ctx, int R, const TraceTask &one, const TraceTask *many, uint32_t ntasks);

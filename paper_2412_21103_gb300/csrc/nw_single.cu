@@ -316,7 +316,7 @@ static int run_pair(nw_ctx *ctx, const uint8_t *a2b, uint32_t m, const uint8_t *
     if ((rc = launch_pair_fill(ctx, a2b, m, b2b, n, pf, f))) return rc;
     TraceTask tt{f.ptr_words, ncg, m, n, (uint8_t *)mv, (uint64_t *)nm, a2b, b2b, cigar, cigar_len, kNoBand, 0,
                  nullptr};
-    return launch_trace(ctx, R, tt, nullptr, 1, (flags & NW_CIGAR_M) ? 1u : 0u);
+    return launch_trace(ctx, R, &tt, nullptr, 1, (flags & NW_CIGAR_M) ? 1u : 0u);
 }
 
 // Score-only fill with 16 rows per lane on `stream`, using scratch the

@@ -2,6 +2,9 @@
 // batched paths.  A task describes one pair: its pointer words (layout
 // [stripe][lane][column group], R rows x 16/R columns per word), its
 // sequences and where its moves and CIGAR go.  One CTA per task.
+#include <algorithm>
+#include <vector>
+
 #include "nw_internal.cuh"
 
 namespace nw {
@@ -97,6 +100,314 @@ __global__ void __launch_bounds__(32) k_traceback(TraceTask one, const TraceTask
             p.state[4] = 1;
         }
     }
+}
+
+// ------------------------------------------------------ stripe-parallel walk
+// The walk is sequential, but its pieces need not be found in order.  Every
+// stripe of a long pair gets two walks, all stripes at once:
+//   spec -- from a guessed cell (on the proportional diagonal) of the
+//           bottom row of the stripe below, unrecorded through that stripe,
+//           then recorded through this one until it leaves it (the last
+//           stripe starts at (m, n) itself).  It records, per row, the
+//           columns it visited and its move count on entering the row.
+//   link -- from the cell where the stripe below's spec walk left, until it
+//           steps onto this stripe's spec path (from there the two are one
+//           walk: a move depends only on the cell) or leaves the stripe.
+// Then one warp per pair follows the true path stripe by stripe: where the
+// true entry is the link walk's start, the stripe's moves are the link
+// prefix plus the spec suffix; otherwise (guess too far off, a walk past its
+// move cap) it walks the stripe itself, still joining the spec path where it
+// can.  Tracebacks from nearby cells merge within a few gap lengths, so for
+// similar sequences the sequential pass mostly just links the pieces.  The
+// moves are those of the plain walk, one for one.
+constexpr uint32_t kWalkDone = 0, kWalkJoined = 1, kWalkFull = 2, kWalkBand = 3, kWalkNone = 4;
+constexpr int kWalkWarps = 4;
+constexpr uint32_t kParMinStripes = 3;  // shorter pairs walk sequentially
+
+struct StripeJob {
+    uint64_t moff;  // byte offset of the stripe's spec moves; its link moves follow at moff + lcap
+    uint64_t roff;  // offset (uint2 units) of its row records
+    uint32_t task, s, lcap, pad;
+};
+
+// Job g when the jobs are implicit (one task, stripes 0..S-1, cap lcap).
+__device__ __forceinline__ StripeJob job_of(const StripeJob *jobs, uint32_t g, uint32_t lcap, uint32_t SH) {
+    if (jobs) return jobs[g];
+    StripeJob j;
+    j.moff = (uint64_t)g * 2u * lcap;
+    j.roff = (uint64_t)g * SH;
+    j.task = 0;
+    j.s = g;
+    j.lcap = lcap;
+    j.pad = 0;
+    return j;
+}
+
+// Walk from (i, j) inside stripe s (rows s*SH+1 .. s*SH+SH) until the walk
+// leaves the stripe or reaches row / column 0 (kWalkDone), steps on a cell
+// of the spec path in `arow` (kWalkJoined; JOIN only; a_from = the spec's
+// move count there), has made `cap` moves (kWalkFull) or would read a column
+// left of the stored band (kWalkBand).  RECORD writes the row records
+// {entry column, (entry - exit column) | moves-before-entry << 16}.  Moves
+// go to out[k..].  Lane 0 walks, the warp stages 8-lane x 32-word pointer
+// tiles; i, j, k and the status are valid in every lane on return.
+template <int R, bool RECORD, bool JOIN>
+__device__ uint32_t walk_stripe(const TraceTask &p, uint32_t s, uint32_t &i, uint32_t &j, uint32_t &k, uint32_t cap,
+                                uint8_t *out, uint2 *rec, const uint2 *arow, uint32_t &a_from, uint32_t *tile) {
+    constexpr uint32_t SH = 32u * R, CPW = 16u / R;
+    const uint32_t lane = threadIdx.x & 31u;
+    const uint32_t top = s * SH;
+    uint32_t cb = 0;
+    if (p.band_lo != kNoBand) {
+        const int64_t v = (int64_t)top + p.band_lo;
+        cb = v > 0 ? (uint32_t)v : 0u;
+    }
+    uint32_t ckt = 0xffffffffu, cct = 0xffffffffu;
+    uint32_t status = kWalkDone, rjhi = j, ridx = k;
+    for (;;) {
+        uint32_t need = 0, nkt = 0, nct = 0;
+        if (lane == 0) {
+            for (;;) {
+                if (i == 0 || j == 0 || i <= top) {
+                    status = kWalkDone;
+                    break;
+                }
+                if (JOIN) {
+                    const uint2 r = arow[i - 1 - top];
+                    if (j <= r.x && j + (r.y & 0xffffu) >= r.x) {
+                        status = kWalkJoined;
+                        a_from = (r.y >> 16) + (r.x - j);
+                        break;
+                    }
+                }
+                if (k >= cap) {
+                    status = kWalkFull;
+                    break;
+                }
+                const uint32_t a1 = i - 1, b1 = j - 1;
+                if (b1 < cb) {
+                    status = kWalkBand;
+                    break;
+                }
+                const uint32_t kk = (a1 - top) / R, cg = (b1 - cb) / CPW;
+                if (kk / kTileLanes != ckt || cg / kTileWords != cct) {
+                    need = 1;
+                    nkt = kk / kTileLanes;
+                    nct = cg / kTileWords;
+                    break;
+                }
+                const uint32_t word = tile[(kk % kTileLanes) * kTileWords + cg % kTileWords];
+                const uint32_t code = (word >> (2u * (((b1 - cb) % CPW) * R + (a1 % R)))) & 3u;
+                const uint32_t mv = (code & 1u) ? 0u : ((code & 2u) ? 1u : 2u);
+                out[k] = (uint8_t)mv;
+                ++k;
+                if (RECORD && mv != 2u) {  // leaving row i
+                    rec[a1 - top] = make_uint2(rjhi, (rjhi - j) | (ridx << 16));
+                    rjhi = j - (mv == 0u);
+                    ridx = k;
+                }
+                i -= (mv != 2u);
+                j -= (mv != 1u);
+            }
+        }
+        need = __shfl_sync(kFull, need, 0);
+        if (!need) break;
+        nkt = __shfl_sync(kFull, nkt, 0);
+        nct = __shfl_sync(kFull, nct, 0);
+        __syncwarp();
+        const uint32_t rl = lane >> 2, part = lane & 3u;
+        const size_t base =
+            (size_t)((s - p.s_lo) * 32u + nkt * kTileLanes + rl) * p.ncg + nct * kTileWords + part * 8u;
+        const uint4 v0 = __ldcg(reinterpret_cast<const uint4 *>(p.ptr + base));
+        const uint4 v1 = __ldcg(reinterpret_cast<const uint4 *>(p.ptr + base + 4));
+        uint4 *dst = reinterpret_cast<uint4 *>(tile + rl * kTileWords + part * 8u);
+        dst[0] = v0;
+        dst[1] = v1;
+        __syncwarp();
+        ckt = nkt;
+        cct = nct;
+    }
+    if (RECORD && lane == 0 && status == kWalkDone && j == 0 && i > top)
+        rec[i - 1 - top] = make_uint2(rjhi, rjhi | (ridx << 16));
+    i = __shfl_sync(kFull, i, 0);
+    j = __shfl_sync(kFull, j, 0);
+    k = __shfl_sync(kFull, k, 0);
+    a_from = __shfl_sync(kFull, a_from, 0);
+    return __shfl_sync(kFull, status, 0);
+}
+
+// Spec (LINK = false) or link (LINK = true) walks, one warp per stripe job.
+template <int R, bool LINK>
+__global__ void __launch_bounds__(kWalkWarps * 32) k_tb_stripes(TraceTask one, const TraceTask *many,
+                                                                const StripeJob *jobs, uint32_t njobs, uint32_t lcap,
+                                                                uint8_t *mbuf, uint2 *rows, uint4 *asum, uint4 *bsum) {
+    constexpr uint32_t SH = 32u * R, CPW = 16u / R;
+    __shared__ __align__(16) uint32_t tiles[kWalkWarps][kTileLanes * kTileWords];
+    __shared__ uint2 arows[LINK ? kWalkWarps : 1][LINK ? SH : 1];
+    const uint32_t lane = threadIdx.x & 31u, wi = threadIdx.x >> 5;
+    const uint32_t g = blockIdx.x * kWalkWarps + wi;
+    if (g >= njobs) return;
+    const StripeJob jb = job_of(jobs, g, lcap, SH);
+    const TraceTask &p = many ? many[jb.task] : one;
+    const uint32_t s = jb.s, top = s * SH;
+    const uint32_t S = (p.m + SH - 1) / SH;
+    uint2 *rec = rows + jb.roff;
+    uint32_t a_from = 0, k = 0;
+    if (!LINK) {
+        for (uint32_t r = lane; r < SH; r += 32) rec[r] = make_uint2(0u, 0u);
+        __syncwarp();
+        // guess for the bottom row of stripe q: the proportional diagonal,
+        // kept inside the stored columns
+        auto guess = [&](uint32_t q, uint32_t row) -> uint32_t {
+            uint32_t g = (uint32_t)(((uint64_t)row * p.n + p.m / 2) / p.m), lo = 1, hi = p.n;
+            if (p.band_lo != kNoBand) {
+                const int64_t v = (int64_t)q * SH + p.band_lo;
+                const uint32_t cb = v > 0 ? (uint32_t)v : 0u;
+                lo = cb + 1;
+                hi = min(hi, cb + p.ncg * CPW);
+            }
+            return max(lo, min(g, hi));
+        };
+        uint32_t i = min(p.m, top + SH), j = p.n;
+        if (s + 1 < S) {
+            j = guess(s, i);
+            // burn-in: start one stripe lower and walk up to this stripe's
+            // bottom row unrecorded; walks from different cells merge, so the
+            // entry it reaches is usually the true path's
+            uint32_t bi = min(p.m, top + 2 * SH), bj = s + 2 < S ? guess(s + 1, bi) : p.n;
+            uint32_t bk = 0, bf = 0;
+            const uint32_t bst = walk_stripe<R, false, false>(p, s + 1, bi, bj, bk, jb.lcap, mbuf + jb.moff, nullptr,
+                                                              nullptr, bf, tiles[wi]);
+            if (bst == kWalkDone && bi == i && bj > 0) j = bj;
+        }
+        const uint32_t st = walk_stripe<R, true, false>(p, s, i, j, k, jb.lcap, mbuf + jb.moff, rec, nullptr, a_from,
+                                                        tiles[wi]);
+        if (lane == 0) asum[g] = make_uint4(i, j, k, st);
+    } else {
+        uint32_t si = p.m, sj = p.n;
+        if (s + 1 < S) {
+            const uint4 a = asum[g + 1];  // the stripe below (jobs of a task are consecutive)
+            if (a.w != kWalkDone || a.x == 0 || a.y == 0) {
+                if (lane == 0) {
+                    bsum[2 * (size_t)g] = make_uint4(0u, 0u, 0u, 0u);
+                    bsum[2 * (size_t)g + 1] = make_uint4(0u, 0u, kWalkNone, 0u);
+                }
+                return;
+            }
+            si = a.x;
+            sj = a.y;
+        }
+        const bool av = asum[g].w == kWalkDone;
+        for (uint32_t r = lane; r < SH; r += 32) arows[wi][r] = av ? rec[r] : make_uint2(0u, 0u);
+        __syncwarp();
+        uint32_t i = si, j = sj;
+        const uint32_t st = walk_stripe<R, false, true>(p, s, i, j, k, jb.lcap, mbuf + jb.moff + jb.lcap, nullptr,
+                                                        arows[wi], a_from, tiles[wi]);
+        if (lane == 0) {
+            bsum[2 * (size_t)g] = make_uint4(si, sj, i, j);
+            bsum[2 * (size_t)g + 1] = make_uint4(k, a_from, st, 0u);
+        }
+    }
+}
+
+// The true path, one warp per pair: links the stripes' pieces (recording
+// the copies in `seg`) and walks the stripes no piece resolves, writing
+// those moves in place.  Pairs without stripe jobs (job_base ~0) walk every
+// stripe here.  Ends with the row-0 / column-0 moves and the move count.
+template <int R>
+__global__ void __launch_bounds__(32) k_tb_stitch(TraceTask one, const TraceTask *many, const uint32_t *job_base,
+                                                  const StripeJob *jobs, uint32_t njobs, uint32_t lcap,
+                                                  const uint2 *rows, const uint4 *asum, const uint4 *bsum, uint4 *seg,
+                                                  uint32_t *err) {
+    constexpr uint32_t SH = 32u * R;
+    __shared__ __align__(16) uint32_t tile[kTileLanes * kTileWords];
+    __shared__ uint2 arow[SH];
+    __shared__ uint4 win[32][3];  // summaries of stripes [wlo, wlo + 32)
+    const TraceTask &p = many ? many[blockIdx.x] : one;
+    const uint32_t lane = threadIdx.x;
+    const uint32_t gb = job_base ? job_base[blockIdx.x] : (njobs ? 0u : 0xffffffffu);
+    const bool par = gb != 0xffffffffu;
+    const uint32_t S = (p.m + SH - 1) / SH;
+    if (par)
+        for (uint32_t s = lane; s < S; s += 32) seg[gb + s] = make_uint4(0xffffffffu, 0u, 0u, 0u);
+    __syncwarp();
+    uint32_t i = p.m, j = p.n, k = 0, wlo = 0xffffffffu;
+    while (i > 0 && j > 0) {
+        const uint32_t s = (i - 1) / SH;
+        uint4 A = make_uint4(0u, 0u, 0u, kWalkNone), B0 = make_uint4(0u, 0u, 0u, 0u),
+              B1 = make_uint4(0u, 0u, kWalkNone, 0u);
+        if (par) {
+            if (wlo == 0xffffffffu || s < wlo || s >= wlo + 32) {
+                wlo = s >= 31 ? s - 31 : 0;
+                __syncwarp();
+                const uint32_t q = wlo + lane;
+                if (q < S) {
+                    win[lane][0] = asum[gb + q];
+                    win[lane][1] = bsum[2 * (size_t)(gb + q)];
+                    win[lane][2] = bsum[2 * (size_t)(gb + q) + 1];
+                }
+                __syncwarp();
+            }
+            A = win[s - wlo][0];
+            B0 = win[s - wlo][1];
+            B1 = win[s - wlo][2];
+        }
+        if (B0.x == i && B0.y == j && (B1.z == kWalkDone || B1.z == kWalkJoined)) {
+            const bool joined = B1.z == kWalkJoined;
+            if (lane == 0) seg[gb + s] = make_uint4(k, B1.x, joined ? B1.y : 0u, joined ? A.z - B1.y : 0u);
+            k += B1.x;
+            if (joined) {
+                k += A.z - B1.y;
+                i = A.x;
+                j = A.y;
+            } else {
+                i = B0.z;
+                j = B0.w;
+            }
+            continue;
+        }
+        const bool av = par && A.w == kWalkDone;
+        const uint64_t roff = av ? job_of(jobs, gb + s, lcap, SH).roff : 0;
+        __syncwarp();
+        for (uint32_t r = lane; r < SH; r += 32) arow[r] = av ? rows[roff + r] : make_uint2(0u, 0u);
+        __syncwarp();
+        uint32_t a_from = 0;
+        const uint32_t st =
+            walk_stripe<R, false, true>(p, s, i, j, k, 0xffffffffu, p.moves, nullptr, arow, a_from, tile);
+        if (st == kWalkJoined) {
+            if (lane == 0) seg[gb + s] = make_uint4(k, 0u, a_from, A.z - a_from);
+            k += A.z - a_from;
+            i = A.x;
+            j = A.y;
+        } else if (st != kWalkDone) {
+            // the true path never leaves the stored columns of an accepted band
+            if (lane == 0) raise_error(err, NW_ERR_UNSUPPORTED, 0x70000u + s);
+            break;
+        }
+    }
+    const uint32_t rest = i + j;
+    const uint8_t mv = i ? 1 : 2;
+    for (uint32_t q = lane; q < rest; q += 32) p.moves[(uint64_t)k + q] = mv;
+    if (lane == 0) *p.nmoves = (uint64_t)k + rest;
+}
+
+// Copies of the linked pieces into the move list, one warp per stripe job.
+template <int R>
+__global__ void __launch_bounds__(kWalkWarps * 32) k_tb_copy(TraceTask one, const TraceTask *many,
+                                                             const StripeJob *jobs, uint32_t njobs, uint32_t lcap,
+                                                             const uint8_t *mbuf, const uint4 *seg) {
+    constexpr uint32_t SH = 32u * R;
+    const uint32_t lane = threadIdx.x & 31u;
+    const uint32_t g = blockIdx.x * kWalkWarps + (threadIdx.x >> 5);
+    if (g >= njobs) return;
+    const uint4 sg = seg[g];
+    if (sg.x == 0xffffffffu) return;
+    const StripeJob jb = job_of(jobs, g, lcap, SH);
+    const TraceTask &p = many ? many[jb.task] : one;
+    uint8_t *dst = p.moves + sg.x;
+    const uint8_t *spec = mbuf + jb.moff, *link = spec + jb.lcap;
+    for (uint32_t q = lane; q < sg.y; q += 32) dst[q] = link[q];
+    for (uint32_t q = lane; q < sg.w; q += 32) dst[sg.y + q] = spec[sg.z + q];
 }
 
 // ------------------------------------------------------------------ finish
@@ -290,9 +601,102 @@ int launch_finish(nw_ctx *ctx, const TraceTask &one, const TraceTask *many, uint
     return e == cudaSuccess ? NW_OK : cuda_fail(ctx, e, "CIGAR launch");
 }
 
-int launch_trace(nw_ctx *ctx, int R, const TraceTask &one, const TraceTask *many, uint32_t ntasks, uint32_t mflag) {
-    const int rc = launch_traceback(ctx, R, one, many, ntasks);
-    return rc ? rc : launch_finish(ctx, one, many, ntasks, mflag);
+// Stripe jobs of the pairs with at least kParMinStripes stripes, scratch
+// for their walks, and the four walk kernels.
+template <int R>
+static int launch_walks(nw_ctx *ctx, const TraceTask *host, const TraceTask *dev, uint32_t ntasks) {
+    constexpr uint32_t SH = 32u * R;
+    const TraceTask one = dev ? TraceTask{} : host[0];
+    std::vector<StripeJob> jobs;
+    std::vector<uint32_t> base(ntasks, 0xffffffffu);
+    uint64_t moff = 0, roff = 0;
+    for (uint32_t t = 0; t < ntasks; ++t) {
+        const uint64_t m = host[t].m, n = host[t].n;
+        if (m == 0 || n == 0 || host[t].state) continue;
+        const uint32_t S = (uint32_t)((m + SH - 1) / SH);
+        if (S < kParMinStripes) continue;
+        // moves of a stripe's walks: its rows, twice the proportional columns, slack
+        uint64_t cap = SH + 2 * ((SH * n + m - 1) / m) + 512;
+        cap = std::min<uint64_t>((cap + 15) / 16 * 16, 65520);
+        base[t] = (uint32_t)jobs.size();
+        for (uint32_t s = 0; s < S; ++s) {
+            jobs.push_back(StripeJob{moff, roff, t, s, (uint32_t)cap, 0u});
+            moff += 2 * cap;
+            roff += SH;
+        }
+    }
+    uint32_t njobs = (uint32_t)jobs.size();
+    const uint64_t need = moff + roff * 8 + (uint64_t)njobs * (16 + 32 + 16 + sizeof(StripeJob)) + 4u * ntasks + 4096;
+    const auto it = ctx->bufs.find("tb_moves");
+    const uint64_t have = it == ctx->bufs.end() ? 0 : it->second.cap;
+    if (njobs && ctx->used - std::min(ctx->used, have) + need > ctx->budget) {
+        njobs = 0;  // not enough scratch: every pair walks sequentially
+        std::fill(base.begin(), base.end(), 0xffffffffu);
+    }
+    int rc;
+    void *vm = nullptr, *vr = nullptr, *va = nullptr, *vb = nullptr, *vs = nullptr, *vj = nullptr, *vbase = nullptr;
+    if (njobs) {
+        if ((rc = scratch(ctx, "tb_moves", moff, &vm))) return rc;
+        if ((rc = scratch(ctx, "tb_rows", roff * 8, &vr))) return rc;
+        if ((rc = scratch(ctx, "tb_asum", (size_t)njobs * 16, &va))) return rc;
+        if ((rc = scratch(ctx, "tb_bsum", (size_t)njobs * 32, &vb))) return rc;
+        if ((rc = scratch(ctx, "tb_seg", (size_t)njobs * 16, &vs))) return rc;
+    }
+    // one pair: the jobs are implicit (stripe s = job s); else upload them
+    const bool implicit = !dev;
+    const uint32_t lcap = njobs ? jobs[0].lcap : 0u;
+    if (!implicit) {
+        if ((rc = scratch(ctx, "tb_base", (size_t)ntasks * 4, &vbase))) return rc;
+        cudaError_t e = cudaMemcpyAsync(vbase, base.data(), (size_t)ntasks * 4, cudaMemcpyHostToDevice, ctx->stream);
+        if (e == cudaSuccess && njobs) {
+            if ((rc = scratch(ctx, "tb_jobs", (size_t)njobs * sizeof(StripeJob), &vj))) return rc;
+            e = cudaMemcpyAsync(vj, jobs.data(), (size_t)njobs * sizeof(StripeJob), cudaMemcpyHostToDevice,
+                                ctx->stream);
+        }
+        // the host vectors die on return: wait for the copies
+        if (e == cudaSuccess) e = cudaStreamSynchronize(ctx->stream);
+        if (e != cudaSuccess) return cuda_fail(ctx, e, "stripe job upload");
+    }
+    const StripeJob *dj = (const StripeJob *)vj;
+    const uint32_t blocks = (njobs + kWalkWarps - 1) / kWalkWarps;
+    if (njobs) {
+        {
+            LaunchTimer t(ctx, "tb_spec");
+            k_tb_stripes<R, false><<<blocks, kWalkWarps * 32, 0, ctx->stream>>>(
+                one, dev, dj, njobs, lcap, (uint8_t *)vm, (uint2 *)vr, (uint4 *)va, (uint4 *)vb);
+        }
+        {
+            LaunchTimer t(ctx, "tb_link");
+            k_tb_stripes<R, true><<<blocks, kWalkWarps * 32, 0, ctx->stream>>>(
+                one, dev, dj, njobs, lcap, (uint8_t *)vm, (uint2 *)vr, (uint4 *)va, (uint4 *)vb);
+        }
+    }
+    {
+        LaunchTimer t(ctx, "tb_stitch");
+        k_tb_stitch<R><<<ntasks, 32, 0, ctx->stream>>>(one, dev, (const uint32_t *)vbase, dj, njobs, lcap,
+                                                       (const uint2 *)vr, (const uint4 *)va, (const uint4 *)vb,
+                                                       (uint4 *)vs, ctx->d_err);
+    }
+    if (njobs) {
+        LaunchTimer t(ctx, "tb_copy");
+        k_tb_copy<R><<<blocks, kWalkWarps * 32, 0, ctx->stream>>>(one, dev, dj, njobs, lcap, (const uint8_t *)vm,
+                                                                  (const uint4 *)vs);
+    }
+    cudaError_t e = cudaGetLastError();
+    return e == cudaSuccess ? NW_OK : cuda_fail(ctx, e, "traceback launch");
+}
+
+int launch_trace(nw_ctx *ctx, int R, const TraceTask *host, const TraceTask *dev, uint32_t ntasks, uint32_t mflag) {
+    if (ntasks == 0) return NW_OK;
+    int rc;
+    switch (R) {
+        case 2: rc = launch_walks<2>(ctx, host, dev, ntasks); break;
+        case 4: rc = launch_walks<4>(ctx, host, dev, ntasks); break;
+        case 8: rc = launch_walks<8>(ctx, host, dev, ntasks); break;
+        case 16: rc = launch_walks<16>(ctx, host, dev, ntasks); break;
+        default: return fail(ctx, NW_ERR_ARG, "unsupported rows per lane %d", R);
+    }
+    return rc ? rc : launch_finish(ctx, host[0], dev, ntasks, mflag);
 }
 
 }  // namespace nw
