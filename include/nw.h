@@ -135,8 +135,8 @@ uint64_t nw_cigar_bound(uint64_t m, uint64_t n);
  * Memory.  The CIGAR normally comes from a full matrix of 2-bit pointers,
  * about m*n/4 bytes of scratch.  When that does not fit the context budget
  * (or with NW_RECOMPUTE) the call switches to stripe-checkpoint recompute:
- * a score-only fill keeps one W row per 32*R*4 rows (R = 4 rows per lane
- * from m >= 1024, else 2; about 8*(n+128) bytes per kept row), then the
+ * a score-only fill keeps one W row per 32*R*4 rows (R = 8 rows per lane
+ * from m >= 2048, else 4; about 4*(n+128) bytes per kept row), then the
  * pointers are filled again wave by wave from the bottom, each wave as many
  * row groups as the remaining budget holds, and the traceback walks each
  * wave before the next is computed.  Same result, at most twice the fill

@@ -11,9 +11,9 @@
 // take pairs from an atomic queue sorted by descending cell count (longest
 // processing time first), which balances uneven lengths.
 //
-// The cell update is the one of nw_single.cu (W domain, prmt + DPX add-max
-// + max; with pointers: prmt + add + two max, the pointer bits taken from
-// differences).
+// The cell update is the one of the single-pair kernels (W domain: prmt +
+// DPX add-max + max; with pointers: prmt + max + DPX add-max, and two sign
+// bits appended by funnel shifts, see ptr_append).
 #include <algorithm>
 #include <cstring>
 #include <numeric>
@@ -117,7 +117,7 @@ __global__ void __launch_bounds__(kBatchWarps * 32) k_batch(BatchArgs p) {
         uint32_t prof[R];
         int32_t Wl[R];
         int32_t dtop = 0;
-        uint32_t xout = 0, bits = 0;
+        uint32_t xout = 0, accL = 0, accH = 0;
         int32_t cb = cbeg(0), ce = cend(0);   // this lane's stripe columns
         auto init_rows = [&](uint32_t codes, uint32_t st) {
             const uint32_t i0 = st * SH + (uint32_t)lane * R;  // 1-based row above the lane's first row
@@ -174,21 +174,18 @@ __global__ void __launch_bounds__(kBatchWarps * 32) k_batch(BatchArgs p) {
                 const int32_t up = (int32_t)x >> 2;
                 const uint32_t sel = sext_selector(x & 3u);
                 int32_t d = dtop, u = up;
-                uint32_t code = 0;
 #pragma unroll
                 for (int r = 0; r < R; ++r) {
                     const int32_t sv = (int32_t)prmt(prof[r], 0u, sel);
                     int32_t w;
                     if constexpr (PTR) {
-                        // bit0: diagonal is the maximum; bit1: W == up (the
-                        // vertical candidate wins over the horizontal one
-                        // whenever the diagonal loses) -- from differences,
+                        // pointer bits: signs of d + s' - max(u, l) and u - l,
                         // off the dependency chain
-                        const int32_t t1 = d + sv;
-                        w = max(t1, max(u, Wl[r]));
+                        const int32_t l = Wl[r], m2 = max(u, l);
+                        w = __viaddmax_s32(d, sv, m2);
                         if (mask && (uint32_t)(D0 - r - lo) > (uint32_t)(hi - lo)) w = kNegW;
-                        const uint32_t bits = 3u - (uint32_t)min(w - t1, 1) - (uint32_t)min(2 * (w - u), 2);
-                        code |= bits << (2 * r);
+                        accL = ptr_append(accL, d + sv - m2);
+                        accH = ptr_append(accH, u - l);
                     } else {
                         w = max(__viaddmax_s32(d, sv, Wl[r]), u);
                         if (mask && (uint32_t)(D0 - r - lo) > (uint32_t)(hi - lo)) w = kNegW;
@@ -201,10 +198,10 @@ __global__ void __launch_bounds__(kBatchWarps * 32) k_batch(BatchArgs p) {
                 xout = ((uint32_t)u << 2) | (x & 3u);
                 if constexpr (PTR) {
                     const uint32_t cc = (uint32_t)c % CPW;
-                    bits |= code << (2u * R * cc);
                     if (cc == CPW - 1 || col == ce) {
-                        pbase[(size_t)(s * 32u + lane) * tk.ncg + (uint32_t)c / CPW] = bits;
-                        bits = 0;
+                        const uint32_t miss = (CPW - 1 - cc) * R;  // cells a row's last word lacks
+                        pbase[(size_t)(s * 32u + lane) * tk.ncg + (uint32_t)c / CPW] =
+                            ptr_word(accL << miss, accH << miss);
                     }
                 }
                 if (lane == 31 && s + 1 < S) ring[col] = xout;

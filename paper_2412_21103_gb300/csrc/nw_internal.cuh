@@ -80,6 +80,26 @@ __device__ __forceinline__ uint32_t prmt(uint32_t lo, uint32_t hi, uint32_t sel)
 // it to 32 bits: nibble 0 picks the byte, nibbles 1..3 replicate its sign.
 __device__ __forceinline__ uint32_t sext_selector(uint32_t code) { return code * 0x1111u + 0x8880u; }
 
+// Pointer words (the fill kernels write them, the traceback reads them).
+// Each cell gets two bits: L = its diagonal candidate is below the maximum,
+// H = its horizontal candidate is above the vertical one.  The Sec. 2.4 walk
+// with priority diagonal > vertical > horizontal reads: !L -> diagonal, else
+// !H -> vertical (consumes a base of A: 'I'), else horizontal ('D').  A word
+// holds R rows x 16/R columns of one lane; the cell in row r, column c of the
+// word has index o = c*R + r, its L bit at 31 - o and its H bit at 15 - o.
+// The fill appends sign bits -- of d + s' - max(u, l) for L and of u - l for
+// H -- cells in index order, one funnel shift each, into two registers, and
+// joins their low halves with one byte permute.
+__device__ __forceinline__ uint32_t ptr_append(uint32_t acc, int32_t diff) {
+    return __funnelshift_l((uint32_t)diff, acc, 1);  // (acc << 1) | sign bit of diff
+}
+__device__ __forceinline__ uint32_t ptr_word(uint32_t accL, uint32_t accH) { return __byte_perm(accH, accL, 0x5410); }
+// Move of cell o of a word: 0 diagonal, 1 vertical, 2 horizontal.
+__device__ __forceinline__ uint32_t ptr_move(uint32_t word, uint32_t o) {
+    const uint32_t L = (word >> (31u - o)) & 1u, H = (word >> (15u - o)) & 1u;
+    return L ? (H ? 2u : 1u) : 0u;
+}
+
 // 2-bit code of base k of a packed sequence.
 __device__ __forceinline__ uint32_t base_at(const uint8_t *s2b, uint64_t k) {
     return (s2b[k >> 2] >> ((k & 3) * 2)) & 3u;
@@ -207,7 +227,8 @@ cudaError_t fill_score_with_scratch(const uint8_t *a2b, uint32_t m, const uint8_
 // CTA ("group"); the bottom W row of every group but the last is kept in
 // `bnd` (the checkpoints of the recompute traceback).
 struct PairFill {
-    int R = 4, nw = 4;
+    int R = 4, C = 4, nw = 4;      // rows per lane, columns per step, warps per CTA
+    const uint32_t *sel = nullptr; // column selector table (null: built here)
     bool ptr = false;              // write 2-bit pointers
     uint32_t *ptr_words = nullptr; // pointer words of stripes [cs_lo*nw, ...)
     uint32_t ncg = 0;              // pointer words per lane row

@@ -2,57 +2,61 @@
 //
 // Work split.  Stripes of 32*R rows go to warps; lane k of a warp owns R
 // consecutive rows.  At step t lane k updates a register block of R rows x C
-// columns (C = 16/R, so the block's 2-bit pointers make exactly one 32-bit
-// word) for column block q = t - k.  The block's top row arrives from lane
-// k-1 by C warp shuffles, its left column and corner stay in registers; the
-// dependency chain through a block runs along its anti-diagonal (R+C-1
-// cells), and one shuffle latency is paid per C columns instead of per
-// column.
+// columns for column block q = t - k.  The block's top row arrives from lane
+// k-1 by C warp shuffles, its left column and corner stay in registers, and
+// the column selectors (which byte of the row profile a column's base picks)
+// come from a per-column table that stays in L1.  The dependency chain
+// through a block runs along its anti-diagonals (R+C-1 cells), and one
+// shuffle latency is paid per C columns instead of per column.
 //
-// Handoffs.  The NW warps of a CTA own NW consecutive stripes.  A stripe's
-// bottom row goes to the next warp through a ring in shared memory (Q
-// columns; the producer publishes a head every KQ columns after a CTA-scope
-// fence, the consumer a tail; both waits are bounded).  The first warp of a
-// CTA fills its own ring: from B for stripe 0, else from the previous CTA's
-// last warp, which writes its bottom row to global memory and releases a
-// gpu-scope progress counter every GQ columns.  Lane 0's input reaches it
-// through the rotation shuffle: lane 31 loads the ring block (after storing
-// its own finished block) and shuffles it to lane 0 with everything else.
-// CTAs take CTA-stripes round robin; the grid never exceeds the co-resident
-// CTA count, so every wait ends (and all of them are bounded regardless).
+// Handoffs.  The NW compute warps of a CTA own NW consecutive stripes (a
+// "group").  A stripe's bottom row goes to the next warp through a ring in
+// shared memory (Q columns; the producer publishes a head every KQ columns
+// after a CTA-scope fence, the consumer a tail; both waits are bounded).
+// One more warp per CTA, the courier, does all global-memory traffic: it
+// fills the first warp's ring with the previous group's bottom row (zeros
+// for grid row 0) as that group releases it, and drains the last warp's
+// ring to global memory, releasing a gpu-scope progress counter; its L2
+// round trips stall no compute warp.  Lane 0's input reaches it from the
+// ring, broadcast to the warp; lane 31 stores its finished block into the
+// next ring.  CTAs take groups round robin; the grid never exceeds the
+// co-resident CTA count, so every wait ends (and all of them are bounded
+// regardless).
 //
-// The cell update (W domain: prmt + DPX add-max + max) and the pointer
-// encoding (bit0: diagonal is the maximum, bit1: vertical >= horizontal) are
-// those of the other kernels (the pointer bits are computed from differences
-// rather than with the predicate-returning DPX max, whose dependent latency
-// is several times longer); the pointer word layout [stripe][lane][block]
-// with bit 2*(c*R + r) for block row r, column c is the one the traceback
-// reads.  The step loop runs in three phases (lanes starting, all lanes busy,
-// lanes finishing) so the busy phase has no per-lane tests.
+// The kept group rows double as the checkpoints of the recompute traceback:
+// a launch may run a range of groups, each starting from the previous
+// group's kept row, write no rows, and compute only the columns left of a
+// device-resident column count.
+//
+// The cell update is W = max(d + s', max(u, l)) in the W domain (one prmt,
+// one max, one DPX add-max); with pointers each cell also appends the sign
+// bits of d + s' - max(u, l) and u - l (ptr_append), and words of R rows x
+// 16/R columns are stored [stripe][lane][word].  The step loop runs in three
+// phases (lanes starting, all lanes busy, lanes finishing) so the busy phase
+// has no per-lane tests.
 #include <algorithm>
 
 #include "nw_internal.cuh"
 
 namespace nw {
 
-constexpr int kPairQ = 256;      // ring columns per warp
-constexpr int kPairKQ = 32;      // ring flag granularity (columns)
-constexpr int kPairGQ = 64;      // global progress granularity (columns)
+constexpr int kPairQ = 256;   // ring columns per warp
+constexpr int kPairKQ = 16;   // ring flag granularity (columns)
 constexpr int kPairMaxWarps = 8;
 
 struct PairArgs {
     const uint8_t *a;
-    const uint8_t *b;
+    const uint32_t *sel;  // column selectors (sext_selector of each base of B), >= NB*C entries
     uint32_t m, n;
     uint32_t prof[4];
     int32_t gap;
-    uint32_t S;          // stripes
-    uint32_t bstride;    // words per global boundary row (>= NB*C, multiple of 64)
-    uint32_t *bnd;       // global boundary rows: row g = bottom of group g (0-based columns)
-    uint32_t *progress;  // per group: columns of its global row released
-    uint32_t *ptr;       // pointer words of stripes s_ptr0.. (null: score only)
-    uint32_t ncg;        // pointer words per lane row (>= NB)
-    uint32_t s_ptr0;     // first stripe with pointer words in `ptr`
+    uint32_t S;              // stripes
+    uint32_t bstride;        // words per global group row (>= NB*C)
+    uint32_t *bnd;           // global rows: row g = bottom W row of group g (0-based columns)
+    uint32_t *progress;      // per group: columns of its global row released
+    uint32_t *ptr;           // pointer words of stripes s_ptr0.. (null: score only)
+    uint32_t ncg;            // pointer words per lane row (>= NB*C/(16/R))
+    uint32_t s_ptr0;         // first stripe with pointer words in `ptr`
     uint32_t cs_lo, cs_hi;   // groups (CTA-stripes) to run
     const uint32_t *ncols;   // null, or a device word: only columns [0, *ncols) are needed
     uint32_t recompute;      // groups start from kept rows and write none
@@ -86,6 +90,8 @@ __device__ __forceinline__ void st_vec(uint32_t *dst, const uint32_t (&v)[N]) {
         *reinterpret_cast<uint4 *>(dst) = make_uint4(v[0], v[1], v[2], v[3]);
     } else if constexpr (N == 2) {
         *reinterpret_cast<uint2 *>(dst) = make_uint2(v[0], v[1]);
+    } else if constexpr (N == 1) {
+        *dst = v[0];
     } else {
 #pragma unroll
         for (int c = 0; c < N; c += 4) *reinterpret_cast<uint4 *>(dst + c) = make_uint4(v[c], v[c + 1], v[c + 2], v[c + 3]);
@@ -100,12 +106,51 @@ __device__ __forceinline__ void ld_vec(uint32_t (&v)[N], const uint32_t *src) {
     } else if constexpr (N == 2) {
         const uint2 q = *reinterpret_cast<const uint2 *>(src);
         v[0] = q.x; v[1] = q.y;
+    } else if constexpr (N == 1) {
+        v[0] = *src;
     } else {
 #pragma unroll
         for (int c = 0; c < N; c += 4) {
             const uint4 q = *reinterpret_cast<const uint4 *>(src + c);
             v[c] = q.x; v[c + 1] = q.y; v[c + 2] = q.z; v[c + 3] = q.w;
         }
+    }
+}
+
+// Predicated vector store through a generic address: one store instruction
+// with a predicate, no branch (a lane-divergent branch around the store
+// costs a warp tens of cycles per step).
+template <int N>
+__device__ __forceinline__ void st_vec_if(bool p, uint32_t *dst, const uint32_t (&v)[N]) {
+    if constexpr (N == 4) {
+        asm volatile("{.reg .pred q; setp.ne.b32 q, %0, 0; @q st.v4.u32 [%1], {%2, %3, %4, %5};}" ::"r"((uint32_t)p),
+                     "l"(dst), "r"(v[0]), "r"(v[1]), "r"(v[2]), "r"(v[3])
+                     : "memory");
+    } else if constexpr (N == 2) {
+        asm volatile("{.reg .pred q; setp.ne.b32 q, %0, 0; @q st.v2.u32 [%1], {%2, %3};}" ::"r"((uint32_t)p), "l"(dst),
+                     "r"(v[0]), "r"(v[1])
+                     : "memory");
+    } else {
+#pragma unroll
+        for (int c = 0; c < N; c += 4)
+            asm volatile("{.reg .pred q; setp.ne.b32 q, %0, 0; @q st.v4.u32 [%1], {%2, %3, %4, %5};}" ::"r"((uint32_t)p),
+                         "l"(dst + c), "r"(v[c]), "r"(v[c + 1]), "r"(v[c + 2]), "r"(v[c + 3])
+                         : "memory");
+    }
+}
+
+// Column selectors of block q (read-only path: the table stays in L1).
+template <int C>
+__device__ __forceinline__ void ld_sel(uint32_t (&v)[C], const uint32_t *tab, uint32_t q) {
+    if constexpr (C == 4) {
+        const uint4 x = __ldg(reinterpret_cast<const uint4 *>(tab) + q);
+        v[0] = x.x; v[1] = x.y; v[2] = x.z; v[3] = x.w;
+    } else if constexpr (C == 2) {
+        const uint2 x = __ldg(reinterpret_cast<const uint2 *>(tab) + q);
+        v[0] = x.x; v[1] = x.y;
+    } else {
+#pragma unroll
+        for (int c = 0; c < C; ++c) v[c] = __ldg(tab + q * C + c);
     }
 }
 
@@ -116,32 +161,29 @@ struct LaneState {
     int32_t Wl[R];     // left column of the next block
     int32_t last[R];   // values of column n-1 (for the score)
     int32_t corner;    // W(top-1, left column)
-    uint32_t outW[C];  // bottom row of the last block (lane 31: ring input for lane 0)
-    uint32_t outS[C];  // column selectors travelling with it
+    uint32_t outW[C];  // bottom row of the last block (lane 31: the next stripe's input)
+    uint32_t accL, accH;  // pointer bits of the word being filled
 };
 
-// One step of a lane: block q = t - lane.  inW/inS: the ring block of
-// column block t (lane 0's top row).  CHECK: lanes may be idle (lead / drain
-// phases) and the last block may be in this step.  Cells are visited along
-// anti-diagonals of the R x C block so consecutive instructions are
-// independent.
+// One step of a lane: block q = t - lane.  inW: the ring block of column
+// block t (lane 0's top row); sel: the selectors of block q.  CHECK: lanes
+// may be idle (lead / drain phases) and the last block may be in this step.
+// Cells are visited along anti-diagonals of the R x C block so consecutive
+// instructions are independent.
 template <int R, int C, bool PTR, bool CHECK>
-__device__ __forceinline__ void pair_block(LaneState<R, C> &st, const uint32_t (&inW)[C], const uint32_t (&inS)[C],
+__device__ __forceinline__ void pair_block(LaneState<R, C> &st, const uint32_t (&inW)[C], const uint32_t (&sel)[C],
                                            int32_t q, uint32_t NB, uint32_t qL, uint32_t cL, int lane,
                                            uint32_t *prow) {
+    constexpr uint32_t SPW = (16u / R) / C;  // steps per pointer word
     int32_t up[C];
-    uint32_t sel[C];
 #pragma unroll
     for (int c = 0; c < C; ++c) {
         const uint32_t w = __shfl_up_sync(kFull, st.outW[c], 1);
-        const uint32_t x = __shfl_up_sync(kFull, st.outS[c], 1);
         up[c] = (int32_t)(lane == 0 ? inW[c] : w);
-        sel[c] = lane == 0 ? inS[c] : x;
     }
     if (CHECK && !(q >= 0 && q < (int32_t)NB)) return;
-    // V[r][c] after the step; inputs: left column st.Wl, top row up, corner
     int32_t V[R][C];
-    uint32_t code = 0;
+    int32_t DL[R][C], DH[R][C];
 #pragma unroll
     for (int k = 0; k < R + C - 1; ++k) {
 #pragma unroll
@@ -152,26 +194,16 @@ __device__ __forceinline__ void pair_block(LaneState<R, C> &st, const uint32_t (
             const int32_t l = c ? V[r][c - 1] : st.Wl[r];
             const int32_t d = r ? (c ? V[r - 1][c - 1] : st.Wl[r - 1]) : (c ? up[c - 1] : st.corner);
             const int32_t sv = (int32_t)prmt(st.prof[r], 0u, sel[c]);
+            const int32_t m2 = max(u, l);
+            V[r][c] = __viaddmax_s32(d, sv, m2);
             if constexpr (PTR) {
-                // plain maxes on the dependency chain; the two pointer bits
-                // come from differences off the chain: bit0 = diagonal is the
-                // maximum (W == d+s'), bit1 = vertical >= horizontal, which
-                // when the diagonal loses is W == u
-                const int32_t t1 = d + sv;
-                const int32_t wv = max(t1, max(u, l));
-                V[r][c] = wv;
-                const uint32_t bits = 3u - (uint32_t)min(wv - t1, 1) - (uint32_t)min(2 * (wv - u), 2);
-                code |= bits << (2 * (c * R + r));
-            } else {
-                V[r][c] = max(__viaddmax_s32(d, sv, l), u);
+                DL[r][c] = d + sv - m2;  // < 0: the diagonal candidate loses
+                DH[r][c] = u - l;        // < 0: horizontal beats vertical
             }
         }
     }
 #pragma unroll
-    for (int c = 0; c < C; ++c) {
-        st.outW[c] = (uint32_t)V[R - 1][c];
-        st.outS[c] = sel[c];
-    }
+    for (int c = 0; c < C; ++c) st.outW[c] = (uint32_t)V[R - 1][c];
     if (CHECK && (uint32_t)q == qL) {
 #pragma unroll
         for (int c = 0; c < C; ++c)
@@ -183,30 +215,132 @@ __device__ __forceinline__ void pair_block(LaneState<R, C> &st, const uint32_t (
 #pragma unroll
     for (int r = 0; r < R; ++r) st.Wl[r] = V[r][C - 1];
     st.corner = up[C - 1];
-    if constexpr (PTR) prow[q] = code;
+    if constexpr (PTR) {
+        // two independent chains of funnel shifts, cells in word order
+#pragma unroll
+        for (int c = 0; c < C; ++c)
+#pragma unroll
+            for (int r = 0; r < R; ++r) {
+                st.accL = ptr_append(st.accL, DL[r][c]);
+                st.accH = ptr_append(st.accH, DH[r][c]);
+            }
+        const uint32_t qq = (uint32_t)q;
+        if (SPW == 1 || qq % SPW == SPW - 1) {
+            prow[qq / SPW] = ptr_word(st.accL, st.accH);
+        } else if (CHECK && qq == NB - 1) {
+            const uint32_t miss = (SPW - 1 - qq % SPW) * R * C;  // the row's last word is short
+            prow[qq / SPW] = ptr_word(st.accL << miss, st.accH << miss);
+        }
+    }
 }
 
-template <int R, bool PTR>
-__global__ void __launch_bounds__(kPairMaxWarps * 32, 1) k_pair(PairArgs p) {
-    constexpr int C = 16 / R;
+// The courier warp of a CTA: all global-memory traffic of the group's rows.
+// Incoming: the previous group's kept bottom row (or the zeros of grid row
+// 0) into ring 0, published by head[0] as the producer releases it.
+// Outgoing: the last compute warp's bottom row from ring NW to global
+// memory, released every few chunks.  The compute warps only ever wait on
+// shared-memory counters; the round trips to L2 stall this warp alone.
+template <int C>
+__device__ __forceinline__ void pair_courier(const PairArgs &p, uint32_t cs, uint32_t NW, uint32_t NB,
+                                             uint32_t (*ringW)[kPairQ], volatile uint32_t *head,
+                                             volatile uint32_t *tail) {
+    constexpr uint32_t QB = kPairQ / C;
+    constexpr uint32_t KB = kPairKQ / C;
+    constexpr uint32_t MAXB = 8 * KB;  // blocks moved per step of the loop (128 columns)
+    const int lane = threadIdx.x & 31;
+    const uint32_t last_s = min((cs + 1) * NW, p.S) - 1;
+    const bool in_glob = cs > 0;
+    const bool out_needed = !p.recompute && last_s + 1 < p.S;  // (then the group is full)
+    const uint32_t *gin = in_glob ? p.bnd + (size_t)(cs - 1) * p.bstride : nullptr;
+    uint32_t *gout = out_needed ? p.bnd + (size_t)cs * p.bstride : nullptr;
+    uint32_t delivered = 0, forwarded = 0;
+    uint32_t avail_in = in_glob ? 0u : NB * C;  // columns released upstream (as last seen)
+    uint64_t t_moved = global_ns();
+    uint32_t idle = 0;
+    for (;;) {
+        bool moved = false;
+        if (delivered < NB) {
+            uint32_t next = min(delivered + MAXB, NB);
+            next = min(next, (uint32_t)vld(tail) + QB);  // ring 0 space
+            if (in_glob && avail_in < next * C && avail_in < NB * C) {
+                uint32_t v = 0;
+                if (lane == 0) v = ld_acquire(&p.progress[cs - 1]);
+                avail_in = __shfl_sync(kFull, v, 0);
+            }
+            next = min(next, avail_in / C);
+            if (next > delivered) {
+                if (in_glob) (void)ld_acquire(&p.progress[cs - 1]);  // every lane's loads after the flag
+#pragma unroll
+                for (uint32_t k = 0; k < MAXB * C / 32; ++k) {
+                    const uint32_t col = delivered * C + k * 32u + lane;
+                    if (col < next * C) ringW[0][col % kPairQ] = in_glob ? __ldcg(gin + col) : 0u;
+                }
+                __syncwarp();
+                __threadfence_block();
+                if (lane == 0) head[0] = next;
+                delivered = next;
+                moved = true;
+            }
+        }
+        if (out_needed && forwarded < NB) {
+            const uint32_t avail = vld(head + NW);
+            if (avail > forwarded) {
+                __threadfence_block();
+                const uint32_t upto = min(avail, forwarded + MAXB);
+                uint32_t v[MAXB * C / 32];
+#pragma unroll
+                for (uint32_t k = 0; k < MAXB * C / 32; ++k) {
+                    const uint32_t col = forwarded * C + k * 32u + lane;
+                    v[k] = col < upto * C ? ringW[NW][col % kPairQ] : 0u;
+                }
+                __syncwarp();
+                if (lane == 0) tail[NW] = upto;  // the slots are free once read
+#pragma unroll
+                for (uint32_t k = 0; k < MAXB * C / 32; ++k) {
+                    const uint32_t col = forwarded * C + k * 32u + lane;
+                    if (col < upto * C) __stcg(gout + col, v[k]);
+                }
+                __threadfence();
+                __syncwarp();
+                if (lane == 0) st_release(&p.progress[cs], upto * C);
+                forwarded = upto;
+                moved = true;
+            }
+        }
+        if (delivered >= NB && (!out_needed || forwarded >= NB)) break;
+        if (moved) {
+            idle = 0;
+            t_moved = global_ns();
+        } else {
+            if (vld(p.err) != 0u) break;
+            if ((++idle & 63u) == 0 && global_ns() - t_moved > kSpinNanos) {
+                if (lane == 0) raise_error(p.err, NW_ERR_TIMEOUT, 0x30000u + cs);
+                break;
+            }
+            __nanosleep(20);
+        }
+    }
+}
+
+template <int R, int C, bool PTR>
+__global__ void __launch_bounds__((kPairMaxWarps + 1) * 32, 1) k_pair(PairArgs p) {
     constexpr uint32_t SH = 32u * R;
     constexpr uint32_t QB = kPairQ / C;   // ring capacity in blocks
-    constexpr uint32_t KB = kPairKQ / C;  // blocks per chunk (flags and self-fill)
-    __shared__ __align__(16) uint32_t ringW[kPairMaxWarps][kPairQ];
-    __shared__ __align__(16) uint32_t ringS[kPairMaxWarps][kPairQ];
-    __shared__ uint32_t head[kPairMaxWarps];  // blocks written into ring[w]
-    __shared__ uint32_t tail[kPairMaxWarps];  // blocks of ring[w] consumed
+    constexpr uint32_t KB = kPairKQ / C;  // blocks per chunk (flags)
+    // ring w < NW: input of compute warp w (ring 0 filled by the courier);
+    // ring NW: output of the last compute warp, drained by the courier
+    __shared__ __align__(16) uint32_t ringW[kPairMaxWarps + 1][kPairQ];
+    __shared__ uint32_t head[kPairMaxWarps + 1];  // blocks written into ring[w]
+    __shared__ uint32_t tail[kPairMaxWarps + 1];  // blocks of ring[w] consumed
 
     const int lane = threadIdx.x & 31;
     const int w = threadIdx.x >> 5;
-    const int NW = blockDim.x >> 5;
-    const int src = (lane + 31) & 31;  // rotation: lane 0 hears lane 31
+    const int NW = (int)(blockDim.x >> 5) - 1;  // compute warps; warp NW is the courier
     const uint32_t m = p.m;
     // recompute passes need only the columns left of the traceback's entry
     const uint32_t n = p.ncols ? min(p.n, *p.ncols) : p.n;
     if (n == 0) return;
     const uint32_t NB = (n + C - 1) / C;
-    const uint32_t NBC = NB * C;
     const uint32_t CS = (p.S + NW - 1) / NW;
     const uint32_t sM = (m - 1) / SH, lM = ((m - 1) % SH) / R, rM = (m - 1) % R;
     const uint32_t qL = NB - 1, cL = (n - 1) % C;
@@ -219,7 +353,9 @@ __global__ void __launch_bounds__(kPairMaxWarps * 32, 1) k_pair(PairArgs p) {
         }
         __syncthreads();
         const uint32_t s = cs * NW + w;
-        if (s < p.S) {
+        if (w == NW) {
+            pair_courier<C>(p, cs, NW, NB, ringW, head, tail);
+        } else if (s < p.S) {
             LaneState<R, C> st;
             {
                 const uint32_t row0 = s * SH + lane * R;
@@ -232,71 +368,25 @@ __global__ void __launch_bounds__(kPairMaxWarps * 32, 1) k_pair(PairArgs p) {
                     st.last[r] = 0;
                 }
 #pragma unroll
-                for (int c = 0; c < C; ++c) {
-                    st.outW[c] = 0;
-                    st.outS[c] = 0;
-                }
+                for (int c = 0; c < C; ++c) st.outW[c] = 0;
                 st.corner = 0;
+                st.accL = 0;
+                st.accH = 0;
             }
-            const bool self_fill = w == 0;
             const bool has_next = s + 1 < p.S;
-            const bool out_ring = has_next && w + 1 < NW;
-            const bool out_glob = has_next && w + 1 == NW && !p.recompute;
-            const uint32_t *ginW = (self_fill && cs > 0) ? p.bnd + (size_t)(cs - 1) * 2 * p.bstride : nullptr;
-            const uint32_t *ginS = ginW ? ginW + p.bstride : nullptr;
-            uint32_t *goutW = out_glob ? p.bnd + (size_t)cs * 2 * p.bstride : nullptr;
-            uint32_t *goutS = goutW ? goutW + p.bstride : nullptr;
+            // output ring w+1 (ring NW goes to global memory; not in recompute passes)
+            const bool out_ring = has_next && (w + 1 < NW || !p.recompute);
             uint32_t *prow = PTR ? p.ptr + (size_t)((s - p.s_ptr0) * 32u + lane) * p.ncg : nullptr;
-            const int nx = w + 1 < NW ? w + 1 : w;
             volatile uint32_t *my_head = head + w;
             volatile uint32_t *my_tail = tail + w;
-            volatile uint32_t *nx_head = head + nx;
-            volatile uint32_t *nx_tail = tail + nx;
-            uint32_t *myW = ringW[w], *myS = ringS[w], *nxW = ringW[nx], *nxS = ringS[nx];
-
-            // Self-fill of ring[0]: chunks of 32 columns, lane l holds column
-            // 32k + l; written two chunks ahead of use.
-            uint32_t stW = 0, stS = 0;
+            volatile uint32_t *nx_head = head + w + 1;
+            volatile uint32_t *nx_tail = tail + w + 1;
+            uint32_t *myW = ringW[w], *nxW = ringW[w + 1];
             bool ok = true;
-            auto load_chunk = [&](uint32_t k) -> bool {
-                const uint32_t col = 32u * k + lane;
-                if (32u * k >= NBC) return true;
-                if (ginW) {
-                    int good = 1;
-                    if (lane == 0) good = wait_geq(&p.progress[cs - 1], min(32u * k + 32u, NBC), p.err, s) ? 1 : 0;
-                    good = __shfl_sync(kFull, good, 0);
-                    if (!good) return false;
-                    (void)ld_acquire(&p.progress[cs - 1]);
-                    stW = __ldcg(ginW + col);
-                    stS = __ldcg(ginS + col);
-                } else {
-                    stW = 0;  // grid row 0
-                    stS = sext_selector(col < n ? base_at(p.b, col) : 0u);
-                }
-                return true;
-            };
-            auto put_chunk = [&](uint32_t k) {
-                const uint32_t slot = (32u * k + lane) & (kPairQ - 1);
-                myW[slot] = stW;
-                myS[slot] = stS;
-            };
-            if (self_fill) {
-                ok = load_chunk(0);
-                put_chunk(0);
-                ok = ok && load_chunk(1);
-                put_chunk(1);
-                ok = ok && load_chunk(2);
-                __syncwarp();
-            }
 
             // Chunk bookkeeping before steps [t, t+KB) (warp-uniform).
             auto chunk_begin = [&](uint32_t t) -> bool {
-                if (self_fill) {
-                    const uint32_t k = t / KB + 2;
-                    put_chunk(k);
-                    if (!load_chunk(k + 1)) return false;
-                    __syncwarp();
-                } else if (t < NB) {
+                if (t < NB) {
                     if (!smem_wait_geq(my_head, min(t + KB, NB), p.err, 0x10000u + s)) return false;
                     __threadfence_block();
                 }
@@ -307,74 +397,63 @@ __global__ void __launch_bounds__(kPairMaxWarps * 32, 1) k_pair(PairArgs p) {
                 }
                 return true;
             };
-            // After steps [t, t+KB): publish what lane 31 wrote / lane 31 read.
+            // After steps [t, t+KB): publish what lane 31 wrote / what was read.
             auto chunk_end = [&](uint32_t t) {
                 if (lane == 31) {
-                    if (!self_fill) *my_tail = t + KB;
+                    *my_tail = t + KB;
                     const int32_t done = min((int32_t)t + (int32_t)KB - 31, (int32_t)NB);
-                    if (done > 0) {
-                        if (out_ring) {
-                            __threadfence_block();
-                            *nx_head = (uint32_t)done;
-                        } else if (out_glob) {
-                            st_release(&p.progress[cs], (uint32_t)done * C);
-                        }
+                    if (out_ring && done > 0) {
+                        __threadfence_block();
+                        *nx_head = (uint32_t)done;
                     }
                 }
             };
-            // Input block t for lane 0 (all lanes read it: a broadcast), and
-            // lane 31 hands block t-31 on.
-            auto ring_in = [&](uint32_t t, uint32_t (&iw)[C], uint32_t (&is)[C]) {
-                const uint32_t slot = (t % QB) * C;
-                ld_vec<C>(iw, myW + slot);
-                ld_vec<C>(is, myS + slot);
-            };
+            // Input block t for lane 0 (all lanes read it: a broadcast).
+            auto ring_in = [&](uint32_t t, uint32_t (&iw)[C]) { ld_vec<C>(iw, myW + (t % QB) * C); };
+            // Lane 31 hands block t-31 on (a predicated store: no branch).
             auto lane31_out = [&](uint32_t t) {
                 const int32_t q31 = (int32_t)t - 31;
-                const bool valid = lane == 31 && q31 >= 0 && q31 < (int32_t)NB;
-                if (out_ring) {
-                    if (valid) {
-                        st_vec<C>(nxW + ((uint32_t)q31 % QB) * C, st.outW);
-                        st_vec<C>(nxS + ((uint32_t)q31 % QB) * C, st.outS);
-                    }
-                } else if (out_glob) {
-                    if (valid) {
-                        st_vec<C>(goutW + (uint32_t)q31 * C, st.outW);
-                        st_vec<C>(goutS + (uint32_t)q31 * C, st.outS);
-                    }
-                }
+                const bool valid = out_ring && lane == 31 && q31 >= 0 && q31 < (int32_t)NB;
+                const uint32_t qv = valid ? (uint32_t)q31 : 0u;
+                st_vec_if<C>(valid, nxW + (qv % QB) * C, st.outW);
             };
 
             const uint32_t T = NB + 31;
             // busy chunks: every lane active, none on the last block
             const uint32_t busy_end = NB >= 1 ? NB - 1 : 0;
             uint32_t t = 0;
-            uint32_t inW[C], inS[C];
+            uint32_t inW[C], sel[C];
             while (ok && t < T) {
                 if (!chunk_begin(t)) {
                     ok = false;
                     break;
                 }
                 if (t >= 32 && t + KB <= busy_end) {
-                    ring_in(t, inW, inS);
+                    // selectors two steps ahead (an L1 miss costs more than a step)
+                    uint32_t sel1[C];
+                    ring_in(t, inW);
+                    ld_sel<C>(sel, p.sel, t - (uint32_t)lane);
+                    ld_sel<C>(sel1, p.sel, t + 1 - (uint32_t)lane);
 #pragma unroll
                     for (uint32_t u = 0; u < KB; ++u) {
                         uint32_t nW[C], nS[C];
-                        if (u + 1 < KB) ring_in(t + u + 1, nW, nS);
-                        pair_block<R, C, PTR, false>(st, inW, inS, (int32_t)(t + u) - lane, NB, qL, cL, lane, prow);
+                        if (u + 1 < KB) ring_in(t + u + 1, nW);
+                        if (u + 2 < KB) ld_sel<C>(nS, p.sel, t + u + 2 - (uint32_t)lane);
+                        pair_block<R, C, PTR, false>(st, inW, sel, (int32_t)(t + u) - lane, NB, qL, cL, lane, prow);
                         lane31_out(t + u);
-                        if (u + 1 < KB) {
 #pragma unroll
-                            for (int c = 0; c < C; ++c) {
-                                inW[c] = nW[c];
-                                inS[c] = nS[c];
-                            }
+                        for (int c = 0; c < C; ++c) {
+                            if (u + 1 < KB) inW[c] = nW[c];
+                            sel[c] = sel1[c];
+                            if (u + 2 < KB) sel1[c] = nS[c];
                         }
                     }
                 } else {
                     for (uint32_t u = 0; u < KB; ++u) {
-                        ring_in(t + u, inW, inS);
-                        pair_block<R, C, PTR, true>(st, inW, inS, (int32_t)(t + u) - lane, NB, qL, cL, lane, prow);
+                        ring_in(t + u, inW);
+                        const int32_t q = (int32_t)(t + u) - lane;
+                        ld_sel<C>(sel, p.sel, (uint32_t)min(max(q, 0), (int32_t)NB - 1));
+                        pair_block<R, C, PTR, true>(st, inW, sel, q, NB, qL, cL, lane, prow);
                         lane31_out(t + u);
                     }
                 }
@@ -393,10 +472,16 @@ __global__ void __launch_bounds__(kPairMaxWarps * 32, 1) k_pair(PairArgs p) {
     }
 }
 
-template <int R, bool PTR>
+// Column selectors of B: entry j = sext_selector(B_j), zero-code past n.
+__global__ void k_selectors(const uint8_t *b, uint32_t n, uint32_t count, uint32_t *sel) {
+    for (uint32_t j = blockIdx.x * blockDim.x + threadIdx.x; j < count; j += gridDim.x * blockDim.x)
+        sel[j] = sext_selector(j < n ? base_at(b, j) : 0u);
+}
+
+template <int R, int C, bool PTR>
 static int launch_pair_R(nw_ctx *ctx, PairArgs &pa, int nw) {
     int occ = 0;
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_pair<R, PTR>, nw * 32, 0);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_pair<R, C, PTR>, (nw + 1) * 32, 0);
     if (occ < 1) occ = 1;
     const uint32_t CS = (pa.S + nw - 1) / nw;
     const uint32_t hi = std::min(CS, pa.cs_hi);
@@ -405,22 +490,21 @@ static int launch_pair_R(nw_ctx *ctx, PairArgs &pa, int nw) {
     const uint32_t cap = (uint32_t)occ * (uint32_t)ctx->sm_count;  // co-resident
     if (blocks > cap) blocks = cap;
     LaunchTimer t(ctx, pa.recompute ? "fill_recompute" : PTR ? "fill_ptr" : "fill_score");
-    k_pair<R, PTR><<<blocks, nw * 32, 0, ctx->stream>>>(pa);
+    k_pair<R, C, PTR><<<blocks, (nw + 1) * 32, 0, ctx->stream>>>(pa);
     return NW_OK;
 }
 
-uint32_t pair_bstride(uint32_t n) { return ((n + 64 + 63) / 64) * 64; }  // W row then selector row
+uint32_t pair_bstride(uint32_t n) { return ((n + 64 + 63) / 64) * 64; }
 
 int launch_pair_fill(nw_ctx *ctx, const uint8_t *a2b, uint32_t m, const uint8_t *b2b, uint32_t n, const Profile &pf,
                      const PairFill &f) {
     PairArgs pa{};
     pa.a = a2b;
-    pa.b = b2b;
     pa.m = m;
     pa.n = n;
     for (int c = 0; c < 4; ++c) pa.prof[c] = pf.prof[c];
     pa.gap = pf.gap;
-    const int R = f.R;
+    const int R = f.R, C = f.C;
     const int nw = std::max(1, std::min(f.nw, kPairMaxWarps));
     pa.S = (m + 32u * R - 1) / (32u * R);
     pa.bstride = pair_bstride(n);
@@ -438,7 +522,7 @@ int launch_pair_fill(nw_ctx *ctx, const uint8_t *a2b, uint32_t m, const uint8_t 
     const uint32_t CS = (pa.S + nw - 1) / nw;
     pa.bnd = f.bnd;
     if (!pa.bnd && CS > 1) {
-        if ((rc = scratch(ctx, "pair_bnd", (size_t)(CS - 1) * 2 * pa.bstride * 4, &v))) return rc;
+        if ((rc = scratch(ctx, "pair_bnd", (size_t)(CS - 1) * pa.bstride * 4, &v))) return rc;
         pa.bnd = (uint32_t *)v;
     }
     pa.progress = f.progress;
@@ -447,14 +531,28 @@ int launch_pair_fill(nw_ctx *ctx, const uint8_t *a2b, uint32_t m, const uint8_t 
         pa.progress = (uint32_t *)v;
     }
     if (!f.recompute) cudaMemsetAsync(pa.progress, 0, (size_t)CS * 4, ctx->stream);
-    switch (R * 2 + (f.ptr ? 1 : 0)) {
-        case 4: return launch_pair_R<2, false>(ctx, pa, nw);
-        case 5: return launch_pair_R<2, true>(ctx, pa, nw);
-        case 8: return launch_pair_R<4, false>(ctx, pa, nw);
-        case 9: return launch_pair_R<4, true>(ctx, pa, nw);
-        case 16: return launch_pair_R<8, false>(ctx, pa, nw);
-        case 17: return launch_pair_R<8, true>(ctx, pa, nw);
-        default: return fail(ctx, NW_ERR_ARG, "unsupported rows per lane %d", R);
+    pa.sel = f.sel;
+    if (!pa.sel) {
+        const uint32_t count = pa.bstride;  // >= NB*C for every C
+        if ((rc = scratch(ctx, "pair_sel", (size_t)count * 4, &v))) return rc;
+        LaunchTimer t(ctx, "selectors");
+        k_selectors<<<(count + 255) / 256, 256, 0, ctx->stream>>>(b2b, n, count, (uint32_t *)v);
+        pa.sel = (const uint32_t *)v;
+    }
+    switch (R * 100 + C * 10 + (f.ptr ? 1 : 0)) {
+        case 220: return launch_pair_R<2, 2, false>(ctx, pa, nw);
+        case 221: return launch_pair_R<2, 2, true>(ctx, pa, nw);
+        case 240: return launch_pair_R<2, 4, false>(ctx, pa, nw);
+        case 241: return launch_pair_R<2, 4, true>(ctx, pa, nw);
+        case 280: return launch_pair_R<2, 8, false>(ctx, pa, nw);
+        case 281: return launch_pair_R<2, 8, true>(ctx, pa, nw);
+        case 420: return launch_pair_R<4, 2, false>(ctx, pa, nw);
+        case 421: return launch_pair_R<4, 2, true>(ctx, pa, nw);
+        case 440: return launch_pair_R<4, 4, false>(ctx, pa, nw);
+        case 441: return launch_pair_R<4, 4, true>(ctx, pa, nw);
+        case 820: return launch_pair_R<8, 2, false>(ctx, pa, nw);
+        case 821: return launch_pair_R<8, 2, true>(ctx, pa, nw);
+        default: return fail(ctx, NW_ERR_ARG, "unsupported block shape %d x %d", R, C);
     }
 }
 

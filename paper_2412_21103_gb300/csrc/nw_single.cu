@@ -54,10 +54,11 @@ __device__ __forceinline__ bool warp_wait(const uint32_t *flag, uint32_t target,
     return ok != 0;
 }
 
-template <int R, bool PTR>
+// Score-only fill with a global boundary row between consecutive stripes
+// (the allocation-free entry point's kernel).
+template <int R>
 __global__ void __launch_bounds__(kFillWarps * 32) k_fill(FillArgs p) {
     constexpr uint32_t SH = 32u * R;
-    constexpr uint32_t CPW = PTR ? 16u / R : 1u;
     const int lane = threadIdx.x & 31;
     const uint32_t gw = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const uint32_t nwarps = (gridDim.x * blockDim.x) >> 5;
@@ -78,10 +79,8 @@ __global__ void __launch_bounds__(kFillWarps * 32) k_fill(FillArgs p) {
         for (int r = 0; r < R; ++r) Wl[r] = 0;  // column 0: W(i,0) = 0
         int32_t dtop = 0;                        // W(top-1, j-1)
         uint32_t xout = 0;
-        uint32_t bits = 0;
         const uint32_t *in = s ? p.bnd + (size_t)(s - 1) * p.bstride : nullptr;
         uint32_t *outb = (s + 1 < p.S) ? p.bnd + (size_t)s * p.bstride : nullptr;
-        uint32_t *prow = PTR ? p.ptr + (size_t)(s * 32u + lane) * p.ncg : nullptr;
 
         // Lane-0 input chunks: lane l of `stage` holds the word of column c0 + l
         // (row 0 of the grid: W = 0, only the base code).
@@ -111,33 +110,16 @@ __global__ void __launch_bounds__(kFillWarps * 32) k_fill(FillArgs p) {
                 const int32_t up = (int32_t)(x >> 2);
                 const uint32_t sel = sext_selector(x & 3u);
                 int32_t d = dtop, u = up;
-                uint32_t code = 0;
 #pragma unroll
                 for (int r = 0; r < R; ++r) {
                     const int32_t sv = (int32_t)prmt(prof[r], 0u, sel);
-                    int32_t w;
-                    if constexpr (PTR) {
-                        bool pu, pd;
-                        const int32_t mx = __vibmax_s32(u, Wl[r], &pu);  // vertical >= horizontal
-                        w = __vibmax_s32(d + sv, mx, &pd);                // diagonal is the max
-                        code |= ((uint32_t)pd | ((uint32_t)pu << 1)) << (2 * r);
-                    } else {
-                        w = max(__viaddmax_s32(d, sv, Wl[r]), u);
-                    }
+                    const int32_t w = max(__viaddmax_s32(d, sv, Wl[r]), u);
                     d = Wl[r];
                     Wl[r] = w;
                     u = w;
                 }
                 dtop = up;
                 xout = ((uint32_t)u << 2) | (x & 3u);
-                if constexpr (PTR) {
-                    const uint32_t cc = (uint32_t)c % CPW;
-                    bits |= code << (2u * R * cc);
-                    if (cc == CPW - 1 || c == (int32_t)n - 1) {
-                        prow[(uint32_t)c / CPW] = bits;
-                        bits = 0;
-                    }
-                }
                 if (lane == 31 && outb) {
                     outb[c + 1] = xout;
                     if (((c + 1) & 31) == 0 || c + 1 == (int32_t)n) st_release(&p.progress[s], (uint32_t)c + 1);
@@ -178,26 +160,17 @@ __global__ void k_trivial(uint32_t m, uint32_t n, int32_t gap, int32_t *score, c
 }
 
 // ----------------------------------------------------------------- dispatch
-template <int R, bool PTR>
-static int launch_fill(nw_ctx *ctx, FillArgs &fa) {
-    int occ = 0;
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_fill<R, PTR>, kFillWarps * 32, 0);
-    if (occ < 1) occ = 1;
-    uint32_t blocks = (fa.S + kFillWarps - 1) / kFillWarps;
-    const uint32_t cap = (uint32_t)occ * (uint32_t)ctx->sm_count;  // all CTAs co-resident
-    if (blocks > cap) blocks = cap;
-    LaunchTimer t(ctx, PTR ? "fill_ptr" : "fill_score");
-    k_fill<R, PTR><<<blocks, kFillWarps * 32, 0, ctx->stream>>>(fa);
-    return NW_OK;
-}
-
 // Rows per lane and warps per CTA for the single-pair fill (tunable at run
 // time through NW_PAIR_R / NW_PAIR_WARPS for sweeps).
-static void pair_shape(nw_ctx *ctx, uint64_t m, int &R, int &nw) {
+static void pair_shape(nw_ctx *ctx, uint64_t m, int &R, int &C, int &nw) {
     (void)ctx;
-    R = m >= 32u * 4 * 8 ? 4 : 2;
+    // measured on GB300 (32k x 32k): 8 x 2 blocks lead for long pairs,
+    // 4 x 2 for short ones (fewer idle lanes in the last stripe)
+    R = m >= 2048 ? 8 : 4;
+    C = 2;
     nw = 4;
     if (const char *e = getenv("NW_PAIR_R")) R = atoi(e);
+    if (const char *e = getenv("NW_PAIR_C")) C = atoi(e);
     if (const char *e = getenv("NW_PAIR_WARPS")) nw = atoi(e);
 }
 
@@ -224,12 +197,12 @@ static uint64_t headroom(nw_ctx *ctx, const char *slot) {
 // kept row, so the groups of a wave run side by side -- and the traceback
 // walks through the wave and pauses at its top.  Each wave computes only the
 // columns left of the walk's current cell (read on the device: no host round
-// trip).  Memory: (groups-1) rows of 8(n+128) bytes plus one wave of
+// trip).  Memory: (groups-1) rows of 4(n+128) bytes plus one wave of
 // pointers; work: at most twice the fill.  Decisions depend only on the
 // pointers, which the second pass reproduces exactly, so the alignment is
 // the one the full pointer matrix gives.
 static int run_pair_recompute(nw_ctx *ctx, const uint8_t *a2b, uint32_t m, const uint8_t *b2b, uint32_t n,
-                              const Profile &pf, uint32_t flags, int R, int nw, int32_t *score, char *cigar,
+                              const Profile &pf, uint32_t flags, int R, int C, int nw, int32_t *score, char *cigar,
                               uint64_t *cigar_len, uint8_t *moves, uint64_t *nmoves) {
     const uint32_t SH = 32u * R;
     const uint32_t S = (m + SH - 1) / SH;
@@ -239,7 +212,7 @@ static int run_pair_recompute(nw_ctx *ctx, const uint8_t *a2b, uint32_t m, const
     void *v = nullptr;
     uint32_t *bnd = nullptr;
     if (CS > 1) {
-        if ((rc = scratch(ctx, "ckpt_rows", (size_t)(CS - 1) * 2 * pair_bstride(n) * 4, &v))) return rc;
+        if ((rc = scratch(ctx, "ckpt_rows", (size_t)(CS - 1) * pair_bstride(n) * 4, &v))) return rc;
         bnd = (uint32_t *)v;
     }
     if ((rc = scratch(ctx, "ckpt_progress", (size_t)CS * 4 + 16, &v))) return rc;
@@ -248,6 +221,7 @@ static int run_pair_recompute(nw_ctx *ctx, const uint8_t *a2b, uint32_t m, const
     uint32_t *state = (uint32_t *)v;
     PairFill f;
     f.R = R;
+    f.C = C;
     f.nw = nw;
     f.score = score;
     f.bnd = bnd;
@@ -287,10 +261,11 @@ static int run_pair_recompute(nw_ctx *ctx, const uint8_t *a2b, uint32_t m, const
 static int run_pair(nw_ctx *ctx, const uint8_t *a2b, uint32_t m, const uint8_t *b2b, uint32_t n, const Profile &pf,
                     uint32_t flags, int32_t *score, char *cigar, uint64_t *cigar_len) {
     const bool want = flags & NW_CIGAR;
-    int R, nw;
-    pair_shape(ctx, m, R, nw);
+    int R, C, nw;
+    pair_shape(ctx, m, R, C, nw);
     PairFill f;
     f.R = R;
+    f.C = C;
     f.nw = nw;
     f.score = score;
     if (!want) return launch_pair_fill(ctx, a2b, m, b2b, n, pf, f);
@@ -303,10 +278,10 @@ static int run_pair(nw_ctx *ctx, const uint8_t *a2b, uint32_t m, const uint8_t *
     const uint32_t ncg = ptr_words_per_lane_row(n, R);
     const uint64_t ptr_bytes = (uint64_t)S * 32u * ncg * 4u;
     const uint64_t CS = (S + nw - 1) / nw;
-    const uint64_t rows_bytes = (CS > 1 ? (CS - 1) * 2 * pair_bstride(n) * 4 : 0) + CS * 4 + 1024;
+    const uint64_t rows_bytes = (CS > 1 ? (CS - 1) * pair_bstride(n) * 4 : 0) + 4 * pair_bstride(n) + CS * 4 + 1024;
     // the full pointer matrix, unless it (with the fill's rows) exceeds the budget
     if ((flags & NW_RECOMPUTE) || ptr_bytes + ptr_bytes / 8 + rows_bytes > headroom(ctx, "ptr"))
-        return run_pair_recompute(ctx, a2b, m, b2b, n, pf, flags, R, nw, score, cigar, cigar_len, (uint8_t *)mv,
+        return run_pair_recompute(ctx, a2b, m, b2b, n, pf, flags, R, C, nw, score, cigar, cigar_len, (uint8_t *)mv,
                                   (uint64_t *)nm);
     void *v = nullptr;
     if ((rc = scratch(ctx, "ptr", ptr_bytes, &v))) return rc;
@@ -342,13 +317,13 @@ cudaError_t fill_score_with_scratch(const uint8_t *a2b, uint32_t m, const uint8_
     fa.score = score;
     fa.err = err;
     int occ = 0;
-    cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_fill<R, false>, kFillWarps * 32, 0);
+    cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_fill<R>, kFillWarps * 32, 0);
     if (e != cudaSuccess) return e;
     if (occ < 1) occ = 1;
     uint32_t blocks = (fa.S + kFillWarps - 1) / kFillWarps;
     const uint32_t cap = (uint32_t)occ * (uint32_t)sm_count;  // all CTAs co-resident
     if (blocks > cap) blocks = cap;
-    k_fill<R, false><<<blocks, kFillWarps * 32, 0, stream>>>(fa);
+    k_fill<R><<<blocks, kFillWarps * 32, 0, stream>>>(fa);
     return cudaGetLastError();
 }
 

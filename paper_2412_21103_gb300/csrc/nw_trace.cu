@@ -66,8 +66,7 @@ __global__ void __launch_bounds__(32) k_traceback(TraceTask one, const TraceTask
                 const uint32_t cg = (b1 - cb) / CPW;
                 if (kk / kTileLanes != ckt || cg / kTileWords != cct) break;
                 const uint32_t word = tile[(kk - ckt * kTileLanes) * kTileWords + (cg - cct * kTileWords)];
-                const uint32_t code = (word >> (2u * (((b1 - cb) % CPW) * R + (a1 % R)))) & 3u;
-                const uint32_t mv = (code & 1u) ? 0u : ((code & 2u) ? 1u : 2u);
+                const uint32_t mv = ptr_move(word, ((b1 - cb) % CPW) * R + (a1 % R));
                 p.moves[k++] = (uint8_t)mv;
                 i -= (mv != 2u);
                 j -= (mv != 1u);
@@ -197,8 +196,7 @@ __device__ uint32_t walk_stripe(const TraceTask &p, uint32_t s, uint32_t &i, uin
                     break;
                 }
                 const uint32_t word = tile[(kk % kTileLanes) * kTileWords + cg % kTileWords];
-                const uint32_t code = (word >> (2u * (((b1 - cb) % CPW) * R + (a1 % R)))) & 3u;
-                const uint32_t mv = (code & 1u) ? 0u : ((code & 2u) ? 1u : 2u);
+                const uint32_t mv = ptr_move(word, ((b1 - cb) % CPW) * R + (a1 % R));
                 out[k] = (uint8_t)mv;
                 ++k;
                 if (RECORD && mv != 2u) {  // leaving row i
@@ -238,7 +236,7 @@ __device__ uint32_t walk_stripe(const TraceTask &p, uint32_t s, uint32_t &i, uin
 
 // Spec (LINK = false) or link (LINK = true) walks, one warp per stripe job.
 template <int R, bool LINK>
-__global__ void __launch_bounds__(kWalkWarps * 32) k_tb_stripes(TraceTask one, const TraceTask *many,
+__global__ void __launch_bounds__(kWalkWarps * 32, 1) k_tb_stripes(TraceTask one, const TraceTask *many,
                                                                 const StripeJob *jobs, uint32_t njobs, uint32_t lcap,
                                                                 uint8_t *mbuf, uint2 *rows, uint4 *asum, uint4 *bsum) {
     constexpr uint32_t SH = 32u * R, CPW = 16u / R;

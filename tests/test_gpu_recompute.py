@@ -14,8 +14,8 @@ pytestmark = pytest.mark.gpu
 
 def _geometry(m, n):
     """Rows per lane, groups and per-group pointer bytes of the single-pair
-    path (R = 4 from m >= 1024, else 2; 4 stripes per group)."""
-    R = 4 if m >= 1024 else 2
+    path (R = 8 from m >= 2048, else 4; 4 stripes per group)."""
+    R = 8 if m >= 2048 else 4
     cpw = 16 // R
     ncg = -(-(-(-n // cpw)) // 32) * 32
     S = -(-m // (32 * R))
@@ -28,7 +28,7 @@ def _budget_for(m, n, waves_of=2):
     groups of pointers, but not the whole pointer matrix."""
     R, groups, group_bytes, full = _geometry(m, n)
     bstride = (n + 64 + 63) // 64 * 64
-    rows = max(groups - 1, 0) * 2 * bstride * 4
+    rows = max(groups - 1, 0) * bstride * 4 + 4 * bstride
     small = 64 * 1024 + 8 * (m + n)
     return rows + small + int(waves_of * group_bytes * 1.13) + 4096, full
 

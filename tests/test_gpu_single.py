@@ -159,14 +159,17 @@ def test_cigar_m_flag(ctx):
     assert cig == oracle.rle(ops.replace("=", "M").replace("X", "M"))
 
 
-@pytest.mark.parametrize("R", [2, 4, 8])
+@pytest.mark.parametrize("R,C", [(2, 2), (2, 4), (2, 8), (4, 2), (4, 4), (8, 2)])
 @pytest.mark.parametrize("nwarps", [1, 2, 4, 8])
-def test_pair_kernel_shapes(ctx, R, nwarps, monkeypatch):
-    """Every rows-per-lane / warps-per-CTA shape of the single-pair fill:
-    several CTA stripes (global handoffs) and several warps per CTA (shared
-    memory handoffs), ragged last stripe."""
+def test_pair_kernel_shapes(ctx, R, C, nwarps, monkeypatch):
+    """Every block shape (rows per lane x columns per step) and warps-per-CTA
+    count of the single-pair fill: several CTA stripes (global handoffs),
+    several warps per CTA (shared memory handoffs), ragged last stripe, rows
+    whose last pointer word is short."""
     monkeypatch.setenv("NW_PAIR_R", str(R))
+    monkeypatch.setenv("NW_PAIR_C", str(C))
     monkeypatch.setenv("NW_PAIR_WARPS", str(nwarps))
-    for seed, m, n in [(1, 32 * R * nwarps * 3 + 17, 700), (2, 5000, 301), (3, 64, 2000), (4, 2 * 32 * R + 1, 31)]:
+    for seed, m, n in [(1, 32 * R * nwarps * 3 + 17, 700), (2, 5000, 301), (3, 64, 2000), (4, 2 * 32 * R + 1, 31),
+                       (5, 300, 16 // R * 7 + 1)]:
         p = seqgen.long_mutated_pair(seed, m=m)
         _check(ctx, p.a, p.b[:n] if n < p.b.size else p.b)
