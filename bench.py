@@ -34,12 +34,15 @@ METRIC = "GCUPS on 1 GB300 and % of int/DPX roofline; learned-band+batched vs pl
 SCORING = (1, -1, -1)
 L2_FLUSH_BYTES = 256 << 20   # > 129 MB L2
 OPS_PER_CELL = 3             # algorithmic minimum in the W domain: prmt + add-max + max
+PEAK_KINDS = (0, 2, 4)       # nw_peak_int kinds: DPX add-max, max, prmt (lane-ops/s each)
+STEPS_DEFAULT = {"pair32k": 100, "pair1k": 200, "allpairs": 20, "band": 3}
 
 
 def parse():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--steps", type=int, default=None,
+                    help="timed steps (default per workload: pair32k 100, pair1k 200, allpairs 20, band 3)")
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="pair32k", choices=["pair32k", "pair1k", "allpairs", "band", "serve"])
@@ -91,7 +94,8 @@ class ClockSampler:
     def __init__(self, index: int):
         self.index = index
         self.proc = None
-        self.lines: list[str] = []
+        self.lines: list[tuple[float, str]] = []
+        self.t0 = self.t1 = None
 
     def __enter__(self):
         try:
@@ -110,7 +114,11 @@ class ClockSampler:
 
     def _read(self):
         for ln in self.proc.stdout:
-            self.lines.append(ln.strip())
+            self.lines.append((time.perf_counter(), ln.strip()))
+
+    def window(self, t0: float, t1: float):
+        """The timed region; only samples taken inside it count."""
+        self.t0, self.t1 = t0, t1
 
     def __exit__(self, *exc):
         if self.proc:
@@ -123,7 +131,9 @@ class ClockSampler:
     def summary(self):
         sm, mx, reasons = [], 0.0, set()
         names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
-        for ln in self.lines:
+        for ts, ln in self.lines:
+            if self.t0 is not None and not (self.t0 <= ts <= self.t1 + 0.15):
+                continue  # (a sample reaches us up to one period after it was taken)
             parts = [x.strip() for x in ln.split(",")]
             if len(parts) < 7:
                 continue
@@ -195,7 +205,7 @@ def run_reference(args):
     for _ in range(args.warmup):
         sample_fn(data, budget_s=1.0)
     for _ in range(args.steps):
-        g, cores, sample = sample_fn(data, budget_s=max(2.0, 60.0 / max(args.steps, 1)))
+        g, cores, sample = sample_fn(data, budget_s=max(0.5, 60.0 / max(args.steps, 1)))
         vals.append(g)
     v = statistics.mean(vals)
     line = {"impl": "reference", "metric": METRIC, "value": v, "unit": "GCUPS", "n_gpus": args.gpus,
@@ -477,13 +487,17 @@ def run_ours(args):
     work = {"allpairs": AllPairsWork, "band": BandWork}.get(args.workload, PairWork)(nw, ctx, dev, args.workload)
     flush = torch.empty(L2_FLUSH_BYTES, dtype=torch.uint8, device=dev)
 
+    # clock samples: nvidia-smi starts now (it takes a while to print its
+    # first line); only the samples inside the timed region are kept
+    clk = ClockSampler(local) if not args.no_clocks else _Null()
+    clk.__enter__()
     for _ in range(max(args.warmup, 3)):
         work.step()
     ctx.sync()
 
-    # integer-pipe peak (roofline denominator), measured live: lane-ops/s of
-    # the score-only cell mix (3 ALU-pipe instructions per cell)
-    peak_ops = nw.nw_peak_int(ctx, 5, 1 << 15) * OPS_PER_CELL
+    # integer-pipe peak (roofline denominator), measured live: the instructions of the cell update, each alone on every SM; the slowest
+    # of them bounds the cell rate (3 of them per cell)
+    peak_ops = min(nw.nw_peak_int(ctx, kind, 1 << 15) for kind in PEAK_KINDS)
 
     band0 = nw.nw_ctx_band_stats(ctx)["band_cells"]
     ctx.reset_stats()
@@ -493,14 +507,17 @@ def run_ours(args):
     torch.cuda.synchronize(dev)
     evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
     wall0 = time.perf_counter()
-    with (ClockSampler(local) if not args.no_clocks else _Null()) as clk:
-        for k in range(args.steps):
-            flush.zero_()                       # evict L2 between timed steps
-            evs[k][0].record(stream)
-            work.step()
-            evs[k][1].record(stream)
-        torch.cuda.synchronize(dev)
-    wall = time.perf_counter() - wall0
+    for k in range(args.steps):
+        flush.zero_()                       # evict L2 between timed steps
+        evs[k][0].record(stream)
+        work.step()
+        evs[k][1].record(stream)
+    torch.cuda.synchronize(dev)
+    wall1 = time.perf_counter()
+    wall = wall1 - wall0
+    clk.window(wall0, wall1)
+    time.sleep(0.2)                         # the last in-window sample arrives
+    clk.__exit__(None, None, None)
     ctx.set_profiling(False)
     ms = statistics.mean(e0.elapsed_time(e1) for e0, e1 in evs)
     ctx.sync()
@@ -543,7 +560,8 @@ def run_ours(args):
         "roofline": {"bound": "alu", "kernel": work.dominant, "achieved": achieved, "peak": peak_ops,
                      "unit": "Gop/s", "frac": (achieved / peak_ops) if achieved else None, "traffic": None,
                      "ops_per_cell": OPS_PER_CELL, "kernel_ms": dom_avg_ms, "cells_per_launch": kcells,
-                     "peak_source": "measured live by nw_peak_int kind 5 (score-only cell mix on every SM) x 3"},
+                     "peak_source": "measured live: slowest of nw_peak_int kinds 0/2/4 (DPX add-max, max, prmt; "
+                                    "independent chains on every SM)"},
         "kernels": {k_: {"launches": v[0], "ms_total": v[1]} for k_, v in stats.items()},
         "gpu_launches": launches,
         "e2e": {"value": e2e_val, "unit": "GCUPS", "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
@@ -569,12 +587,17 @@ class _Null:
     def __exit__(self, *a):
         return False
 
+    def window(self, t0, t1):
+        pass
+
     def summary(self):
         return {}
 
 
 def main():
     args = parse()
+    if args.steps is None:
+        args.steps = STEPS_DEFAULT.get(args.workload, 10)
     WL_ARGS.update(nseq=args.nseq, m=args.m, npairs=args.npairs)
     if args.impl == "reference":
         run_reference(args)
