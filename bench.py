@@ -33,9 +33,28 @@ import seqgen  # noqa: E402
 METRIC = "GCUPS on 1 GB300 and % of int/DPX roofline; learned-band+batched vs plain NW, exact"
 SCORING = (1, -1, -1)
 L2_FLUSH_BYTES = 256 << 20   # > 129 MB L2
+HERE = os.path.dirname(os.path.abspath(__file__))
 OPS_PER_CELL = 3             # algorithmic minimum in the W domain: prmt + add-max + max
 PEAK_KINDS = (0, 2, 4)       # nw_peak_int kinds: DPX add-max, max, prmt (lane-ops/s each)
 STEPS_DEFAULT = {"pair32k": 100, "pair1k": 200, "allpairs": 20, "band": 3}
+
+
+def dram_traffic(kernel: str, workload: str):
+    """DRAM bytes per launch of `kernel` on `workload` from the committed ncu
+    record, or None when there is none or the kernel's sources changed since."""
+    import hashlib
+    path = os.path.join(HERE, "profiles", "dram_traffic.json")
+    try:
+        rec = json.load(open(path))["entries"][f"{kernel}@{workload}"]
+        h = hashlib.sha256()
+        for f in sorted(rec["sources"]):
+            h.update(os.path.basename(f).encode())
+            h.update(open(os.path.join(HERE, f), "rb").read())
+        if h.hexdigest()[:16] != rec["sha"]:
+            return None
+        return rec["dram_read"] + rec["dram_write"]
+    except (OSError, KeyError, ValueError):
+        return None
 
 
 def parse():
@@ -558,7 +577,10 @@ def run_ours(args):
                        l2="flushed between timed steps (256 MB device write)", cells=work.cells,
                        **work.config, **work.result()),
         "roofline": {"bound": "alu", "kernel": work.dominant, "achieved": achieved, "peak": peak_ops,
-                     "unit": "Gop/s", "frac": (achieved / peak_ops) if achieved else None, "traffic": None,
+                     "unit": "Gop/s", "frac": (achieved / peak_ops) if achieved else None,
+                     "traffic": dram_traffic(work.dominant, args.workload),
+                     "traffic_note": "DRAM bytes per launch (ncu, profiles/dram_traffic.json); "
+                                     "algorithmic: 0.25 B/cell of pointers for *_ptr kernels, ~0 for score-only",
                      "ops_per_cell": OPS_PER_CELL, "kernel_ms": dom_avg_ms, "cells_per_launch": kcells,
                      "peak_source": "measured live: slowest of nw_peak_int kinds 0/2/4 (DPX add-max, max, prmt; "
                                     "independent chains on every SM)"},
