@@ -70,6 +70,11 @@ typedef enum {
 #define NW_BAND_RAW     16u   /* nw_align_batch_banded: one banded round, the
                                  banded score itself, no certificate or
                                  fallback (score only; for inspection)      */
+#define NW_GRAPH        64u   /* nw_score_all_pairs / score-only nw_align_batch
+                                 on device buffers: capture the launches into a
+                                 CUDA graph kept on the context, keyed by every
+                                 pointer, size and host metadata of the call;
+                                 a repeated call replays it (see below)     */
 #define NW_RECOMPUTE    32u   /* nw_align with NW_CIGAR: take the stripe-
                                  checkpoint recompute path even when the
                                  pointer matrix fits (see nw_align)         */
@@ -108,6 +113,33 @@ const char *nw_strerror(int status);
 int nw_ctx_set_profiling(nw_ctx *ctx, int on);
 int nw_ctx_kernel_stats(nw_ctx *ctx, const char **names, uint64_t *launches, double *total_ms, int cap);
 int nw_ctx_reset_stats(nw_ctx *ctx);
+
+/* ---------------------------------------------------- autotuning, graphs */
+
+/* Autotuning (off by default; not in the paper).  When on, the first call
+ * of a workload signature -- a batch's mean lengths and pair count, or a
+ * single pair's lengths, each bucketed by powers of two -- runs the fill with
+ * every candidate shape (rows per lane of the batched kernel: 4, 8, 16; rows
+ * x columns x warps of the single-pair kernel), times each with CUDA events
+ * and keeps the fastest for later calls of that signature.  The timed runs
+ * compute the real result, so the first call only costs more time. */
+int nw_ctx_set_autotune(nw_ctx *ctx, int on);
+/* The tuning table as text, one "key value" line per entry: written into
+ * buf[0..cap) NUL-terminated (truncated if short); returns the full length
+ * without the NUL, or -NW_ERR_ARG.  Values: rows per lane for batch_rows
+ * keys, R*100 + C*10 + warps for pair_shape keys. */
+int64_t nw_ctx_tuning(nw_ctx *ctx, char *buf, uint64_t cap);
+/* Adds or replaces entries from text in the same format (e.g. a table
+ * saved by an earlier process).  NW_ERR_ARG on a malformed line (nothing
+ * is changed then).  A value that is not a valid shape makes the calls of
+ * that signature fail with NW_ERR_ARG. */
+int nw_ctx_set_tuning(nw_ctx *ctx, const char *text);
+/* NW_GRAPH cache: out[0] graphs held (at most 8, least recently used
+ * evicted with the scratch they own), out[1] captures, out[2] replays.
+ * Returns 3.  A replay re-reads the sequence pool and writes the same output
+ * buffer as the captured call; it is valid as long as those buffers (and the
+ * host metadata, which is part of the key) are the caller's current ones. */
+int nw_ctx_graph_stats(nw_ctx *ctx, uint64_t *out, int cap);
 
 /* ---------------------------------------------------------------- packing */
 

@@ -35,6 +35,7 @@ NW_HOST_IO = 4
 NW_CIGAR_M = 8
 NW_BAND_RAW = 16
 NW_RECOMPUTE = 32
+NW_GRAPH = 64
 
 DEFAULT_SCORING = (1, -1, -1)
 
@@ -83,6 +84,10 @@ def load():
         "nw_ctx_kernel_stats": (ctypes.c_int, [vp, ctypes.POINTER(ctypes.c_char_p), u64p,
                                                ctypes.POINTER(ctypes.c_double), ctypes.c_int]),
         "nw_ctx_reset_stats": (ctypes.c_int, [vp]),
+        "nw_ctx_set_autotune": (ctypes.c_int, [vp, ctypes.c_int]),
+        "nw_ctx_tuning": (ctypes.c_int64, [vp, ctypes.c_char_p, u64]),
+        "nw_ctx_set_tuning": (ctypes.c_int, [vp, ctypes.c_char_p]),
+        "nw_ctx_graph_stats": (ctypes.c_int, [vp, u64p, ctypes.c_int]),
         "nw_pack": (ctypes.c_int, [ctypes.c_char_p, u64, vp]),
         "nw_pack_device": (ctypes.c_int, [vp, vp, u64, vp]),
         "nw_cigar_bound": (u64, [u64, u64]),
@@ -208,6 +213,30 @@ class Context:
 
     def reset_stats(self):
         _check(self, load().nw_ctx_reset_stats(self.handle))
+
+    def set_autotune(self, on: bool):
+        _check(self, load().nw_ctx_set_autotune(self.handle, int(bool(on))))
+
+    def tuning(self) -> dict[str, int]:
+        """The autotuner's table {key: choice}."""
+        L = load()
+        n = L.nw_ctx_tuning(self.handle, None, 0)
+        buf = ctypes.create_string_buffer(int(n) + 1)
+        L.nw_ctx_tuning(self.handle, buf, n + 1)
+        out = {}
+        for line in buf.value.decode().splitlines():
+            k, v = line.rsplit(" ", 1)
+            out[k] = int(v)
+        return out
+
+    def set_tuning(self, table: dict[str, int]):
+        text = "".join(f"{k} {int(v)}\n" for k, v in table.items())
+        _check(self, load().nw_ctx_set_tuning(self.handle, text.encode()))
+
+    def graph_stats(self) -> dict[str, int]:
+        out = (ctypes.c_uint64 * 3)()
+        load().nw_ctx_graph_stats(self.handle, out, 3)
+        return {"graphs": int(out[0]), "captures": int(out[1]), "replays": int(out[2])}
 
     def kernel_stats(self) -> dict[str, tuple[int, float]]:
         L = load()

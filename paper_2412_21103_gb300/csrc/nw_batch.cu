@@ -241,7 +241,7 @@ __global__ void k_diag(const uint32_t *len, uint32_t nseq, int32_t match, int32_
 
 // ------------------------------------------------------------------- host
 template <int R, bool PTR, bool BAND>
-static int launch_batch_R(nw_ctx *ctx, BatchArgs &ba, uint32_t max_n) {
+static int launch_batch_R(nw_ctx *ctx, BatchArgs &ba, uint32_t max_n, const std::string &prefix) {
     int occ = 0;
     cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_batch<R, PTR, BAND>, kBatchWarps * 32, 0);
     if (occ < 1) occ = 1;
@@ -251,10 +251,10 @@ static int launch_batch_R(nw_ctx *ctx, BatchArgs &ba, uint32_t max_n) {
     const uint32_t warps = blocks * kBatchWarps;
     ba.ring_stride = ((max_n + 31) / 32) * 32 + 32;
     void *v = nullptr;
-    int rc = scratch(ctx, "batch_ring", (size_t)warps * ba.ring_stride * 4, &v);
+    int rc = scratch(ctx, (prefix + "_ring").c_str(), (size_t)warps * ba.ring_stride * 4, &v);
     if (rc) return rc;
     ba.ring = (uint32_t *)v;
-    if ((rc = scratch(ctx, "batch_counter", 16, &v))) return rc;
+    if ((rc = scratch(ctx, (prefix + "_counter").c_str(), 16, &v))) return rc;
     ba.counter = (uint32_t *)v;
     cudaMemsetAsync(ba.counter, 0, 4, ctx->stream);
     LaunchTimer t(ctx, BAND ? (PTR ? "band_fill_ptr" : "band_score") : (PTR ? "batch_fill_ptr" : "batch_score"));
@@ -262,12 +262,13 @@ static int launch_batch_R(nw_ctx *ctx, BatchArgs &ba, uint32_t max_n) {
     return NW_OK;
 }
 
-static int launch_batch(nw_ctx *ctx, int R, bool ptr, BatchArgs &ba, uint32_t max_n, bool band = false) {
-#define NW_BATCH_CASES(PTRV, BANDV)                                         \
-    switch (R) {                                                           \
-        case 4: return launch_batch_R<4, PTRV, BANDV>(ctx, ba, max_n);     \
-        case 8: return launch_batch_R<8, PTRV, BANDV>(ctx, ba, max_n);     \
-        default: return launch_batch_R<16, PTRV, BANDV>(ctx, ba, max_n);   \
+static int launch_batch(nw_ctx *ctx, int R, bool ptr, BatchArgs &ba, uint32_t max_n, bool band = false,
+                        const std::string &prefix = "batch") {
+#define NW_BATCH_CASES(PTRV, BANDV)                                                 \
+    switch (R) {                                                                   \
+        case 4: return launch_batch_R<4, PTRV, BANDV>(ctx, ba, max_n, prefix);     \
+        case 8: return launch_batch_R<8, PTRV, BANDV>(ctx, ba, max_n, prefix);     \
+        default: return launch_batch_R<16, PTRV, BANDV>(ctx, ba, max_n, prefix);   \
     }
     if (band) {
         if (ptr) NW_BATCH_CASES(true, true)
@@ -298,6 +299,61 @@ static int pick_rows(const std::vector<BatchTask> &tasks) {
         }
     }
     return bestR;
+}
+
+// Autotuner for the rows per lane of a score-only batch: the first call of a
+// workload signature (mean lengths and pair count, bucketed by powers of
+// two) runs the launch with each candidate, times it with CUDA events and
+// keeps the fastest; later calls of the signature take the kept choice.
+// Every candidate computes the same scores, so the timed runs are real work.
+template <typename F>
+static int tune_rows(nw_ctx *ctx, const std::vector<BatchTask> &tasks, int fallback, F launch, int *R) {
+    *R = fallback;
+    if (!ctx->autotune || tasks.empty()) return NW_OK;
+    double sm = 0, sn = 0;
+    for (const auto &t : tasks) {
+        sm += t.m;
+        sn += t.n;
+    }
+    const std::string key = "batch_rows:m" + size_bucket((uint64_t)(sm / tasks.size())) + ":n" +
+                            size_bucket((uint64_t)(sn / tasks.size())) + ":p" + size_bucket(tasks.size());
+    uint32_t c = 0;
+    if (tuned(ctx, key, &c)) {
+        if (c != 4 && c != 8 && c != 16) return fail(ctx, NW_ERR_ARG, "tuning %s: rows per lane %u", key.c_str(), c);
+        *R = (int)c;
+        return NW_OK;
+    }
+    cudaEvent_t a, b;
+    cudaEventCreate(&a);
+    cudaEventCreate(&b);
+    float best = 1e30f;
+    int rc = NW_OK;
+    for (int r : {4, 8, 16}) {
+        cudaEventRecord(a, ctx->stream);
+        if ((rc = launch(r))) break;
+        cudaEventRecord(b, ctx->stream);
+        cudaEventSynchronize(b);
+        float ms = 0.f;
+        cudaEventElapsedTime(&ms, a, b);
+        if (ms < best) {
+            best = ms;
+            *R = r;
+        }
+    }
+    cudaEventDestroy(a);
+    cudaEventDestroy(b);
+    if (!rc) set_tuned(ctx, key, (uint32_t)*R);
+    return rc;
+}
+
+// Graph-cache key of a batch call: the entry point, every device pointer it
+// bakes in, the sizes and host metadata it was planned from.
+static std::string batch_key(const char *what, const void *pool, const void *out, uint32_t count, const nw_scoring &sc,
+                             uint32_t flags, uint64_t meta_hash) {
+    char buf[256];
+    snprintf(buf, sizeof buf, "%s|%p|%p|%u|%d,%d,%d|%x|%016llx", what, pool, out, count, sc.match, sc.mismatch, sc.gap,
+             flags, (unsigned long long)meta_hash);
+    return buf;
 }
 
 template <typename T>
@@ -682,6 +738,21 @@ int batch_device_impl(nw_ctx *ctx, const uint8_t *pool, const uint64_t *a_off, c
     const Profile pf = make_profile(sc);
     const bool want = flags & NW_CIGAR;
     int rc;
+    // NW_GRAPH (score-only calls on all the caller's pairs): a repeated call
+    // replays the launches captured the first time
+    bool graph = (flags & NW_GRAPH) && !want && !ids;
+    std::string gkey, pre = "batch";
+    if (graph) {
+        uint64_t h = 1469598103934665603ull;
+        h = hash_bytes(a_off, (size_t)npairs * 8, h);
+        h = hash_bytes(a_len, (size_t)npairs * 4, h);
+        h = hash_bytes(b_off, (size_t)npairs * 8, h);
+        h = hash_bytes(b_len, (size_t)npairs * 4, h);
+        gkey = batch_key("batch", pool, scores, npairs, sc, flags, h);
+        bool replayed = false;
+        if ((rc = graph_launch(ctx, gkey, "batch_score", 1, &replayed)) || replayed) return rc;
+        pre = "g" + std::to_string(++ctx->graph_seq);
+    }
     std::vector<BatchTask> tasks(npairs);
     uint32_t max_n = 1;
     for (uint32_t q = 0; q < npairs; ++q) {
@@ -737,6 +808,7 @@ int batch_device_impl(nw_ctx *ctx, const uint8_t *pool, const uint64_t *a_off, c
             std::vector<BatchTask> keep;
             for (size_t q = 0; q < tasks.size(); ++q)
                 if (!routed[q]) keep.push_back(tasks[q]);
+            graph = false;  // the single-pair launches are not captured
             if (keep.empty()) return NW_OK;
             tasks.swap(keep);
             npairs = (uint32_t)tasks.size();
@@ -744,20 +816,32 @@ int batch_device_impl(nw_ctx *ctx, const uint8_t *pool, const uint64_t *a_off, c
             for (const auto &t : tasks) max_n = std::max(max_n, t.n);
         }
     }
-    const int R = pick_rows(tasks);
     BatchArgs ba{};
     ba.pool = pool;
     for (int c = 0; c < 4; ++c) ba.prof[c] = pf.prof[c];
     ba.gap = pf.gap;
     ba.scores = scores;
     ba.err = ctx->d_err;
-    if (!want) {
-        sort_lpt(tasks);
+    // rows per lane: the padding-cost model, or the autotuner's measured
+    // choice (tuned on score-only launches of the whole list)
+    int R = pick_rows(tasks);
+    if (!want || ctx->autotune) {
+        std::vector<BatchTask> lpt = tasks;
+        sort_lpt(lpt);
         BatchTask *dt = nullptr;
-        if ((rc = upload(ctx, "batch_tasks", tasks, &dt))) return rc;
-        ba.tasks = dt;
-        ba.ntasks = npairs;
-        return launch_batch(ctx, R, false, ba, max_n);
+        if ((rc = upload(ctx, (pre + "_tasks").c_str(), lpt, &dt))) return rc;
+        BatchArgs bs = ba;
+        bs.tasks = dt;
+        bs.ntasks = npairs;
+        if ((rc = tune_rows(ctx, lpt, R, [&](int r) { return launch_batch(ctx, r, false, bs, max_n, false, pre); },
+                            &R)))
+            return rc;
+        if (!want) {
+            auto launches = [&]() -> int { return launch_batch(ctx, R, false, bs, max_n, false, pre); };
+            if ((rc = launches())) return rc;
+            if (graph) return capture_graph(ctx, gkey, pre, "batch_score", 1, launches);
+            return NW_OK;
+        }
     }
     // CIGAR: waves whose pointer words fit half of the remaining budget.
     // (a wave always takes at least one pair; scratch() reports NW_ERR_OOM if
@@ -869,6 +953,7 @@ extern "C" int nw_align_batch(nw_ctx *ctx, const uint8_t *pool2b, const uint64_t
     int rc = check_batch_args(ctx, sc, pool2b, a_off, a_len, b_off, b_len, flags, scores, cigar_pool, cigar_off,
                               cigar_len);
     if (rc) return rc;
+    if ((flags & NW_GRAPH) && (flags & NW_HOST_IO)) return fail(ctx, NW_ERR_ARG, "NW_GRAPH needs device buffers");
     auto body = [&](const uint8_t *pool, int32_t *sc_out, char *cig, uint64_t *clen) -> int {
         const uint32_t fl = flags & ~NW_HOST_IO;
         if (!(flags & NW_LEARNED_BAND))
@@ -924,6 +1009,17 @@ extern "C" int nw_score_all_pairs(nw_ctx *ctx, const uint8_t *pool2b, const uint
     if (nseq > 65535) return fail(ctx, NW_ERR_ARG, "at most 65535 sequences");
     for (uint32_t i = 0; i < nseq; ++i)
         if ((rc = check_len(ctx, sc, len[i], len[i]))) return rc;
+    const bool graph = flags & NW_GRAPH;
+    if (graph && (flags & NW_HOST_IO)) return fail(ctx, NW_ERR_ARG, "NW_GRAPH needs device buffers");
+    std::string gkey, pre = "batch";
+    if (graph) {
+        // a repeated call replays its captured launches
+        const uint64_t h = hash_bytes(len, (size_t)nseq * 4, hash_bytes(off, (size_t)nseq * 8, 1469598103934665603ull));
+        gkey = batch_key("allpairs", pool2b, out, nseq, sc, flags, h);
+        bool replayed = false;
+        if ((rc = graph_launch(ctx, gkey, "batch_score", 2, &replayed)) || replayed) return rc;
+        pre = "g" + std::to_string(++ctx->graph_seq);
+    }
     const uint8_t *pool = pool2b;
     int32_t *dout = out;
     if (flags & NW_HOST_IO) {
@@ -965,21 +1061,29 @@ extern "C" int nw_score_all_pairs(nw_ctx *ctx, const uint8_t *pool2b, const uint
     ba.scores = dout;
     ba.err = ctx->d_err;
     BatchTask *dt = nullptr;
-    if ((rc = upload(ctx, "batch_tasks", tasks, &dt))) return rc;
+    if ((rc = upload(ctx, (pre + "_tasks").c_str(), tasks, &dt))) return rc;
     ba.tasks = dt;
     ba.ntasks = (uint32_t)tasks.size();
-    void *dl = nullptr;
     std::vector<uint32_t> lens(len, len + nseq);
     uint32_t *dlen = nullptr;
-    if ((rc = upload(ctx, "allpairs_len", lens, &dlen))) return rc;
-    (void)dl;
-    if ((rc = launch_batch(ctx, pick_rows(tasks), false, ba, max_n))) return rc;
-    {
-        LaunchTimer t(ctx, "diag");
-        k_diag<<<(nseq + 255) / 256, 256, 0, ctx->stream>>>(dlen, nseq, sc.match, dout);
-    }
-    cudaError_t e = cudaGetLastError();
-    if (e != cudaSuccess) return cuda_fail(ctx, e, "all-pairs launch");
+    if ((rc = upload(ctx, (pre + "_len").c_str(), lens, &dlen))) return rc;
+    int R = 16;
+    if ((rc = tune_rows(ctx, tasks, pick_rows(tasks), [&](int r) { return launch_batch(ctx, r, false, ba, max_n, false, pre); },
+                        &R)))
+        return rc;
+    auto launches = [&]() -> int {
+        int r = launch_batch(ctx, R, false, ba, max_n, false, pre);
+        if (r) return r;
+        {
+            LaunchTimer t(ctx, "diag");
+            k_diag<<<(nseq + 255) / 256, 256, 0, ctx->stream>>>(dlen, nseq, sc.match, dout);
+        }
+        cudaError_t e = cudaGetLastError();
+        return e == cudaSuccess ? NW_OK : cuda_fail(ctx, e, "all-pairs launch");
+    };
+    if ((rc = launches())) return rc;
+    if (graph && (rc = capture_graph(ctx, gkey, pre, "batch_score", 2, launches))) return rc;
+    cudaError_t e = cudaSuccess;
     if (flags & NW_HOST_IO) {
         e = cudaMemcpyAsync(out, dout, (size_t)nseq * nseq * 4, cudaMemcpyDeviceToHost, ctx->stream);
         if (e != cudaSuccess) return cuda_fail(ctx, e, "matrix D2H");

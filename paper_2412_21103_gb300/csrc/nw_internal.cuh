@@ -119,6 +119,18 @@ struct KernelStat {
     uint64_t launches = 0;
     double ms = 0.0;
     std::vector<std::pair<cudaEvent_t, cudaEvent_t>> pending;
+    std::vector<uint32_t> pending_count;  // kernels per pending pair (a graph replay holds several)
+};
+
+// A CUDA graph of a repeated call: its instantiated executable, the prefix
+// of the scratch slots it owns (never shared with other calls, so its baked
+// pointers stay valid), the kernel-stat name and kernel count of a replay.
+struct GraphEntry {
+    cudaGraphExec_t exec = nullptr;
+    std::string prefix;
+    const char *label = "";
+    uint32_t kernels = 0;
+    uint64_t last_use = 0;
 };
 
 struct Buf {
@@ -150,6 +162,15 @@ struct nw_ctx {
     // host staging for NW_HOST_IO (pinned, grown on demand)
     void *pinned = nullptr;
     size_t pinned_cap = 0;
+    // autotuning: when on, the first call of a workload signature times the
+    // candidate shapes and keeps the fastest (key -> packed choice)
+    bool autotune = false;
+    std::map<std::string, uint32_t> tuning;
+    // CUDA graphs of repeated calls (NW_GRAPH), at most kMaxGraphs, LRU
+    std::map<std::string, nw::GraphEntry> graphs;
+    uint64_t graph_seq = 0, graph_replays = 0, graph_captures = 0;
+    bool capturing = false;            // LaunchTimer records nothing while capturing
+    cudaStream_t capture_stream = nullptr;
 };
 
 namespace nw {
@@ -170,10 +191,53 @@ int check_scoring(nw_ctx *ctx, const nw_scoring &sc);
 struct LaunchTimer {
     nw_ctx *ctx;
     const char *name;
+    uint32_t count;
     cudaEvent_t e0 = nullptr, e1 = nullptr;
-    LaunchTimer(nw_ctx *c, const char *n);
+    LaunchTimer(nw_ctx *c, const char *n, uint32_t kernels = 1);
     ~LaunchTimer();
 };
+
+// Autotuning keys and the graph cache (nw_runtime.cu).
+constexpr size_t kMaxGraphs = 8;
+bool tuned(nw_ctx *ctx, const std::string &key, uint32_t *choice);
+void set_tuned(nw_ctx *ctx, const std::string &key, uint32_t choice);
+std::string size_bucket(uint64_t v);  // "2^k" bucket of a size
+// Runs `launches` once normally, then captures it into a graph stored under
+// `key` (scratch slots named from the returned prefix); replays if present.
+int graph_launch(nw_ctx *ctx, const std::string &key, const char *label, uint32_t kernels, bool *replayed);
+int graph_store(nw_ctx *ctx, const std::string &key, const std::string &prefix, const char *label,
+                uint32_t kernels, cudaGraph_t g);
+uint64_t hash_bytes(const void *p, size_t n, uint64_t h);
+void free_prefix(nw_ctx *ctx, const std::string &prefix);
+
+// Capture `launches` (a callable returning a status; it must only enqueue
+// work: its scratch slots already exist from an uncaptured run) into a graph
+// stored under `key`.  The capture runs on a private stream (the caller's
+// may be the legacy default stream, which cannot be captured); LaunchTimer
+// records nothing meanwhile.
+template <typename F>
+int capture_graph(nw_ctx *ctx, const std::string &key, const std::string &prefix, const char *label,
+                  uint32_t kernels, F launches) {
+    if (!ctx->capture_stream) {
+        cudaError_t e = cudaStreamCreateWithFlags(&ctx->capture_stream, cudaStreamNonBlocking);
+        if (e != cudaSuccess) return cuda_fail(ctx, e, "capture stream");
+    }
+    cudaStream_t saved = ctx->stream;
+    ctx->stream = ctx->capture_stream;
+    ctx->capturing = true;
+    cudaError_t e = cudaStreamBeginCapture(ctx->capture_stream, cudaStreamCaptureModeThreadLocal);
+    int rc = e == cudaSuccess ? launches() : NW_OK;
+    cudaGraph_t g = nullptr;
+    const cudaError_t e2 = e == cudaSuccess ? cudaStreamEndCapture(ctx->capture_stream, &g) : e;
+    ctx->stream = saved;
+    ctx->capturing = false;
+    if (rc || e2 != cudaSuccess) {
+        if (g) cudaGraphDestroy(g);
+        cudaGetLastError();
+        return rc ? rc : cuda_fail(ctx, e2, "graph capture");
+    }
+    return graph_store(ctx, key, prefix, label, kernels, g);
+}
 
 // Copy helpers for NW_HOST_IO.
 int to_device(nw_ctx *ctx, const void *host, size_t bytes, const char *slot, void **dev);

@@ -1,6 +1,9 @@
-// Context, scratch pool, errors, per-kernel timing and 2-bit packing.
+// Context, scratch pool, errors, per-kernel timing, the tuning table and
+// graph cache, and 2-bit packing.
+#include <algorithm>
 #include <cstdarg>
 #include <cstdio>
+#include <cstdlib>
 #include <cstring>
 
 #include "nw_internal.cuh"
@@ -92,8 +95,8 @@ static cudaEvent_t get_event(nw_ctx *ctx) {
     return e;
 }
 
-LaunchTimer::LaunchTimer(nw_ctx *c, const char *n) : ctx(c), name(n) {
-    if (ctx->profiling) {
+LaunchTimer::LaunchTimer(nw_ctx *c, const char *n, uint32_t kernels) : ctx(c), name(n), count(kernels) {
+    if (ctx->profiling && !ctx->capturing) {
         e0 = get_event(ctx);
         e1 = get_event(ctx);
         cudaEventRecord(e0, ctx->stream);
@@ -104,7 +107,87 @@ LaunchTimer::~LaunchTimer() {
     if (ctx->profiling && e0 && e1) {
         cudaEventRecord(e1, ctx->stream);
         ctx->stats[name].pending.emplace_back(e0, e1);
+        ctx->stats[name].pending_count.push_back(count);
     }
+}
+
+// ------------------------------------------------------- tuning and graphs
+bool tuned(nw_ctx *ctx, const std::string &key, uint32_t *choice) {
+    const auto it = ctx->tuning.find(key);
+    if (it == ctx->tuning.end()) return false;
+    *choice = it->second;
+    return true;
+}
+
+void set_tuned(nw_ctx *ctx, const std::string &key, uint32_t choice) { ctx->tuning[key] = choice; }
+
+std::string size_bucket(uint64_t v) {
+    int k = 0;
+    while ((1ull << (k + 1)) <= v && k < 62) ++k;
+    return std::to_string(k);
+}
+
+uint64_t hash_bytes(const void *p, size_t n, uint64_t h) {
+    // FNV-1a, 64-bit
+    const uint8_t *b = (const uint8_t *)p;
+    for (size_t i = 0; i < n; ++i) {
+        h ^= b[i];
+        h *= 1099511628211ull;
+    }
+    return h;
+}
+
+void free_prefix(nw_ctx *ctx, const std::string &prefix) {
+    for (auto it = ctx->bufs.begin(); it != ctx->bufs.end();) {
+        if (it->first.compare(0, prefix.size(), prefix) == 0) {
+            if (it->second.p) cudaFreeAsync(it->second.p, ctx->stream);
+            ctx->used -= it->second.cap;
+            it = ctx->bufs.erase(it);
+        } else {
+            ++it;
+        }
+    }
+}
+
+int graph_launch(nw_ctx *ctx, const std::string &key, const char *label, uint32_t kernels, bool *replayed) {
+    *replayed = false;
+    auto it = ctx->graphs.find(key);
+    if (it == ctx->graphs.end()) return NW_OK;
+    cudaError_t e;
+    {
+        LaunchTimer t(ctx, label, kernels);
+        e = cudaGraphLaunch(it->second.exec, ctx->stream);
+    }
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "cudaGraphLaunch");
+    it->second.last_use = ++ctx->graph_seq;
+    ++ctx->graph_replays;
+    *replayed = true;
+    return NW_OK;
+}
+
+int graph_store(nw_ctx *ctx, const std::string &key, const std::string &prefix, const char *label,
+                uint32_t kernels, cudaGraph_t g) {
+    cudaGraphExec_t exec = nullptr;
+    cudaError_t e = cudaGraphInstantiate(&exec, g, 0);
+    cudaGraphDestroy(g);
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "cudaGraphInstantiate");
+    while (ctx->graphs.size() >= kMaxGraphs) {  // evict the least recently used
+        auto old = ctx->graphs.begin();
+        for (auto it = ctx->graphs.begin(); it != ctx->graphs.end(); ++it)
+            if (it->second.last_use < old->second.last_use) old = it;
+        cudaStreamSynchronize(ctx->stream);  // a replay of it may still run
+        cudaGraphExecDestroy(old->second.exec);
+        free_prefix(ctx, old->second.prefix);
+        ctx->graphs.erase(old);
+    }
+    GraphEntry &ge = ctx->graphs[key];
+    ge.exec = exec;
+    ge.prefix = prefix;
+    ge.label = label;
+    ge.kernels = kernels;
+    ge.last_use = ++ctx->graph_seq;
+    ++ctx->graph_captures;
+    return NW_OK;
 }
 
 int to_device(nw_ctx *ctx, const void *host, size_t bytes, const char *slot, void **dev) {
@@ -201,6 +284,8 @@ void nw_ctx_destroy(nw_ctx *ctx) {
             cudaEventDestroy(pr.second);
         }
     for (auto e : ctx->event_pool) cudaEventDestroy(e);
+    for (auto &kv : ctx->graphs) cudaGraphExecDestroy(kv.second.exec);
+    if (ctx->capture_stream) cudaStreamDestroy(ctx->capture_stream);
     free_band_model(ctx);
     if (ctx->d_err) cudaFree(ctx->d_err);
     if (ctx->pinned) cudaFreeHost(ctx->pinned);
@@ -243,14 +328,16 @@ int nw_ctx_kernel_stats(nw_ctx *ctx, const char **names, uint64_t *launches, dou
     int k = 0;
     for (auto &kv : ctx->stats) {
         KernelStat &st = kv.second;
-        for (auto &pr : st.pending) {
+        for (size_t q = 0; q < st.pending.size(); ++q) {
+            const auto &pr = st.pending[q];
             float ms = 0.f;
             if (cudaEventElapsedTime(&ms, pr.first, pr.second) == cudaSuccess) st.ms += ms;
-            st.launches += 1;
+            st.launches += q < st.pending_count.size() ? st.pending_count[q] : 1;
             ctx->event_pool.push_back(pr.first);
             ctx->event_pool.push_back(pr.second);
         }
         st.pending.clear();
+        st.pending_count.clear();
         if (k < cap) {
             if (names) names[k] = kv.first.c_str();
             if (launches) launches[k] = st.launches;
@@ -270,6 +357,52 @@ int nw_ctx_reset_stats(nw_ctx *ctx) {
         kv.second.ms = 0.0;
     }
     return NW_OK;
+}
+
+int nw_ctx_set_autotune(nw_ctx *ctx, int on) {
+    if (!ctx) return NW_ERR_ARG;
+    ctx->autotune = on != 0;
+    return NW_OK;
+}
+
+int64_t nw_ctx_tuning(nw_ctx *ctx, char *buf, uint64_t cap) {
+    if (!ctx) return -NW_ERR_ARG;
+    std::string text;
+    for (const auto &kv : ctx->tuning) text += kv.first + " " + std::to_string(kv.second) + "\n";
+    if (buf && cap) {
+        const uint64_t k = std::min<uint64_t>(cap - 1, text.size());
+        std::memcpy(buf, text.data(), k);
+        buf[k] = 0;
+    }
+    return (int64_t)text.size();
+}
+
+int nw_ctx_set_tuning(nw_ctx *ctx, const char *text) {
+    if (!ctx || !text) return NW_ERR_ARG;
+    std::map<std::string, uint32_t> add;
+    const char *p = text;
+    while (*p) {
+        const char *e = std::strchr(p, '\n');
+        const std::string line(p, e ? (size_t)(e - p) : std::strlen(p));
+        p = e ? e + 1 : p + line.size();
+        if (line.empty()) continue;
+        const size_t sp = line.rfind(' ');
+        if (sp == std::string::npos || sp == 0 || sp + 1 >= line.size())
+            return fail(ctx, NW_ERR_ARG, "tuning line without 'key value': %s", line.c_str());
+        char *end = nullptr;
+        const unsigned long v = std::strtoul(line.c_str() + sp + 1, &end, 10);
+        if (!end || *end) return fail(ctx, NW_ERR_ARG, "tuning value is not a number: %s", line.c_str());
+        add[line.substr(0, sp)] = (uint32_t)v;
+    }
+    for (const auto &kv : add) ctx->tuning[kv.first] = kv.second;
+    return NW_OK;
+}
+
+int nw_ctx_graph_stats(nw_ctx *ctx, uint64_t *out, int cap) {
+    if (!ctx) return -NW_ERR_ARG;
+    const uint64_t v[3] = {(uint64_t)ctx->graphs.size(), ctx->graph_captures, ctx->graph_replays};
+    for (int k = 0; k < cap && k < 3; ++k) out[k] = v[k];
+    return 3;
 }
 
 int nw_pack(const char *ascii, uint64_t len, uint8_t *out2b) {

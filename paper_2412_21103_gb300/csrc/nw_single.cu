@@ -22,6 +22,7 @@
 #include <algorithm>
 #include <cstdio>
 #include <cstdlib>
+#include <string>
 
 #include "nw_internal.cuh"
 
@@ -169,6 +170,9 @@ static void pair_shape(nw_ctx *ctx, uint64_t m, int &R, int &C, int &nw) {
     R = m >= 2048 ? 8 : 4;
     C = 2;
     nw = 4;
+    // a short pair fits one CTA: no row group boundary at all
+    const uint64_t S = (m + 32u * R - 1) / (32u * R);
+    if (S <= 8) nw = (int)S;
     if (const char *e = getenv("NW_PAIR_R")) R = atoi(e);
     if (const char *e = getenv("NW_PAIR_C")) C = atoi(e);
     if (const char *e = getenv("NW_PAIR_WARPS")) nw = atoi(e);
@@ -258,11 +262,63 @@ static int run_pair_recompute(nw_ctx *ctx, const uint8_t *a2b, uint32_t m, const
     return launch_finish(ctx, tt, nullptr, 1, (flags & NW_CIGAR_M) ? 1u : 0u);
 }
 
+// Autotuner for the single-pair block shape: the first pair of a size
+// bucket (powers of two of m and n) runs the score-only fill with each
+// candidate R x C x warps, timed by CUDA events, and keeps the fastest.  The
+// runs compute the real score.  Environment overrides take precedence.
+static int tune_pair_shape(nw_ctx *ctx, const uint8_t *a2b, uint32_t m, const uint8_t *b2b, uint32_t n,
+                           const Profile &pf, int32_t *score, int &R, int &C, int &nw) {
+    if (!ctx->autotune || getenv("NW_PAIR_R") || getenv("NW_PAIR_C") || getenv("NW_PAIR_WARPS")) return NW_OK;
+    const std::string key = "pair_shape:m" + size_bucket(m) + ":n" + size_bucket(n);
+    uint32_t c = 0;
+    if (tuned(ctx, key, &c)) {
+        R = (int)(c / 100);
+        C = (int)(c / 10 % 10);
+        nw = (int)(c % 10);
+        const bool shape_ok = (R == 2 && (C == 2 || C == 4 || C == 8)) || (R == 4 && (C == 2 || C == 4)) ||
+                              (R == 8 && C == 2);
+        if (!shape_ok || nw < 1 || nw > 8) return fail(ctx, NW_ERR_ARG, "tuning %s: shape %u", key.c_str(), c);
+        return NW_OK;
+    }
+    static const int cand[][3] = {{8, 2, 4}, {4, 2, 4}, {4, 4, 4}, {8, 2, 3}, {4, 2, 8}, {2, 2, 4}};
+    cudaEvent_t a, b;
+    cudaEventCreate(&a);
+    cudaEventCreate(&b);
+    float best = 1e30f;
+    int rc = NW_OK;
+    for (const auto &k : cand) {
+        PairFill f;
+        f.R = k[0];
+        f.C = k[1];
+        const uint64_t S = (m + 32u * f.R - 1) / (32u * f.R);
+        f.nw = (int)std::min<uint64_t>((uint64_t)k[2], S);
+        f.score = score;
+        cudaEventRecord(a, ctx->stream);
+        if ((rc = launch_pair_fill(ctx, a2b, m, b2b, n, pf, f))) break;
+        cudaEventRecord(b, ctx->stream);
+        cudaEventSynchronize(b);
+        float ms = 0.f;
+        cudaEventElapsedTime(&ms, a, b);
+        if (ms < best) {
+            best = ms;
+            R = f.R;
+            C = f.C;
+            nw = f.nw;
+        }
+    }
+    cudaEventDestroy(a);
+    cudaEventDestroy(b);
+    if (!rc) set_tuned(ctx, key, (uint32_t)(R * 100 + C * 10 + nw));
+    return rc;
+}
+
 static int run_pair(nw_ctx *ctx, const uint8_t *a2b, uint32_t m, const uint8_t *b2b, uint32_t n, const Profile &pf,
                     uint32_t flags, int32_t *score, char *cigar, uint64_t *cigar_len) {
     const bool want = flags & NW_CIGAR;
     int R, C, nw;
     pair_shape(ctx, m, R, C, nw);
+    int rc0 = tune_pair_shape(ctx, a2b, m, b2b, n, pf, score, R, C, nw);
+    if (rc0) return rc0;
     PairFill f;
     f.R = R;
     f.C = C;
@@ -281,7 +337,9 @@ static int run_pair(nw_ctx *ctx, const uint8_t *a2b, uint32_t m, const uint8_t *
     const uint64_t rows_bytes = (CS > 1 ? (CS - 1) * pair_bstride(n) * 4 : 0) + 4 * pair_bstride(n) + CS * 4 + 1024;
     // the full pointer matrix, unless it (with the fill's rows) exceeds the budget
     if ((flags & NW_RECOMPUTE) || ptr_bytes + ptr_bytes / 8 + rows_bytes > headroom(ctx, "ptr"))
-        return run_pair_recompute(ctx, a2b, m, b2b, n, pf, flags, R, C, nw, score, cigar, cigar_len, (uint8_t *)mv,
+        // (groups of at most 4 stripes: the recompute's unit of memory)
+        return run_pair_recompute(ctx, a2b, m, b2b, n, pf, flags, R, C, std::min(nw, 4), score, cigar, cigar_len,
+                                  (uint8_t *)mv,
                                   (uint64_t *)nm);
     void *v = nullptr;
     if ((rc = scratch(ctx, "ptr", ptr_bytes, &v))) return rc;

@@ -121,7 +121,9 @@ __global__ void __launch_bounds__(32) k_traceback(TraceTask one, const TraceTask
 // moves are those of the plain walk, one for one.
 constexpr uint32_t kWalkDone = 0, kWalkJoined = 1, kWalkFull = 2, kWalkBand = 3, kWalkNone = 4;
 constexpr int kWalkWarps = 4;
-constexpr uint32_t kParMinStripes = 3;  // shorter pairs walk sequentially
+constexpr uint32_t kParMinStripes = 3;     // shorter pairs walk sequentially,
+constexpr uint64_t kParMinMoves = 8192;    // and so do pairs with m + n below this (the three
+                                           // extra launches cost more than they save)
 
 struct StripeJob {
     uint64_t moff;  // byte offset of the stripe's spec moves; its link moves follow at moff + lcap
@@ -612,7 +614,7 @@ static int launch_walks(nw_ctx *ctx, const TraceTask *host, const TraceTask *dev
         const uint64_t m = host[t].m, n = host[t].n;
         if (m == 0 || n == 0 || host[t].state) continue;
         const uint32_t S = (uint32_t)((m + SH - 1) / SH);
-        if (S < kParMinStripes) continue;
+        if (S < kParMinStripes || m + n < kParMinMoves) continue;
         // moves of a stripe's walks: its rows, twice the proportional columns, slack
         uint64_t cap = SH + 2 * ((SH * n + m - 1) / m) + 512;
         cap = std::min<uint64_t>((cap + 15) / 16 * 16, 65520);
