@@ -61,7 +61,9 @@ def _load():
                                       ctypes.POINTER(i64)]
             lib.nwo_score.argtypes = [u8p, i64, u8p, i64, i32, i32, i32, i32p]
             lib.nwo_banded.argtypes = [u8p, i64, u8p, i64, i32, i32, i32, i64, i32p, i32p, i32p]
-            for f in (lib.nwo_fill, lib.nwo_align, lib.nwo_score, lib.nwo_banded):
+            i64p = ctypes.POINTER(ctypes.c_int64)
+            lib.nwo_region.argtypes = [u8p, i64, u8p, i64, i32, i32, i32, i64p, i64p, i64, i64, i32p]
+            for f in (lib.nwo_fill, lib.nwo_align, lib.nwo_score, lib.nwo_banded, lib.nwo_region):
                 f.restype = ctypes.c_int
             _lib = lib
     return _lib
@@ -137,6 +139,25 @@ def banded(a, b, w: int, match: int = 1, mismatch: int = -1, gap: int = -1,
     if want_grid:
         return int(sb.value), int(ub.value), H
     return int(sb.value), int(ub.value)
+
+
+def region(a, b, row_lo, row_hi, row0_hi: int, col0_hi: int, match: int = 1, mismatch: int = -1,
+           gap: int = -1) -> int:
+    """Score of the DP restricted to a cell set: row i (1-based) may use
+    columns row_lo[i-1]..row_hi[i-1], row 0 columns 0..row0_hi, column 0 rows
+    0..col0_hi; everything else is -infinity (NEG_INF when unreachable)."""
+    a, b = _codes(a), _codes(b)
+    lo = np.ascontiguousarray(row_lo, dtype=np.int64)
+    hi = np.ascontiguousarray(row_hi, dtype=np.int64)
+    assert lo.size == a.size and hi.size == a.size
+    sc = ctypes.c_int32(0)
+    pa, ka = _ptr(a)
+    pb, kb = _ptr(b)
+    i64p = ctypes.POINTER(ctypes.c_int64)
+    rc = _load().nwo_region(pa, a.size, pb, b.size, match, mismatch, gap, lo.ctypes.data_as(i64p),
+                            hi.ctypes.data_as(i64p), row0_hi, col0_hi, ctypes.byref(sc))
+    assert rc == 0, rc
+    return int(sc.value)
 
 
 def band_limits(m: int, n: int, w: int) -> tuple[int, int]:

@@ -160,6 +160,49 @@ static int32_t rest_bound(int64_t m, int64_t n, int64_t qi, int64_t qj, int32_t 
     return (int32_t)(match * mn + gap * diff);
 }
 
+/* The same recurrence restricted to an arbitrary set of cells: row i (1..m)
+ * may use columns row_lo[i-1]..row_hi[i-1] (inclusive, 1-based), row 0 the
+ * columns 0..row0_hi, column 0 the rows 0..col0_hi; every other cell is
+ * -infinity.  The score is H(m,n) (-infinity when unreachable).  Two rolling
+ * rows.  This is the plain definition of a DP over a cell subset: any
+ * subset containing a band gives a score between the banded and the full
+ * one. */
+int nwo_region(const uint8_t *a, int64_t m, const uint8_t *b, int64_t n,
+               int32_t match, int32_t mismatch, int32_t gap,
+               const int64_t *row_lo, const int64_t *row_hi, int64_t row0_hi, int64_t col0_hi,
+               int32_t *score) {
+    if (m < 0 || n < 0 || !score || (m > 0 && (!row_lo || !row_hi))) return NWO_ERR_ARG;
+    int32_t *prev = (int32_t *)malloc((size_t)(n + 1) * sizeof(int32_t));
+    int32_t *cur = (int32_t *)malloc((size_t)(n + 1) * sizeof(int32_t));
+    if (!prev || !cur) {
+        free(prev);
+        free(cur);
+        return NWO_ERR_OOM;
+    }
+    for (int64_t j = 0; j <= n; ++j) prev[j] = j <= row0_hi ? (int32_t)j * gap : NWO_NEG_INF;
+    for (int64_t i = 1; i <= m; ++i) {
+        cur[0] = i <= col0_hi ? (int32_t)i * gap : NWO_NEG_INF;
+        for (int64_t j = 1; j <= n; ++j) {
+            if (j < row_lo[i - 1] || j > row_hi[i - 1]) {
+                cur[j] = NWO_NEG_INF;
+                continue;
+            }
+            int32_t best = NWO_NEG_INF;
+            if (prev[j - 1] > NWO_NEG_INF) best = max2(best, prev[j - 1] + subst(a[i - 1], b[j - 1], match, mismatch));
+            if (prev[j] > NWO_NEG_INF) best = max2(best, prev[j] + gap);
+            if (cur[j - 1] > NWO_NEG_INF) best = max2(best, cur[j - 1] + gap);
+            cur[j] = best;
+        }
+        int32_t *t = prev;
+        prev = cur;
+        cur = t;
+    }
+    *score = prev[n];
+    free(prev);
+    free(cur);
+    return NWO_OK;
+}
+
 int nwo_banded(const uint8_t *a, int64_t m, const uint8_t *b, int64_t n,
                int32_t match, int32_t mismatch, int32_t gap, int64_t w,
                int32_t *score_band, int32_t *bound_out, int32_t *Hout) {

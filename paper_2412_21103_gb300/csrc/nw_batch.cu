@@ -71,12 +71,16 @@ __device__ __forceinline__ uint32_t load_rows(const uint8_t *s, uint32_t i0, uin
 // wraps.
 constexpr int32_t kNegW = -(1 << 27);
 
-// BAND: only the diagonals d = j - i in [lo, hi] are computed.  Stripe s
-// runs over its band columns [cbeg(s), cend(s)] (0-based) only, cells of the
-// stripe rectangle outside the band are forced to kNegW (which stops every
-// path through them), and the boundary row/column cells outside the band
-// are kNegW too.  The stripe period is the task's fixed `period`.
-template <int R, bool PTR, bool BAND>
+// BAND (1, 2): only the diagonals d = j - i in [lo, hi] matter.  Stripe s
+// runs over its band columns [cbeg(s), cend(s)] (0-based) only, and the
+// boundary row/column cells outside the band are kNegW (which stops every
+// path through them).  BAND 1 (the strict band) also forces the cells of
+// the stripe rectangle outside the band to kNegW; BAND 2 (the region) keeps
+// them: the DP then runs over the union of the stripe rectangles, a superset
+// of the band, which gives a score between the banded and the full one and
+// the same certificate (every path leaving the band is bounded).  The
+// stripe period is the task's fixed `period`.
+template <int R, bool PTR, int BAND>
 __global__ void __launch_bounds__(kBatchWarps * 32) k_batch(BatchArgs p) {
     constexpr uint32_t SH = 32u * R;
     constexpr uint32_t CPW = PTR ? 16u / R : 1u;
@@ -169,7 +173,7 @@ __global__ void __launch_bounds__(kBatchWarps * 32) k_batch(BatchArgs p) {
             const int32_t D0 = col - (int32_t)(s * SH + (uint32_t)lane * R);  // j - i of row 0 of the lane
             // Banded: mask only when some active lane has rows outside the
             // band this step (warp-uniform; most steps need no masking).
-            const bool mask = BAND && __any_sync(kFull, act && !(D0 - (R - 1) >= lo && D0 <= hi));
+            const bool mask = BAND == 1 && __any_sync(kFull, act && !(D0 - (R - 1) >= lo && D0 <= hi));
             if (act) {
                 const int32_t up = (int32_t)x >> 2;
                 const uint32_t sel = sext_selector(x & 3u);
@@ -240,7 +244,7 @@ __global__ void k_diag(const uint32_t *len, uint32_t nseq, int32_t match, int32_
 }
 
 // ------------------------------------------------------------------- host
-template <int R, bool PTR, bool BAND>
+template <int R, bool PTR, int BAND>
 static int launch_batch_R(nw_ctx *ctx, BatchArgs &ba, uint32_t max_n, const std::string &prefix) {
     int occ = 0;
     cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_batch<R, PTR, BAND>, kBatchWarps * 32, 0);
@@ -262,7 +266,8 @@ static int launch_batch_R(nw_ctx *ctx, BatchArgs &ba, uint32_t max_n, const std:
     return NW_OK;
 }
 
-static int launch_batch(nw_ctx *ctx, int R, bool ptr, BatchArgs &ba, uint32_t max_n, bool band = false,
+// band: 0 full grid, 1 strict band, 2 band region (see k_batch)
+static int launch_batch(nw_ctx *ctx, int R, bool ptr, BatchArgs &ba, uint32_t max_n, int band = 0,
                         const std::string &prefix = "batch") {
 #define NW_BATCH_CASES(PTRV, BANDV)                                                 \
     switch (R) {                                                                   \
@@ -270,12 +275,13 @@ static int launch_batch(nw_ctx *ctx, int R, bool ptr, BatchArgs &ba, uint32_t ma
         case 8: return launch_batch_R<8, PTRV, BANDV>(ctx, ba, max_n, prefix);     \
         default: return launch_batch_R<16, PTRV, BANDV>(ctx, ba, max_n, prefix);   \
     }
-    if (band) {
-        if (ptr) NW_BATCH_CASES(true, true)
-        NW_BATCH_CASES(false, true)
+    if (band == 2) {
+        if (ptr) NW_BATCH_CASES(true, 2)
+        NW_BATCH_CASES(false, 2)
     }
-    if (ptr) NW_BATCH_CASES(true, false)
-    NW_BATCH_CASES(false, false)
+    if (band == 1) NW_BATCH_CASES(false, 1)  // strict band: score-only inspection
+    if (ptr) NW_BATCH_CASES(true, 0)
+    NW_BATCH_CASES(false, 0)
 #undef NW_BATCH_CASES
 }
 
@@ -609,7 +615,7 @@ static int band_rounds(nw_ctx *ctx, const uint8_t *pool, const uint64_t *a_off, 
             ba.tasks = dt;
             ba.ntasks = (uint32_t)fill.size();
             ba.ptr = (uint32_t *)pv;
-            if ((rc = launch_batch(ctx, R, want, ba, max_n, true))) return rc;
+            if ((rc = launch_batch(ctx, R, want, ba, max_n, 2))) return rc;
             // certificate on the banded scores
             hs.resize(wave.size());
             for (size_t q = 0; q < wave.size(); ++q) {
@@ -704,7 +710,7 @@ static int band_raw(nw_ctx *ctx, const uint8_t *pool, const uint64_t *a_off, con
     ba.err = ctx->d_err;
     ba.tasks = dt;
     ba.ntasks = npairs;
-    return launch_batch(ctx, R, false, ba, max_n, true);
+    return launch_batch(ctx, R, false, ba, max_n, 1);
 }
 
 // Certified band for every pair with the given starting half-widths, then
@@ -833,11 +839,11 @@ int batch_device_impl(nw_ctx *ctx, const uint8_t *pool, const uint64_t *a_off, c
         BatchArgs bs = ba;
         bs.tasks = dt;
         bs.ntasks = npairs;
-        if ((rc = tune_rows(ctx, lpt, R, [&](int r) { return launch_batch(ctx, r, false, bs, max_n, false, pre); },
+        if ((rc = tune_rows(ctx, lpt, R, [&](int r) { return launch_batch(ctx, r, false, bs, max_n, 0, pre); },
                             &R)))
             return rc;
         if (!want) {
-            auto launches = [&]() -> int { return launch_batch(ctx, R, false, bs, max_n, false, pre); };
+            auto launches = [&]() -> int { return launch_batch(ctx, R, false, bs, max_n, 0, pre); };
             if ((rc = launches())) return rc;
             if (graph) return capture_graph(ctx, gkey, pre, "batch_score", 1, launches);
             return NW_OK;
@@ -1068,11 +1074,11 @@ extern "C" int nw_score_all_pairs(nw_ctx *ctx, const uint8_t *pool2b, const uint
     uint32_t *dlen = nullptr;
     if ((rc = upload(ctx, (pre + "_len").c_str(), lens, &dlen))) return rc;
     int R = 16;
-    if ((rc = tune_rows(ctx, tasks, pick_rows(tasks), [&](int r) { return launch_batch(ctx, r, false, ba, max_n, false, pre); },
+    if ((rc = tune_rows(ctx, tasks, pick_rows(tasks), [&](int r) { return launch_batch(ctx, r, false, ba, max_n, 0, pre); },
                         &R)))
         return rc;
     auto launches = [&]() -> int {
-        int r = launch_batch(ctx, R, false, ba, max_n, false, pre);
+        int r = launch_batch(ctx, R, false, ba, max_n, 0, pre);
         if (r) return r;
         {
             LaunchTimer t(ctx, "diag");

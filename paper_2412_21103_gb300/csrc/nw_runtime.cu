@@ -155,10 +155,13 @@ int graph_launch(nw_ctx *ctx, const std::string &key, const char *label, uint32_
     if (it == ctx->graphs.end()) return NW_OK;
     cudaError_t e;
     {
-        LaunchTimer t(ctx, label, kernels);
+        // timed under the dominant kernel's name (one launch of it); the
+        // graph's other kernels are counted, untimed, under their own entry
+        LaunchTimer t(ctx, label, 1);
         e = cudaGraphLaunch(it->second.exec, ctx->stream);
     }
     if (e != cudaSuccess) return cuda_fail(ctx, e, "cudaGraphLaunch");
+    if (ctx->profiling && kernels > 1) ctx->stats["graph_other_kernels"].launches += kernels - 1;
     it->second.last_use = ++ctx->graph_seq;
     ++ctx->graph_replays;
     *replayed = true;

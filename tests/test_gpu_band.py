@@ -70,8 +70,22 @@ def test_certified_band_scores_and_cigars_exact(ctx, sc):
     assert s_only.tolist() == [s for s, _ in want]
 
 
+def _region_score(a, b, w, SH=256):
+    """The banded kernel's cell set: per stripe of SH rows, the columns from
+    the band's left edge at its top row to its right edge at its bottom row
+    (the stripe rectangle); boundary cells only where the band reaches them."""
+    m, n = a.size, b.size
+    lo, hi = oracle.band_limits(m, n, w)
+    i = np.arange(1, m + 1)
+    s = (i - 1) // SH
+    cbeg = np.maximum(0, s * SH + lo)
+    cend = np.minimum(n - 1, s * SH + SH - 1 + hi)
+    return oracle.region(a, b, cbeg + 1, cend + 1, min(n, hi), min(m, max(0, -lo)))
+
+
 def test_certificate_decisions_match_the_closed_form(ctx):
-    """Round-1 certifications = pairs whose oracle banded score beats U0."""
+    """Round-1 certifications = pairs whose oracle score over the kernel's
+    cell region (stripe rectangles around the band) beats U0."""
     import torch
     import paper_2412_21103_gb300 as nw
     c = nw.Context(0, torch.cuda.current_stream())
@@ -92,7 +106,9 @@ def test_certificate_decisions_match_the_closed_form(ctx):
         if rows * period * 10 >= rows * max(b.size, 96) * 6:
             continue            # the band would cover most of the grid: straight to full
         tried += 1
-        sb, _ = oracle.banded(a, b, w)
+        sb = _region_score(a, b, w)
+        sb_strict, _ = oracle.banded(a, b, w)
+        assert sb >= sb_strict  # a superset of the band
         U = oracle.exit_bound(a.size, b.size, w)
         expect += U is None or sb > U
     assert st["tried"] == tried

@@ -257,3 +257,59 @@ def test_exit_bound_is_attained_by_identical_sequences():
             assert (U0 is None) == (not out)
             if out:
                 assert U0 == max(out)
+
+
+def _path_cells(path):
+    i = j = 0
+    cells = [(0, 0)]
+    for mv in path:
+        i += mv in "du"
+        j += mv in "dl"
+        cells.append((i, j))
+    return cells
+
+
+def _allowed(i, j, lo, hi, row0_hi, col0_hi):
+    if i == 0:
+        return j <= row0_hi
+    if j == 0:
+        return i <= col0_hi
+    return lo[i - 1] <= j <= hi[i - 1]
+
+
+@pytest.mark.parametrize("seed", range(40))
+def test_region_dp_brute_force(seed):
+    """The region DP is the best path that stays inside the allowed cells
+    (brute force over every path for lengths <= 6, random regions)."""
+    rng = np.random.default_rng(seed)
+    m, n = int(rng.integers(1, 7)), int(rng.integers(1, 7))
+    a, b = rng.integers(0, 4, m).astype(np.uint8), rng.integers(0, 4, n).astype(np.uint8)
+    lo = rng.integers(1, n + 1, m)
+    hi = np.minimum(n, lo + rng.integers(0, n, m))
+    row0_hi, col0_hi = int(rng.integers(0, n + 1)), int(rng.integers(0, m + 1))
+    sc = [(1, -1, -1), (2, -1, -2), (1, 0, 0)][seed % 3]
+    best = None
+    for p in all_paths(m, n):
+        if all(_allowed(i, j, lo, hi, row0_hi, col0_hi) for i, j in _path_cells(p)):
+            s = path_score(p, a, b, *sc)
+            best = s if best is None else max(best, s)
+    got = oracle.region(a, b, lo, hi, row0_hi, col0_hi, *sc)
+    assert got == (best if best is not None else oracle.NEG_INF)
+
+
+@pytest.mark.parametrize("seed", range(6))
+def test_region_dp_reduces_to_full_and_band(seed):
+    """Whole grid -> full NW; exactly the band -> the banded DP."""
+    p = seqgen.long_mutated_pair(500 + seed, m=150 + 37 * seed)
+    a, b = p.a, p.b
+    m, n = a.size, b.size
+    full = oracle.region(a, b, np.ones(m, np.int64), np.full(m, n, np.int64), n, m)
+    assert full == oracle.score(a, b)
+    for w in (0, 3, 20):
+        lo_d, hi_d = oracle.band_limits(m, n, w)
+        i = np.arange(1, m + 1)
+        lo = np.maximum(1, i + lo_d)
+        hi = np.minimum(n, i + hi_d)
+        sb, _ = oracle.banded(a, b, w)
+        got = oracle.region(a, b, lo, hi, max(0, hi_d), max(0, -lo_d))
+        assert got == sb, w
