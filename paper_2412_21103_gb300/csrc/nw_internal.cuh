@@ -302,6 +302,7 @@ struct PairFill {
     uint32_t cs_lo = 0, cs_hi = 0xffffffffu;  // groups to run
     const uint32_t *ncols = nullptr;          // device word: columns needed (null: all)
     bool recompute = false;        // groups start from kept checkpoints, write none
+    bool keep_rows = false;        // every group's bottom row goes to `bnd` (the checkpoints)
 };
 uint32_t pair_bstride(uint32_t n);
 int launch_pair_fill(nw_ctx *ctx, const uint8_t *a2b, uint32_t m, const uint8_t *b2b, uint32_t n, const Profile &pf,

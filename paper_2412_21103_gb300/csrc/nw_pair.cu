@@ -35,6 +35,8 @@
 // phases (lanes starting, all lanes busy, lanes finishing) so the busy phase
 // has no per-lane tests.
 #include <algorithm>
+#include <cstdlib>
+#include <type_traits>
 
 #include "nw_internal.cuh"
 
@@ -60,6 +62,7 @@ struct PairArgs {
     uint32_t cs_lo, cs_hi;   // groups (CTA-stripes) to run
     const uint32_t *ncols;   // null, or a device word: only columns [0, *ncols) are needed
     uint32_t recompute;      // groups start from kept rows and write none
+    uint32_t keep_rows;      // every group's bottom row must reach global memory (checkpoints)
     int32_t *score;          // null: no score
     uint32_t *err;
 };
@@ -73,6 +76,76 @@ __device__ __forceinline__ bool smem_wait_geq(const volatile uint32_t *flag, uin
     const uint64_t t0 = global_ns();
     uint32_t spins = 0;
     while (vld(flag) < target) {
+        if ((++spins & 255u) == 0) {
+            if (vld(err) != 0u) return false;
+            if (global_ns() - t0 > kSpinNanos) {
+                raise_error(err, NW_ERR_TIMEOUT, where);
+                return false;
+            }
+        }
+    }
+    return true;
+}
+
+// Shared memory at cluster scope.  Ring counters and ring data may belong to
+// this CTA or to a neighbour CTA of the same thread-block cluster; every
+// access goes through a 32-bit shared::cluster address (mapa of the local
+// address to a CTA rank), so one instruction serves both cases.
+__device__ __forceinline__ uint32_t cl_rank() {
+    uint32_t r;
+    asm volatile("mov.u32 %0, %%cluster_ctarank;" : "=r"(r));
+    return r;
+}
+__device__ __forceinline__ uint32_t cl_id() {
+    uint32_t r;
+    asm volatile("mov.u32 %0, %%clusterid.x;" : "=r"(r));
+    return r;
+}
+__device__ __forceinline__ uint32_t cl_count() {
+    uint32_t r;
+    asm volatile("mov.u32 %0, %%nclusterid.x;" : "=r"(r));
+    return r;
+}
+__device__ __forceinline__ uint32_t cl_map(const void *local, uint32_t rank) {
+    uint32_t r;
+    asm volatile("mapa.shared::cluster.u32 %0, %1, %2;" : "=r"(r) : "r"((uint32_t)__cvta_generic_to_shared(local)), "r"(rank));
+    return r;
+}
+__device__ __forceinline__ uint32_t ld_acq_cl(uint32_t a) {
+    uint32_t v;
+    asm volatile("ld.acquire.cluster.shared::cluster.u32 %0, [%1];" : "=r"(v) : "r"(a) : "memory");
+    return v;
+}
+__device__ __forceinline__ void st_rel_cl(uint32_t a, uint32_t v) {
+    asm volatile("st.release.cluster.shared::cluster.u32 [%0], %1;" ::"r"(a), "r"(v) : "memory");
+}
+__device__ __forceinline__ void cluster_sync() {
+    asm volatile("barrier.cluster.arrive.release.aligned;\n\tbarrier.cluster.wait.acquire.aligned;" ::: "memory");
+}
+// Predicated vector store to a shared::cluster address (no branch).
+template <int N>
+__device__ __forceinline__ void st_cl_if(bool p, uint32_t a, const uint32_t (&v)[N]) {
+    if constexpr (N == 2) {
+        asm volatile("{.reg .pred q; setp.ne.b32 q, %0, 0; @q st.shared::cluster.v2.u32 [%1], {%2, %3};}" ::"r"((uint32_t)p),
+                     "r"(a), "r"(v[0]), "r"(v[1])
+                     : "memory");
+    } else {
+#pragma unroll
+        for (int c = 0; c < N; c += 4)
+            asm volatile(
+                "{.reg .pred q; setp.ne.b32 q, %0, 0; @q st.shared::cluster.v4.u32 [%1], {%2, %3, %4, %5};}" ::"r"(
+                    (uint32_t)p),
+                "r"(a + 16u * (c / 4)), "r"(v[c]), "r"(v[c + 1]), "r"(v[c + 2]), "r"(v[c + 3])
+                : "memory");
+    }
+}
+// Bounded wait on a shared::cluster counter (acquire: the ring data written
+// before its release is visible afterwards).
+__device__ __forceinline__ bool cl_wait_geq(uint32_t a, uint32_t target, uint32_t *err, uint32_t where) {
+    if (ld_acq_cl(a) >= target) return true;
+    const uint64_t t0 = global_ns();
+    uint32_t spins = 0;
+    while (ld_acq_cl(a) < target) {
         if ((++spins & 255u) == 0) {
             if (vld(err) != 0u) return false;
             if (global_ns() - t0 > kSpinNanos) {
@@ -235,33 +308,33 @@ __device__ __forceinline__ void pair_block(LaneState<R, C> &st, const uint32_t (
 }
 
 // The courier warp of a CTA: all global-memory traffic of the group's rows.
-// Incoming: the previous group's kept bottom row (or the zeros of grid row
-// 0) into ring 0, published by head[0] as the producer releases it.
-// Outgoing: the last compute warp's bottom row from ring NW to global
-// memory, released every few chunks.  The compute warps only ever wait on
-// shared-memory counters; the round trips to L2 stall this warp alone.
+// Incoming (do_in): the previous group's kept bottom row (or the zeros of
+// grid row 0) into ring 0, published by head[0] as the producer releases it.
+// Outgoing (do_out): the last compute warp's bottom row from ring NW to
+// global memory, released every few chunks.  The compute warps only ever
+// wait on shared-memory counters; the round trips to L2 stall this warp.
 template <int C>
-__device__ __forceinline__ void pair_courier(const PairArgs &p, uint32_t cs, uint32_t NW, uint32_t NB,
-                                             uint32_t (*ringW)[kPairQ], volatile uint32_t *head,
-                                             volatile uint32_t *tail) {
+__device__ __forceinline__ void pair_courier(const PairArgs &p, uint32_t cs, uint32_t NW, uint32_t NB, bool do_in,
+                                             bool do_out, uint32_t (*ringW)[kPairQ], uint32_t *head, uint32_t *tail,
+                                             uint32_t me) {
     constexpr uint32_t QB = kPairQ / C;
     constexpr uint32_t KB = kPairKQ / C;
     constexpr uint32_t MAXB = 8 * KB;  // blocks moved per step of the loop (128 columns)
     const int lane = threadIdx.x & 31;
-    const uint32_t last_s = min((cs + 1) * NW, p.S) - 1;
-    const bool in_glob = cs > 0;
-    const bool out_needed = !p.recompute && last_s + 1 < p.S;  // (then the group is full)
+    const bool in_glob = do_in && cs > 0;
     const uint32_t *gin = in_glob ? p.bnd + (size_t)(cs - 1) * p.bstride : nullptr;
-    uint32_t *gout = out_needed ? p.bnd + (size_t)cs * p.bstride : nullptr;
-    uint32_t delivered = 0, forwarded = 0;
+    uint32_t *gout = do_out ? p.bnd + (size_t)cs * p.bstride : nullptr;
+    (void)me;  // (the courier's rings are this CTA's: CTA-scope ordering)
+    volatile uint32_t *v_head = head, *v_tail = tail;
+    uint32_t delivered = do_in ? 0u : NB, forwarded = do_out ? 0u : NB;
     uint32_t avail_in = in_glob ? 0u : NB * C;  // columns released upstream (as last seen)
     uint64_t t_moved = global_ns();
     uint32_t idle = 0;
-    for (;;) {
+    while (delivered < NB || forwarded < NB) {
         bool moved = false;
         if (delivered < NB) {
             uint32_t next = min(delivered + MAXB, NB);
-            next = min(next, (uint32_t)vld(tail) + QB);  // ring 0 space
+            next = min(next, vld(v_tail) + QB);  // ring 0 space
             if (in_glob && avail_in < next * C && avail_in < NB * C) {
                 uint32_t v = 0;
                 if (lane == 0) v = ld_acquire(&p.progress[cs - 1]);
@@ -277,13 +350,13 @@ __device__ __forceinline__ void pair_courier(const PairArgs &p, uint32_t cs, uin
                 }
                 __syncwarp();
                 __threadfence_block();
-                if (lane == 0) head[0] = next;
+                if (lane == 0) v_head[0] = next;
                 delivered = next;
                 moved = true;
             }
         }
-        if (out_needed && forwarded < NB) {
-            const uint32_t avail = vld(head + NW);
+        if (forwarded < NB) {
+            const uint32_t avail = vld(v_head + NW);
             if (avail > forwarded) {
                 __threadfence_block();
                 const uint32_t upto = min(avail, forwarded + MAXB);
@@ -294,7 +367,7 @@ __device__ __forceinline__ void pair_courier(const PairArgs &p, uint32_t cs, uin
                     v[k] = col < upto * C ? ringW[NW][col % kPairQ] : 0u;
                 }
                 __syncwarp();
-                if (lane == 0) tail[NW] = upto;  // the slots are free once read
+                if (lane == 0) v_tail[NW] = upto;  // the slots are free once read
 #pragma unroll
                 for (uint32_t k = 0; k < MAXB * C / 32; ++k) {
                     const uint32_t col = forwarded * C + k * 32u + lane;
@@ -307,7 +380,6 @@ __device__ __forceinline__ void pair_courier(const PairArgs &p, uint32_t cs, uin
                 moved = true;
             }
         }
-        if (delivered >= NB && (!out_needed || forwarded >= NB)) break;
         if (moved) {
             idle = 0;
             t_moved = global_ns();
@@ -322,16 +394,24 @@ __device__ __forceinline__ void pair_courier(const PairArgs &p, uint32_t cs, uin
     }
 }
 
-template <int R, int C, bool PTR>
+// CLS: CTAs per thread-block cluster (1: no cluster).  With clusters the
+// groups of one cluster are consecutive and hand their rows over through
+// distributed shared memory: the last compute warp of rank r stores its
+// bottom row straight into ring 0 of rank r+1 and releases rank r+1's
+// head[0]; rank r+1's first warp returns its consumption into rank r's
+// `tail_rem`.  Only the first and last rank of a cluster use the courier.
+template <int R, int C, bool PTR, int CLS>
 __global__ void __launch_bounds__((kPairMaxWarps + 1) * 32, 1) k_pair(PairArgs p) {
     constexpr uint32_t SH = 32u * R;
     constexpr uint32_t QB = kPairQ / C;   // ring capacity in blocks
     constexpr uint32_t KB = kPairKQ / C;  // blocks per chunk (flags)
-    // ring w < NW: input of compute warp w (ring 0 filled by the courier);
-    // ring NW: output of the last compute warp, drained by the courier
+    // ring w < NW: input of compute warp w (ring 0 filled by the courier or
+    // by the previous rank); ring NW: output of the last compute warp,
+    // drained by the courier
     __shared__ __align__(16) uint32_t ringW[kPairMaxWarps + 1][kPairQ];
     __shared__ uint32_t head[kPairMaxWarps + 1];  // blocks written into ring[w]
     __shared__ uint32_t tail[kPairMaxWarps + 1];  // blocks of ring[w] consumed
+    __shared__ uint32_t tail_rem;                 // blocks of the next rank's ring 0 consumed
 
     const int lane = threadIdx.x & 31;
     const int w = threadIdx.x >> 5;
@@ -339,23 +419,37 @@ __global__ void __launch_bounds__((kPairMaxWarps + 1) * 32, 1) k_pair(PairArgs p
     const uint32_t m = p.m;
     // recompute passes need only the columns left of the traceback's entry
     const uint32_t n = p.ncols ? min(p.n, *p.ncols) : p.n;
-    if (n == 0) return;
+    if (n == 0) return;  // (uniform over the grid: every CTA returns)
     const uint32_t NB = (n + C - 1) / C;
     const uint32_t CS = (p.S + NW - 1) / NW;
     const uint32_t sM = (m - 1) / SH, lM = ((m - 1) % SH) / R, rM = (m - 1) % R;
     const uint32_t qL = NB - 1, cL = (n - 1) % C;
-
+    const uint32_t me = CLS > 1 ? cl_rank() : 0u;
     const uint32_t cs_end = min(CS, p.cs_hi);
-    for (uint32_t cs = p.cs_lo + blockIdx.x; cs < cs_end; cs += gridDim.x) {
+    const uint32_t first = CLS > 1 ? cl_id() * CLS : blockIdx.x;
+    const uint32_t stride = CLS > 1 ? cl_count() * CLS : gridDim.x;
+
+    for (uint32_t base = p.cs_lo + first; base < cs_end; base += stride) {
+        const uint32_t cs = base + me;  // this CTA's group (past cs_end: idle this round)
+        const bool active = cs < cs_end;
         if (lane == 0) {
             head[w] = 0;
             tail[w] = 0;
+            if (w == 0) tail_rem = 0;
         }
         __syncthreads();
+        if (CLS > 1) cluster_sync();  // every rank reset before any remote write
+        // hand-overs inside the cluster (never in recompute passes: there
+        // every group starts from its kept row)
+        const bool in_dsm = CLS > 1 && me > 0 && active && !p.recompute;
+        const bool next_here = CLS > 1 && me + 1 < CLS && cs + 1 < cs_end;
+        const uint32_t last_s = min((cs + 1) * NW, p.S) - 1;
+        const bool out_any = active && !p.recompute && last_s + 1 < p.S;
+        const bool out_dsm = out_any && next_here;
         const uint32_t s = cs * NW + w;
         if (w == NW) {
-            pair_courier<C>(p, cs, NW, NB, ringW, head, tail);
-        } else if (s < p.S) {
+            if (active) pair_courier<C>(p, cs, NW, NB, !in_dsm, out_any && !out_dsm, ringW, head, tail, me);
+        } else if (active && s < p.S) {
             LaneState<R, C> st;
             {
                 const uint32_t row0 = s * SH + lane * R;
@@ -374,92 +468,126 @@ __global__ void __launch_bounds__((kPairMaxWarps + 1) * 32, 1) k_pair(PairArgs p
                 st.accH = 0;
             }
             const bool has_next = s + 1 < p.S;
-            // output ring w+1 (ring NW goes to global memory; not in recompute passes)
-            const bool out_ring = has_next && (w + 1 < NW || !p.recompute);
+            const bool last_w = w + 1 == NW;
+            // output: ring w+1 of this CTA, ring NW (the courier's), or ring 0
+            // of the next rank (not in recompute passes)
+            const bool out_ring = has_next && (!last_w || out_any);
+            const bool remote_out = last_w && out_dsm;
             uint32_t *prow = PTR ? p.ptr + (size_t)((s - p.s_ptr0) * 32u + lane) * p.ncg : nullptr;
+            // Same-CTA rings: volatile counters and CTA-scope fences.  The ring
+            // to / from a neighbour rank: shared::cluster addresses with
+            // cluster-scope release / acquire.
+            const bool remote_in = w == 0 && in_dsm;
             volatile uint32_t *my_head = head + w;
             volatile uint32_t *my_tail = tail + w;
             volatile uint32_t *nx_head = head + w + 1;
             volatile uint32_t *nx_tail = tail + w + 1;
-            uint32_t *myW = ringW[w], *nxW = ringW[w + 1];
+            uint32_t *nxW = ringW[w + 1];
+            const uint32_t a_my_head = cl_map(head + w, me);
+            const uint32_t a_rem_tail = remote_in ? cl_map(&tail_rem, me - 1) : 0u;
+            const uint32_t a_nx_head = remote_out ? cl_map(head, me + 1) : 0u;
+            const uint32_t a_nx_tail = cl_map(&tail_rem, me);
+            const uint32_t a_nx_ring = remote_out ? cl_map(ringW[0], me + 1) : 0u;
+            const uint32_t *myW = ringW[w];
             bool ok = true;
 
             // Chunk bookkeeping before steps [t, t+KB) (warp-uniform).
             auto chunk_begin = [&](uint32_t t) -> bool {
                 if (t < NB) {
-                    if (!smem_wait_geq(my_head, min(t + KB, NB), p.err, 0x10000u + s)) return false;
-                    __threadfence_block();
+                    if (remote_in) {
+                        if (!cl_wait_geq(a_my_head, min(t + KB, NB), p.err, 0x10000u + s)) return false;
+                    } else {
+                        if (!smem_wait_geq(my_head, min(t + KB, NB), p.err, 0x10000u + s)) return false;
+                        __threadfence_block();
+                    }
                 }
                 if (out_ring) {
                     // lane 31 will write blocks [t-31, t-31+KB): their slots must be free
                     const int32_t need = (int32_t)t - 31 + (int32_t)KB - (int32_t)QB;
-                    if (need > 0 && !smem_wait_geq(nx_tail, (uint32_t)need, p.err, 0x20000u + s)) return false;
+                    if (need > 0) {
+                        const bool ok2 = remote_out ? cl_wait_geq(a_nx_tail, (uint32_t)need, p.err, 0x20000u + s)
+                                                    : smem_wait_geq(nx_tail, (uint32_t)need, p.err, 0x20000u + s);
+                        if (!ok2) return false;
+                    }
                 }
                 return true;
             };
             // After steps [t, t+KB): publish what lane 31 wrote / what was read.
             auto chunk_end = [&](uint32_t t) {
                 if (lane == 31) {
-                    *my_tail = t + KB;
+                    if (remote_in) st_rel_cl(a_rem_tail, t + KB);
+                    else *my_tail = t + KB;
                     const int32_t done = min((int32_t)t + (int32_t)KB - 31, (int32_t)NB);
                     if (out_ring && done > 0) {
-                        __threadfence_block();
-                        *nx_head = (uint32_t)done;
+                        if (remote_out) {
+                            st_rel_cl(a_nx_head, (uint32_t)done);
+                        } else {
+                            __threadfence_block();
+                            *nx_head = (uint32_t)done;
+                        }
                     }
                 }
             };
             // Input block t for lane 0 (all lanes read it: a broadcast).
             auto ring_in = [&](uint32_t t, uint32_t (&iw)[C]) { ld_vec<C>(iw, myW + (t % QB) * C); };
-            // Lane 31 hands block t-31 on (a predicated store: no branch).
-            auto lane31_out = [&](uint32_t t) {
-                const int32_t q31 = (int32_t)t - 31;
-                const bool valid = out_ring && lane == 31 && q31 >= 0 && q31 < (int32_t)NB;
-                const uint32_t qv = valid ? (uint32_t)q31 : 0u;
-                st_vec_if<C>(valid, nxW + (qv % QB) * C, st.outW);
-            };
 
-            const uint32_t T = NB + 31;
-            // busy chunks: every lane active, none on the last block
-            const uint32_t busy_end = NB >= 1 ? NB - 1 : 0;
-            uint32_t t = 0;
-            uint32_t inW[C], sel[C];
-            while (ok && t < T) {
-                if (!chunk_begin(t)) {
-                    ok = false;
-                    break;
-                }
-                if (t >= 32 && t + KB <= busy_end) {
-                    // selectors two steps ahead (an L1 miss costs more than a step)
-                    uint32_t sel1[C];
-                    ring_in(t, inW);
-                    ld_sel<C>(sel, p.sel, t - (uint32_t)lane);
-                    ld_sel<C>(sel1, p.sel, t + 1 - (uint32_t)lane);
+            // The step loop, instantiated for a local or a remote output ring
+            // (lane 31's predicated store; no branch per step).
+            auto run = [&](auto remote_tag) {
+                constexpr bool RO = decltype(remote_tag)::value;
+                auto lane31_out = [&](uint32_t t) {
+                    const int32_t q31 = (int32_t)t - 31;
+                    const bool valid = out_ring && lane == 31 && q31 >= 0 && q31 < (int32_t)NB;
+                    const uint32_t qv = valid ? (uint32_t)q31 : 0u;
+                    if constexpr (RO) st_cl_if<C>(valid, a_nx_ring + (qv % QB) * C * 4u, st.outW);
+                    else st_vec_if<C>(valid, nxW + (qv % QB) * C, st.outW);
+                };
+                const uint32_t T = NB + 31;
+                // busy chunks: every lane active, none on the last block
+                const uint32_t busy_end = NB >= 1 ? NB - 1 : 0;
+                uint32_t t = 0;
+                uint32_t inW[C], sel[C];
+                while (ok && t < T) {
+                    if (!chunk_begin(t)) {
+                        ok = false;
+                        break;
+                    }
+                    if (t >= 32 && t + KB <= busy_end) {
+                        // selectors two steps ahead (an L1 miss costs more than a step)
+                        uint32_t sel1[C];
+                        ring_in(t, inW);
+                        ld_sel<C>(sel, p.sel, t - (uint32_t)lane);
+                        ld_sel<C>(sel1, p.sel, t + 1 - (uint32_t)lane);
 #pragma unroll
-                    for (uint32_t u = 0; u < KB; ++u) {
-                        uint32_t nW[C], nS[C];
-                        if (u + 1 < KB) ring_in(t + u + 1, nW);
-                        if (u + 2 < KB) ld_sel<C>(nS, p.sel, t + u + 2 - (uint32_t)lane);
-                        pair_block<R, C, PTR, false>(st, inW, sel, (int32_t)(t + u) - lane, NB, qL, cL, lane, prow);
-                        lane31_out(t + u);
+                        for (uint32_t u = 0; u < KB; ++u) {
+                            uint32_t nW[C], nS[C];
+                            if (u + 1 < KB) ring_in(t + u + 1, nW);
+                            if (u + 2 < KB) ld_sel<C>(nS, p.sel, t + u + 2 - (uint32_t)lane);
+                            pair_block<R, C, PTR, false>(st, inW, sel, (int32_t)(t + u) - lane, NB, qL, cL, lane,
+                                                         prow);
+                            lane31_out(t + u);
 #pragma unroll
-                        for (int c = 0; c < C; ++c) {
-                            if (u + 1 < KB) inW[c] = nW[c];
-                            sel[c] = sel1[c];
-                            if (u + 2 < KB) sel1[c] = nS[c];
+                            for (int c = 0; c < C; ++c) {
+                                if (u + 1 < KB) inW[c] = nW[c];
+                                sel[c] = sel1[c];
+                                if (u + 2 < KB) sel1[c] = nS[c];
+                            }
+                        }
+                    } else {
+                        for (uint32_t u = 0; u < KB; ++u) {
+                            ring_in(t + u, inW);
+                            const int32_t q = (int32_t)(t + u) - lane;
+                            ld_sel<C>(sel, p.sel, (uint32_t)min(max(q, 0), (int32_t)NB - 1));
+                            pair_block<R, C, PTR, true>(st, inW, sel, q, NB, qL, cL, lane, prow);
+                            lane31_out(t + u);
                         }
                     }
-                } else {
-                    for (uint32_t u = 0; u < KB; ++u) {
-                        ring_in(t + u, inW);
-                        const int32_t q = (int32_t)(t + u) - lane;
-                        ld_sel<C>(sel, p.sel, (uint32_t)min(max(q, 0), (int32_t)NB - 1));
-                        pair_block<R, C, PTR, true>(st, inW, sel, q, NB, qL, cL, lane, prow);
-                        lane31_out(t + u);
-                    }
+                    chunk_end(t);
+                    t += KB;
                 }
-                chunk_end(t);
-                t += KB;
-            }
+            };
+            if (CLS > 1 && remote_out) run(std::true_type{});
+            else run(std::false_type{});
             if (ok && p.score && s == sM && (uint32_t)lane == lM) {
                 int32_t wmn = 0;
 #pragma unroll
@@ -469,6 +597,7 @@ __global__ void __launch_bounds__((kPairMaxWarps + 1) * 32, 1) k_pair(PairArgs p
             }
         }
         __syncthreads();
+        if (CLS > 1) cluster_sync();  // no rank resets while a neighbour still reads or writes it
     }
 }
 
@@ -478,19 +607,79 @@ __global__ void k_selectors(const uint8_t *b, uint32_t n, uint32_t count, uint32
         sel[j] = sext_selector(j < n ? base_at(b, j) : 0u);
 }
 
+// Cluster launch of CLS CTAs per cluster; grid = the resident clusters (or
+// fewer), so every wait across clusters ends.  Returns 1 (nothing launched)
+// when the cluster shape cannot be scheduled.
+template <int R, int C, bool PTR, int CLS>
+static int launch_pair_cl(nw_ctx *ctx, PairArgs &pa, int nw, uint32_t groups) {
+    auto kern = k_pair<R, C, PTR, CLS>;
+    cudaLaunchConfig_t cfg = {};
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeClusterDimension;
+    attr[0].val.clusterDim.x = CLS;
+    attr[0].val.clusterDim.y = 1;
+    attr[0].val.clusterDim.z = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    cfg.blockDim = dim3((unsigned)(nw + 1) * 32u);
+    cfg.stream = ctx->stream;
+    // unused dynamic shared memory so that each SM takes one CTA of the
+    // cluster (the scheduler would otherwise stack several on one SM, whose
+    // compute warps then share schedulers)
+    int pad_kb = 110;
+    if (const char *e = getenv("NW_PAIR_CL_PAD")) pad_kb = atoi(e);
+    cfg.dynamicSmemBytes = (size_t)pad_kb * 1024;
+    if (pad_kb > 0 &&
+        cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)cfg.dynamicSmemBytes) != cudaSuccess) {
+        cudaGetLastError();
+        return 1;
+    }
+    uint32_t want = (groups + CLS - 1) / CLS;
+    cfg.gridDim = dim3(want * CLS);
+    int ncl = 0;
+    if (cudaOccupancyMaxActiveClusters(&ncl, kern, &cfg) != cudaSuccess || ncl < 1) {
+        cudaGetLastError();
+        return 1;
+    }
+    if (want > (uint32_t)ncl) want = (uint32_t)ncl;
+    cfg.gridDim = dim3(want * CLS);
+    cudaError_t e;
+    {
+        LaunchTimer t(ctx, PTR ? "fill_ptr" : "fill_score");
+        e = cudaLaunchKernelEx(&cfg, kern, pa);
+    }
+    return e == cudaSuccess ? NW_OK : cuda_fail(ctx, e, "cluster launch");
+}
+
 template <int R, int C, bool PTR>
 static int launch_pair_R(nw_ctx *ctx, PairArgs &pa, int nw) {
-    int occ = 0;
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_pair<R, C, PTR>, (nw + 1) * 32, 0);
-    if (occ < 1) occ = 1;
     const uint32_t CS = (pa.S + nw - 1) / nw;
     const uint32_t hi = std::min(CS, pa.cs_hi);
     if (pa.cs_lo >= hi) return NW_OK;
-    uint32_t blocks = hi - pa.cs_lo;
+    const uint32_t groups = hi - pa.cs_lo;
+    // Optional (NW_PAIR_CLUSTER = 2, 4 or 8): consecutive groups in one
+    // thread-block cluster hand rows over through distributed shared memory.
+    // Measured on GB300 it is slower than the courier path (32k x 32k: 6.6
+    // vs 4.6 ms): the cluster-scope release that publishes each chunk also
+    // waits for the warp's outstanding global pointer stores.  Never for
+    // recompute passes or checkpoint fills (every group's row must reach
+    // global memory there).
+    int cls = 1;
+    if (const char *e = getenv("NW_PAIR_CLUSTER")) cls = atoi(e);
+    if (pa.recompute || pa.keep_rows || groups < 2) cls = 1;
+    int rc = 1;
+    if (cls == 8) rc = launch_pair_cl<R, C, PTR, 8>(ctx, pa, nw, groups);
+    else if (cls == 4) rc = launch_pair_cl<R, C, PTR, 4>(ctx, pa, nw, groups);
+    else if (cls == 2) rc = launch_pair_cl<R, C, PTR, 2>(ctx, pa, nw, groups);
+    if (rc != 1) return rc;
+    int occ = 0;
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_pair<R, C, PTR, 1>, (nw + 1) * 32, 0);
+    if (occ < 1) occ = 1;
+    uint32_t blocks = groups;
     const uint32_t cap = (uint32_t)occ * (uint32_t)ctx->sm_count;  // co-resident
     if (blocks > cap) blocks = cap;
     LaunchTimer t(ctx, pa.recompute ? "fill_recompute" : PTR ? "fill_ptr" : "fill_score");
-    k_pair<R, C, PTR><<<blocks, (nw + 1) * 32, 0, ctx->stream>>>(pa);
+    k_pair<R, C, PTR, 1><<<blocks, (nw + 1) * 32, 0, ctx->stream>>>(pa);
     return NW_OK;
 }
 
@@ -515,6 +704,7 @@ int launch_pair_fill(nw_ctx *ctx, const uint8_t *a2b, uint32_t m, const uint8_t 
     pa.s_ptr0 = f.cs_lo * (uint32_t)nw;
     pa.ncols = f.ncols;
     pa.recompute = f.recompute ? 1u : 0u;
+    pa.keep_rows = f.keep_rows ? 1u : 0u;
     pa.score = f.score;
     pa.err = ctx->d_err;
     int rc;

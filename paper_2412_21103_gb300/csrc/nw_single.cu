@@ -230,7 +230,9 @@ static int run_pair_recompute(nw_ctx *ctx, const uint8_t *a2b, uint32_t m, const
     f.score = score;
     f.bnd = bnd;
     f.progress = progress;
+    f.keep_rows = true;
     if ((rc = launch_pair_fill(ctx, a2b, m, b2b, n, pf, f))) return rc;  // checkpoints + score
+    f.keep_rows = false;
     {
         LaunchTimer t(ctx, "walk_init");
         k_walk_init<<<1, 1, 0, ctx->stream>>>(state, m, n);

@@ -173,3 +173,20 @@ def test_pair_kernel_shapes(ctx, R, C, nwarps, monkeypatch):
                        (5, 300, 16 // R * 7 + 1)]:
         p = seqgen.long_mutated_pair(seed, m=m)
         _check(ctx, p.a, p.b[:n] if n < p.b.size else p.b)
+
+
+@pytest.mark.parametrize("cls", [2, 4, 8])
+@pytest.mark.parametrize("R,C,nwarps", [(8, 2, 4), (4, 2, 2), (4, 4, 1)])
+def test_pair_kernel_cluster_handoffs(ctx, cls, R, C, nwarps, monkeypatch):
+    """Row groups handed over through distributed shared memory inside a
+    thread-block cluster (opt-in path): exact, including partial clusters
+    (groups not a multiple of the cluster size) and several clusters."""
+    monkeypatch.setenv("NW_PAIR_CLUSTER", str(cls))
+    monkeypatch.setenv("NW_PAIR_R", str(R))
+    monkeypatch.setenv("NW_PAIR_C", str(C))
+    monkeypatch.setenv("NW_PAIR_WARPS", str(nwarps))
+    group_rows = 32 * R * nwarps
+    cases = [(1, 2), (2, cls + 1)] + ([(3, 3 * cls)] if group_rows * 3 * cls <= 6200 else [])
+    for seed, groups in cases:
+        p = seqgen.long_mutated_pair(900 + seed, m=group_rows * groups - 13)
+        _check(ctx, p.a, p.b)
