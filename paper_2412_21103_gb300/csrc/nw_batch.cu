@@ -50,6 +50,12 @@ struct BatchArgs {
     uint32_t *err;
 };
 
+// One predicated 32-bit global store (no branch around it).
+__device__ __forceinline__ void st_global_if(bool p, uint32_t *dst, uint32_t v) {
+    asm volatile("{.reg .pred q; setp.ne.b32 q, %0, 0; @q st.global.u32 [%1], %2;}" ::"r"((uint32_t)p), "l"(dst), "r"(v)
+                 : "memory");
+}
+
 // Base codes of rows [i0, i0+R) of a packed sequence of length m (R = 4, 8
 // or 16, i0 a multiple of 4), two bits per row; rows >= m read as 0.
 template <int R>
@@ -164,6 +170,52 @@ __global__ void __launch_bounds__(kBatchWarps * 32) k_batch(BatchArgs p) {
                 __threadfence_block();
                 __syncwarp();
                 stage_next = chunk_word(t + 32u + (uint32_t)lane);
+                // Fast chunk: for the next 32 steps every lane stays inside its
+                // stripe and short of the stripe's last column, so no step
+                // needs the activity test, the stripe change, the last-column
+                // word flush or the score check (not for the strict band,
+                // whose edge mask lives in the general step).
+                if (BAND != 1 && __all_sync(kFull, c >= 0 && s < S && c + 32 <= ce - cb)) {
+                    const bool ring_out = lane == 31 && s + 1 < S;
+                    uint32_t cc = (uint32_t)c % CPW;
+                    uint32_t *prow = PTR ? pbase + (size_t)(s * 32u + lane) * tk.ncg : nullptr;
+#pragma unroll 4
+                    for (uint32_t u = 0; u < 32u; ++u) {
+                        uint32_t x = __shfl_up_sync(kFull, xout, 1);
+                        const uint32_t x0 = __shfl_sync(kFull, stage, u);
+                        if (lane == 0) x = x0;
+                        const int32_t up = (int32_t)x >> 2;
+                        const uint32_t sel = sext_selector(x & 3u);
+                        int32_t d = dtop, uv = up;
+#pragma unroll
+                        for (int r = 0; r < R; ++r) {
+                            const int32_t sv = (int32_t)prmt(prof[r], 0u, sel);
+                            int32_t w;
+                            if constexpr (PTR) {
+                                const int32_t l = Wl[r], m2 = max(uv, l);
+                                w = __viaddmax_s32(d, sv, m2);
+                                accL = ptr_append(accL, d + sv - m2);
+                                accH = ptr_append(accH, uv - l);
+                            } else {
+                                w = max(__viaddmax_s32(d, sv, Wl[r]), uv);
+                            }
+                            d = Wl[r];
+                            Wl[r] = w;
+                            uv = w;
+                        }
+                        dtop = up;
+                        xout = ((uint32_t)uv << 2) | (x & 3u);
+                        const uint32_t cu = (uint32_t)c + u;
+                        if constexpr (PTR) {
+                            if (cc == CPW - 1) prow[cu / CPW] = ptr_word(accL, accH);
+                            cc = (cc + 1) & (CPW - 1);
+                        }
+                        st_global_if(ring_out, ring + cb + cu, xout);
+                    }
+                    c += 32;
+                    t += 31;
+                    continue;
+                }
             }
             uint32_t x = __shfl_up_sync(kFull, xout, 1);
             const uint32_t x0 = __shfl_sync(kFull, stage, t & 31u);
