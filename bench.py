@@ -552,6 +552,7 @@ def run_ours(args):
     ms = statistics.mean(e0.elapsed_time(e1) for e0, e1 in evs)
     ctx.sync()
     stats = ctx.kernel_stats()
+    band_cells = nw.nw_ctx_band_stats(ctx)["band_cells"] - band0  # the timed steps' banded cells
     if world > 1:
         t = torch.tensor([ms], device=dev)
         dist.all_reduce(t, op=dist.ReduceOp.MAX)
@@ -575,7 +576,6 @@ def run_ours(args):
     dom_avg_ms = dms / max(dl, 1)
     # cells the dominant kernel computed per launch: the full grid, or for
     # the banded kernel the band cells it actually swept
-    band_cells = nw.nw_ctx_band_stats(ctx)["band_cells"] - band0
     kcells = (band_cells / max(dl, 1)) if work.dominant.startswith("band") else work.cells
     achieved = kcells * OPS_PER_CELL / (dom_avg_ms * 1e-3) / 1e9 if dom_avg_ms else None
     launches = sum(v[0] for k_, v in stats.items() if k_ != "peak")

@@ -18,6 +18,7 @@
 #include <cuda_bf16.h>
 
 #include <algorithm>
+#include <cstdlib>
 #include <cmath>
 #include <vector>
 
@@ -282,6 +283,8 @@ int learned_band_widths(nw_ctx *ctx, const uint8_t *pool, const uint64_t *a_off,
     w.assign(npairs, 64u);
     BandModel *bm = nullptr;
     if (!ctx->band_model) return NW_OK;  // no model: fixed starting width 64
+    double margin = 2.0;                 // (NW_BAND_MARGIN for sweeps)
+    if (const char *e = getenv("NW_BAND_MARGIN")) margin = std::max(0.5, atof(e));
     int rc = model_of(ctx, &bm, false);
     if (rc) return rc;
     void *v = nullptr;
@@ -310,7 +313,7 @@ int learned_band_widths(nw_ctx *ctx, const uint8_t *pool, const uint64_t *a_off,
     cudaMemcpyAsync(y.data(), a.y, (size_t)npairs * 4, cudaMemcpyDeviceToHost, ctx->stream);
     if ((rc = nw_ctx_sync(ctx))) return rc;
     for (uint32_t k = 0; k < npairs; ++k) {
-        const double pred = std::exp((double)y[k]) * 2.0;  // safety factor against under-prediction
+        const double pred = std::exp((double)y[k]) * margin;  // safety factor against under-prediction
         const double cap = (double)std::max(a_len[k], b_len[k]);
         w[k] = (uint32_t)std::min(cap, std::max(8.0, std::ceil(pred)));
     }

@@ -70,7 +70,10 @@ def test_certified_band_scores_and_cigars_exact(ctx, sc):
     assert s_only.tolist() == [s for s, _ in want]
 
 
-def _region_score(a, b, w, SH=256):
+BAND_R = 16  # rows per lane of the certified band's kernel (stripes of 32 * BAND_R rows)
+
+
+def _region_score(a, b, w, SH=32 * BAND_R):
     """The banded kernel's cell set: per stripe of SH rows, the columns from
     the band's left edge at its top row to its right edge at its bottom row
     (the stripe rectangle); boundary cells only where the band reaches them."""
@@ -98,7 +101,7 @@ def test_certificate_decisions_match_the_closed_form(ctx):
     tried = 0
     for a, b in pairs:
         lo, hi = oracle.band_limits(a.size, b.size, w)
-        R = 8
+        R = BAND_R
         SH = 32 * R
         width = min(b.size, SH + hi - lo)
         period = max(width, SH + 96)
