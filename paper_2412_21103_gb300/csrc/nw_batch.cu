@@ -801,6 +801,9 @@ static int band_batch(nw_ctx *ctx, const uint8_t *pool, const uint64_t *a_off, c
     int rc = band_rounds(ctx, pool, a_off, a_len, b_off, b_len, ids, width, sc, flags, scores, cigar_pool, cigar_off,
                          cigar_len, rest);
     if (rc || rest.empty()) return rc;
+    // the banded pointer words are dead now: hand their memory to the full
+    // kernel's waves (it stays in the context's pool for the next call)
+    free_prefix(ctx, "band_ptr");
     ctx->band_stats[5] += rest.size();
     return batch_device_impl(ctx, pool, a_off, a_len, b_off, b_len, rest.data(), (uint32_t)rest.size(), sc, flags,
                              scores, cigar_pool, cigar_off, cigar_len);
@@ -925,8 +928,15 @@ int batch_device_impl(nw_ctx *ctx, const uint8_t *pool, const uint64_t *a_off, c
     // (a wave always takes at least one pair; scratch() reports NW_ERR_OOM if
     // even that does not fit)
     const uint64_t wave_budget = (ctx->budget - std::min(ctx->budget, ctx->used)) / 2;
+    // waves in longest-first order: pairs of similar size run together, so a
+    // wave's time is not set by one long pair among many short ones; within
+    // a wave, the pairs that would keep it waiting on one warp go to the
+    // multi-warp kernel (same rule as for the whole batch)
     std::vector<uint32_t> order(npairs);
     std::iota(order.begin(), order.end(), 0u);  // positions in `tasks`
+    std::stable_sort(order.begin(), order.end(), [&](uint32_t x, uint32_t y) {
+        return (uint64_t)tasks[x].m * tasks[x].n > (uint64_t)tasks[y].m * tasks[y].n;
+    });
     size_t k0 = 0;
     while (k0 < npairs) {
         std::vector<BatchTask> wave;
@@ -944,6 +954,32 @@ int batch_device_impl(nw_ctx *ctx, const uint8_t *pool, const uint64_t *a_off, c
             mvbytes += (uint64_t)t.m + t.n + 16;
             wave.push_back(t);
             ids_w.push_back(t.out0);
+        }
+        if (k < npairs || k0 > 0) {  // a true wave (not the whole batch): route its stragglers
+            std::vector<double> wc(wave.size());
+            for (size_t q = 0; q < wave.size(); ++q) wc[q] = (double)wave[q].m * wave[q].n;
+            const std::vector<size_t> strag = pick_stragglers(wc, wc);
+            if (!strag.empty() && strag.size() < wave.size()) {
+                std::vector<char> routed(wave.size(), 0);
+                for (size_t q : strag) {
+                    const BatchTask &t = wave[q];
+                    const uint32_t id = t.out0;
+                    if ((rc = run_straggler(ctx, pool, t.a_off, t.m, t.b_off, t.n, sc, flags, scores + id,
+                                            cigar_pool + cigar_off[id], cigar_off[id + 1] - cigar_off[id],
+                                            cigar_len + id)))
+                        return rc;
+                    routed[q] = 1;
+                }
+                std::vector<BatchTask> keep;
+                std::vector<uint32_t> keep_ids;
+                for (size_t q = 0; q < wave.size(); ++q)
+                    if (!routed[q]) {
+                        keep.push_back(wave[q]);
+                        keep_ids.push_back(ids_w[q]);
+                    }
+                wave.swap(keep);
+                ids_w.swap(keep_ids);
+            }
         }
         void *pv = nullptr, *mv = nullptr, *nm = nullptr;
         if ((rc = scratch(ctx, "batch_ptr", words * 4 + 16, &pv))) return rc;

@@ -171,6 +171,9 @@ struct nw_ctx {
     uint64_t graph_seq = 0, graph_replays = 0, graph_captures = 0;
     bool capturing = false;            // LaunchTimer records nothing while capturing
     cudaStream_t capture_stream = nullptr;
+    // private stream-ordered pool of the scratch slots: freed slots stay
+    // reserved in it (release threshold: never), so regrowing is cheap
+    cudaMemPool_t mempool = nullptr;
 };
 
 namespace nw {

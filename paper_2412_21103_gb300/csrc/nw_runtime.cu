@@ -49,7 +49,8 @@ int scratch(nw_ctx *ctx, const char *name, size_t bytes, void **out) {
         b.cap = 0;
     }
     void *p = nullptr;
-    cudaError_t e = cudaMallocAsync(&p, want, ctx->stream);
+    cudaError_t e = ctx->mempool ? cudaMallocFromPoolAsync(&p, want, ctx->mempool, ctx->stream)
+                                 : cudaMallocAsync(&p, want, ctx->stream);
     if (e != cudaSuccess) {
         cudaGetLastError();
         return fail(ctx, NW_ERR_OOM, "cudaMallocAsync(%zu) for '%s': %s", want, name, cudaGetErrorString(e));
@@ -272,6 +273,17 @@ nw_ctx *nw_ctx_create(int device, void *stream, uint64_t mem_budget) {
         delete ctx;
         return nullptr;
     }
+    cudaMemPoolProps props = {};
+    props.allocType = cudaMemAllocationTypePinned;
+    props.location.type = cudaMemLocationTypeDevice;
+    props.location.id = device;
+    if (cudaMemPoolCreate(&ctx->mempool, &props) == cudaSuccess) {
+        uint64_t keep = UINT64_MAX;
+        cudaMemPoolSetAttribute(ctx->mempool, cudaMemPoolAttrReleaseThreshold, &keep);
+    } else {
+        cudaGetLastError();
+        ctx->mempool = nullptr;  // the device's default pool then
+    }
     return ctx;
 }
 
@@ -280,7 +292,8 @@ void nw_ctx_destroy(nw_ctx *ctx) {
     cudaSetDevice(ctx->device);
     cudaStreamSynchronize(ctx->stream);
     for (auto &kv : ctx->bufs)
-        if (kv.second.p) cudaFree(kv.second.p);
+        if (kv.second.p) cudaFreeAsync(kv.second.p, ctx->stream);
+    cudaStreamSynchronize(ctx->stream);
     for (auto &kv : ctx->stats)
         for (auto &pr : kv.second.pending) {
             cudaEventDestroy(pr.first);
@@ -292,6 +305,7 @@ void nw_ctx_destroy(nw_ctx *ctx) {
     free_band_model(ctx);
     if (ctx->d_err) cudaFree(ctx->d_err);
     if (ctx->pinned) cudaFreeHost(ctx->pinned);
+    if (ctx->mempool) cudaMemPoolDestroy(ctx->mempool);
     delete ctx;
 }
 
