@@ -404,8 +404,22 @@ class BandWork:
         mism = int((plain != self.scores).sum().item())
         cig_mism = int((cl != self.clen).sum().item())
         st = nw.nw_ctx_band_stats(self.ctx)
+        # the same certified band without the network (fixed start): what the
+        # trained network gains, on a context that has no model
+        nonet = torch.zeros_like(self.scores)
+        with nw.Context(self.ctx.device, torch.cuda.current_stream()) as c2:
+            c2.set_autotune(True)
+            for k in range(2):
+                torch.cuda.synchronize()
+                t0 = time.perf_counter()
+                nw.nw_align_batch(c2, self.pool, self.ao, self.al, self.bo, self.bl, SCORING, self.flags, nonet, cp,
+                                  self.coff, cl)
+                c2.sync()
+                nonet_s = time.perf_counter() - t0
+        nonet_mism = int((nonet != self.scores).sum().item())
         return {"plain_full_gcups": self.cells / plain_s / 1e9, "plain_full_s": plain_s,
                 "score_mismatches_vs_plain": mism, "cigar_length_mismatches_vs_plain": cig_mism,
+                "no_network_gcups": self.cells / nonet_s / 1e9, "no_network_score_mismatches": nonet_mism,
                 "band_stats_cumulative": st}
 
     def oracle_sample(self):

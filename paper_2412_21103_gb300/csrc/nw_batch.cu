@@ -591,7 +591,7 @@ static int band_rounds(nw_ctx *ctx, const uint8_t *pool, const uint64_t *a_off, 
         // pairs whose band would cover most of the grid go straight to full
         std::vector<BatchTask> tasks;
         std::vector<uint32_t> tw;  // width used per task
-        std::vector<uint32_t> next;
+        std::vector<uint32_t> next, nextw;  // rejected pairs and their next widths
         for (size_t q = 0; q < pending.size(); ++q) {
             const uint32_t id = pending[q];
             BatchTask t{};
@@ -601,13 +601,15 @@ static int band_rounds(nw_ctx *ctx, const uint8_t *pool, const uint64_t *a_off, 
             t.n = b_len[id];
             t.out0 = id;
             t.out1 = ~0u;
-            const uint32_t w = width[q] << round;
+            const uint32_t w = width[q];
             if (t.m == 0 || t.n == 0) {
                 rest.push_back(id);
                 continue;
             }
             band_task(t, R, w);
-            if (band_cells(t, R) * 10 >= full_cells(t, R) * 6 ||
+            // (a banded cell costs about what a full-grid cell costs, so the
+            // band pays off up to ~85% of the grid)
+            if (band_cells(t, R) * 20 >= full_cells(t, R) * 17 ||
                 (want && band_cells(t, R) / 4 > (ctx->budget - std::min(ctx->budget, ctx->used)) / 2)) {
                 rest.push_back(id);
                 continue;
@@ -619,10 +621,10 @@ static int band_rounds(nw_ctx *ctx, const uint8_t *pool, const uint64_t *a_off, 
         {
             // banded pairs that would leave the GPU idle on one warp run full
             // on the single-pair kernel instead (counted as fallbacks); a
-            // banded warp is ~4x slower per cell than a full-grid one
+            // banded warp is ~1.5x slower per cell than a full-grid one
             std::vector<double> wc(tasks.size()), fc(tasks.size());
             for (size_t q = 0; q < tasks.size(); ++q) {
-                wc[q] = 4.0 * (double)band_cells(tasks[q], R);
+                wc[q] = 1.5 * (double)band_cells(tasks[q], R);
                 fc[q] = (double)tasks[q].m * tasks[q].n;
             }
             const std::vector<size_t> strag = pick_stragglers(wc, fc);
@@ -698,14 +700,28 @@ static int band_rounds(nw_ctx *ctx, const uint8_t *pool, const uint64_t *a_off, 
             std::vector<TraceTask> tt;
             for (size_t q = 0; q < wave.size(); ++q) {
                 const BatchTask &t = wave[q];
-                const uint32_t w = tw[k0 + q] << round;
+                const uint32_t w = tw[k0 + q];
                 int64_t U = 0;
                 const bool can_leave = band_exit_bound(t.m, t.n, w, sc.match, sc.gap, &U);
                 // score: S_b >= U suffices; the alignment needs S_b > U (a
                 // tie outside the band could win the diagonal-first order)
-                const bool ok = !can_leave || (want ? (int64_t)hs[q] > U : (int64_t)hs[q] >= U);
-                if (!ok) {
+                auto certifies = [&](bool leave, int64_t u) {
+                    return !leave || (want ? (int64_t)hs[q] > u : (int64_t)hs[q] >= u);
+                };
+                if (!certifies(can_leave, U)) {
+                    // The next width: at least double, and at least the
+                    // smallest w' whose bound lies below this banded score --
+                    // a wider band scores no less, so w' certifies for sure.
+                    uint32_t lo_w = w + 1, hi_w = std::max(t.m, t.n) + 1;
+                    while (lo_w < hi_w) {
+                        const uint32_t mid = lo_w + (hi_w - lo_w) / 2;
+                        int64_t Um = 0;
+                        const bool lv = band_exit_bound(t.m, t.n, mid, sc.match, sc.gap, &Um);
+                        if (certifies(lv, Um)) hi_w = mid;
+                        else lo_w = mid + 1;
+                    }
                     next.push_back(t.out0);
+                    nextw.push_back(std::max(2 * w, lo_w));
                     continue;
                 }
                 ctx->band_stats[1 + round] += 1;
@@ -729,17 +745,10 @@ static int band_rounds(nw_ctx *ctx, const uint8_t *pool, const uint64_t *a_off, 
             }
             k0 = k;
         }
-        // widen: pairs rejected this round keep their starting width
-        std::vector<uint32_t> nw_width;
-        for (uint32_t id : next)
-            for (size_t q = 0; q < pending.size(); ++q)
-                if (pending[q] == id) {
-                    nw_width.push_back(width[q]);
-                    break;
-                }
+        // widen: the rejected pairs with their next widths
         if (round + 1 < kRounds) {
             pending.swap(next);
-            width.swap(nw_width);
+            width.swap(nextw);
         } else {
             for (uint32_t id : next) rest.push_back(id);
             pending.clear();

@@ -283,8 +283,13 @@ int learned_band_widths(nw_ctx *ctx, const uint8_t *pool, const uint64_t *a_off,
     w.assign(npairs, 64u);
     BandModel *bm = nullptr;
     if (!ctx->band_model) return NW_OK;  // no model: fixed starting width 64
-    double margin = 2.0;                 // (NW_BAND_MARGIN for sweeps)
-    if (const char *e = getenv("NW_BAND_MARGIN")) margin = std::max(0.5, atof(e));
+    // The first round's width is 0.75x the predicted one: a round that fails
+    // its certificate is followed by one at the smallest width the failed
+    // score proves sufficient, so under-predicting costs one narrow pass
+    // while over-predicting widens every band (measured on GB300: 0.75
+    // beats 1 and 2; NW_BAND_MARGIN for sweeps).
+    double margin = 0.75;
+    if (const char *e = getenv("NW_BAND_MARGIN")) margin = std::max(0.25, atof(e));
     int rc = model_of(ctx, &bm, false);
     if (rc) return rc;
     void *v = nullptr;
@@ -313,7 +318,7 @@ int learned_band_widths(nw_ctx *ctx, const uint8_t *pool, const uint64_t *a_off,
     cudaMemcpyAsync(y.data(), a.y, (size_t)npairs * 4, cudaMemcpyDeviceToHost, ctx->stream);
     if ((rc = nw_ctx_sync(ctx))) return rc;
     for (uint32_t k = 0; k < npairs; ++k) {
-        const double pred = std::exp((double)y[k]) * margin;  // safety factor against under-prediction
+        const double pred = std::exp((double)y[k]) * margin;
         const double cap = (double)std::max(a_len[k], b_len[k]);
         w[k] = (uint32_t)std::min(cap, std::max(8.0, std::ceil(pred)));
     }

@@ -106,7 +106,7 @@ def test_certificate_decisions_match_the_closed_form(ctx):
         width = min(b.size, SH + hi - lo)
         period = max(width, SH + 96)
         rows = -(-a.size // SH) * SH
-        if rows * period * 10 >= rows * max(b.size, 96) * 6:
+        if rows * period * 20 >= rows * max(b.size, 96) * 17:
             continue            # the band would cover most of the grid: straight to full
         tried += 1
         sb = _region_score(a, b, w)
