@@ -134,6 +134,15 @@ int64_t nw_ctx_tuning(nw_ctx *ctx, char *buf, uint64_t cap);
  * is changed then).  A value that is not a valid shape makes the calls of
  * that signature fail with NW_ERR_ARG. */
 int nw_ctx_set_tuning(nw_ctx *ctx, const char *text);
+/* Failure-path test hook (not in the paper).  NW_TEST_DROP_PROGRESS makes
+ * the next single-pair fill on this context run with row-group progress
+ * counters that nothing releases: every wait on them gives up after its
+ * time limit (2 s), the kernel returns, and the call reports NW_ERR_TIMEOUT;
+ * the context stays usable.  The hook clears itself after one use.  It
+ * exists so that tests can exercise the bounded waits without a GPU fault. */
+#define NW_TEST_DROP_PROGRESS 1u
+int nw_ctx_set_test_hook(nw_ctx *ctx, uint32_t hook);
+
 /* NW_GRAPH cache: out[0] graphs held (at most 8, least recently used
  * evicted with the scratch they own), out[1] captures, out[2] replays.
  * Returns 3.  A replay re-reads the sequence pool and writes the same output

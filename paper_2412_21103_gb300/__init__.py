@@ -36,6 +36,7 @@ NW_CIGAR_M = 8
 NW_BAND_RAW = 16
 NW_RECOMPUTE = 32
 NW_GRAPH = 64
+NW_TEST_DROP_PROGRESS = 1
 
 DEFAULT_SCORING = (1, -1, -1)
 
@@ -85,6 +86,7 @@ def load():
                                                ctypes.POINTER(ctypes.c_double), ctypes.c_int]),
         "nw_ctx_reset_stats": (ctypes.c_int, [vp]),
         "nw_ctx_set_autotune": (ctypes.c_int, [vp, ctypes.c_int]),
+        "nw_ctx_set_test_hook": (ctypes.c_int, [vp, u32]),
         "nw_ctx_tuning": (ctypes.c_int64, [vp, ctypes.c_char_p, u64]),
         "nw_ctx_set_tuning": (ctypes.c_int, [vp, ctypes.c_char_p]),
         "nw_ctx_graph_stats": (ctypes.c_int, [vp, u64p, ctypes.c_int]),

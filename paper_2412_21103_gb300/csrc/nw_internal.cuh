@@ -174,6 +174,7 @@ struct nw_ctx {
     // private stream-ordered pool of the scratch slots: freed slots stay
     // reserved in it (release threshold: never), so regrowing is cheap
     cudaMemPool_t mempool = nullptr;
+    uint32_t test_hook = 0;            // NW_TEST_DROP_PROGRESS (one use)
 };
 
 namespace nw {

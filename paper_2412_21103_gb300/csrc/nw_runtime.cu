@@ -376,6 +376,12 @@ int nw_ctx_reset_stats(nw_ctx *ctx) {
     return NW_OK;
 }
 
+int nw_ctx_set_test_hook(nw_ctx *ctx, uint32_t hook) {
+    if (!ctx || (hook & ~NW_TEST_DROP_PROGRESS)) return NW_ERR_ARG;
+    ctx->test_hook = hook;
+    return NW_OK;
+}
+
 int nw_ctx_set_autotune(nw_ctx *ctx, int on) {
     if (!ctx) return NW_ERR_ARG;
     ctx->autotune = on != 0;

@@ -326,6 +326,22 @@ static int run_pair(nw_ctx *ctx, const uint8_t *a2b, uint32_t m, const uint8_t *
     f.C = C;
     f.nw = nw;
     f.score = score;
+    if (ctx->test_hook & NW_TEST_DROP_PROGRESS) {
+        // failure-path test: every group after the first waits for a kept
+        // row whose progress counter nothing releases (zeroed, and recompute
+        // passes release none) -- the waits run out and report a timeout
+        ctx->test_hook &= ~NW_TEST_DROP_PROGRESS;
+        const uint64_t S = (m + 32u * R - 1) / (32u * R), CS = (S + nw - 1) / nw;
+        void *v = nullptr, *g = nullptr;
+        int rc = scratch(ctx, "hook_rows", (size_t)std::max<uint64_t>(CS, 2) * pair_bstride(n) * 4, &v);
+        if (!rc) rc = scratch(ctx, "hook_progress", (size_t)CS * 4 + 16, &g);
+        if (rc) return rc;
+        cudaMemsetAsync(g, 0, (size_t)CS * 4 + 16, ctx->stream);
+        f.bnd = (uint32_t *)v;
+        f.progress = (uint32_t *)g;
+        f.recompute = true;
+        return launch_pair_fill(ctx, a2b, m, b2b, n, pf, f);
+    }
     if (!want) return launch_pair_fill(ctx, a2b, m, b2b, n, pf, f);
     int rc;
     void *mv = nullptr, *nm = nullptr;
