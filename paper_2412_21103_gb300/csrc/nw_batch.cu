@@ -290,6 +290,12 @@ __global__ void __launch_bounds__(kBatchWarps * 32) k_batch(BatchArgs p) {
     }
 }
 
+// scores[tasks[i].out0] for the tasks of a launch, gathered for one copy back.
+__global__ void k_gather_scores(const BatchTask *tasks, uint32_t n, const int32_t *scores, int32_t *out) {
+    for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x)
+        out[i] = scores[tasks[i].out0];
+}
+
 // Diagonal of the all-vs-all matrix: score(a, a) = len * match.
 __global__ void k_diag(const uint32_t *len, uint32_t nseq, int32_t match, int32_t *out) {
     for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < nseq; i += gridDim.x * blockDim.x)
@@ -576,6 +582,7 @@ static int band_rounds(nw_ctx *ctx, const uint8_t *pool, const uint64_t *a_off, 
                        const uint64_t *b_off, const uint32_t *b_len, const std::vector<uint32_t> &ids,
                        const std::vector<uint32_t> &w0, const nw_scoring &sc, uint32_t flags, int32_t *scores,
                        char *cigar_pool, const uint64_t *cigar_off, uint64_t *cigar_len, std::vector<uint32_t> &rest) {
+    HostTimer ht_all(ctx, "band_rounds");
     const Profile pf = make_profile(sc);
     const bool want = flags & NW_CIGAR;
     // 512-row stripes: measured on GB300 (20,000 pairs of 2-20 kb) the
@@ -587,6 +594,9 @@ static int band_rounds(nw_ctx *ctx, const uint8_t *pool, const uint64_t *a_off, 
     int rc;
     std::vector<uint32_t> pending(ids), width(w0);
     std::vector<int32_t> hs;
+    uint32_t npairs_total = 0;  // banded scores by pair id
+    for (uint32_t id : ids) npairs_total = std::max(npairs_total, id + 1);
+    std::vector<int32_t> by_id;
     for (int round = 0; round < kRounds && !pending.empty(); ++round) {
         // pairs whose band would cover most of the grid go straight to full
         std::vector<BatchTask> tasks;
@@ -690,13 +700,27 @@ static int band_rounds(nw_ctx *ctx, const uint8_t *pool, const uint64_t *a_off, 
             ba.ntasks = (uint32_t)fill.size();
             ba.ptr = (uint32_t *)pv;
             if ((rc = launch_batch(ctx, R, want, ba, max_n, 2))) return rc;
-            // certificate on the banded scores
-            hs.resize(wave.size());
-            for (size_t q = 0; q < wave.size(); ++q) {
-                cudaError_t e = cudaMemcpyAsync(&hs[q], scores + wave[q].out0, 4, cudaMemcpyDeviceToHost, ctx->stream);
+            // certificate on the banded scores: one gather, one copy back
+            {
+                void *g = nullptr;
+                if ((rc = scratch(ctx, "band_gather", fill.size() * 4 + 16, &g))) return rc;
+                {
+                    LaunchTimer t(ctx, "gather");
+                    k_gather_scores<<<(unsigned)((fill.size() + 255) / 256), 256, 0, ctx->stream>>>(
+                        dt, (uint32_t)fill.size(), scores, (int32_t *)g);
+                }
+                std::vector<int32_t> gs(fill.size());
+                cudaError_t e = cudaMemcpyAsync(gs.data(), g, fill.size() * 4, cudaMemcpyDeviceToHost, ctx->stream);
                 if (e != cudaSuccess) return cuda_fail(ctx, e, "banded score D2H");
+                {
+                    HostTimer ht(ctx, "band_wait");  // the banded fill itself, seen from the host
+                    if ((rc = nw_ctx_sync(ctx))) return rc;
+                }
+                if (by_id.empty()) by_id.assign(npairs_total, 0);
+                for (size_t q = 0; q < fill.size(); ++q) by_id[fill[q].out0] = gs[q];
+                hs.resize(wave.size());
+                for (size_t q = 0; q < wave.size(); ++q) hs[q] = by_id[wave[q].out0];
             }
-            if ((rc = nw_ctx_sync(ctx))) return rc;
             std::vector<TraceTask> tt;
             for (size_t q = 0; q < wave.size(); ++q) {
                 const BatchTask &t = wave[q];
@@ -813,6 +837,7 @@ static int band_batch(nw_ctx *ctx, const uint8_t *pool, const uint64_t *a_off, c
     // the banded pointer words are dead now: hand their memory to the full
     // kernel's waves (it stays in the context's pool for the next call)
     free_prefix(ctx, "band_ptr");
+    HostTimer ht(ctx, "band_fallback");
     ctx->band_stats[5] += rest.size();
     return batch_device_impl(ctx, pool, a_off, a_len, b_off, b_len, rest.data(), (uint32_t)rest.size(), sc, flags,
                              scores, cigar_pool, cigar_off, cigar_len);
@@ -1083,7 +1108,11 @@ extern "C" int nw_align_batch(nw_ctx *ctx, const uint8_t *pool2b, const uint64_t
             return batch_device_impl(ctx, pool, a_off, a_len, b_off, b_len, nullptr, npairs, sc, fl, sc_out, cig,
                                      cigar_off, clen);
         std::vector<uint32_t> w;
-        int r = learned_band_widths(ctx, pool, a_off, a_len, b_off, b_len, npairs, w);
+        int r;
+        {
+            HostTimer ht(ctx, "band_widths");
+            r = learned_band_widths(ctx, pool, a_off, a_len, b_off, b_len, npairs, w);
+        }
         if (r) return r;
         return band_batch(ctx, pool, a_off, a_len, b_off, b_len, npairs, w.data(), sc, fl, sc_out, cig, cigar_off,
                           clen);

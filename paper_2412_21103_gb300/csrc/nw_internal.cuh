@@ -201,6 +201,16 @@ struct LaunchTimer {
     ~LaunchTimer();
 };
 
+// Host-side section timer: with profiling on, the section's wall time (the
+// host work and any waits in it) is added to the stat "host:<name>".
+struct HostTimer {
+    nw_ctx *ctx;
+    const char *name;
+    double t0;
+    HostTimer(nw_ctx *c, const char *n);
+    ~HostTimer();
+};
+
 // Autotuning keys and the graph cache (nw_runtime.cu).
 constexpr size_t kMaxGraphs = 8;
 bool tuned(nw_ctx *ctx, const std::string &key, uint32_t *choice);

@@ -1,6 +1,7 @@
 // Context, scratch pool, errors, per-kernel timing, the tuning table and
 // graph cache, and 2-bit packing.
 #include <algorithm>
+#include <chrono>
 #include <cstdarg>
 #include <cstdio>
 #include <cstdlib>
@@ -110,6 +111,19 @@ LaunchTimer::~LaunchTimer() {
         ctx->stats[name].pending.emplace_back(e0, e1);
         ctx->stats[name].pending_count.push_back(count);
     }
+}
+
+static double wall_ms() {
+    return std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now().time_since_epoch()).count();
+}
+
+HostTimer::HostTimer(nw_ctx *c, const char *n) : ctx(c), name(n), t0(c->profiling ? wall_ms() : 0.0) {}
+
+HostTimer::~HostTimer() {
+    if (!ctx->profiling) return;
+    KernelStat &st = ctx->stats[std::string("host:") + name];
+    st.ms += wall_ms() - t0;
+    st.launches += 1;
 }
 
 // ------------------------------------------------------- tuning and graphs

@@ -606,6 +606,7 @@ int launch_finish(nw_ctx *ctx, const TraceTask &one, const TraceTask *many, uint
 template <int R>
 static int launch_walks(nw_ctx *ctx, const TraceTask *host, const TraceTask *dev, uint32_t ntasks) {
     constexpr uint32_t SH = 32u * R;
+    HostTimer ht(ctx, "trace_plan");
     const TraceTask one = dev ? TraceTask{} : host[0];
     std::vector<StripeJob> jobs;
     std::vector<uint32_t> base(ntasks, 0xffffffffu);
