@@ -283,12 +283,12 @@ int learned_band_widths(nw_ctx *ctx, const uint8_t *pool, const uint64_t *a_off,
     w.assign(npairs, 64u);
     BandModel *bm = nullptr;
     if (!ctx->band_model) return NW_OK;  // no model: fixed starting width 64
-    // The first round's width is 0.75x the predicted one: a round that fails
+    // The first round's width is half the predicted one: a round that fails
     // its certificate is followed by one at the smallest width the failed
     // score proves sufficient, so under-predicting costs one narrow pass
-    // while over-predicting widens every band (measured on GB300: 0.75
-    // beats 1 and 2; NW_BAND_MARGIN for sweeps).
-    double margin = 0.75;
+    // while over-predicting widens every band (measured on GB300 on 20,000
+    // pairs: 0.5 beats 0.75, 1 and 2; NW_BAND_MARGIN for sweeps).
+    double margin = 0.5;
     if (const char *e = getenv("NW_BAND_MARGIN")) margin = std::max(0.25, atof(e));
     int rc = model_of(ctx, &bm, false);
     if (rc) return rc;
