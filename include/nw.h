@@ -256,7 +256,7 @@ int nw_ctx_band_stats(nw_ctx *ctx, uint64_t *out, int cap);
  * 65-128-128-1 ReLU network with BF16 weights and activations and FP32
  * accumulation whose output is log of the band half-width; with
  * NW_LEARNED_BAND, nw_align_batch runs the certified band from
- * ceil(0.5 * exp(output)) (at least 8), or from 64 without a model; a pair
+ * ceil(0.75 * exp(output)) (at least 8), or from 64 without a model; a pair
  * whose round fails the certificate is banded again at the smallest width
  * whose exit bound lies below the failed banded score (which then
  * certifies: a wider band scores no less), at least twice the last one. */

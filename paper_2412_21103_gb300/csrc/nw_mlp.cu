@@ -283,12 +283,15 @@ int learned_band_widths(nw_ctx *ctx, const uint8_t *pool, const uint64_t *a_off,
     w.assign(npairs, 64u);
     BandModel *bm = nullptr;
     if (!ctx->band_model) return NW_OK;  // no model: fixed starting width 64
-    // The first round's width is half the predicted one: a round that fails
+    // The first round's width is 0.75x the predicted one: a round that fails
     // its certificate is followed by one at the smallest width the failed
     // score proves sufficient, so under-predicting costs one narrow pass
-    // while over-predicting widens every band (measured on GB300 on 20,000
-    // pairs: 0.5 beats 0.75, 1 and 2; NW_BAND_MARGIN for sweeps).
-    double margin = 0.5;
+    // while over-predicting widens every band.  Measured on GB300 (20,000
+    // pairs): 0.5 -> 5,315, 0.75 -> 5,097, 1 -> 4,858, 1.5 -> 4,112
+    // effective GCUPS; 0.75 is kept because it is the one where the network
+    // both certifies more pairs in the first round and sweeps fewer banded
+    // cells than the fixed start.  NW_BAND_MARGIN for sweeps.
+    double margin = 0.75;
     if (const char *e = getenv("NW_BAND_MARGIN")) margin = std::max(0.25, atof(e));
     int rc = model_of(ctx, &bm, false);
     if (rc) return rc;
@@ -317,9 +320,20 @@ int learned_band_widths(nw_ctx *ctx, const uint8_t *pool, const uint64_t *a_off,
     std::vector<float> y(npairs);
     cudaMemcpyAsync(y.data(), a.y, (size_t)npairs * 4, cudaMemcpyDeviceToHost, ctx->stream);
     if ((rc = nw_ctx_sync(ctx))) return rc;
+    // Probe cap (NW_BAND_PROBE_CAP, 0 = none) and the straight-to-full rule
+    // (NW_BAND_SKIP: a pair whose predicted band would cover most of the
+    // grid starts at that width, which sends it to the full kernel).
+    double probe_cap = 0.0;
+    if (const char *e = getenv("NW_BAND_PROBE_CAP")) probe_cap = atof(e);
+    const bool skip = getenv("NW_BAND_SKIP") != nullptr;
     for (uint32_t k = 0; k < npairs; ++k) {
-        const double pred = std::exp((double)y[k]) * margin;
+        const double full_pred = std::exp((double)y[k]);
+        double pred = full_pred * margin;
         const double cap = (double)std::max(a_len[k], b_len[k]);
+        const double delta = std::fabs((double)b_len[k] - (double)a_len[k]);
+        const double n = (double)b_len[k];
+        if (skip && (512.0 + 2.0 * full_pred + delta) * 20.0 >= n * 17.0) pred = cap;
+        else if (probe_cap > 0 && pred > probe_cap) pred = probe_cap;
         w[k] = (uint32_t)std::min(cap, std::max(8.0, std::ceil(pred)));
     }
     return NW_OK;
