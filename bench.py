@@ -467,7 +467,7 @@ def run_serve(args):
     # warm-up: a few requests through every worker
     srv.submit_many(pool, ao[:16], al[:16], bo[:16], bl[:16], want[:16])
     srv.drain(300.0)
-    srv.poll(1 << 16)
+    srv.poll_all()
     arrivals = np.cumsum(-np.log1p(-seqgen.Stream(1005, 77).uniform(int(args.rate * args.duration) + 1)) / args.rate)
     arrivals = arrivals[arrivals < args.duration]
     idx = np.arange(arrivals.size) % len(reqs)
@@ -486,11 +486,11 @@ def run_serve(args):
             k = j
         else:
             time.sleep(0.0005)
-        done += srv.poll(1 << 16)
+        done += srv.poll_all()
     submit_end = time.perf_counter() - t0
     backlog = srv.stats()
     drained = srv.drain(600.0)
-    done += srv.poll(1 << 20)
+    done += srv.poll_all()
     wall = time.perf_counter() - t0
     lat = np.array([d[4] for d in done]) if done else np.zeros(1)
     cells = float(sum(cells_of[ticket_req[d[0]]] for d in done if d[0] in ticket_req))
@@ -553,12 +553,14 @@ def run_ours(args):
     torch.cuda.synchronize(dev)
     evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
     wall0 = time.perf_counter()
+    torch.cuda.nvtx.range_push("timed")     # lets a profiler select the timed steps' launches
     for k in range(args.steps):
         flush.zero_()                       # evict L2 between timed steps
         evs[k][0].record(stream)
         work.step()
         evs[k][1].record(stream)
     torch.cuda.synchronize(dev)
+    torch.cuda.nvtx.range_pop()
     wall1 = time.perf_counter()
     wall = wall1 - wall0
     clk.window(wall0, wall1)

@@ -327,7 +327,10 @@ int nw_server_submit_many(nw_server *srv, const uint8_t *pool2b, const uint64_t 
                           const uint64_t *b_off, const uint32_t *b_len, const uint8_t *want_cigar, uint32_t count,
                           uint64_t *tickets);
 /* Move up to `cap` finished requests (oldest first) into out; their CIGARs
- * go to cigar_buf (stops early when cigar_cap would overflow). */
+ * go to cigar_buf, NUL-terminated (stops early when cigar_cap would
+ * overflow).  When the oldest one's CIGAR alone does not fit, nothing moves,
+ * *cigar_used receives the bytes it needs (with the NUL) and the call
+ * returns NW_ERR_CIGAR_TRUNC. */
 int nw_server_poll(nw_server *srv, nw_completion *out, uint32_t cap, uint32_t *count, char *cigar_buf,
                    uint64_t cigar_cap, uint64_t *cigar_used);
 /* Wait until nothing is queued or running (NW_ERR_TIMEOUT after timeout_s). */

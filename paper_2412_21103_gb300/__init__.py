@@ -484,6 +484,9 @@ class Server:
         used = ctypes.c_uint64(0)
         rc = load().nw_server_poll(self.handle, out, cap, ctypes.byref(cnt), _ptr(self._cbuf), self._cbuf.size,
                                    ctypes.byref(used))
+        if rc == NW_ERR_CIGAR_TRUNC:  # the oldest CIGAR needs a larger buffer
+            self._cbuf = np.zeros(max(int(used.value), 2 * self._cbuf.size), np.uint8)
+            return self.poll(cap)
         if rc != NW_OK:
             raise NWError(rc, "poll failed")
         res = []
@@ -494,6 +497,16 @@ class Server:
                 cig = self._cbuf[c.cigar_off: c.cigar_off + c.cigar_len].tobytes().decode()
             res.append((int(c.ticket), int(c.status), int(c.score), cig, float(c.latency_s)))
         return res
+
+    def poll_all(self):
+        """Every completion queued now: polls until the queue is empty (one poll stops when the
+        CIGAR buffer fills)."""
+        res = []
+        while True:
+            got = self.poll(1 << 16)
+            if not got:
+                return res
+            res += got
 
     def drain(self, timeout_s: float = 600.0) -> bool:
         return load().nw_server_drain(self.handle, timeout_s) == NW_OK

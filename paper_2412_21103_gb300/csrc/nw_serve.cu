@@ -275,7 +275,14 @@ int nw_server_poll(nw_server *srv, nw_completion *out, uint32_t cap, uint32_t *c
     while (k < cap && !srv->done.empty()) {
         Done &d = srv->done.front();
         const uint64_t need = d.cigar.empty() ? 0 : d.cigar.size() + 1;
-        if (need && (!cigar_buf || used + need > cigar_cap)) break;
+        if (need && (!cigar_buf || used + need > cigar_cap)) {
+            if (k == 0) {  // the oldest CIGAR alone does not fit: report its size, move nothing
+                *count = 0;
+                if (cigar_used) *cigar_used = need;
+                return NW_ERR_CIGAR_TRUNC;
+            }
+            break;
+        }
         out[k].ticket = d.ticket;
         out[k].status = d.status;
         out[k].score = d.score;
