@@ -596,7 +596,7 @@ def run_ours(args):
     # the banded kernel the band cells it actually swept
     kcells = (band_cells / max(dl, 1)) if work.dominant.startswith("band") else work.cells
     achieved = kcells * OPS_PER_CELL / (dom_avg_ms * 1e-3) / 1e9 if dom_avg_ms else None
-    launches = sum(v[0] for k_, v in stats.items() if k_ != "peak")
+    launches = sum(v[0] for k_, v in stats.items() if k_ != "peak" and not k_.startswith("host:"))
 
     line = {
         "metric": METRIC, "value": world * work.cells / (ms * 1e-3) / 1e9, "unit": "GCUPS", "n_gpus": world,

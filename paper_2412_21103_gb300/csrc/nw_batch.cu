@@ -15,6 +15,7 @@
 // DPX add-max + max; with pointers: prmt + max + DPX add-max, and two sign
 // bits appended by funnel shifts, see ptr_append).
 #include <algorithm>
+#include <chrono>
 #include <cstdlib>
 #include <cstring>
 #include <numeric>
@@ -497,7 +498,7 @@ static std::vector<size_t> pick_stragglers(const std::vector<double> &warp_cells
 static int run_straggler(nw_ctx *ctx, const uint8_t *pool, uint64_t a_off, uint32_t m, uint64_t b_off, uint32_t n,
                          const nw_scoring &sc, uint32_t flags, int32_t *score, char *cigar, uint64_t cigar_cap,
                          uint64_t *cigar_len) {
-    LaunchTimer t(ctx, "straggler");
+    LaunchTimer t(ctx, "straggler", 0);  // spans the single-pair kernels, which count themselves
     return align_single(ctx, pool + a_off, m, pool + b_off, n, sc, flags & (NW_CIGAR | NW_CIGAR_M | NW_RECOMPUTE), score,
                         (flags & NW_CIGAR) ? cigar : nullptr, cigar_cap, (flags & NW_CIGAR) ? cigar_len : nullptr);
 }
@@ -597,7 +598,9 @@ static int band_rounds(nw_ctx *ctx, const uint8_t *pool, const uint64_t *a_off, 
     uint32_t npairs_total = 0;  // banded scores by pair id
     for (uint32_t id : ids) npairs_total = std::max(npairs_total, id + 1);
     std::vector<int32_t> by_id;
+    const bool band_log = getenv("NW_BAND_LOG") != nullptr;
     for (int round = 0; round < kRounds && !pending.empty(); ++round) {
+        size_t routed_full = 0;
         // pairs whose band would cover most of the grid go straight to full
         std::vector<BatchTask> tasks;
         std::vector<uint32_t> tw;  // width used per task
@@ -638,6 +641,7 @@ static int band_rounds(nw_ctx *ctx, const uint8_t *pool, const uint64_t *a_off, 
                 fc[q] = (double)tasks[q].m * tasks[q].n;
             }
             const std::vector<size_t> strag = pick_stragglers(wc, fc);
+            routed_full = strag.size();
             if (!strag.empty()) {
                 std::vector<char> routed(tasks.size(), 0);
                 for (size_t q : strag) {
@@ -688,6 +692,7 @@ static int band_rounds(nw_ctx *ctx, const uint8_t *pool, const uint64_t *a_off, 
             }
             std::vector<BatchTask> fill = wave;
             sort_lpt(fill);
+            const auto wave_t0 = std::chrono::steady_clock::now();
             BatchTask *dt = nullptr;
             if ((rc = upload(ctx, "band_tasks", fill, &dt))) return rc;
             BatchArgs ba{};
@@ -715,6 +720,19 @@ static int band_rounds(nw_ctx *ctx, const uint8_t *pool, const uint64_t *a_off, 
                 {
                     HostTimer ht(ctx, "band_wait");  // the banded fill itself, seen from the host
                     if ((rc = nw_ctx_sync(ctx))) return rc;
+                }
+                if (band_log) {  // diagnostics: one line per banded wave
+                    double sum = 0, mx = 0;
+                    for (const BatchTask &t : fill) {
+                        const double c = (double)band_cells_updated(t, R);
+                        sum += c;
+                        mx = std::max(mx, c);
+                    }
+                    const double ms =
+                        std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - wave_t0).count();
+                    fprintf(stderr, "[nw band] round %d wave %zu pairs (%zu routed full) cells %.3g max %.3g (m %u n %u) %.2f ms\n",
+                            round, fill.size(), routed_full, sum, mx, fill.empty() ? 0u : fill[0].m,
+                            fill.empty() ? 0u : fill[0].n, ms);
                 }
                 if (by_id.empty()) by_id.assign(npairs_total, 0);
                 for (size_t q = 0; q < fill.size(); ++q) by_id[fill[q].out0] = gs[q];

@@ -238,7 +238,7 @@ static int forward(nw_ctx *ctx, BandModel *bm, const float *x, uint32_t nb, Acts
     a.h1 = (float *)v;
     a.h2 = a.h1 + (size_t)nb * kH;
     a.y = a.h2 + (size_t)nb * kH;
-    LaunchTimer t(ctx, "mlp_forward");
+    LaunchTimer t(ctx, "mlp_forward", 3);
     k_layer_fwd<<<blocks_for((uint64_t)nb * kH), 256, 0, ctx->stream>>>(x, kF, bm->wb + kOffW1, bm->master + kOffB1,
                                                                          kH, nb, a.h1, 1, 1);
     k_layer_fwd<<<blocks_for((uint64_t)nb * kH), 256, 0, ctx->stream>>>(a.h1, kH, bm->wb + kOffW2, bm->master + kOffB2,
@@ -256,7 +256,7 @@ static int gradients(nw_ctx *ctx, BandModel *bm, const float *x, const float *t,
     if ((rc = scratch(ctx, "mlp_grads", (size_t)nb * (2 * kH + 1) * 4 + 64, &v))) return rc;
     float *dy = (float *)v, *dh2 = dy + nb, *dh1 = dh2 + (size_t)nb * kH;
     cudaMemsetAsync(loss, 0, 4, ctx->stream);
-    LaunchTimer lt(ctx, "mlp_backward");
+    LaunchTimer lt(ctx, "mlp_backward", 6);
     k_dloss<<<blocks_for(nb), 256, 0, ctx->stream>>>(a.y, t, nb, dy, loss);
     // layer 3: dW3, db3; dh2 = W3^T dy masked by h2 > 0
     k_layer_bwd_w<<<blocks_for(kNW3 + 1), 256, 0, ctx->stream>>>(dy, 1, a.h2, kH, nb, bm->grad + kOffW3,
