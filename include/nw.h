@@ -293,15 +293,21 @@ int nw_score_all_pairs(nw_ctx *ctx, const uint8_t *pool2b, const uint64_t *off, 
 
 /* ---------------------------------------------------------------- serving
  * Not in the paper (its Sec. 3.2 splits a fixed set of alignments over MPI
- * ranks): a continuous-batching server on one GPU.  `workers` threads each
- * own a context and stream and repeatedly admit the oldest waiting requests
- * into a batch of at most `max_batch` pairs while the traceback buffers in
- * flight stay within `trace_budget` bytes (a CIGAR request reserves
- * ceil((m+1)(n+1)/4) rounded up to 256 bytes, a score-only request
- * nothing; a request alone on an idle server is always admitted).  Batches
- * run through nw_align_batch (with NW_LEARNED_BAND if given in `flags` and
- * the creating context holds a model, which every worker copies); batches
- * of different workers overlap on the GPU.  Results equal those of
+ * ranks): a continuous-batching server on one GPU.  The queue is device
+ * memory: submitting copies a request's 2-bit sequences into a device arena
+ * (`queue_bytes`) and its descriptor into a device ring (`queue_slots`
+ * slots, a power of two); one device word holds how many requests were
+ * admitted and how many traceback bytes are reserved in flight.  `workers`
+ * threads each own a context and stream; each repeatedly runs the device
+ * admission kernel, which admits the oldest waiting requests into a batch
+ * of at most `max_batch` pairs while the reserved bytes stay within
+ * `trace_budget` (a CIGAR request reserves ceil((m+1)(n+1)/4) rounded up to
+ * 256 bytes, a score-only request nothing; a request alone on an idle
+ * server is always admitted) and claims them atomically.  Batches run from
+ * the arena through nw_align_batch (with NW_LEARNED_BAND if given in
+ * `flags` and the creating context holds a model, which every worker
+ * copies); batches of different workers overlap on the GPU; a finished
+ * batch returns its reservation on the device.  Results equal those of
  * nw_align on the same pair. */
 typedef struct nw_server nw_server;
 typedef struct {
@@ -313,11 +319,21 @@ typedef struct {
     double latency_s;    /* completion minus submission (host clock)       */
 } nw_completion;
 
-/* NULL on failure.  The context must outlive the server. */
+/* NULL on failure (bad sizes: workers 1..16, max_batch 1..2^20,
+ * queue_bytes >= 4096, queue_slots a power of two in 2..2^30; or device
+ * memory).  The context must outlive the server.  The arena and the ring
+ * are allocated on the context's device outside its scratch budget
+ * (queue_bytes + 40 * queue_slots bytes). */
+nw_server *nw_server_create_ex(nw_ctx *ctx, uint32_t workers, uint32_t max_batch, uint64_t trace_budget,
+                               uint64_t queue_bytes, uint32_t queue_slots, nw_scoring sc, uint32_t flags);
+/* nw_server_create_ex with a 1 GiB arena and 2^20 slots. */
 nw_server *nw_server_create(nw_ctx *ctx, uint32_t workers, uint32_t max_batch, uint64_t trace_budget, nw_scoring sc,
                             uint32_t flags);
-/* Queue one request; sequences are host 2-bit arrays, copied before
- * return.  *ticket identifies its completion. */
+/* Queue one request; sequences are host 2-bit arrays, copied to the
+ * device before return.  *ticket identifies its completion.  While the
+ * arena or the ring is full of unfinished requests the call waits for
+ * completions (NW_ERR_TIMEOUT after 60 s); a request larger than the arena
+ * is NW_ERR_ARG. */
 int nw_server_submit(nw_server *srv, const uint8_t *a2b, uint32_t m, const uint8_t *b2b, uint32_t n,
                      uint32_t want_cigar, uint64_t *ticket);
 /* Queue `count` requests at once from a host pool (same layout as
@@ -338,6 +354,9 @@ int nw_server_drain(nw_server *srv, double timeout_s);
 /* [0] submitted, [1] completed, [2] waiting, [3] running, [4] full-grid
  * cells completed, [5] traceback bytes reserved, [6] batches, [7] budget. */
 int nw_server_stats(nw_server *srv, uint64_t *out, int cap);
+/* Read the device queue word: requests admitted so far and traceback bytes
+ * reserved in flight (synchronises with the intake stream). */
+int nw_server_queue_state(nw_server *srv, uint64_t *admitted, uint64_t *reserved_bytes);
 /* Finish queued work, stop the workers, free everything. */
 void nw_server_destroy(nw_server *srv);
 

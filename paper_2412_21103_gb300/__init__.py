@@ -110,6 +110,8 @@ def load():
         "nw_band_model_grad": (ctypes.c_int, [vp, vp, vp, u32, vp, vp]),
         "nw_band_model_train_step": (ctypes.c_int, [vp, vp, vp, u32, ctypes.c_float, vp]),
         "nw_server_create": (vp, [vp, u32, u32, u64, Scoring, u32]),
+        "nw_server_create_ex": (vp, [vp, u32, u32, u64, u64, u32, Scoring, u32]),
+        "nw_server_queue_state": (ctypes.c_int, [vp, u64p, u64p]),
         "nw_server_submit": (ctypes.c_int, [vp, vp, u32, vp, u32, u32, u64p]),
         "nw_server_submit_many": (ctypes.c_int, [vp, vp, u64p, u32p, u64p, u32p, vp, u32, u64p]),
         "nw_server_poll": (ctypes.c_int, [vp, ctypes.POINTER(Completion), u32, u32p, vp, u64, u64p]),
@@ -449,8 +451,9 @@ class Server:
     completions.  See include/nw.h."""
 
     def __init__(self, ctx: Context, workers: int = 3, max_batch: int = 1024, trace_budget: int = 16 << 30,
-                 scoring=DEFAULT_SCORING, flags: int = 0):
-        self.handle = load().nw_server_create(ctx.handle, workers, max_batch, trace_budget, _sc(scoring), flags)
+                 scoring=DEFAULT_SCORING, flags: int = 0, queue_bytes: int = 1 << 30, queue_slots: int = 1 << 20):
+        self.handle = load().nw_server_create_ex(ctx.handle, workers, max_batch, trace_budget, queue_bytes,
+                                                 queue_slots, _sc(scoring), flags)
         if not self.handle:
             raise NWError(NW_ERR_ARG, "nw_server_create failed")
         self._cbuf = np.zeros(1 << 24, np.uint8)
@@ -507,6 +510,14 @@ class Server:
             if not got:
                 return res
             res += got
+
+    def queue_state(self) -> dict:
+        """The device queue word: requests admitted, traceback bytes reserved."""
+        adm, res = ctypes.c_uint64(0), ctypes.c_uint64(0)
+        rc = load().nw_server_queue_state(self.handle, ctypes.byref(adm), ctypes.byref(res))
+        if rc != NW_OK:
+            raise NWError(rc, "queue state failed")
+        return {"admitted": int(adm.value), "reserved": int(res.value)}
 
     def drain(self, timeout_s: float = 600.0) -> bool:
         return load().nw_server_drain(self.handle, timeout_s) == NW_OK

@@ -94,3 +94,55 @@ def test_server_submit_many_and_budget_admission():
             assert got[int(t)][1] == oracle.rle(ops)
     srv.close()
     ctx.close()
+
+
+def test_device_queue_word_after_drain():
+    """The queue's consumer state lives on the device: after a drain its word
+    says every submitted request was admitted and no traceback bytes are
+    reserved."""
+    import torch
+    import paper_2412_21103_gb300 as nw
+    ctx = nw.Context(0, torch.cuda.current_stream())
+    srv = nw.Server(ctx, workers=2, max_batch=16, trace_budget=4 << 20)
+    reqs = _requests(7, 30)
+    for a, b, cig in reqs:
+        srv.submit(nw.pack_codes(a), a.size, nw.pack_codes(b), b.size, cig)
+    assert srv.drain(120.0)
+    assert srv.queue_state() == {"admitted": 30, "reserved": 0}
+    assert len(srv.poll_all()) == 30
+    srv.close()
+    ctx.close()
+
+
+def test_small_arena_and_ring_wrap_and_wait():
+    """An arena of 12 KiB and a ring of 8 slots: submissions wait for
+    completions, placements wrap around both, and every result still equals
+    the oracle's."""
+    import torch
+    import paper_2412_21103_gb300 as nw
+    ctx = nw.Context(0, torch.cuda.current_stream())
+    srv = nw.Server(ctx, workers=2, max_batch=3, trace_budget=64 << 20, queue_bytes=12 << 10, queue_slots=8)
+    reqs = _requests(11, 60)
+    seqs = []
+    for a, b, _ in reqs:
+        seqs += [a, b]
+    pool, off, lens = nw.pool_of(seqs)
+    tickets = srv.submit_many(pool, off[0::2], lens[0::2], off[1::2], lens[1::2], [c for _, _, c in reqs])
+    assert srv.drain(120.0)
+    got = {t: (st, sc, cg) for t, st, sc, cg, lat in srv.poll_all()}
+    assert len(got) == 60
+    for k, t in enumerate(tickets):
+        a, b, cig = reqs[k]
+        st, sc, cg = got[int(t)]
+        assert st == nw.NW_OK
+        s, ops = oracle.align(a, b)
+        assert sc == s, k
+        if cig:
+            assert cg == oracle.rle(ops), k
+    assert srv.queue_state() == {"admitted": 60, "reserved": 0}
+    # a request larger than the arena is refused
+    big = np.zeros(40000, np.uint8)
+    with pytest.raises(nw.NWError):
+        srv.submit(nw.pack_codes(big), big.size, nw.pack_codes(big), big.size, False)
+    srv.close()
+    ctx.close()
