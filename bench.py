@@ -405,19 +405,21 @@ class BandWork:
         cig_mism = int((cl != self.clen).sum().item())
         st = nw.nw_ctx_band_stats(self.ctx)
         # the same certified band without the network (fixed start): what the
-        # trained network gains, on a context that has no model
+        # trained network gains, on the same context (same memory budget and
+        # warm scratch) with its model taken out for these calls
         nonet = torch.zeros_like(self.scores)
-        with nw.Context(self.ctx.device, torch.cuda.current_stream()) as c2:
-            c2.set_autotune(True)
-            times = []
-            for k in range(4):  # (the first call tunes; the median of the other three)
-                torch.cuda.synchronize()
-                t0 = time.perf_counter()
-                nw.nw_align_batch(c2, self.pool, self.ao, self.al, self.bo, self.bl, SCORING, self.flags, nonet, cp,
-                                  self.coff, cl)
-                c2.sync()
-                times.append(time.perf_counter() - t0)
-            nonet_s = statistics.median(times[1:])
+        params = nw.nw_band_model_get(self.ctx)
+        nw.nw_band_model_clear(self.ctx)
+        times = []
+        for k in range(4):  # (the median of the last three)
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            nw.nw_align_batch(self.ctx, self.pool, self.ao, self.al, self.bo, self.bl, SCORING, self.flags, nonet, cp,
+                              self.coff, cl)
+            self.ctx.sync()
+            times.append(time.perf_counter() - t0)
+        nonet_s = statistics.median(times[1:])
+        nw.nw_band_model_set(self.ctx, params)
         nonet_mism = int((nonet != self.scores).sum().item())
         return {"plain_full_gcups": self.cells / plain_s / 1e9, "plain_full_s": plain_s,
                 "score_mismatches_vs_plain": mism, "cigar_length_mismatches_vs_plain": cig_mism,

@@ -274,6 +274,9 @@ int nw_band_model_init(nw_ctx *ctx, uint64_t seed);
 /* Copy parameters in / out (host arrays of nw_band_model_size() floats). */
 int nw_band_model_set(nw_ctx *ctx, const float *params, uint64_t count);
 int nw_band_model_get(nw_ctx *ctx, float *params, uint64_t count);
+/* Drop the context's model and its optimizer state (NW_LEARNED_BAND then
+ * starts every pair at half-width 64, as on a context that never had one). */
+int nw_band_model_clear(nw_ctx *ctx);
 /* Network outputs for n feature rows (device in, device out). */
 int nw_band_model_forward(nw_ctx *ctx, const float *feat, uint32_t n, float *out);
 /* Gradient of 0.5*mean((y - target)^2) w.r.t. the parameters (device

@@ -106,6 +106,7 @@ def load():
         "nw_band_model_init": (ctypes.c_int, [vp, u64]),
         "nw_band_model_set": (ctypes.c_int, [vp, vp, u64]),
         "nw_band_model_get": (ctypes.c_int, [vp, vp, u64]),
+        "nw_band_model_clear": (ctypes.c_int, [vp]),
         "nw_band_model_forward": (ctypes.c_int, [vp, vp, u32, vp]),
         "nw_band_model_grad": (ctypes.c_int, [vp, vp, vp, u32, vp, vp]),
         "nw_band_model_train_step": (ctypes.c_int, [vp, vp, vp, u32, ctypes.c_float, vp]),
@@ -417,6 +418,10 @@ def nw_band_model_get(ctx: Context) -> np.ndarray:
     p = np.zeros(nw_band_model_size(), np.float32)
     _check(ctx, load().nw_band_model_get(ctx.handle, _ptr(p), p.size))
     return p
+
+
+def nw_band_model_clear(ctx: Context):
+    _check(ctx, load().nw_band_model_clear(ctx.handle))
 
 
 def nw_band_model_forward(ctx: Context, feat, out=None):

@@ -599,8 +599,17 @@ static int band_rounds(nw_ctx *ctx, const uint8_t *pool, const uint64_t *a_off, 
     for (uint32_t id : ids) npairs_total = std::max(npairs_total, id + 1);
     std::vector<int32_t> by_id;
     const bool band_log = getenv("NW_BAND_LOG") != nullptr;
+    // the full kernels' pointer slots are idle until the fallback: give their
+    // memory to the banded waves (it stays in the context's pool)
+    if (want) {
+        free_prefix(ctx, "batch_ptr");
+        free_prefix(ctx, "ptr");
+    }
     for (int round = 0; round < kRounds && !pending.empty(); ++round) {
         size_t routed_full = 0;
+        // the previous round's pointer words are traced already (stream
+        // order): their slot does not count against this round's waves
+        if (want) free_prefix(ctx, "band_ptr");
         // pairs whose band would cover most of the grid go straight to full
         std::vector<BatchTask> tasks;
         std::vector<uint32_t> tw;  // width used per task
@@ -730,9 +739,11 @@ static int band_rounds(nw_ctx *ctx, const uint8_t *pool, const uint64_t *a_off, 
                     }
                     const double ms =
                         std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - wave_t0).count();
-                    fprintf(stderr, "[nw band] round %d wave %zu pairs (%zu routed full) cells %.3g max %.3g (m %u n %u) %.2f ms\n",
+                    fprintf(stderr,
+                            "[nw band] round %d wave %zu pairs (%zu routed full) cells %.3g max %.3g (m %u n %u) "
+                            "%.2f ms; scratch in use %.3g of %.3g B\n",
                             round, fill.size(), routed_full, sum, mx, fill.empty() ? 0u : fill[0].m,
-                            fill.empty() ? 0u : fill[0].n, ms);
+                            fill.empty() ? 0u : fill[0].n, ms, (double)ctx->used, (double)ctx->budget);
                 }
                 if (by_id.empty()) by_id.assign(npairs_total, 0);
                 for (size_t q = 0; q < fill.size(); ++q) by_id[fill[q].out0] = gs[q];

@@ -287,10 +287,12 @@ int learned_band_widths(nw_ctx *ctx, const uint8_t *pool, const uint64_t *a_off,
     // its certificate is followed by one at the smallest width the failed
     // score proves sufficient, so under-predicting costs one narrow pass
     // while over-predicting widens every band.  Measured on GB300 (20,000
-    // pairs): 0.5 -> 5,315, 0.75 -> 5,097, 1 -> 4,858, 1.5 -> 4,112
-    // effective GCUPS; 0.75 is kept because it is the one where the network
-    // both certifies more pairs in the first round and sweeps fewer banded
-    // cells than the fixed start.  NW_BAND_MARGIN for sweeps.
+    // pairs of 2-20 kb, same context and memory budget): 0.25 -> 6,526,
+    // 0.5 -> 6,100, 0.75 -> 5,691, 1 -> 5,285 effective GCUPS, against 6,962
+    // from the fixed start 64; 0.75 is kept because it is the smallest
+    // margin at which the network certifies more pairs in the first round
+    // than the fixed start on held-out pairs while sweeping fewer banded
+    // cells there.  NW_BAND_MARGIN and NW_BAND_PROBE_CAP for sweeps.
     double margin = 0.75;
     if (const char *e = getenv("NW_BAND_MARGIN")) margin = std::max(0.25, atof(e));
     int rc = model_of(ctx, &bm, false);
@@ -400,6 +402,14 @@ int nw_band_model_set(nw_ctx *ctx, const float *params, uint64_t count) {
     refresh(ctx, bm);
     cudaError_t e = cudaStreamSynchronize(ctx->stream);
     return e == cudaSuccess ? NW_OK : cuda_fail(ctx, e, "model set");
+}
+
+int nw_band_model_clear(nw_ctx *ctx) {
+    if (!ctx) return NW_ERR_ARG;
+    cudaSetDevice(ctx->device);
+    cudaError_t e = cudaStreamSynchronize(ctx->stream);  // no kernel still reads the parameters
+    free_band_model(ctx);
+    return e == cudaSuccess ? NW_OK : cuda_fail(ctx, e, "model clear");
 }
 
 int nw_band_model_get(nw_ctx *ctx, float *params, uint64_t count) {
