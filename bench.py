@@ -84,6 +84,26 @@ def parse():
     return ap.parse_args()
 
 
+def slowest_rank_ms(ms: float, device=None) -> float:
+    """The largest of each rank's time over the default process group (the
+    rank's own time when there is none): a multi-rank job is as fast as its
+    slowest rank.  `device` is where the reduction tensor lives (a CUDA
+    device for NCCL, None = CPU for gloo)."""
+    import torch
+    import torch.distributed as dist
+    if not (dist.is_available() and dist.is_initialized()) or dist.get_world_size() == 1:
+        return ms
+    t = torch.tensor([float(ms)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_gcups(cells_per_rank: float, world: int, ms: float) -> float:
+    """Whole-job throughput: the cells every rank aligned over the slowest
+    rank's time."""
+    return world * cells_per_rank / (ms * 1e-3) / 1e9
+
+
 def dist_env():
     rank = int(os.environ.get("RANK", "0"))
     world = int(os.environ.get("WORLD_SIZE", "1"))
@@ -574,9 +594,7 @@ def run_ours(args):
     stats = ctx.kernel_stats()
     band_cells = nw.nw_ctx_band_stats(ctx)["band_cells"] - band0  # the timed steps' banded cells
     if world > 1:
-        t = torch.tensor([ms], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = float(t.item())
+        ms = slowest_rank_ms(ms, dev)
         dist.barrier()
 
     # end to end through the public API with host buffers, copies inside
@@ -590,7 +608,7 @@ def run_ours(args):
         t1 = time.perf_counter()
         if k:
             e2e_ms.append((t1 - t0) * 1e3)
-    e2e_val = world * work.cells / (statistics.mean(e2e_ms) * 1e-3) / 1e9
+    e2e_val = job_gcups(work.cells, world, slowest_rank_ms(statistics.mean(e2e_ms), dev))
 
     dl, dms = stats.get(work.dominant, (0, 0.0))
     dom_avg_ms = dms / max(dl, 1)
@@ -601,7 +619,7 @@ def run_ours(args):
     launches = sum(v[0] for k_, v in stats.items() if k_ != "peak" and not k_.startswith("host:"))
 
     line = {
-        "metric": METRIC, "value": world * work.cells / (ms * 1e-3) / 1e9, "unit": "GCUPS", "n_gpus": world,
+        "metric": METRIC, "value": job_gcups(work.cells, world, ms), "unit": "GCUPS", "n_gpus": world,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "int32", "data": "synthetic",
         "config": dict(workload=work.desc, scoring=list(SCORING), parallelism=f"replicas{world}",

@@ -5,6 +5,8 @@
 #include <algorithm>
 #include <vector>
 
+#include <cstdlib>
+
 #include "nw_internal.cuh"
 
 namespace nw {
@@ -122,8 +124,12 @@ __global__ void __launch_bounds__(32) k_traceback(TraceTask one, const TraceTask
 constexpr uint32_t kWalkDone = 0, kWalkJoined = 1, kWalkFull = 2, kWalkBand = 3, kWalkNone = 4;
 constexpr int kWalkWarps = 4;
 constexpr uint32_t kParMinStripes = 3;     // shorter pairs walk sequentially,
-constexpr uint64_t kParMinMoves = 8192;    // and so do pairs with m + n below this (the three
-                                           // extra launches cost more than they save)
+constexpr uint64_t kParMinMoves = 8192;    // and so do pairs of a batch with m + n below this (the
+                                           // other pairs' walks keep the GPU busy, and the
+                                           // speculative walks add work)
+constexpr uint64_t kParMinMovesOne = 1024; // a lone pair walks in parallel from m + n = 1024 up:
+                                           // a 1,000 x 1,000 pair's traceback takes 0.10 ms
+                                           // instead of 0.17 ms sequentially (GB300)
 
 struct StripeJob {
     uint64_t moff;  // byte offset of the stripe's spec moves; its link moves follow at moff + lcap
@@ -607,6 +613,8 @@ template <int R>
 static int launch_walks(nw_ctx *ctx, const TraceTask *host, const TraceTask *dev, uint32_t ntasks) {
     constexpr uint32_t SH = 32u * R;
     HostTimer ht(ctx, "trace_plan");
+    static const char *min_env = getenv("NW_TB_MIN_MOVES");  // sweep knob
+    const uint64_t min_moves = min_env ? (uint64_t)atoll(min_env) : ntasks == 1 ? kParMinMovesOne : kParMinMoves;
     const TraceTask one = dev ? TraceTask{} : host[0];
     std::vector<StripeJob> jobs;
     std::vector<uint32_t> base(ntasks, 0xffffffffu);
@@ -615,7 +623,7 @@ static int launch_walks(nw_ctx *ctx, const TraceTask *host, const TraceTask *dev
         const uint64_t m = host[t].m, n = host[t].n;
         if (m == 0 || n == 0 || host[t].state) continue;
         const uint32_t S = (uint32_t)((m + SH - 1) / SH);
-        if (S < kParMinStripes || m + n < kParMinMoves) continue;
+        if (S < kParMinStripes || m + n < min_moves) continue;
         // moves of a stripe's walks: its rows, twice the proportional columns, slack
         uint64_t cap = SH + 2 * ((SH * n + m - 1) / m) + 512;
         cap = std::min<uint64_t>((cap + 15) / 16 * 16, 65520);

@@ -1,0 +1,72 @@
+"""The bench's multi-rank host logic on CPU ranks (gloo, world size 2): the
+job's time is the slowest rank's, its value counts every rank's cells, and
+the reference arm runs on rank 0 only.  Every rank of the GPU path runs an
+independent replica (no data-path collective), so this is the whole N > 1
+logic."""
+import os
+import socket
+import sys
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def _free_port() -> int:
+    with socket.socket() as s:
+        s.bind(("127.0.0.1", 0))
+        return s.getsockname()[1]
+
+
+def _rank(rank: int, world: int, port: int, q):
+    os.environ.update(MASTER_ADDR="127.0.0.1", MASTER_PORT=str(port), RANK=str(rank), WORLD_SIZE=str(world),
+                      LOCAL_RANK=str(rank))
+    import torch.distributed as dist
+    sys.path.insert(0, ROOT)
+    import bench
+    dist.init_process_group("gloo", rank=rank, world_size=world)
+    try:
+        ms = bench.slowest_rank_ms(10.0 + 5.0 * rank)   # rank 1 is the slow one
+        q.put((rank, ms, bench.job_gcups(2e9, world, ms), bench.dist_env()))
+    finally:
+        dist.destroy_process_group()
+
+
+def test_two_ranks_take_the_slowest_time_and_count_all_cells():
+    import torch.multiprocessing as mp
+    ctx = mp.get_context("spawn")
+    q = ctx.Queue()
+    port = _free_port()
+    procs = [ctx.Process(target=_rank, args=(r, 2, port, q)) for r in range(2)]
+    for p in procs:
+        p.start()
+    try:
+        got = sorted(q.get(timeout=120) for _ in procs)
+    finally:
+        for p in procs:
+            p.join(timeout=60)
+            if p.is_alive():
+                p.kill()
+    assert [g[0] for g in got] == [0, 1]
+    for rank, ms, val, env in got:
+        assert ms == 15.0
+        assert val == pytest.approx(2 * 2e9 / 15e-3 / 1e9)
+        assert env == (rank, 2, rank)
+    assert all(p.exitcode == 0 for p in procs)
+
+
+def test_single_process_time_is_its_own():
+    sys.path.insert(0, ROOT)
+    import bench
+    assert bench.slowest_rank_ms(12.5) == 12.5
+    assert bench.job_gcups(1e9, 1, 1000.0) == pytest.approx(1.0)
+
+
+def test_reference_arm_runs_on_rank_zero_only(monkeypatch, capsys):
+    sys.path.insert(0, ROOT)
+    import bench
+    monkeypatch.setenv("RANK", "1")
+    monkeypatch.setenv("WORLD_SIZE", "2")
+    args = bench.argparse.Namespace(workload="band", gpus=2, steps=1, warmup=0)
+    assert bench.run_reference(args) is None
+    assert capsys.readouterr().out == ""
