@@ -77,6 +77,8 @@ def parse():
     ap.add_argument("--rate", type=float, default=50000.0, help="serve: Poisson arrival rate (requests/s)")
     ap.add_argument("--duration", type=float, default=3.0, help="serve: seconds of arrivals")
     ap.add_argument("--serve-pool", type=int, default=1500, help="serve: distinct requests the stream cycles through")
+    ap.add_argument("--serve-workers", type=int, default=8, help="serve: worker threads (contexts, streams)")
+    ap.add_argument("--serve-batch", type=int, default=64, help="serve: most requests one admission takes")
     ap.add_argument("--npairs", type=int, default=20000, help="band: evaluation pairs (20,000 = the full workload)")
     ap.add_argument("--no-clocks", action="store_true")
     ap.add_argument("--nseq", type=int, default=512, help="allpairs: number of sequences (512 = the full workload)")
@@ -485,7 +487,8 @@ def run_serve(args):
     want = np.array([r.want_cigar for r in reqs], np.uint8)
     cells_of = al.astype(np.float64) * bl.astype(np.float64)
     train_loss = train_band_model(nw, ctx, dev)
-    srv = nw.Server(ctx, workers=4, max_batch=512, trace_budget=64 << 30, flags=nw.NW_LEARNED_BAND)
+    srv = nw.Server(ctx, workers=args.serve_workers, max_batch=args.serve_batch, trace_budget=64 << 30,
+                    flags=nw.NW_LEARNED_BAND)
     # warm-up: a few requests through every worker
     srv.submit_many(pool, ao[:16], al[:16], bo[:16], bl[:16], want[:16])
     srv.drain(300.0)
@@ -525,7 +528,8 @@ def run_serve(args):
         "config": {"workload": (f"serving: Poisson arrivals at {args.rate:,.0f} req/s for {args.duration} s, pair "
                                 "lengths log-uniform [50, 50,000], divergence U[0.01,0.30], half score-only / half "
                                 f"score+CIGAR, requests cycled from {len(reqs)} drawn from seed 1005; certified learned "
-                                "band, 4 workers, 64 GiB traceback budget"),
+                                f"band, {args.serve_workers} workers, batches of at most {args.serve_batch}, "
+                                "64 GiB traceback budget"),
                    "requests": int(arrivals.size), "completed": len(done), "ok": ok, "drained": drained,
                    "offered_gcups": offered / 1e9, "backlog_at_end_of_arrivals": backlog["waiting"] + backlog["running"],
                    "arrival_window_s": submit_end, "train_loss": train_loss},

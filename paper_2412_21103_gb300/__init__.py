@@ -455,7 +455,7 @@ class Server:
     """Continuous-batching server (nw_server): submit host requests, poll
     completions.  See include/nw.h."""
 
-    def __init__(self, ctx: Context, workers: int = 3, max_batch: int = 1024, trace_budget: int = 16 << 30,
+    def __init__(self, ctx: Context, workers: int = 8, max_batch: int = 64, trace_budget: int = 16 << 30,
                  scoring=DEFAULT_SCORING, flags: int = 0, queue_bytes: int = 1 << 30, queue_slots: int = 1 << 20):
         self.handle = load().nw_server_create_ex(ctx.handle, workers, max_batch, trace_budget, queue_bytes,
                                                  queue_slots, _sc(scoring), flags)
