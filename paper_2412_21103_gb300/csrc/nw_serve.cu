@@ -24,7 +24,6 @@
 // results.  Batches of different workers run on different streams, so
 // requests that arrive while others are on the GPU are admitted as soon as
 // a worker and memory are free, and their kernels overlap on the device.
-#include <atomic>
 #include <chrono>
 #include <condition_variable>
 #include <cstring>
@@ -130,7 +129,7 @@ __global__ void k_release(DevQueue *q, uint32_t units) {
 }
 
 struct Live {  // a published or staged request, in ticket order
-    uint64_t start, end;  // absolute arena positions of its bytes
+    uint64_t start;  // absolute arena position of its bytes
     double t_submit;
     bool done;
 };
@@ -395,7 +394,7 @@ static int enqueue(nw_server *srv, uint32_t count, Get get, uint64_t *tickets) {
                 if (!dsegs.empty() && dsegs.back().dst + dsegs.back().len == slot) dsegs.back().len += 1;
                 else dsegs.push_back(Seg{slot, dstage.size(), 1});
                 dstage.push_back(r);
-                srv->live.push_back(Live{pos, pos + need, t, false});
+                srv->live.push_back(Live{pos, t, false});
                 srv->arena_tail = pos + need;
                 if (tickets) tickets[k + planned] = r.ticket;
                 ++planned;
