@@ -274,6 +274,12 @@ int nw_band_model_init(nw_ctx *ctx, uint64_t seed);
 /* Copy parameters in / out (host arrays of nw_band_model_size() floats). */
 int nw_band_model_set(nw_ctx *ctx, const float *params, uint64_t count);
 int nw_band_model_get(nw_ctx *ctx, float *params, uint64_t count);
+/* Save the parameters to a file / load them from one (then as
+ * nw_band_model_set: optimizer state cleared).  Format: "NWBAND01", the
+ * parameter count (little-endian uint64), the FP32 parameters.  A file of
+ * another format or size is NW_ERR_ARG. */
+int nw_band_model_save(nw_ctx *ctx, const char *path);
+int nw_band_model_load(nw_ctx *ctx, const char *path);
 /* Drop the context's model and its optimizer state (NW_LEARNED_BAND then
  * starts every pair at half-width 64, as on a context that never had one). */
 int nw_band_model_clear(nw_ctx *ctx);

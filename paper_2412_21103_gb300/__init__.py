@@ -107,6 +107,8 @@ def load():
         "nw_band_model_set": (ctypes.c_int, [vp, vp, u64]),
         "nw_band_model_get": (ctypes.c_int, [vp, vp, u64]),
         "nw_band_model_clear": (ctypes.c_int, [vp]),
+        "nw_band_model_save": (ctypes.c_int, [vp, ctypes.c_char_p]),
+        "nw_band_model_load": (ctypes.c_int, [vp, ctypes.c_char_p]),
         "nw_band_model_forward": (ctypes.c_int, [vp, vp, u32, vp]),
         "nw_band_model_grad": (ctypes.c_int, [vp, vp, vp, u32, vp, vp]),
         "nw_band_model_train_step": (ctypes.c_int, [vp, vp, vp, u32, ctypes.c_float, vp]),
@@ -418,6 +420,14 @@ def nw_band_model_get(ctx: Context) -> np.ndarray:
     p = np.zeros(nw_band_model_size(), np.float32)
     _check(ctx, load().nw_band_model_get(ctx.handle, _ptr(p), p.size))
     return p
+
+
+def nw_band_model_save(ctx: Context, path):
+    _check(ctx, load().nw_band_model_save(ctx.handle, os.fsencode(path)))
+
+
+def nw_band_model_load(ctx: Context, path):
+    _check(ctx, load().nw_band_model_load(ctx.handle, os.fsencode(path)))
 
 
 def nw_band_model_clear(ctx: Context):

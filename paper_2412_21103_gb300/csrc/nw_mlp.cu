@@ -18,8 +18,10 @@
 #include <cuda_bf16.h>
 
 #include <algorithm>
-#include <cstdlib>
 #include <cmath>
+#include <cstdio>
+#include <cstdlib>
+#include <cstring>
 #include <vector>
 
 #include "nw_internal.cuh"
@@ -402,6 +404,37 @@ int nw_band_model_set(nw_ctx *ctx, const float *params, uint64_t count) {
     refresh(ctx, bm);
     cudaError_t e = cudaStreamSynchronize(ctx->stream);
     return e == cudaSuccess ? NW_OK : cuda_fail(ctx, e, "model set");
+}
+
+// File format of a saved model: the 8 bytes "NWBAND01", the parameter
+// count as a little-endian uint64, then the FP32 master parameters in the
+// layout nw_band_model_get returns (little-endian IEEE-754).
+int nw_band_model_save(nw_ctx *ctx, const char *path) {
+    if (!ctx || !path) return NW_ERR_ARG;
+    std::vector<float> p(kNParams);
+    int rc = nw_band_model_get(ctx, p.data(), p.size());
+    if (rc) return rc;
+    FILE *f = fopen(path, "wb");
+    if (!f) return fail(ctx, NW_ERR_ARG, "cannot open '%s' for writing", path);
+    const uint64_t count = kNParams;
+    const bool ok = fwrite("NWBAND01", 1, 8, f) == 8 && fwrite(&count, 8, 1, f) == 1 &&
+                    fwrite(p.data(), 4, p.size(), f) == p.size();
+    const bool closed = fclose(f) == 0;
+    return ok && closed ? NW_OK : fail(ctx, NW_ERR_ARG, "short write to '%s'", path);
+}
+
+int nw_band_model_load(nw_ctx *ctx, const char *path) {
+    if (!ctx || !path) return NW_ERR_ARG;
+    FILE *f = fopen(path, "rb");
+    if (!f) return fail(ctx, NW_ERR_ARG, "cannot open '%s'", path);
+    char magic[8] = {0};
+    uint64_t count = 0;
+    std::vector<float> p(kNParams);
+    const bool ok = fread(magic, 1, 8, f) == 8 && memcmp(magic, "NWBAND01", 8) == 0 && fread(&count, 8, 1, f) == 1 &&
+                    count == (uint64_t)kNParams && fread(p.data(), 4, p.size(), f) == p.size() && fgetc(f) == EOF;
+    fclose(f);
+    if (!ok) return fail(ctx, NW_ERR_ARG, "'%s' is not a saved band model of %d parameters", path, kNParams);
+    return nw_band_model_set(ctx, p.data(), p.size());
 }
 
 int nw_band_model_clear(nw_ctx *ctx) {

@@ -96,3 +96,30 @@ def test_learned_band_beats_fixed_start_and_full_grid():
     assert band1 + fb1 * per_pair < 0.8 * full_cells
     c0.close()
     c1.close()
+
+
+def test_model_checkpoint_roundtrip(tmp_path):
+    """A trained model saved to a file and loaded into a fresh context gives
+    bit-identical network outputs; a file of the wrong size is refused."""
+    import torch
+    import paper_2412_21103_gb300 as nw
+    c1 = nw.Context(0, torch.cuda.current_stream())
+    _train(nw, c1, epochs=2)
+    path = tmp_path / "band_model.bin"
+    nw.nw_band_model_save(c1, path)
+    assert path.stat().st_size == 16 + 4 * nw.nw_band_model_size()
+    pairs = [(p.a, p.b) for p in seqgen.band_pairs(1004, npairs=64)]
+    pool, ao, al, bo, bl = _pool(pairs)
+    feat = nw.nw_band_features(c1, torch.from_numpy(pool).cuda(), ao, al, bo, bl)
+    y1 = nw.nw_band_model_forward(c1, feat).cpu().numpy()
+    c2 = nw.Context(0, torch.cuda.current_stream())
+    nw.nw_band_model_load(c2, path)
+    y2 = nw.nw_band_model_forward(c2, feat).cpu().numpy()
+    assert np.array_equal(y1, y2)
+    assert np.array_equal(nw.nw_band_model_get(c1), nw.nw_band_model_get(c2))
+    bad = tmp_path / "short.bin"
+    bad.write_bytes(path.read_bytes()[:-4])
+    with pytest.raises(nw.NWError):
+        nw.nw_band_model_load(c2, bad)
+    c1.close()
+    c2.close()
