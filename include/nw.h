@@ -165,6 +165,19 @@ int nw_pack_device(nw_ctx *ctx, const char *ascii, uint64_t len, uint8_t *out2b)
 /* Worst-case CIGAR size in bytes, NUL included: 2*(m+n)+1. */
 uint64_t nw_cigar_bound(uint64_t m, uint64_t n);
 
+/* The certificate of the banded rounds (no GPU needed): an upper bound on
+ * the score of any path of an m x n grid that leaves the band of half-width
+ * w around the diagonals [min(0,n-m), max(0,n-m)].  Such a path reaches
+ * diagonal max(0,n-m)+w+1 or min(0,n-m)-w-1, so it has at least G gap moves
+ * (the fewer of the two sides' minimum counts that fit the grid), hence at
+ * most k = floor((m+n-G)/2) diagonal moves worth at most `match` each:
+ * *bound = match*k + gap*(m+n-2k), the larger over the two sides.  Returns 1
+ * with *bound set, 0 when no path can leave the band (*bound = 0), or
+ * -NW_ERR_ARG (sizes >= 2^31, gap > 0, match < 0, null bound).  A banded
+ * score above the bound equals the full score, and its alignment is the
+ * full alignment. */
+int nw_band_exit_bound(uint64_t m, uint64_t n, uint64_t w, nw_scoring sc, int64_t *bound);
+
 /* -------------------------------------------------------------- alignment */
 
 /* One pair (Sec. 2.2-2.4).  Writes the score H(m,n) to *score; with

@@ -107,6 +107,7 @@ def load():
         "nw_band_model_set": (ctypes.c_int, [vp, vp, u64]),
         "nw_band_model_get": (ctypes.c_int, [vp, vp, u64]),
         "nw_band_model_clear": (ctypes.c_int, [vp]),
+        "nw_band_exit_bound": (ctypes.c_int, [u64, u64, u64, Scoring, ctypes.POINTER(ctypes.c_int64)]),
         "nw_band_model_save": (ctypes.c_int, [vp, ctypes.c_char_p]),
         "nw_band_model_load": (ctypes.c_int, [vp, ctypes.c_char_p]),
         "nw_band_model_forward": (ctypes.c_int, [vp, vp, u32, vp]),
@@ -428,6 +429,16 @@ def nw_band_model_save(ctx: Context, path):
 
 def nw_band_model_load(ctx: Context, path):
     _check(ctx, load().nw_band_model_load(ctx.handle, os.fsencode(path)))
+
+
+def nw_band_exit_bound(m: int, n: int, w: int, scoring=DEFAULT_SCORING):
+    """The banded certificate's exit bound (None when no path can leave the
+    band); host arithmetic of the library, no GPU needed."""
+    b = ctypes.c_int64(0)
+    rc = load().nw_band_exit_bound(m, n, w, _sc(scoring), ctypes.byref(b))
+    if rc < 0:
+        raise NWError(-rc, "nw_band_exit_bound: bad argument")
+    return int(b.value) if rc == 1 else None
 
 
 def nw_band_model_clear(ctx: Context):

@@ -242,6 +242,9 @@ __global__ void k_pack(const char *__restrict__ ascii, uint64_t len, uint8_t *__
     }
 }
 
+// certificate bound of the banded rounds (defined with them)
+bool band_exit_bound(int64_t m, int64_t n, int64_t w, int32_t match, int32_t gap, int64_t *bound);
+
 }  // namespace nw
 
 using namespace nw;
@@ -485,6 +488,12 @@ int nw_pack_device(nw_ctx *ctx, const char *ascii, uint64_t len, uint8_t *out2b)
 }
 
 uint64_t nw_cigar_bound(uint64_t m, uint64_t n) { return 2 * (m + n) + 1; }
+
+int nw_band_exit_bound(uint64_t m, uint64_t n, uint64_t w, nw_scoring sc, int64_t *bound) {
+    if (!bound || m >= (1ull << 31) || n >= (1ull << 31) || w >= (1ull << 31) || sc.gap > 0 || sc.match < 0)
+        return -NW_ERR_ARG;
+    return nw::band_exit_bound((int64_t)m, (int64_t)n, (int64_t)w, sc.match, sc.gap, bound) ? 1 : 0;
+}
 
 int nw_align(nw_ctx *ctx, const uint8_t *a2b, uint64_t m, const uint8_t *b2b, uint64_t n, nw_scoring sc,
              uint32_t flags, int32_t *score, char *cigar, uint64_t cigar_cap, uint64_t *cigar_len) {

@@ -1,0 +1,39 @@
+"""Host arithmetic of the CUDA path that needs no GPU, against the oracle:
+the banded certificate's exit bound (reading 9 of the design notes; the
+oracle's `exit_bound` is pinned by brute force in test_oracle_pins)."""
+import numpy as np
+import pytest
+
+import oracle
+
+
+@pytest.fixture(scope="module")
+def nw():
+    import paper_2412_21103_gb300 as nw
+    nw.load()
+    return nw
+
+
+def test_exit_bound_matches_the_oracle(nw):
+    rng = np.random.default_rng(17)
+    cases = [(0, 0, 0), (0, 5, 1), (7, 0, 3), (1, 1, 0), (10, 10, 20), (50, 3, 2), (3, 50, 2)]
+    cases += [(int(rng.integers(0, 3000)), int(rng.integers(0, 3000)), int(rng.integers(0, 400))) for _ in range(3000)]
+    scorings = [(1, -1, -1), (2, -1, -3), (3, -2, -1), (1, 0, 0), (0, -1, -1)]
+    for m, n, w in cases:
+        for sc in scorings:
+            got = nw.nw_band_exit_bound(m, n, w, sc)
+            want = oracle.exit_bound(m, n, w, sc[0], sc[2])
+            assert got == want, (m, n, w, sc, got, want)
+
+
+def test_exit_bound_large_sizes_match(nw):
+    for m, n, w in [(20000, 20000, 64), (32768, 32741, 1000), (50000, 2000, 10), (2000, 50000, 10),
+                    (1 << 30, (1 << 30) + 7, 5000)]:
+        assert nw.nw_band_exit_bound(m, n, w) == oracle.exit_bound(m, n, w)
+
+
+def test_exit_bound_rejects_bad_arguments(nw):
+    with pytest.raises(nw.NWError):
+        nw.nw_band_exit_bound(1 << 31, 10, 1)
+    with pytest.raises(nw.NWError):
+        nw.nw_band_exit_bound(10, 10, 1, (1, -1, 1))  # positive gap
