@@ -313,6 +313,21 @@ def _u32(a):
     return a, a.ctypes.data_as(ctypes.POINTER(ctypes.c_uint32))
 
 
+def _cigar_offsets(a_len, b_len) -> np.ndarray:
+    """Offsets of a CIGAR pool with nw_cigar_bound(m, n) = 2*(m+n)+1 bytes
+    per pair (npairs+1 entries)."""
+    caps = 2 * (np.asarray(a_len, np.uint64) + np.asarray(b_len, np.uint64)) + np.uint64(1)
+    out = np.zeros(caps.size + 1, np.uint64)
+    np.cumsum(caps, out=out[1:])
+    return out
+
+
+def _cigars(cpool: np.ndarray, off, length, npairs: int) -> list[str]:
+    mv = memoryview(cpool)
+    return [str(mv[o:o + n], "ascii") for o, n in zip(np.asarray(off[:npairs]).tolist(),
+                                                     np.asarray(length[:npairs]).tolist())]
+
+
 def nw_align_batch(ctx: Context, pool2b, a_off, a_len, b_off, b_len, scoring=DEFAULT_SCORING, flags: int = 0,
                    scores=None, cigar_pool=None, cigar_off=None, cigar_len=None):
     """Align many pairs from one packed pool.  Metadata arrays are host
@@ -326,8 +341,7 @@ def nw_align_batch(ctx: Context, pool2b, a_off, a_len, b_off, b_len, scoring=DEF
     bl, blp = _u32(b_len)
     want = bool(flags & NW_CIGAR)
     if cigar_off is None and want:
-        caps = [nw_cigar_bound(int(x), int(y)) for x, y in zip(al, bl)]
-        cigar_off = np.concatenate([[0], np.cumsum(caps)]).astype(np.uint64)
+        cigar_off = _cigar_offsets(al, bl)
     co, cop = _u64(cigar_off) if want else (None, None)
     if _is_host(pool2b):
         flags |= NW_HOST_IO
@@ -339,7 +353,7 @@ def nw_align_batch(ctx: Context, pool2b, a_off, a_len, b_off, b_len, scoring=DEF
         _check(ctx, rc)
         cigars = None
         if want:
-            cigars = [cpool[int(co[k]): int(co[k]) + int(clen[k])].tobytes().decode() for k in range(npairs)]
+            cigars = _cigars(cpool, co, clen, npairs)
         return sc_out[:npairs], cigars
     rc = L.nw_align_batch(ctx.handle, _ptr(pool2b), aop, alp, bop, blp, npairs, _sc(scoring), flags, _ptr(scores),
                           _ptr(cigar_pool) if want else None, cop, _ptr(cigar_len) if want else None)
@@ -360,8 +374,7 @@ def nw_align_batch_banded(ctx: Context, pool2b, a_off, a_len, b_off, b_len, band
     ww, wwp = _u32(band_w)
     want = bool(flags & NW_CIGAR)
     if cigar_off is None and want:
-        caps = [nw_cigar_bound(int(x), int(y)) for x, y in zip(al, bl)]
-        cigar_off = np.concatenate([[0], np.cumsum(caps)]).astype(np.uint64)
+        cigar_off = _cigar_offsets(al, bl)
     co, cop = _u64(cigar_off) if want else (None, None)
     if _is_host(pool2b):
         flags |= NW_HOST_IO
@@ -373,7 +386,7 @@ def nw_align_batch_banded(ctx: Context, pool2b, a_off, a_len, b_off, b_len, band
         _check(ctx, rc)
         cigars = None
         if want:
-            cigars = [cpool[int(co[k]): int(co[k]) + int(clen[k])].tobytes().decode() for k in range(npairs)]
+            cigars = _cigars(cpool, co, clen, npairs)
         return sc_out[:npairs], cigars
     rc = L.nw_align_batch_banded(ctx.handle, _ptr(pool2b), aop, alp, bop, blp, npairs, wwp, _sc(scoring), flags,
                                  _ptr(scores), _ptr(cigar_pool) if want else None, cop,

@@ -37,3 +37,19 @@ def test_exit_bound_rejects_bad_arguments(nw):
         nw.nw_band_exit_bound(1 << 31, 10, 1)
     with pytest.raises(nw.NWError):
         nw.nw_band_exit_bound(10, 10, 1, (1, -1, 1))  # positive gap
+
+
+def test_binding_cigar_offsets_follow_the_library_bound(nw):
+    rng = np.random.default_rng(3)
+    a = rng.integers(0, 50000, 500).astype(np.uint32)
+    b = rng.integers(0, 50000, 500).astype(np.uint32)
+    off = nw._cigar_offsets(a, b)
+    caps = [nw.nw_cigar_bound(int(x), int(y)) for x, y in zip(a, b)]
+    assert off[0] == 0 and np.array_equal(np.diff(off), np.array(caps, np.uint64))
+
+
+def test_binding_cigar_decoding(nw):
+    pool = np.zeros(32, np.uint8)
+    pool[0:4] = np.frombuffer(b"3=1X", np.uint8)
+    pool[20:22] = np.frombuffer(b"5D", np.uint8)
+    assert nw._cigars(pool, np.array([0, 10, 20], np.uint64), np.array([4, 0, 2], np.uint64), 3) == ["3=1X", "", "5D"]
