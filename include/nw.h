@@ -330,7 +330,8 @@ int nw_score_all_pairs(nw_ctx *ctx, const uint8_t *pool2b, const uint64_t *off, 
  * `flags` and the creating context holds a model, which every worker
  * copies); batches of different workers overlap on the GPU; a finished
  * batch returns its reservation on the device.  Results equal those of
- * nw_align on the same pair. */
+ * nw_align on the same pair.  Submit, poll, drain and the state queries
+ * may be called from several host threads at once. */
 typedef struct nw_server nw_server;
 typedef struct {
     uint64_t ticket;     /* from nw_server_submit                          */
@@ -379,7 +380,8 @@ int nw_server_stats(nw_server *srv, uint64_t *out, int cap);
 /* Read the device queue word: requests admitted so far and traceback bytes
  * reserved in flight (synchronises with the intake stream). */
 int nw_server_queue_state(nw_server *srv, uint64_t *admitted, uint64_t *reserved_bytes);
-/* Finish queued work, stop the workers, free everything. */
+/* Finish queued work, stop the workers, free everything.  No other call on
+ * this server may be in progress or made afterwards. */
 void nw_server_destroy(nw_server *srv);
 
 /* ------------------------------------------------------------ measurement */
