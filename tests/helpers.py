@@ -1,4 +1,4 @@
-"""Independent checks used to pin the oracle and to judge the GPU path.
+"""Independent checks used to pin the oracle and to check the GPU path.
 
 Nothing here shares code with ``oracle/`` or with the library: brute-force
 enumeration, bit-parallel edit distance and LCS, CIGAR parsing and re-scoring.
