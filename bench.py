@@ -48,18 +48,49 @@ PEAK_KINDS = (0, 2, 4)       # nw_peak_int kinds: DPX add-max, max, prmt (lane-o
 STEPS_DEFAULT = {"pair32k": 100, "pair1k": 200, "allpairs": 20, "band": 3}
 
 
+def code_only(text: str) -> str:
+    """C/C++/CUDA source without its comments and trailing blanks (string
+    and character literals kept): what the compiler sees of the code."""
+    out, i, n = [], 0, len(text)
+    while i < n:
+        c = text[i]
+        if c in "\"'":
+            j = i + 1
+            while j < n and text[j] != c:
+                j += 2 if text[j] == "\\" else 1
+            out.append(text[i:j + 1])
+            i = j + 1
+        elif text.startswith("//", i):
+            j = text.find("\n", i)
+            i = n if j < 0 else j
+        elif text.startswith("/*", i):
+            j = text.find("*/", i + 2)
+            i = n if j < 0 else j + 2
+        else:
+            out.append(c)
+            i += 1
+    return "\n".join(ln.rstrip() for ln in "".join(out).splitlines() if ln.strip())
+
+
+def sources_sha(files) -> str:
+    """First 16 hex digits of the sha256 over the code (comments removed) of
+    the given files, in name order."""
+    import hashlib
+    h = hashlib.sha256()
+    for f in sorted(files):
+        h.update(os.path.basename(f).encode())
+        h.update(code_only(open(os.path.join(HERE, f), encoding="utf-8").read()).encode())
+    return h.hexdigest()[:16]
+
+
 def dram_traffic(kernel: str, workload: str):
     """DRAM bytes per launch of `kernel` on `workload` from the committed ncu
-    record, or None when there is none or the kernel's sources changed since."""
-    import hashlib
+    record, or None when there is none or the kernel's code changed since
+    (comments do not count)."""
     path = os.path.join(HERE, "profiles", "dram_traffic.json")
     try:
         rec = json.load(open(path))["entries"][f"{kernel}@{workload}"]
-        h = hashlib.sha256()
-        for f in sorted(rec["sources"]):
-            h.update(os.path.basename(f).encode())
-            h.update(open(os.path.join(HERE, f), "rb").read())
-        if h.hexdigest()[:16] != rec["sha"]:
+        if sources_sha(rec["sources"]) != rec["sha"]:
             return None
         return rec["dram_read"] + rec["dram_write"]
     except (OSError, KeyError, ValueError):

@@ -1,4 +1,7 @@
-// Batched pairs (a7) and the banded rounds (a8): the persistent kernel.
+// Batched pairs (a7) and the banded rounds (a8): the persistent kernel.  The
+// pairwise alignments of Sec. 3.2 (all pairs of a sequence family, Eq. 2),
+// batched on one GPU instead of split over MPI ranks; each pair's fill is the
+// Sec. 2.3 recurrence from the Sec. 2.2 boundary, in the W domain.
 //
 // One warp owns one pair at a time and runs all of its stripes (32*R rows
 // each) back to back: lane k at step t works on global index g = t - k,

@@ -1,4 +1,9 @@
-// One long pair: the fill (a3/a4) spread over many warps.
+// One long pair: the fill (a3/a4) spread over many warps.  It computes the
+// Sec. 2.3 recurrence (Eq. 1, read as in standard NW: the match/mismatch
+// score on the diagonal only, the gap on vertical and horizontal moves) from
+// the Sec. 2.2 boundary, in the W domain of nw_internal.cuh.  Sec. 3.1
+// parallelises the same fill with one thread per cell that polls its
+// neighbours; here dependencies are met by construction instead.
 //
 // Work split.  Stripes of 32*R rows go to warps; lane k of a warp owns R
 // consecutive rows.  At step t lane k updates a register block of R rows x C

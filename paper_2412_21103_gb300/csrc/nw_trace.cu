@@ -1,5 +1,7 @@
 // Traceback (a5) and CIGAR assembly, shared by the single-pair and the
-// batched paths.  A task describes one pair: its pointer words (layout
+// batched paths.  The walk of Sec. 2.4 from (m,n) back to (0,0), taking one
+// optimal path in the priority order diagonal > vertical > horizontal (the
+// 1/2/3 codes of Sec. 3.1).  A task describes one pair: its pointer words (layout
 // [stripe][lane][column group], R rows x 16/R columns per word), its
 // sequences and where its moves and CIGAR go.  One CTA per task.
 #include <algorithm>

@@ -1,6 +1,7 @@
-"""The bench's multi-rank host logic on CPU ranks (gloo, world size 2): the
-job's time is the slowest rank's, its value counts every rank's cells, and
-the reference arm runs on rank 0 only.  Every rank of the GPU path runs an
+"""The bench's host logic on CPU: multi-rank timing on gloo ranks (world
+size 2) -- the job's time is the slowest rank's, its value counts every
+rank's cells, the reference arm runs on rank 0 only -- and the code hash
+that ties a DRAM traffic record to its kernel.  Every rank of the GPU path runs an
 independent replica (no data-path collective), so this is the whole N > 1
 logic."""
 import os
@@ -70,3 +71,18 @@ def test_reference_arm_runs_on_rank_zero_only(monkeypatch, capsys):
     args = bench.argparse.Namespace(workload="band", gpus=2, steps=1, warmup=0)
     assert bench.run_reference(args) is None
     assert capsys.readouterr().out == ""
+
+
+def test_traffic_records_ignore_comment_edits_only(tmp_path):
+    """The DRAM traffic the bench reports stays tied to the kernel's code: a
+    comment edit keeps the record's hash, a code edit changes it."""
+    sys.path.insert(0, ROOT)
+    import bench
+    f = tmp_path / "k.cu"
+    f.write_text('__global__ void k(int *p) { p[0] = 1; }  // one\n/* two */\nconst char *s = "//x";\n')
+    h0 = bench.sources_sha([str(f)])
+    f.write_text('// a new header comment\n__global__ void k(int *p) { p[0] = 1; }  // edited\n'
+                 'const char *s = "//x";\n')
+    assert bench.sources_sha([str(f)]) == h0
+    f.write_text('__global__ void k(int *p) { p[0] = 2; }\nconst char *s = "//x";\n')
+    assert bench.sources_sha([str(f)]) != h0
