@@ -177,6 +177,19 @@ uint64_t nw_cigar_bound(uint64_t m, uint64_t n);
  * score above the bound equals the full score, and its alignment is the
  * full alignment. */
 int nw_band_exit_bound(uint64_t m, uint64_t n, uint64_t w, nw_scoring sc, int64_t *bound);
+/* The certificate the banded rounds apply (no GPU needed): 1 when a banded
+ * score of half-width w proves the full result -- the score when
+ * banded_score >= the exit bound, the alignment (want_cigar != 0) only when
+ * banded_score > the bound, always when no path can leave the band -- else
+ * 0; -NW_ERR_ARG as nw_band_exit_bound. */
+int nw_band_certifies(uint64_t m, uint64_t n, uint64_t w, int32_t banded_score, nw_scoring sc, uint32_t want_cigar);
+/* The half-width the next banded round uses after banded_score failed at w:
+ * the larger of 2w and the smallest w' > w at which banded_score itself
+ * would certify (a wider band scores no less, so the round at w' certifies);
+ * at most max(2w, max(m,n)+1).  -NW_ERR_ARG for sizes >= 2^31, w >= 2^30, gap
+ * > 0 or match < 0. */
+int64_t nw_band_next_width(uint64_t m, uint64_t n, uint64_t w, int32_t banded_score, nw_scoring sc,
+                           uint32_t want_cigar);
 
 /* -------------------------------------------------------------- alignment */
 

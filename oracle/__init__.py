@@ -191,6 +191,29 @@ def exit_bound(m: int, n: int, w: int, match: int = 1, gap: int = -1) -> int | N
     return best
 
 
+def certifies(m: int, n: int, w: int, banded_score: int, want_cigar: bool, match: int = 1, gap: int = -1) -> bool:
+    """The certificate on a banded score (not in the paper; the design's
+    reading of banded exactness): no path can leave the band, or the banded
+    score beats every path that does -- at least equal for the score, strictly
+    above for the alignment (an equal path outside the band could win the
+    diagonal-first tie order)."""
+    U = exit_bound(m, n, w, match, gap)
+    if U is None:
+        return True
+    return banded_score > U if want_cigar else banded_score >= U
+
+
+def next_width(m: int, n: int, w: int, banded_score: int, want_cigar: bool, match: int = 1, gap: int = -1) -> int:
+    """Half-width of the next banded round after `banded_score` failed at w:
+    the first w' > w (scanning upward, at most max(m,n)+1) at which the same
+    banded score would certify -- a wider band scores no less, so the round
+    at w' certifies -- and at least 2w."""
+    wp = w + 1
+    while wp <= max(m, n) and not certifies(m, n, wp, banded_score, want_cigar, match, gap):
+        wp += 1
+    return max(2 * w, wp)
+
+
 def rle(ops: str) -> str:
     """Run-length encode an op string into a CIGAR ('3=1X2I')."""
     if not ops:

@@ -108,6 +108,8 @@ def load():
         "nw_band_model_get": (ctypes.c_int, [vp, vp, u64]),
         "nw_band_model_clear": (ctypes.c_int, [vp]),
         "nw_band_exit_bound": (ctypes.c_int, [u64, u64, u64, Scoring, ctypes.POINTER(ctypes.c_int64)]),
+        "nw_band_certifies": (ctypes.c_int, [u64, u64, u64, ctypes.c_int32, Scoring, u32]),
+        "nw_band_next_width": (ctypes.c_int64, [u64, u64, u64, ctypes.c_int32, Scoring, u32]),
         "nw_band_model_save": (ctypes.c_int, [vp, ctypes.c_char_p]),
         "nw_band_model_load": (ctypes.c_int, [vp, ctypes.c_char_p]),
         "nw_band_model_forward": (ctypes.c_int, [vp, vp, u32, vp]),
@@ -452,6 +454,22 @@ def nw_band_exit_bound(m: int, n: int, w: int, scoring=DEFAULT_SCORING):
     if rc < 0:
         raise NWError(-rc, "nw_band_exit_bound: bad argument")
     return int(b.value) if rc == 1 else None
+
+
+def nw_band_certifies(m: int, n: int, w: int, banded_score: int, want_cigar: bool, scoring=DEFAULT_SCORING) -> bool:
+    """Whether a banded score proves the full result (host arithmetic)."""
+    rc = load().nw_band_certifies(m, n, w, banded_score, _sc(scoring), int(bool(want_cigar)))
+    if rc < 0:
+        raise NWError(-rc, "nw_band_certifies: bad argument")
+    return rc == 1
+
+
+def nw_band_next_width(m: int, n: int, w: int, banded_score: int, want_cigar: bool, scoring=DEFAULT_SCORING) -> int:
+    """The next round's half-width after a failed certificate (host arithmetic)."""
+    rc = int(load().nw_band_next_width(m, n, w, banded_score, _sc(scoring), int(bool(want_cigar))))
+    if rc < 0:
+        raise NWError(-rc, "nw_band_next_width: bad argument")
+    return rc
 
 
 def nw_band_model_clear(ctx: Context):

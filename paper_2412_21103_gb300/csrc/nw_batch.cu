@@ -241,6 +241,28 @@ bool band_exit_bound(int64_t m, int64_t n, int64_t w, int32_t match, int32_t gap
     return any;
 }
 
+// The certificate on a banded score S_b of half-width w: the score is exact
+// when S_b >= U, the alignment when S_b > U (a tie outside the band could
+// win the diagonal-first order); no bound when no path can leave the band.
+bool band_certifies(int64_t m, int64_t n, int64_t w, int32_t sb, const nw_scoring &sc, bool want) {
+    int64_t U = 0;
+    const bool leave = band_exit_bound(m, n, w, sc.match, sc.gap, &U);
+    return !leave || (want ? (int64_t)sb > U : (int64_t)sb >= U);
+}
+
+// The next half-width after S_b failed at w: at least double, and at least
+// the smallest w' whose bound lies below S_b -- a wider band scores no less,
+// so w' certifies for sure.
+uint32_t band_next_width(uint32_t m, uint32_t n, uint32_t w, int32_t sb, const nw_scoring &sc, bool want) {
+    uint32_t lo_w = w + 1, hi_w = std::max(m, n) + 1;
+    while (lo_w < hi_w) {
+        const uint32_t mid = lo_w + (hi_w - lo_w) / 2;
+        if (band_certifies(m, n, mid, sb, sc, want)) hi_w = mid;
+        else lo_w = mid + 1;
+    }
+    return std::max(2 * w, lo_w);
+}
+
 // Band of half-width w for an m x n pair: diagonals and the stripe period.
 static void band_task(BatchTask &t, int R, uint32_t w) {
     const int64_t delta = (int64_t)t.n - t.m;
@@ -464,27 +486,9 @@ static int band_rounds(nw_ctx *ctx, const uint8_t *pool, const uint64_t *a_off, 
             for (size_t q = 0; q < wave.size(); ++q) {
                 const BatchTask &t = wave[q];
                 const uint32_t w = tw[k0 + q];
-                int64_t U = 0;
-                const bool can_leave = band_exit_bound(t.m, t.n, w, sc.match, sc.gap, &U);
-                // score: S_b >= U suffices; the alignment needs S_b > U (a
-                // tie outside the band could win the diagonal-first order)
-                auto certifies = [&](bool leave, int64_t u) {
-                    return !leave || (want ? (int64_t)hs[q] > u : (int64_t)hs[q] >= u);
-                };
-                if (!certifies(can_leave, U)) {
-                    // The next width: at least double, and at least the
-                    // smallest w' whose bound lies below this banded score --
-                    // a wider band scores no less, so w' certifies for sure.
-                    uint32_t lo_w = w + 1, hi_w = std::max(t.m, t.n) + 1;
-                    while (lo_w < hi_w) {
-                        const uint32_t mid = lo_w + (hi_w - lo_w) / 2;
-                        int64_t Um = 0;
-                        const bool lv = band_exit_bound(t.m, t.n, mid, sc.match, sc.gap, &Um);
-                        if (certifies(lv, Um)) hi_w = mid;
-                        else lo_w = mid + 1;
-                    }
+                if (!band_certifies(t.m, t.n, w, hs[q], sc, want)) {
                     next.push_back(t.out0);
-                    nextw.push_back(std::max(2 * w, lo_w));
+                    nextw.push_back(band_next_width(t.m, t.n, w, hs[q], sc, want));
                     continue;
                 }
                 ctx->band_stats[1 + round] += 1;

@@ -242,8 +242,10 @@ __global__ void k_pack(const char *__restrict__ ascii, uint64_t len, uint8_t *__
     }
 }
 
-// certificate bound of the banded rounds (defined with them)
+// the certificate of the banded rounds (defined with them)
 bool band_exit_bound(int64_t m, int64_t n, int64_t w, int32_t match, int32_t gap, int64_t *bound);
+bool band_certifies(int64_t m, int64_t n, int64_t w, int32_t sb, const nw_scoring &sc, bool want);
+uint32_t band_next_width(uint32_t m, uint32_t n, uint32_t w, int32_t sb, const nw_scoring &sc, bool want);
 
 }  // namespace nw
 
@@ -488,6 +490,17 @@ int nw_pack_device(nw_ctx *ctx, const char *ascii, uint64_t len, uint8_t *out2b)
 }
 
 uint64_t nw_cigar_bound(uint64_t m, uint64_t n) { return 2 * (m + n) + 1; }
+
+int nw_band_certifies(uint64_t m, uint64_t n, uint64_t w, int32_t banded_score, nw_scoring sc, uint32_t want_cigar) {
+    if (m >= (1ull << 31) || n >= (1ull << 31) || w >= (1ull << 31) || sc.gap > 0 || sc.match < 0) return -NW_ERR_ARG;
+    return nw::band_certifies((int64_t)m, (int64_t)n, (int64_t)w, banded_score, sc, want_cigar != 0) ? 1 : 0;
+}
+
+int64_t nw_band_next_width(uint64_t m, uint64_t n, uint64_t w, int32_t banded_score, nw_scoring sc,
+                           uint32_t want_cigar) {
+    if (m >= (1ull << 31) || n >= (1ull << 31) || w >= (1ull << 30) || sc.gap > 0 || sc.match < 0) return -NW_ERR_ARG;
+    return nw::band_next_width((uint32_t)m, (uint32_t)n, (uint32_t)w, banded_score, sc, want_cigar != 0);
+}
 
 int nw_band_exit_bound(uint64_t m, uint64_t n, uint64_t w, nw_scoring sc, int64_t *bound) {
     if (!bound || m >= (1ull << 31) || n >= (1ull << 31) || w >= (1ull << 31) || sc.gap > 0 || sc.match < 0)

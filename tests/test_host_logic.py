@@ -53,3 +53,19 @@ def test_binding_cigar_decoding(nw):
     pool[0:4] = np.frombuffer(b"3=1X", np.uint8)
     pool[20:22] = np.frombuffer(b"5D", np.uint8)
     assert nw._cigars(pool, np.array([0, 10, 20], np.uint64), np.array([4, 0, 2], np.uint64), 3) == ["3=1X", "", "5D"]
+
+
+def test_certificate_and_next_width_match_the_oracle(nw):
+    """The banded rounds' certificate and next-width rule (host code of the
+    library) against the oracle's plain definitions."""
+    rng = np.random.default_rng(23)
+    for _ in range(1500):
+        m, n = int(rng.integers(1, 2500)), int(rng.integers(1, 2500))
+        w = int(rng.integers(0, 300))
+        sc = [(1, -1, -1), (2, -1, -3), (1, 0, 0)][int(rng.integers(0, 3))]
+        U = oracle.exit_bound(m, n, w, sc[0], sc[2])
+        base = U if U is not None else sc[0] * min(m, n)
+        sb = int(base + rng.integers(-400, 3))
+        for want in (False, True):
+            assert nw.nw_band_certifies(m, n, w, sb, want, sc) == oracle.certifies(m, n, w, sb, want, sc[0], sc[2])
+            assert nw.nw_band_next_width(m, n, w, sb, want, sc) == oracle.next_width(m, n, w, sb, want, sc[0], sc[2])

@@ -313,3 +313,32 @@ def test_region_dp_reduces_to_full_and_band(seed):
         sb, _ = oracle.banded(a, b, w)
         got = oracle.region(a, b, lo, hi, max(0, hi_d), max(0, -lo_d))
         assert got == sb, w
+
+
+@pytest.mark.parametrize("seed", range(6))
+def test_certificate_soundness_and_next_width_guarantee(seed):
+    """Reading 9 by brute force on small pairs: a certified banded score
+    equals the full score, and after a failed round the next width's round
+    certifies (its banded score is no lower, and the same score already
+    clears that width's bound)."""
+    rng = np.random.default_rng(600 + seed)
+    for _ in range(40):
+        m, n = int(rng.integers(1, 40)), int(rng.integers(1, 40))
+        a = rng.integers(0, 4, m).astype(np.uint8)
+        b = a[: n].copy() if n <= m else np.concatenate([a, rng.integers(0, 4, n - m).astype(np.uint8)])
+        mut = rng.random(n) < 0.3
+        b[mut] = rng.integers(0, 4, int(mut.sum())).astype(np.uint8)
+        full = oracle.score(a, b)
+        for want in (False, True):
+            for w in range(0, 6):
+                sb, _ = oracle.banded(a, b, w)
+                if oracle.certifies(m, n, w, sb, want):
+                    assert sb == full, (seed, m, n, w)
+                else:
+                    w2 = oracle.next_width(m, n, w, sb, want)
+                    assert w2 >= 2 * w and w2 > w
+                    sb2, _ = oracle.banded(a, b, w2)
+                    assert sb2 >= sb
+                    if w2 <= max(m, n):
+                        assert oracle.certifies(m, n, w2, sb2, want)
+                        assert sb2 == full
