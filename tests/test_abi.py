@@ -51,3 +51,34 @@ def test_context_without_gpu_fails_cleanly(lib):
     if torch.cuda.is_available():
         pytest.skip("a GPU is present")
     assert lib.nw_ctx_create(0, None, 0) in (None, 0)
+
+
+def test_plain_c_program_uses_the_abi(lib, tmp_path):
+    """nw.h compiles as C99 (no C++ or torch types at the boundary) and a C
+    program linked against libnw.so gets the same answers as the binding."""
+    import os
+    import shutil
+    import subprocess
+    import oracle
+    cc = shutil.which("gcc") or shutil.which("cc")
+    if cc is None:
+        pytest.skip("no C compiler")
+    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+    so = nw.lib_path()
+    exe = tmp_path / "c_abi_check"
+    subprocess.run([cc, "-std=c99", "-Wall", "-Werror", "-I", os.path.join(root, "include"),
+                    os.path.join(root, "tests", "c_abi_check.c"), so, f"-Wl,-rpath,{os.path.dirname(so)}",
+                    "-o", str(exe)], check=True)
+    out = subprocess.run([str(exe)], check=True, capture_output=True, text=True).stdout.split(maxsplit=10)
+    packed = nw.nw_pack("ACGTacgtA").tolist()
+    assert out[0] == "0" and [int(x) for x in out[1:4]] == packed
+    assert int(out[4]) == nw.NW_ERR_BAD_BASE
+    assert out[5] == "1" and int(out[6]) == oracle.exit_bound(100, 120, 5)
+    assert int(out[7]) == nw.nw_cigar_bound(3, 4)
+    assert int(out[8]) == int(nw.nw_band_certifies(1000, 1000, 64, 900, True))
+    assert int(out[9]) == nw.nw_band_next_width(1000, 1000, 64, 500, True)
+    assert out[10].strip() == load_strerror(nw.NW_ERR_BAD_BASE)
+
+
+def load_strerror(code: int) -> str:
+    return nw.load().nw_strerror(code).decode()
