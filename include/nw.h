@@ -306,6 +306,10 @@ int nw_band_model_get(nw_ctx *ctx, float *params, uint64_t count);
  * another format or size is NW_ERR_ARG. */
 int nw_band_model_save(nw_ctx *ctx, const char *path);
 int nw_band_model_load(nw_ctx *ctx, const char *path);
+/* The first banded round's half-width for a pair whose network output is y
+ * (= log of the predicted half-width): ceil(0.75 * e^y), clamped to
+ * [8, max(m, n)]; no GPU needed.  0 for sizes >= 2^31. */
+uint32_t nw_band_start_width(float y, uint64_t m, uint64_t n);
 /* Drop the context's model and its optimizer state (NW_LEARNED_BAND then
  * starts every pair at half-width 64, as on a context that never had one). */
 int nw_band_model_clear(nw_ctx *ctx);

@@ -134,6 +134,17 @@ def loss_and_grad_exact(params, X, t):
     return 0.5 * float(np.mean(e * e)), g
 
 
+def start_width(y: float, m: int, n: int, margin: float = 0.75) -> int:
+    """The first banded round's half-width for a pair whose network output is
+    y = log of the predicted half-width: ceil(margin * e^y), at least 8 and at
+    most max(m, n).  (y is the FP32 output, widened to float64.)"""
+    import math
+    y = float(np.float32(y))
+    if y > 700.0:  # e^y overflows a double; the clamp gives max(m, n)
+        return max(m, n)
+    return int(min(max(m, n), max(8, math.ceil(math.exp(y) * margin))))
+
+
 def band_label(m: int, n: int, score: int, excursion: int, match: int = 1, gap: int = -1) -> int:
     """Training label of a pair: the smallest half-width w whose closed-form
     exit bound lies strictly below the full score (so the certificate accepts

@@ -109,6 +109,7 @@ def load():
         "nw_band_model_clear": (ctypes.c_int, [vp]),
         "nw_band_exit_bound": (ctypes.c_int, [u64, u64, u64, Scoring, ctypes.POINTER(ctypes.c_int64)]),
         "nw_band_certifies": (ctypes.c_int, [u64, u64, u64, ctypes.c_int32, Scoring, u32]),
+        "nw_band_start_width": (u32, [ctypes.c_float, u64, u64]),
         "nw_band_next_width": (ctypes.c_int64, [u64, u64, u64, ctypes.c_int32, Scoring, u32]),
         "nw_band_model_save": (ctypes.c_int, [vp, ctypes.c_char_p]),
         "nw_band_model_load": (ctypes.c_int, [vp, ctypes.c_char_p]),
@@ -454,6 +455,11 @@ def nw_band_exit_bound(m: int, n: int, w: int, scoring=DEFAULT_SCORING):
     if rc < 0:
         raise NWError(-rc, "nw_band_exit_bound: bad argument")
     return int(b.value) if rc == 1 else None
+
+
+def nw_band_start_width(y: float, m: int, n: int) -> int:
+    """First banded half-width from the network output y (host arithmetic)."""
+    return int(load().nw_band_start_width(y, m, n))
 
 
 def nw_band_certifies(m: int, n: int, w: int, banded_score: int, want_cigar: bool, scoring=DEFAULT_SCORING) -> bool:

@@ -280,6 +280,8 @@ static int gradients(nw_ctx *ctx, BandModel *bm, const float *x, const float *t,
 using namespace nw;
 
 // Features -> network -> half-widths (with a safety factor), on the host.
+uint32_t band_start_width(float y, uint32_t m, uint32_t n, double margin, double probe_cap, bool skip);
+
 int learned_band_widths(nw_ctx *ctx, const uint8_t *pool, const uint64_t *a_off, const uint32_t *a_len,
                         const uint64_t *b_off, const uint32_t *b_len, uint32_t npairs, std::vector<uint32_t> &w) {
     w.assign(npairs, 64u);
@@ -330,17 +332,22 @@ int learned_band_widths(nw_ctx *ctx, const uint8_t *pool, const uint64_t *a_off,
     double probe_cap = 0.0;
     if (const char *e = getenv("NW_BAND_PROBE_CAP")) probe_cap = atof(e);
     const bool skip = getenv("NW_BAND_SKIP") != nullptr;
-    for (uint32_t k = 0; k < npairs; ++k) {
-        const double full_pred = std::exp((double)y[k]);
-        double pred = full_pred * margin;
-        const double cap = (double)std::max(a_len[k], b_len[k]);
-        const double delta = std::fabs((double)b_len[k] - (double)a_len[k]);
-        const double n = (double)b_len[k];
-        if (skip && (512.0 + 2.0 * full_pred + delta) * 20.0 >= n * 17.0) pred = cap;
-        else if (probe_cap > 0 && pred > probe_cap) pred = probe_cap;
-        w[k] = (uint32_t)std::min(cap, std::max(8.0, std::ceil(pred)));
-    }
+    for (uint32_t k = 0; k < npairs; ++k) w[k] = band_start_width(y[k], a_len[k], b_len[k], margin, probe_cap, skip);
     return NW_OK;
+}
+
+// First half-width of a pair from the network's output y = log w:
+// ceil(margin * e^y), clamped to [8, max(m, n)].  (Sweep knobs: a probe cap
+// on the width, and the straight-to-full rule for a predicted band that would
+// cover most of the grid.)
+uint32_t band_start_width(float y, uint32_t m, uint32_t n, double margin, double probe_cap, bool skip) {
+    const double full_pred = std::exp((double)y);
+    double pred = full_pred * margin;
+    const double cap = (double)std::max(m, n);
+    const double delta = std::fabs((double)n - (double)m);
+    if (skip && (512.0 + 2.0 * full_pred + delta) * 20.0 >= (double)n * 17.0) pred = cap;
+    else if (probe_cap > 0 && pred > probe_cap) pred = probe_cap;
+    return (uint32_t)std::min(cap, std::max(8.0, std::ceil(pred)));
 }
 
 extern "C" {
@@ -390,6 +397,11 @@ int nw_band_model_init(nw_ctx *ctx, uint64_t seed) {
     refresh(ctx, bm);
     cudaError_t e = cudaGetLastError();
     return e == cudaSuccess ? NW_OK : cuda_fail(ctx, e, "model init");
+}
+
+uint32_t nw_band_start_width(float y, uint64_t m, uint64_t n) {
+    if (m >= (1ull << 31) || n >= (1ull << 31)) return 0;
+    return band_start_width(y, (uint32_t)m, (uint32_t)n, 0.75, 0.0, false);
 }
 
 uint64_t nw_band_model_size(void) { return kNParams; }

@@ -69,3 +69,13 @@ def test_certificate_and_next_width_match_the_oracle(nw):
         for want in (False, True):
             assert nw.nw_band_certifies(m, n, w, sb, want, sc) == oracle.certifies(m, n, w, sb, want, sc[0], sc[2])
             assert nw.nw_band_next_width(m, n, w, sb, want, sc) == oracle.next_width(m, n, w, sb, want, sc[0], sc[2])
+
+
+def test_start_width_matches_the_oracle(nw):
+    from oracle import band_model as bm
+    rng = np.random.default_rng(31)
+    ys = list(rng.normal(4.0, 2.0, 3000)) + [-50.0, -3.0, 0.0, 2.0794415, 9.9, 15.0, 30.0, 80.0]
+    for y in ys:
+        m, n = int(rng.integers(1, 60000)), int(rng.integers(1, 60000))
+        y32 = float(np.float32(y))
+        assert nw.nw_band_start_width(y32, m, n) == bm.start_width(y32, m, n), (y32, m, n)
