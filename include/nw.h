@@ -306,6 +306,16 @@ int nw_band_model_get(nw_ctx *ctx, float *params, uint64_t count);
  * another format or size is NW_ERR_ARG. */
 int nw_band_model_save(nw_ctx *ctx, const char *path);
 int nw_band_model_load(nw_ctx *ctx, const char *path);
+/* The straggler rule of the batched paths (no GPU needed): given each
+ * pair's cost on one warp (warp_cells: cells, scaled for slower kernels) and
+ * its full grid (full_cells), the pairs to run on the multi-warp single-pair
+ * kernel instead.  With the pairs sorted by one-warp cost, routing the
+ * first k costs the sum of their single-pair times plus the larger of the
+ * rest's batch time and the (k+1)-th pair's one-warp time; the k with the
+ * lowest estimate is taken (pairs under 1e7 full cells are never routed).
+ * Writes the indices, costliest first, to out (n entries of room) and
+ * returns how many, or -NW_ERR_ARG. */
+int64_t nw_route_stragglers(const double *warp_cells, const double *full_cells, uint32_t n, uint32_t *out);
 /* The first banded round's half-width for a pair whose network output is y
  * (= log of the predicted half-width): ceil(0.75 * e^y), clamped to
  * [8, max(m, n)]; no GPU needed.  0 for sizes >= 2^31. */

@@ -110,6 +110,7 @@ def load():
         "nw_band_exit_bound": (ctypes.c_int, [u64, u64, u64, Scoring, ctypes.POINTER(ctypes.c_int64)]),
         "nw_band_certifies": (ctypes.c_int, [u64, u64, u64, ctypes.c_int32, Scoring, u32]),
         "nw_band_start_width": (u32, [ctypes.c_float, u64, u64]),
+        "nw_route_stragglers": (ctypes.c_int64, [vp, vp, u32, vp]),
         "nw_band_next_width": (ctypes.c_int64, [u64, u64, u64, ctypes.c_int32, Scoring, u32]),
         "nw_band_model_save": (ctypes.c_int, [vp, ctypes.c_char_p]),
         "nw_band_model_load": (ctypes.c_int, [vp, ctypes.c_char_p]),
@@ -455,6 +456,18 @@ def nw_band_exit_bound(m: int, n: int, w: int, scoring=DEFAULT_SCORING):
     if rc < 0:
         raise NWError(-rc, "nw_band_exit_bound: bad argument")
     return int(b.value) if rc == 1 else None
+
+
+def nw_route_stragglers(warp_cells, full_cells) -> list[int]:
+    """Indices of the pairs the batched paths run on the single-pair kernel
+    (host arithmetic of the straggler rule)."""
+    wc = np.ascontiguousarray(warp_cells, dtype=np.float64)
+    fc = np.ascontiguousarray(full_cells, dtype=np.float64)
+    out = np.zeros(max(wc.size, 1), np.uint32)
+    k = int(load().nw_route_stragglers(_ptr(wc), _ptr(fc), wc.size, _ptr(out)))
+    if k < 0:
+        raise NWError(-k, "nw_route_stragglers: bad argument")
+    return out[:k].tolist()
 
 
 def nw_band_start_width(y: float, m: int, n: int) -> int:

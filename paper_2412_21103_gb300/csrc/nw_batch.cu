@@ -926,6 +926,15 @@ extern "C" int nw_align_batch_banded(nw_ctx *ctx, const uint8_t *pool2b, const u
                         cigar_len, body);
 }
 
+extern "C" int64_t nw_route_stragglers(const double *warp_cells, const double *full_cells, uint32_t n,
+                                       uint32_t *out) {
+    if (n && (!warp_cells || !full_cells || !out)) return -NW_ERR_ARG;
+    const std::vector<size_t> r = pick_stragglers(std::vector<double>(warp_cells, warp_cells + n),
+                                                  std::vector<double>(full_cells, full_cells + n));
+    for (size_t k = 0; k < r.size(); ++k) out[k] = (uint32_t)r[k];
+    return (int64_t)r.size();
+}
+
 extern "C" int nw_ctx_band_stats(nw_ctx *ctx, uint64_t *out, int cap) {
     if (!ctx) return -NW_ERR_ARG;
     for (int k = 0; k < cap && k < 8; ++k) out[k] = ctx->band_stats[k];

@@ -79,3 +79,24 @@ def test_start_width_matches_the_oracle(nw):
         m, n = int(rng.integers(1, 60000)), int(rng.integers(1, 60000))
         y32 = float(np.float32(y))
         assert nw.nw_band_start_width(y32, m, n) == bm.start_width(y32, m, n), (y32, m, n)
+
+
+def test_straggler_rule_properties(nw):
+    """The batched paths' straggler rule (host code): a balanced batch stays
+    on the batched kernel, a pair that would hold one warp far longer than
+    the batch goes to the single-pair kernel, pairs under 1e7 cells never
+    move, and what moves is always the costliest prefix."""
+    assert nw.nw_route_stragglers(np.full(10000, 1e6), np.full(10000, 1e6)) == []
+    w = np.concatenate([[1e6] * 500, [1e9], [1e6] * 500])
+    assert nw.nw_route_stragglers(w, w) == [500]
+    assert nw.nw_route_stragglers([5e6], [5e6]) == []
+    assert nw.nw_route_stragglers([], []) == []
+    rng = np.random.default_rng(41)
+    for _ in range(200):
+        n = int(rng.integers(1, 3000))
+        wc = np.exp(rng.uniform(np.log(1e5), np.log(rng.choice([1e7, 1e9, 1e10])), n))
+        fc = wc * rng.uniform(1.0, 3.0, n)
+        got = nw.nw_route_stragglers(wc, fc)
+        order = list(np.argsort(-wc, kind="stable"))
+        assert got == [int(k) for k in order[: len(got)]]
+        assert all(fc[k] >= 1e7 for k in got)
