@@ -86,3 +86,20 @@ def test_traffic_records_ignore_comment_edits_only(tmp_path):
     assert bench.sources_sha([str(f)]) == h0
     f.write_text('__global__ void k(int *p) { p[0] = 2; }\nconst char *s = "//x";\n')
     assert bench.sources_sha([str(f)]) != h0
+
+
+def test_clock_summary_keeps_the_timed_window_and_reasons():
+    """The bench's clock record: only samples inside the timed window count,
+    the median SM clock and the active throttle reasons are reported."""
+    sys.path.insert(0, ROOT)
+    import bench
+    c = bench.ClockSampler(0)
+    c.lines = [(0.5, "1200, 2070, 900.1, Not Active, Not Active, Not Active, Active"),     # before the window
+               (1.1, "2070, 2070, 1300.0, Not Active, Not Active, Not Active, Not Active"),
+               (1.2, "2055, 2070, 1350.5, Not Active, Not Active, Not Active, Active"),
+               (1.3, "2070, 2070, 1390.2, Not Active, Not Active, Not Active, Not Active"),
+               (1.35, "garbage line"),
+               (9.0, "300, 2070, 100.0, Active, Not Active, Not Active, Not Active")]      # after it
+    c.window(1.0, 1.3)
+    s = c.summary()
+    assert s == {"sm_mhz": 2070.0, "sm_max_mhz": 2070.0, "reasons": ["sw_power_cap"], "samples": 3}
