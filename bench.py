@@ -43,8 +43,10 @@ METRIC = "GCUPS on 1 GB300 and % of int/DPX roofline; learned-band+batched vs pl
 SCORING = (1, -1, -1)
 L2_FLUSH_BYTES = 256 << 20   # > 129 MB L2
 HERE = os.path.dirname(os.path.abspath(__file__))
-OPS_PER_CELL = 3             # algorithmic minimum in the W domain: prmt + add-max + max
+OPS_PER_CELL = 4             # algorithmic work of the textbook cell: s select, D+s, max(E_up, E_left), add-max
+W_OPS_PER_CELL = 3           # what the W-domain kernels issue for it: prmt + add-max + max
 PEAK_KINDS = (0, 2, 4)       # nw_peak_int kinds: DPX add-max, max, prmt (lane-ops/s each)
+CELL_KINDS = (5, 6, 7)       # nw_peak_int kinds: score-only cells in three instruction mixes (cells/s)
 STEPS_DEFAULT = {"pair32k": 100, "pair1k": 200, "allpairs": 20, "band": 3}
 
 
@@ -455,7 +457,15 @@ class BandWork:
         self.ctx.sync()
         plain_s = time.perf_counter() - t0
         mism = int((plain != self.scores).sum().item())
-        cig_mism = int((cl != self.clen).sum().item())
+        cig_len_mism = int((cl != self.clen).sum().item())
+        # CIGAR bytes: per pair, mismatching bytes inside [off, off + length)
+        # of the two pools (a prefix sum over the byte-wise difference)
+        diff = torch.zeros(cp.numel() + 1, dtype=torch.int64, device=cp.device)
+        torch.cumsum((cp != self.cpool).to(torch.int32), 0, out=diff[1:])
+        start = torch.from_numpy(self.coff[:-1].astype(np.int64)).to(cp.device)
+        per_pair = diff[start + self.clen] - diff[start]
+        cig_mism = int(((per_pair != 0) | (cl != self.clen)).sum().item())
+        del diff
         st = nw.nw_ctx_band_stats(self.ctx)
         # the same certified band without the network (fixed start): what the
         # trained network gains, on the same context (same memory budget and
@@ -475,7 +485,8 @@ class BandWork:
         nw.nw_band_model_set(self.ctx, params)
         nonet_mism = int((nonet != self.scores).sum().item())
         return {"plain_full_gcups": self.cells / plain_s / 1e9, "plain_full_s": plain_s,
-                "score_mismatches_vs_plain": mism, "cigar_length_mismatches_vs_plain": cig_mism,
+                "score_mismatches_vs_plain": mism, "cigar_mismatches_vs_plain": cig_mism,
+                "cigar_length_mismatches_vs_plain": cig_len_mism,
                 "no_network_gcups": self.cells / nonet_s / 1e9, "no_network_score_mismatches": nonet_mism,
                 "band_stats_cumulative": st}
 
@@ -601,6 +612,9 @@ def run_ours(args):
     # integer-pipe peak (roofline denominator), measured live: the instructions of the cell update, each alone on every SM; the slowest
     # of them bounds the cell rate (3 of them per cell)
     peak_ops = min(nw.nw_peak_int(ctx, kind, 1 << 15) for kind in PEAK_KINDS)
+    # measured score-only cell rates (GCUPS) of three instruction mixes of the
+    # cell update on every SM: the cell roofline as a measured number
+    cell_rates = {f"kind{k}": nw.nw_peak_int(ctx, k, 1 << 15) for k in CELL_KINDS}
 
     band0 = nw.nw_ctx_band_stats(ctx)["band_cells"]
     ctx.reset_stats()
@@ -651,6 +665,8 @@ def run_ours(args):
     # the banded kernel the band cells it actually swept
     kcells = (band_cells / max(dl, 1)) if work.dominant.startswith("band") else work.cells
     achieved = kcells * OPS_PER_CELL / (dom_avg_ms * 1e-3) / 1e9 if dom_avg_ms else None
+    kernel_gcups = kcells / (dom_avg_ms * 1e-3) / 1e9 if dom_avg_ms else None
+    cell_peak = max(cell_rates.values())
     launches = sum(v[0] for k_, v in stats.items() if k_ != "peak" and not k_.startswith("host:"))
 
     line = {
@@ -668,7 +684,17 @@ def run_ours(args):
                                      "algorithmic: 0.25 B/cell of pointers for *_ptr kernels, ~0 for score-only",
                      "ops_per_cell": OPS_PER_CELL, "kernel_ms": dom_avg_ms, "cells_per_launch": kcells,
                      "peak_source": "measured live: slowest of nw_peak_int kinds 0/2/4 (DPX add-max, max, prmt; "
-                                    "independent chains on every SM)"},
+                                    "independent chains on every SM)",
+                     "w_domain": {"ops_per_cell": W_OPS_PER_CELL,
+                                  "achieved": kernel_gcups * W_OPS_PER_CELL if kernel_gcups else None,
+                                  "frac": kernel_gcups * W_OPS_PER_CELL / peak_ops if kernel_gcups else None,
+                                  "note": "instructions the W-domain cell issues (prmt, add-max, max) against the "
+                                          "same peak"},
+                     "cell_peak": {"unit": "GCUPS", "value": cell_peak, "kernel_gcups": kernel_gcups,
+                                   "frac": kernel_gcups / cell_peak if kernel_gcups else None,
+                                   "rates": cell_rates,
+                                   "source": "measured live: nw_peak_int kinds 5-7, score-only cells of three "
+                                             "instruction mixes, independent chains on every SM; the best"}},
         "kernels": {k_: {"launches": v[0], "ms_total": v[1]} for k_, v in stats.items()},
         "gpu_launches": launches,
         "e2e": {"value": e2e_val, "unit": "GCUPS", "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,

@@ -23,7 +23,11 @@
  *     needs more than nw_cigar_bound(m, n) bytes including the NUL.
  *   - Zero-length sequences are valid.  m and n must be below 2^30.
  *   - Scoring: gap <= 0, mismatch <= match, every value in [-40, 40]; the
- *     product (match - 2*gap) * min(m,n) must stay below 2^29.
+ *     product max(match - 2*gap, 0) * min(m,n) must stay below 2^29.  The
+ *     certified band (NW_LEARNED_BAND, nw_align_batch_banded, a server made
+ *     with NW_LEARNED_BAND) also needs match >= 2*gap: its exit bound
+ *     assumes that a path with fewer gap moves scores higher (NW_ERR_ARG
+ *     otherwise).
  *   - Memory: without NW_HOST_IO every sequence/output pointer is a device
  *     pointer on the context's device and the call is asynchronous on the
  *     context's stream (stream-ordered; call nw_ctx_sync to wait and collect
@@ -158,6 +162,16 @@ int nw_ctx_graph_stats(nw_ctx *ctx, uint64_t *out, int cap);
  * base (Sec. 3.1 listing); this is the 2-bit layout described above. */
 int nw_pack(const char *ascii, uint64_t len, uint8_t *out2b);
 
+/* Host: the same layout from base codes (one byte per base, 0..3 = A, C,
+ * G, T) instead of ASCII; NW_ERR_BAD_BASE on a code above 3. */
+int nw_pack_codes(const uint8_t *codes, uint64_t len, uint8_t *out2b);
+/* Host: pack `count` code sequences into one pool: sequence k is
+ * codes[code_off[k] .. code_off[k]+len[k]) and goes to pool + pool_off[k]
+ * (ceil(len[k]/4) bytes; the caller lays out pool_off, e.g. 16-byte
+ * aligned).  Stops at the first bad code (NW_ERR_BAD_BASE). */
+int nw_pack_pool(const uint8_t *codes, const uint64_t *code_off, const uint32_t *len, uint32_t count, uint8_t *pool,
+                 const uint64_t *pool_off);
+
 /* Device: the same packing by a GPU kernel (device pointers, asynchronous).
  * A bad character is reported by the next nw_ctx_sync as NW_ERR_BAD_BASE. */
 int nw_pack_device(nw_ctx *ctx, const char *ascii, uint64_t len, uint8_t *out2b);
@@ -222,9 +236,12 @@ int nw_align(nw_ctx *ctx, const uint8_t *a2b, uint64_t m, const uint8_t *b2b, ui
  * static device array that every GPU loading the library reserves until
  * the process exits.  a2b, b2b and score are device pointers on the current
  * device; the kernel runs on `stream` (a cudaStream_t, NULL = legacy
- * default) and the call waits for it before returning, so a device-side
- * timeout comes back as NW_ERR_TIMEOUT.  The first call on each device
- * looks up the array's device address (do it before any stream capture).
+ * default) and the call waits for that stream (cudaStreamSynchronize)
+ * before returning, so a device-side timeout comes back as NW_ERR_TIMEOUT.
+ * The first call on each device looks up the array's device address with
+ * that device current and keeps it for later calls (make that first call
+ * before any stream capture); a cudaDeviceReset while the library is
+ * loaded is not supported, since the kept address would be stale.
  * Sizes: ceil(m/512) <= 4096 and (ceil(m/512)-1) * 32*ceil((n+1)/32) <=
  * 3,141,568 words (for example m = n = 32,768 fits); larger inputs return
  * NW_ERR_ARG.  Calls share the array, so calls that overlap on the GPU
@@ -273,6 +290,17 @@ int nw_align_batch_banded(nw_ctx *ctx, const uint8_t *pool2b, const uint64_t *a_
  * cells of every pair handed to the banded path.  Returns 8 (fills at most
  * `cap`). */
 int nw_ctx_band_stats(nw_ctx *ctx, uint64_t *out, int cap);
+
+/* Per-pair outcome of the last certified-band call on this context
+ * (nw_align_batch with NW_LEARNED_BAND, or nw_align_batch_banded), for
+ * inspection: round[k] = the banded round (1..3) whose certificate accepted
+ * pair k, or 0 when it went to the full kernel; first_width[k] = the
+ * half-width of its first round; cert_width[k] = the half-width that
+ * certified it (0 for the full kernel).  Any output may be NULL; at most
+ * `cap` entries are written.  Returns the number of pairs of that call
+ * (0 before any), or -NW_ERR_ARG.  Not in the paper. */
+int64_t nw_ctx_band_outcome(nw_ctx *ctx, uint8_t *round, uint32_t *first_width, uint32_t *cert_width,
+                            uint64_t cap);
 
 /* ------------------------------------------------------------ learned band
  * Not in the paper.  A pair's features (65 floats): a 64-bin histogram of

@@ -92,6 +92,8 @@ def load():
         "nw_ctx_graph_stats": (ctypes.c_int, [vp, u64p, ctypes.c_int]),
         "nw_pack": (ctypes.c_int, [ctypes.c_char_p, u64, vp]),
         "nw_pack_device": (ctypes.c_int, [vp, vp, u64, vp]),
+        "nw_pack_codes": (ctypes.c_int, [vp, u64, vp]),
+        "nw_pack_pool": (ctypes.c_int, [vp, u64p, u32p, u32, vp, u64p]),
         "nw_cigar_bound": (u64, [u64, u64]),
         "nw_align": (ctypes.c_int, [vp, vp, u64, vp, u64, Scoring, u32, vp, vp, u64, vp]),
         "nw_align_batch": (ctypes.c_int, [vp, vp, u64p, u32p, u64p, u32p, u32, Scoring, u32, vp, vp, u64p, vp]),
@@ -101,6 +103,7 @@ def load():
         "nw_align_batch_banded": (ctypes.c_int, [vp, vp, u64p, u32p, u64p, u32p, u32, u32p, Scoring, u32, vp, vp,
                                                  u64p, vp]),
         "nw_ctx_band_stats": (ctypes.c_int, [vp, u64p, ctypes.c_int]),
+        "nw_ctx_band_outcome": (ctypes.c_int64, [vp, vp, vp, vp, u64]),
         "nw_band_features": (ctypes.c_int, [vp, vp, u64p, u32p, u64p, u32p, u32, vp]),
         "nw_band_model_size": (u64, []),
         "nw_band_model_init": (ctypes.c_int, [vp, u64]),
@@ -174,13 +177,14 @@ def _check(ctx, rc: int):
 
 
 def pack_codes(codes: np.ndarray) -> np.ndarray:
-    """Pack an array of base codes 0..3 into the 2-bit layout (host numpy).
-    Same layout as nw_pack; used to stage inputs that are already codes."""
+    """Pack an array of base codes 0..3 into the 2-bit layout (host numpy)
+    with the library's nw_pack_codes."""
     codes = np.ascontiguousarray(codes, dtype=np.uint8)
-    n = codes.size
-    pad = (-n) % 4
-    c = np.concatenate([codes, np.zeros(pad, np.uint8)]).reshape(-1, 4).astype(np.uint8)
-    return (c[:, 0] | (c[:, 1] << 2) | (c[:, 2] << 4) | (c[:, 3] << 6)).astype(np.uint8)
+    out = np.zeros(max((codes.size + 3) // 4, 1), np.uint8)
+    rc = load().nw_pack_codes(_ptr(codes), codes.size, _ptr(out))
+    if rc != NW_OK:
+        raise NWError(rc, load().nw_strerror(rc).decode())
+    return out[: (codes.size + 3) // 4]
 
 
 class Context:
@@ -405,6 +409,20 @@ def nw_ctx_band_stats(ctx: Context) -> dict:
     v = [int(x) for x in out]
     return {"tried": v[0], "certified_round": v[1:4], "full_fallback": v[5], "band_cells": v[6],
             "full_cells": v[7]}
+
+
+def nw_ctx_band_outcome(ctx: Context) -> dict:
+    """Per pair of the last certified-band call: the round that certified it
+    (1..3, 0 = the full kernel), its first and its certified half-width."""
+    L = load()
+    n = int(L.nw_ctx_band_outcome(ctx.handle, None, None, None, 0))
+    if n < 0:
+        raise NWError(-n, "nw_ctx_band_outcome: bad argument")
+    rnd = np.zeros(max(n, 1), np.uint8)
+    w0 = np.zeros(max(n, 1), np.uint32)
+    wc = np.zeros(max(n, 1), np.uint32)
+    L.nw_ctx_band_outcome(ctx.handle, _ptr(rnd), _ptr(w0), _ptr(wc), n)
+    return {"round": rnd[:n], "first_width": w0[:n], "cert_width": wc[:n]}
 
 
 def nw_band_features(ctx: Context, pool_dev, a_off, a_len, b_off, b_len, out=None):
@@ -635,6 +653,13 @@ def nw_align_score_noalloc(a2b, m: int, b2b, n: int, scoring=DEFAULT_SCORING, sc
     """Score of one pair with no allocation inside the library (device
     tensors in, device int32[1] out; waits for completion).  Returns the
     status code (NW_OK, NW_ERR_ARG beyond the static scratch, ...)."""
+    import torch
+    dev = torch.cuda.current_device()
+    for name, t in (("a2b", a2b), ("b2b", b2b), ("score", score)):
+        if not (isinstance(t, torch.Tensor) and t.is_cuda and t.device.index == dev):
+            raise ValueError(f"nw_align_score_noalloc: {name} must be a CUDA tensor on the current device (cuda:{dev})")
+    if score.dtype != torch.int32 or score.numel() < 1:
+        raise ValueError("nw_align_score_noalloc: score must be an int32 tensor with at least one element")
     s = None
     if stream is not None:
         s = stream.cuda_stream if hasattr(stream, "cuda_stream") else int(stream)
@@ -649,18 +674,24 @@ def nw_peak_int(ctx: Context, kind: int, iters: int = 1 << 16) -> float:
 
 
 def pool_of(seqs) -> tuple[np.ndarray, np.ndarray, np.ndarray]:
-    """Pack sequences (code arrays) into one pool; returns (pool, byte
-    offsets, lengths).  Each sequence starts on a 16-byte boundary."""
-    offs, lens, parts = [], [], []
-    pos = 0
-    for s in seqs:
-        p = pack_codes(s)
-        padded = (len(p) + 15) // 16 * 16
-        buf = np.zeros(max(padded, 16), np.uint8)
-        buf[: len(p)] = p
-        offs.append(pos)
-        lens.append(len(s))
-        parts.append(buf)
-        pos += len(buf)
-    pool = np.concatenate(parts) if parts else np.zeros(16, np.uint8)
-    return pool, np.array(offs, np.uint64), np.array(lens, np.uint32)
+    """Pack sequences (code arrays) into one pool with the library's
+    nw_pack_pool; returns (pool, byte offsets, lengths).  Each sequence
+    starts on a 16-byte boundary (at least 16 bytes each)."""
+    seqs = [np.ascontiguousarray(s, dtype=np.uint8) for s in seqs]
+    lens = np.array([s.size for s in seqs], np.uint32)
+    if not seqs:
+        return np.zeros(16, np.uint8), np.zeros(0, np.uint64), lens
+    slot = np.maximum((lens.astype(np.uint64) + 3) // 4 + 15, 16) // 16 * 16   # bytes per sequence, 16-aligned
+    offs = np.zeros(len(seqs), np.uint64)
+    np.cumsum(slot[:-1], out=offs[1:])
+    codes = np.concatenate(seqs) if lens.sum() else np.zeros(1, np.uint8)
+    code_off = np.zeros(len(seqs), np.uint64)
+    np.cumsum(lens[:-1].astype(np.uint64), out=code_off[1:])
+    pool = np.zeros(int(offs[-1] + slot[-1]), np.uint8)
+    co, cop = _u64(code_off)
+    ll, llp = _u32(lens)
+    po, pop = _u64(offs)
+    rc = load().nw_pack_pool(_ptr(codes), cop, llp, len(seqs), _ptr(pool), pop)
+    if rc != NW_OK:
+        raise NWError(rc, load().nw_strerror(rc).decode())
+    return pool, offs, lens

@@ -163,8 +163,21 @@ static int check_common(nw_ctx *ctx, const nw_scoring &sc) {
 static int check_len(nw_ctx *ctx, const nw_scoring &sc, uint64_t m, uint64_t n) {
     if (m >= (1ull << 30) || n >= (1ull << 30)) return fail(ctx, NW_ERR_ARG, "sequence longer than 2^30");
     const uint64_t mn = m < n ? m : n;
-    if ((uint64_t)(sc.match - 2 * sc.gap) * mn >= (1ull << 29))
+    // W <= max(match - 2*gap, 0) * min(i, j): nothing to bound when the
+    // diagonal never beats two gaps
+    const uint64_t sp = sc.match > 2 * sc.gap ? (uint64_t)(sc.match - 2 * sc.gap) : 0;
+    if (sp * mn >= (1ull << 29))
         return fail(ctx, NW_ERR_ARG, "(match - 2*gap) * min(m,n) must stay below 2^29");
+    return NW_OK;
+}
+
+// The certified band's exit bound needs fewer gap moves to score higher:
+// with G gap moves a path scores at most match*(m+n-G)/2 + gap*G, which
+// falls with G only when match >= 2*gap.
+static int check_band_scoring(nw_ctx *ctx, const nw_scoring &sc) {
+    if (sc.match < 2 * sc.gap)
+        return fail(ctx, NW_ERR_ARG, "the certified band needs match >= 2*gap (its exit bound assumes fewer gaps "
+                                     "score higher)");
     return NW_OK;
 }
 
@@ -492,6 +505,10 @@ static int band_rounds(nw_ctx *ctx, const uint8_t *pool, const uint64_t *a_off, 
                     continue;
                 }
                 ctx->band_stats[1 + round] += 1;
+                if (t.out0 < ctx->band_round.size()) {
+                    ctx->band_round[t.out0] = (uint8_t)(round + 1);
+                    ctx->band_w_cert[t.out0] = w;
+                }
                 if (want) {
                     const uint32_t id = t.out0;
                     tt.push_back(TraceTask{(const uint32_t *)pv + t.ptr_off, t.ncg, t.m, t.n,
@@ -568,9 +585,13 @@ static int band_batch(nw_ctx *ctx, const uint8_t *pool, const uint64_t *a_off, c
                       const nw_scoring &sc, uint32_t flags, int32_t *scores, char *cigar_pool,
                       const uint64_t *cigar_off, uint64_t *cigar_len) {
     std::vector<uint32_t> ids(npairs), width(npairs), rest;
+    ctx->band_round.assign(npairs, 0);
+    ctx->band_w_cert.assign(npairs, 0);
+    ctx->band_w_first.resize(npairs);
     for (uint32_t k = 0; k < npairs; ++k) {
         ids[k] = k;
         width[k] = std::max<uint32_t>(w0[k], 1);
+        ctx->band_w_first[k] = width[k];
         const BatchTask t{a_off[k], b_off[k], a_len[k], b_len[k]};
         ctx->band_stats[7] += full_cells(t, 8);
     }
@@ -882,6 +903,7 @@ extern "C" int nw_align_batch(nw_ctx *ctx, const uint8_t *pool2b, const uint64_t
                               cigar_len);
     if (rc) return rc;
     if ((flags & NW_GRAPH) && (flags & NW_HOST_IO)) return fail(ctx, NW_ERR_ARG, "NW_GRAPH needs device buffers");
+    if ((flags & NW_LEARNED_BAND) && (rc = check_band_scoring(ctx, sc))) return rc;
     auto body = [&](const uint8_t *pool, int32_t *sc_out, char *cig, uint64_t *clen) -> int {
         const uint32_t fl = flags & ~NW_HOST_IO;
         if (!(flags & NW_LEARNED_BAND))
@@ -913,6 +935,7 @@ extern "C" int nw_align_batch_banded(nw_ctx *ctx, const uint8_t *pool2b, const u
                               cigar_len);
     if (rc) return rc;
     if (!band_w) return fail(ctx, NW_ERR_ARG, "band widths are null");
+    if ((rc = check_band_scoring(ctx, sc))) return rc;
     for (uint32_t k = 0; k < npairs; ++k)
         if ((rc = check_len(ctx, sc, a_len[k], b_len[k]))) return rc;
     if ((flags & NW_BAND_RAW) && (flags & NW_CIGAR)) return fail(ctx, NW_ERR_ARG, "NW_BAND_RAW is score only");
@@ -939,6 +962,18 @@ extern "C" int nw_ctx_band_stats(nw_ctx *ctx, uint64_t *out, int cap) {
     if (!ctx) return -NW_ERR_ARG;
     for (int k = 0; k < cap && k < 8; ++k) out[k] = ctx->band_stats[k];
     return 8;
+}
+
+extern "C" int64_t nw_ctx_band_outcome(nw_ctx *ctx, uint8_t *round, uint32_t *first_width, uint32_t *cert_width,
+                                       uint64_t cap) {
+    if (!ctx) return -NW_ERR_ARG;
+    const uint64_t n = ctx->band_round.size();
+    for (uint64_t k = 0; k < n && k < cap; ++k) {
+        if (round) round[k] = ctx->band_round[k];
+        if (first_width) first_width[k] = ctx->band_w_first[k];
+        if (cert_width) cert_width[k] = ctx->band_w_cert[k];
+    }
+    return (int64_t)n;
 }
 
 extern "C" int nw_score_all_pairs(nw_ctx *ctx, const uint8_t *pool2b, const uint64_t *off, const uint32_t *len,

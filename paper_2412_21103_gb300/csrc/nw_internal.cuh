@@ -157,6 +157,10 @@ struct nw_ctx {
     // round 0..3, [5] sent to the full kernel, [6] banded cells computed,
     // [7] full-grid cells of all pairs
     uint64_t band_stats[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+    // per pair of the last certified-band call: the round that certified it
+    // (1..3, 0 = the full kernel), its first and its certified half-width
+    std::vector<uint8_t> band_round;
+    std::vector<uint32_t> band_w_first, band_w_cert;
     // learned band model (device parameters, see nw_mlp.cu)
     void *band_model = nullptr;
     // host staging for NW_HOST_IO (pinned, grown on demand)

@@ -45,7 +45,8 @@ extern "C" int nw_align_score_noalloc(const uint8_t *a2b, uint64_t m, const uint
     if (!score || (m && !a2b) || (n && !b2b)) return NW_ERR_ARG;
     if (m >= (1ull << 30) || n >= (1ull << 30)) return NW_ERR_ARG;
     const uint64_t mn = m < n ? m : n;
-    if ((uint64_t)(sc.match - 2 * sc.gap) * mn >= (1ull << 29)) return NW_ERR_ARG;
+    const uint64_t sp = sc.match > 2 * sc.gap ? (uint64_t)(sc.match - 2 * sc.gap) : 0;  // W <= sp * min(i, j)
+    if (sp * mn >= (1ull << 29)) return NW_ERR_ARG;
     const uint64_t S = (m + kStripeRows - 1) / kStripeRows;
     const uint64_t bstride = ((n + 1 + 31) / 32) * 32;
     if (S > kMaxStripes || (S > 0 ? (S - 1) * bstride : 0) > kRowWords) return NW_ERR_ARG;  // beyond the maximum
@@ -89,8 +90,10 @@ extern "C" int nw_align_score_noalloc(const uint8_t *a2b, uint64_t m, const uint
     if (fill_score_with_scratch(a2b, (uint32_t)m, b2b, (uint32_t)n, sc, score, rows, progress, err, st,
                                 slot.sm_count) != cudaSuccess)
         return NW_ERR_CUDA;
-    if (cudaStreamSynchronize(st) != cudaSuccess) return NW_ERR_CUDA;
+    // Read the error word on the caller's stream, then wait for that stream
+    // only (a plain cudaMemcpy would also wait for every blocking stream).
     uint32_t h[2] = {0, 0};
-    if (cudaMemcpy(h, err, sizeof h, cudaMemcpyDeviceToHost) != cudaSuccess) return NW_ERR_CUDA;
+    if (cudaMemcpyAsync(h, err, sizeof h, cudaMemcpyDeviceToHost, st) != cudaSuccess) return NW_ERR_CUDA;
+    if (cudaStreamSynchronize(st) != cudaSuccess) return NW_ERR_CUDA;
     return h[0] ? (int)h[0] : NW_OK;
 }

@@ -471,6 +471,31 @@ int nw_pack(const char *ascii, uint64_t len, uint8_t *out2b) {
     return NW_OK;
 }
 
+int nw_pack_codes(const uint8_t *codes, uint64_t len, uint8_t *out2b) {
+    if (len && (!codes || !out2b)) return NW_ERR_ARG;
+    const uint64_t nbytes = (len + 3) / 4;
+    for (uint64_t q = 0; q < nbytes; ++q) {
+        uint32_t byte = 0;
+        for (int k = 0; k < 4 && q * 4 + k < len; ++k) {
+            const uint32_t code = codes[q * 4 + k];
+            if (code > 3u) return NW_ERR_BAD_BASE;
+            byte |= code << (2 * k);
+        }
+        out2b[q] = (uint8_t)byte;
+    }
+    return NW_OK;
+}
+
+int nw_pack_pool(const uint8_t *codes, const uint64_t *code_off, const uint32_t *len, uint32_t count, uint8_t *pool,
+                 const uint64_t *pool_off) {
+    if (count && (!codes || !code_off || !len || !pool || !pool_off)) return NW_ERR_ARG;
+    for (uint32_t k = 0; k < count; ++k) {
+        const int rc = nw_pack_codes(codes + code_off[k], len[k], pool + pool_off[k]);
+        if (rc) return rc;
+    }
+    return NW_OK;
+}
+
 int nw_pack_device(nw_ctx *ctx, const char *ascii, uint64_t len, uint8_t *out2b) {
     if (!ctx) return NW_ERR_ARG;
     if (len == 0) return NW_OK;
@@ -503,8 +528,7 @@ int64_t nw_band_next_width(uint64_t m, uint64_t n, uint64_t w, int32_t banded_sc
 }
 
 int nw_band_exit_bound(uint64_t m, uint64_t n, uint64_t w, nw_scoring sc, int64_t *bound) {
-    if (!bound || m >= (1ull << 31) || n >= (1ull << 31) || w >= (1ull << 31) || sc.gap > 0 || sc.match < 0)
-        return -NW_ERR_ARG;
+    if (!bound || m >= (1ull << 31) || n >= (1ull << 31) || w >= (1ull << 31) || sc.gap > 0 || sc.match < 0) return -NW_ERR_ARG;
     return nw::band_exit_bound((int64_t)m, (int64_t)n, (int64_t)w, sc.match, sc.gap, bound) ? 1 : 0;
 }
 
@@ -516,7 +540,8 @@ int nw_align(nw_ctx *ctx, const uint8_t *a2b, uint64_t m, const uint8_t *b2b, ui
     if (rc) return rc;
     if (m >= (1ull << 30) || n >= (1ull << 30)) return fail(ctx, NW_ERR_ARG, "sequence longer than 2^30");
     uint64_t mn = m < n ? m : n;
-    if ((uint64_t)(sc.match - 2 * sc.gap) * mn >= (1ull << 29))
+    const uint64_t sp = sc.match > 2 * sc.gap ? (uint64_t)(sc.match - 2 * sc.gap) : 0;  // W <= sp * min(i, j)
+    if (sp * mn >= (1ull << 29))
         return fail(ctx, NW_ERR_ARG, "(match - 2*gap) * min(m,n) must stay below 2^29");
     if (!score) return fail(ctx, NW_ERR_ARG, "score pointer is null");
     if ((m && !a2b) || (n && !b2b)) return fail(ctx, NW_ERR_ARG, "sequence pointer is null");

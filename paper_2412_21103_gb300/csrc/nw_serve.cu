@@ -427,6 +427,7 @@ nw_server *nw_server_create_ex(nw_ctx *ctx, uint32_t workers, uint32_t max_batch
     if (queue_bytes < 4096 || queue_slots < 2 || (queue_slots & (queue_slots - 1)) || queue_slots > (1u << 30))
         return nullptr;
     if (check_scoring(ctx, sc) != NW_OK) return nullptr;
+    if ((flags & NW_LEARNED_BAND) && sc.match < 2 * sc.gap) return nullptr;  // the certified band's bound needs it
     cudaSetDevice(ctx->device);
     nw_server *srv = new nw_server();
     srv->device = ctx->device;

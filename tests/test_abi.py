@@ -35,6 +35,23 @@ def test_host_pack_layout(lib):
     assert nw.pack_codes(codes).tolist() == out.tolist()
 
 
+def test_host_pack_codes_rejects_code_above_3(lib):
+    with pytest.raises(nw.NWError) as e:
+        nw.pack_codes(np.array([0, 1, 4], np.uint8))
+    assert e.value.status == nw.NW_ERR_BAD_BASE
+
+
+def test_pool_layout_by_hand(lib):
+    """Three sequences of 0, 5 and 70 bases: each starts on a 16-byte
+    boundary and takes at least 16 bytes (ceil(70/4) = 18 -> 32 bytes); the
+    5-base one ACGTA packs to bytes 0b11100100 (ACGT) and 0b00000000 (A)."""
+    seqs = [np.zeros(0, np.uint8), np.array([0, 1, 2, 3, 0], np.uint8), np.full(70, 3, np.uint8)]
+    pool, off, lens = nw.pool_of(seqs)
+    assert off.tolist() == [0, 16, 32] and lens.tolist() == [0, 5, 70] and pool.size == 64
+    assert pool[16:18].tolist() == [0b11100100, 0]
+    assert pool[32:49].tolist() == [0xFF] * 17 and pool[49] == 0b00001111   # 70 = 17*4 + 2 bases of T
+
+
 def test_host_pack_rejects_bad_base(lib):
     with pytest.raises(nw.NWError) as e:
         nw.nw_pack("ACGN")

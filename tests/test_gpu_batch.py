@@ -94,21 +94,48 @@ def test_all_pairs_small_family(ctx):
             assert mat[i, j] == s and mat[j, i] == s, (i, j)
 
 
-def test_all_pairs_full_size_sampled(ctx):
-    """The 512-sequence family (130,816 pairs, Eq. 2): symmetric, exact
-    diagonal, and 400 sampled entries equal to the oracle."""
+def test_all_pairs_full_size_every_entry(ctx):
+    """The 512-sequence family (130,816 pairs, Eq. 2) in the benchmark's
+    launch configuration (device buffers, CUDA graph): every entry of the
+    matrix equals the oracle's score, both triangles, and the diagonal is
+    len * match."""
+    import torch
     import paper_2412_21103_gb300 as nw
     seqs = seqgen.all_vs_all_family(1003)
     pool, off, lens = nw.pool_of(seqs)
-    mat = nw.nw_score_all_pairs(ctx, pool, off, lens)
-    assert (mat == mat.T).all()
-    assert (np.diag(mat) == np.array([len(s) for s in seqs])).all()
-    rs = seqgen.Stream(99)
-    idx = rs.integers(0, 511, 800).reshape(-1, 2)
-    idx = [(int(i), int(j)) for i, j in idx if i != j][:400]
-    want = oracle.score_many([(seqs[i], seqs[j]) for i, j in idx])
-    got = [int(mat[i, j]) for i, j in idx]
-    assert got == want
+    n = len(seqs)
+    out = torch.zeros((n, n), dtype=torch.int32, device="cuda")
+    dpool = torch.from_numpy(pool).cuda()
+    for _ in range(2):   # the second call replays the captured graph
+        nw.nw_score_all_pairs(ctx, dpool, off, lens, (1, -1, -1), nw.NW_GRAPH, out)
+    ctx.sync()
+    assert ctx.graph_stats()["replays"] >= 1
+    mat = out.cpu().numpy()
+    iu, ju = np.triu_indices(n, 1)
+    want = np.array(oracle.score_many([(seqs[i], seqs[j]) for i, j in zip(iu.tolist(), ju.tolist())]), np.int32)
+    assert np.array_equal(mat[iu, ju], want)
+    assert np.array_equal(mat[ju, iu], want)
+    assert (np.diag(mat) == lens.astype(np.int32)).all()
+
+
+def test_scoring_where_the_diagonal_never_beats_two_gaps(ctx):
+    """match < 2*gap (here -3 < -2): W stays 0 and every alignment is all
+    gaps; the plain batch is exact against the oracle, and the certified
+    band, whose exit bound needs match >= 2*gap, refuses the scoring."""
+    import paper_2412_21103_gb300 as nw
+    sc = (-3, -5, -1)
+    pairs = _mixed_pairs(77, 30, [0, 1, 40, 300, 700])
+    pool, ao, al, bo, bl = _pairs_pool(pairs)
+    scores, cigars = nw.nw_align_batch(ctx, pool, ao, al, bo, bl, sc, nw.NW_CIGAR)
+    want = oracle.align_many(pairs, *sc)
+    for k, (s, ops) in enumerate(want):
+        assert scores[k] == s and cigars[k] == oracle.rle(ops), k
+    with pytest.raises(nw.NWError) as e:
+        nw.nw_align_batch(ctx, pool, ao, al, bo, bl, sc, nw.NW_LEARNED_BAND)
+    assert e.value.status == nw.NW_ERR_ARG
+    with pytest.raises(nw.NWError) as e:
+        nw.nw_align_batch_banded(ctx, pool, ao, al, bo, bl, [16] * len(pairs), sc, 0)
+    assert e.value.status == nw.NW_ERR_ARG
 
 
 def test_batch_device_io(ctx):

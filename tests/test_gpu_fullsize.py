@@ -3,10 +3,12 @@ launch configuration the benchmark times.
 
 Config 4: all 20,000 pairs of 2-20 kb through nw_align_batch(NW_CIGAR |
 NW_LEARNED_BAND) on device buffers, after training the band network on the
-GPU from the committed oracle labels.  Every score and CIGAR length equals
-the plain full-grid batch's; a seeded sample of 48 pairs (random, the
-longest, the largest length differences) equals the oracle's score and
-CIGAR.
+GPU from the committed oracle labels.  Every score and every CIGAR string
+(byte for byte) equals the plain full-grid batch's; at least 400 pairs equal
+the oracle's score and CIGAR: every pair the first banded round certified
+at the narrowest certified half-width of that round (where an unsound
+certificate would show first), the longest pairs, the largest length
+differences and a seeded random sample.
 
 Config 5: 2,000 requests of the serving stream (lengths 50-50,000, half with
 CIGAR) through the server with the learned band: every score equals the
@@ -82,21 +84,38 @@ def test_config4_full_size_learned_band(trained_ctx):
     s_band, c_band, l_band = run(nw.NW_CIGAR | nw.NW_LEARNED_BAND)
     st = nw.nw_ctx_band_stats(ctx)
     assert st["certified_round"][0] > 0 and st["certified_round"][1] > 0  # both rounds certify some pairs
-    s_full, _, l_full = run(nw.NW_CIGAR)
+    outcome = nw.nw_ctx_band_outcome(ctx)
+    s_full, c_full, l_full = run(nw.NW_CIGAR)
     assert np.array_equal(s_band, s_full)
     assert np.array_equal(l_band, l_full)
+    cb, cf = c_band.cpu().numpy(), c_full.cpu().numpy()
+    bad = [k for k in range(n)
+           if cb[int(coff[k]): int(coff[k]) + int(l_band[k])].tobytes()
+           != cf[int(coff[k]): int(coff[k]) + int(l_full[k])].tobytes()]
+    assert not bad, f"{len(bad)} CIGAR strings differ from the plain batch, first {bad[:5]}"
 
-    rs = seqgen.Stream(4242)
+    # oracle sample: the narrowest round-1 certificates, extremes, random
+    r1 = np.nonzero(outcome["round"] == 1)[0]
+    assert r1.size > 0
+    wmin = int(outcome["cert_width"][r1].min())
+    narrowest = r1[outcome["cert_width"][r1] == wmin]
     longest = np.argsort(-(al.astype(np.int64) * bl.astype(np.int64)))[:16]
     skewed = np.argsort(-np.abs(bl.astype(np.int64) - al.astype(np.int64)))[:16]
-    rand = rs.integers(0, n - 1, 16)
-    sample = sorted(set(int(k) for k in np.concatenate([longest, skewed, rand])))
+    sample = set(int(k) for k in np.concatenate([narrowest, longest, skewed]))
+    rs = seqgen.Stream(4242)
+    for k in rs.integers(0, n - 1, 4 * n):
+        if len(sample) >= 400:
+            break
+        sample.add(int(k))
+    sample = sorted(sample)
+    assert len(sample) >= 400
     want = oracle.align_many([(pairs[k].a, pairs[k].b) for k in sample])
-    cp = c_band.cpu().numpy()
     for k, (s, ops) in zip(sample, want):
         assert int(s_band[k]) == s, k
-        got = bytes(cp[int(coff[k]): int(coff[k]) + int(l_band[k])]).decode()
+        got = cb[int(coff[k]): int(coff[k]) + int(l_band[k])].tobytes().decode()
         assert got == oracle.rle(ops), k
+    print(f"config 4: {narrowest.size} pairs certified in round 1 at half-width {wmin}; "
+          f"{len(sample)} pairs checked against the oracle")
 
 
 def test_config5_two_thousand_requests(trained_ctx):

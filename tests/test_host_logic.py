@@ -1,6 +1,10 @@
 """Host arithmetic of the CUDA path that needs no GPU, against the oracle:
-the banded certificate's exit bound (reading 9 of the design notes; the
-oracle's `exit_bound` is pinned by brute force in test_oracle_pins)."""
+the banded certificate's exit bound -- a path that leaves the band of
+half-width w makes at least G gap moves, so it scores at most
+match*floor((m+n-G)/2) + gap*(m+n-2*floor((m+n-G)/2)) -- the certificate
+and the next round's width built on it, the learned start width and the
+straggler rule.  The oracle's `exit_bound` is pinned by brute force over
+every path in test_oracle_pins."""
 import numpy as np
 import pytest
 

@@ -133,3 +133,132 @@ def test_excursion_of_a_path():
     assert bm.excursion("D=I", 2, 2) == 1
     assert bm.excursion("III====", 7, 4) == 0      # n - m = -3: diagonals -3..0 allowed
     assert bm.excursion("DD==II", 4, 4) == 2
+
+
+# ------------------------------------------------ features: offsets != 0 ----
+ROTATION_BINS = {-32: 0, -31: 0, -20: 11, -7: 24, -1: 30, 1: 32, 5: 36, 13: 44, 31: 62, 32: 63}
+
+
+@pytest.mark.parametrize("k", sorted(ROTATION_BINS))
+def test_features_rotation_lands_in_the_bin_of_its_offset(k):
+    """B = the cyclic de Bruijn sequence rotated by k, A unrotated, m = n =
+    259 (so the expected diagonal is the main one).  Anchor i (0..255, one per
+    position) finds its 4-mer in B only at j = i + k (mod 256), so exactly the
+    256 - |k| anchors with 0 <= i + k <= 255 hit, all at offset +k; the other
+    occurrence lies 256 - |k| > W = 259 // 8 = 32 diagonals away, outside the
+    window.  Hand values of the bin floor((k + 32) * 64 / 65): k = 5 gives
+    floor(37 * 64 / 65) = floor(36.43) = 36, k = -7 gives floor(25 * 64 / 65)
+    = 24, and so on; a sign flip of the offset or a 2W denominator moves the
+    count to another bin."""
+    s = de_bruijn_4()
+    cyc = s[:256]
+    b = np.array([cyc[(j - k) % 256] for j in range(259)], np.uint8)
+    f = bm.features(s, b)
+    want = np.zeros(65)
+    want[ROTATION_BINS[k]] = np.log1p(256 - abs(k)) / np.log1p(256)
+    assert np.allclose(f, want, rtol=0, atol=1e-12)
+
+
+def test_features_expected_diagonal_rounds_the_length_slope():
+    """m = 5, n = 9 (delta = 4), A = ACGTG, B = TTTCGTGTT, worked by hand.
+    K = min(256, 5 - 3) = 2 anchors at i = floor(k * 1 / 1) = 0, 1 with
+    4-mers ACGT and CGTG; W = max(1, 9 // 8) = 1.  e(0) = 0 and e(1) =
+    round(4 / 5) = 1, so anchor 1 searches j in [1, 3]; CGTG sits in B at j =
+    3 only (B's 4-mers: TTTC TTCG TCGT CGTG GTGT TGTT), offset 3 - 1 - 1 = +1,
+    bin floor(2 * 64 / 3) = 42.  ACGT does not occur in B.  So f[42] =
+    log1p(1) / log1p(2) and f[64] = 4 / 9.  Flooring e(1) to 0 (window
+    [0, 2]) loses the hit; a sign flip puts it in bin 0."""
+    lut = {"A": 0, "C": 1, "G": 2, "T": 3}
+    a = np.array([lut[x] for x in "ACGTG"], np.uint8)
+    b = np.array([lut[x] for x in "TTTCGTGTT"], np.uint8)
+    want = np.zeros(65)
+    want[42] = np.log(2) / np.log(3)
+    want[64] = 4 / 9
+    assert np.allclose(bm.features(a, b), want, rtol=0, atol=1e-12)
+
+
+# -------------------------------------------------------- start width ------
+@pytest.mark.parametrize("y,m,n,want", [
+    (float(np.log(100.5)), 5000, 6000, 76),   # 0.75 * 100.5 = 75.375 -> 76
+    (float(np.log(13.0)), 5000, 5000, 10),    # 0.75 * 13 = 9.75 -> 10
+    (float(np.log(9.0)), 5000, 5000, 8),      # 6.75 -> 7, raised to the floor 8
+    (0.0, 5000, 5000, 8),                     # 0.75 -> 1 -> 8
+    (-50.0, 300, 200, 8),
+    (20.0, 3000, 7000, 7000),                 # e^20 * 0.75 far above max(m, n)
+    (800.0, 3000, 7000, 7000),                # e^800 overflows a double: still max(m, n)
+    (10.0, 5, 3, 5),                          # max(m, n) below the floor: max(m, n) wins
+    (-3.0, 5, 3, 5),
+])
+def test_start_width_hand_values(y, m, n, want):
+    assert bm.start_width(y, m, n) == want
+
+
+# ------------------------------------------- forward: BF16 placements ------
+def _index():
+    off, k = {}, 0
+    for name, size in bm.SIZES:
+        off[name] = k
+        k += size
+    return off
+
+
+def _hand_network():
+    """A network with two live units per layer, worked by hand in exact
+    binary fractions.  BF16 keeps 8 significant bits, so on [1, 2) it
+    rounds to multiples of 2^-7, ties to an even last bit.
+
+    x0 = 1 + 2^-7 + 2^-9           -> bf16 1 + 2^-7
+    W1[0][0] = 1 + 2^-9            -> bf16 1;  b1[0] = 2^-9 (FP32 master, not rounded)
+      a1[0] = (1 + 2^-7) + 2^-9     -> H1[0] = bf16 = 1 + 2^-7
+    W1[1][0] = -1                   -> a1[1] < 0, H1[1] = 0 (ReLU)
+    W2[0][0] = 1 + 2^-9 -> bf16 1;  W2[0][1] = 7 (meets H1[1] = 0);  b2[0] = 2^-9
+      a2[0] = (1 + 2^-7) + 2^-9     -> H2[0] = 1 + 2^-7
+    W2[1][0] = -1                   -> H2[1] = 0 (ReLU)
+    W3[0] = 1 + 2^-8 + 2^-10        -> bf16 1 + 2^-7 (nearer than 1);  W3[1] = 3;  b3 = 0
+      y = (1 + 2^-7)^2 = 1 + 2^-6 + 2^-14
+
+    Each rounding step matters: without bf16(x) a1[0] = 1 + 2^-7 + 2^-8 is a
+    tie that rounds to 1 + 2^-6; without bf16(W1) a1[0] = 1 + 2^-7 + 2^-8 +
+    2^-16 rounds up to 1 + 2^-6; without bf16 on H1 or H2 the value keeps its
+    2^-9; without bf16(W3) y gains W3's low bits; without either ReLU the
+    weights 7 and 3 meet negative values."""
+    off = _index()
+    F, H = bm.F, bm.H
+    p = np.zeros(bm.NPARAMS)
+    p[off["W1"] + 0 * F + 0] = 1 + 2 ** -9
+    p[off["b1"] + 0] = 2 ** -9
+    p[off["W1"] + 1 * F + 0] = -1.0
+    p[off["W2"] + 0 * H + 0] = 1 + 2 ** -9
+    p[off["W2"] + 0 * H + 1] = 7.0
+    p[off["b2"] + 0] = 2 ** -9
+    p[off["W2"] + 1 * H + 0] = -1.0
+    p[off["W3"] + 0] = 1 + 2 ** -8 + 2 ** -10
+    p[off["W3"] + 1] = 3.0
+    x = np.zeros((1, F))
+    x[0, 0] = 1 + 2 ** -7 + 2 ** -9
+    return p, x
+
+
+def test_forward_hand_network_rounds_at_every_stage():
+    p, x = _hand_network()
+    y, _ = bm.forward(p, x)
+    assert y[0] == 1 + 2 ** -6 + 2 ** -14
+
+
+def test_forward_parameter_layout_row_major():
+    """W1 is [128][65] and W2 [128][128], row = output unit.  Flat W1 index
+    65 + 1 is W1[1][1] (input 1 -> hidden unit 1) and flat W2 index 1 is
+    W2[0][1] (hidden unit 1 -> second-layer unit 0); with W3[0] = 3 and
+    input 1 = 2, y = 2 * 1 * 1 * 3 = 6.  Read as W1[65][128] the same flat
+    index is input 0 -> hidden unit 66, and with W2 transposed it is hidden
+    unit 0 -> unit 1: both meet zeros and give y = 0."""
+    off = _index()
+    F, H = bm.F, bm.H
+    p = np.zeros(bm.NPARAMS)
+    p[off["W1"] + 1 * F + 1] = 1.0      # hidden unit 1 <- input 1
+    p[off["W2"] + 0 * H + 1] = 1.0      # layer-2 unit 0 <- hidden unit 1
+    p[off["W3"] + 0] = 3.0
+    x = np.zeros((1, F))
+    x[0, 1] = 2.0
+    y, _ = bm.forward(p, x)
+    assert y[0] == 6.0
