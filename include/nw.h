@@ -368,6 +368,47 @@ int nw_band_model_train_step(nw_ctx *ctx, const float *feat, const float *target
 int nw_score_all_pairs(nw_ctx *ctx, const uint8_t *pool2b, const uint64_t *off, const uint32_t *len,
                        uint32_t nseq, nw_scoring sc, uint32_t flags, int32_t *out);
 
+/* Center-star multiple alignment of `nseq` sequences (the paper's Sec.
+ * 3.2): the scoring matrix of all n(n-1)/2 pairs (Eq. 2, as
+ * nw_score_all_pairs), the center = the sequence most similar to the rest
+ * (the largest sum of its scores against the other sequences; the diagonal
+ * is left out; the lowest index on ties), every sequence k aligned as the
+ * query against the center as the reference (as nw_align_batch with
+ * NW_CIGAR), then the pairwise alignments merged with the aligned center as
+ * the reference.  In the merge, G[p] = the most 'I' ops any alignment
+ * places before center base p (p = 0..len[center]; the last slot follows
+ * the last base); center base p lands in column p + G[0] + ... + G[p]; the
+ * I-bases of a row fill their slot from the left; 'D' leaves '-'.
+ * Inputs: pool2b, off, len as nw_score_all_pairs.  Outputs: *center (host);
+ * row_sums (nseq int64, may be NULL); scores (nseq int32: sequence k against
+ * the center); the CIGARs at cigar_pool + cigar_off[k] (cigar_off has
+ * nseq+1 entries, each capacity >= nw_cigar_bound(len[k], len[center]) --
+ * 2*(len[k] + max len) + 1 always suffices) with lengths cigar_len[k]; the
+ * merged rows (bytes 'A','C','G','T','-') at msa + k*msa_ld, NUL-terminated
+ * when msa_ld exceeds the column count, written to *msa_cols (host).  msa
+ * may be NULL (only the column count is returned; nw_msa_merge writes the
+ * rows later from the CIGARs); msa_ld below the column count returns
+ * NW_ERR_CIGAR_TRUNC with every other output written.  Buffers are device
+ * memory on the context's device unless NW_HOST_IO; NW_GRAPH applies to the
+ * scoring stage; NW_CIGAR_M is passed to the alignments.  Synchronises the
+ * context's stream (the center and the column count come to the host).
+ * 1..65535 sequences. */
+int nw_center_star(nw_ctx *ctx, const uint8_t *pool2b, const uint64_t *off, const uint32_t *len, uint32_t nseq,
+                   nw_scoring sc, uint32_t flags, uint32_t *center, int64_t *row_sums, int32_t *scores,
+                   char *cigar_pool, const uint64_t *cigar_off, uint64_t *cigar_len, char *msa, uint64_t msa_ld,
+                   uint64_t *msa_cols);
+/* The merge step of nw_center_star alone, from given alignments of every
+ * sequence k (query) against sequence `center` (reference): CIGAR k at
+ * cigar_pool + cigar_off[k] (nseq entries, host array), cigar_len[k] bytes.
+ * Each CIGAR must consume exactly len[k] bases of sequence k and
+ * len[center] of the center (NW_ERR_ARG from the next sync otherwise, and
+ * no row is written).  Writes *msa_cols and, unless msa is NULL, the rows as
+ * above (NW_ERR_CIGAR_TRUNC when msa_ld is below the column count).
+ * Device buffers unless NW_HOST_IO.  Synchronises the context's stream. */
+int nw_msa_merge(nw_ctx *ctx, const uint8_t *pool2b, const uint64_t *off, const uint32_t *len, uint32_t nseq,
+                 uint32_t center, uint32_t flags, const char *cigar_pool, const uint64_t *cigar_off,
+                 const uint64_t *cigar_len, char *msa, uint64_t msa_ld, uint64_t *msa_cols);
+
 /* ---------------------------------------------------------------- serving
  * Not in the paper (its Sec. 3.2 splits a fixed set of alignments over MPI
  * ranks): a continuous-batching server on one GPU.  The queue is device

@@ -99,6 +99,9 @@ def load():
         "nw_align_batch": (ctypes.c_int, [vp, vp, u64p, u32p, u64p, u32p, u32, Scoring, u32, vp, vp, u64p, vp]),
         "nw_score_all_pairs": (ctypes.c_int, [vp, vp, u64p, u32p, u32, Scoring, u32, vp]),
         "nw_peak_int": (ctypes.c_int, [vp, ctypes.c_int, u64, ctypes.POINTER(ctypes.c_double)]),
+        "nw_center_star": (ctypes.c_int, [vp, vp, u64p, u32p, u32, Scoring, u32, u32p, vp, vp, vp, u64p, vp, vp, u64,
+                                          u64p]),
+        "nw_msa_merge": (ctypes.c_int, [vp, vp, u64p, u32p, u32, u32, u32, vp, u64p, vp, vp, u64, u64p]),
         "nw_align_score_noalloc": (ctypes.c_int, [vp, u64, vp, u64, Scoring, vp, vp]),
         "nw_align_batch_banded": (ctypes.c_int, [vp, vp, u64p, u32p, u64p, u32p, u32, u32p, Scoring, u32, vp, vp,
                                                  u64p, vp]),
@@ -647,6 +650,83 @@ def nw_score_all_pairs(ctx: Context, pool2b, off, lens, scoring=DEFAULT_SCORING,
         return res
     _check(ctx, L.nw_score_all_pairs(ctx.handle, _ptr(pool2b), oop, llp, nseq, _sc(scoring), flags, _ptr(out)))
     return out
+
+
+def _center_cigar_offsets(lens) -> np.ndarray:
+    """CIGAR offsets for nw_center_star: 2*(len[k] + max len) + 1 bytes per
+    sequence (at least nw_cigar_bound against any center)."""
+    L = np.asarray(lens, np.uint64)
+    caps = np.uint64(2) * (L + (L.max() if L.size else np.uint64(0))) + np.uint64(1)
+    out = np.zeros(L.size + 1, np.uint64)
+    np.cumsum(caps, out=out[1:])
+    return out
+
+
+def nw_center_star(ctx: Context, pool2b, off, lens, scoring=DEFAULT_SCORING, flags: int = 0, row_sums=None,
+                   scores=None, cigar_pool=None, cigar_off=None, cigar_len=None, msa=None, msa_ld: int = 0):
+    """Center-star multiple alignment (Sec. 3.2).
+
+    Host mode (pool2b numpy): returns a dict with the center, the row sums,
+    each sequence's score and CIGAR against the center and the merged rows
+    (strings over 'ACGT-'); the rows come from nw_msa_merge once the column
+    count is known.  Device mode: writes into the given CUDA tensors
+    (row_sums int64[nseq] or None, scores int32[nseq], cigar_pool uint8,
+    cigar_len int64[nseq], msa uint8[nseq * msa_ld] or None) and returns
+    (center, msa_cols)."""
+    L = load()
+    nseq = len(lens)
+    oo, oop = _u64(off)
+    ll, llp = _u32(lens)
+    if cigar_off is None:
+        cigar_off = _center_cigar_offsets(ll)
+    co, cop = _u64(cigar_off)
+    center = ctypes.c_uint32(0)
+    cols = ctypes.c_uint64(0)
+    if _is_host(pool2b):
+        sums = np.zeros(max(nseq, 1), np.int64)
+        sc_out = np.zeros(max(nseq, 1), np.int32)
+        cpool = np.zeros(max(int(co[-1]), 1), np.uint8)
+        clen = np.zeros(max(nseq, 1), np.uint64)
+        rc = L.nw_center_star(ctx.handle, _ptr(pool2b), oop, llp, nseq, _sc(scoring), flags | NW_HOST_IO,
+                              ctypes.byref(center), _ptr(sums), _ptr(sc_out), _ptr(cpool), cop, _ptr(clen), None, 0,
+                              ctypes.byref(cols))
+        _check(ctx, rc)
+        ld = int(cols.value) + 1
+        rows = np.zeros(max(nseq * ld, 1), np.uint8)
+        c0, c0p = _u64(co[:nseq])
+        rc = L.nw_msa_merge(ctx.handle, _ptr(pool2b), oop, llp, nseq, center.value, NW_HOST_IO, _ptr(cpool), c0p,
+                            _ptr(clen), _ptr(rows), ld, ctypes.byref(cols))
+        _check(ctx, rc)
+        ncols = int(cols.value)
+        text = rows[: nseq * ld].reshape(nseq, ld)[:, :ncols] if nseq else rows[:0]
+        return {"center": int(center.value), "row_sums": sums[:nseq], "scores": sc_out[:nseq],
+                "cigars": _cigars(cpool, co, clen, nseq), "rows": [bytes(r).decode() for r in text],
+                "columns": ncols}
+    rc = L.nw_center_star(ctx.handle, _ptr(pool2b), oop, llp, nseq, _sc(scoring), flags, ctypes.byref(center),
+                          _ptr(row_sums), _ptr(scores), _ptr(cigar_pool), cop, _ptr(cigar_len), _ptr(msa), msa_ld,
+                          ctypes.byref(cols))
+    if rc == NW_ERR_CIGAR_TRUNC:
+        return int(center.value), int(cols.value), False
+    _check(ctx, rc)
+    return int(center.value), int(cols.value), True
+
+
+def nw_msa_merge(ctx: Context, pool2b, off, lens, center: int, cigar_pool, cigar_off, cigar_len, msa=None,
+                 msa_ld: int = 0, flags: int = 0) -> int:
+    """Merge given alignments against sequence `center` (the last stage of
+    nw_center_star); returns the column count.  Device tensors, or numpy
+    arrays with NW_HOST_IO."""
+    L = load()
+    oo, oop = _u64(off)
+    ll, llp = _u32(lens)
+    co, cop = _u64(np.asarray(cigar_off)[: len(lens)])
+    cols = ctypes.c_uint64(0)
+    if _is_host(pool2b):
+        flags |= NW_HOST_IO
+    rc = L.nw_msa_merge(ctx.handle, _ptr(pool2b), oop, llp, len(lens), center, flags, _ptr(cigar_pool), cop,
+                        _ptr(cigar_len), _ptr(msa), msa_ld, ctypes.byref(cols))
+    _check(ctx, rc)
+    return int(cols.value)
 
 
 def nw_align_score_noalloc(a2b, m: int, b2b, n: int, scoring=DEFAULT_SCORING, score=None, stream=None) -> int:
