@@ -11,10 +11,12 @@ also carries the plain full-matrix batch on the same pairs and the number of
 score and CIGAR mismatches between the two.
 
 Other workloads: pair32k (one 32,768 x 32,768 pair), pair1k (one 1,000 x
-1,000 pair), allpairs (512 sequences, all 130,816 pairwise scores), serve
-(Poisson request stream into the continuous-batching server).
+1,000 pair), allpairs (512 sequences, all 130,816 pairwise scores),
+centerstar (the center-star multiple alignment of the same 512 sequences),
+serve (Poisson request stream into the continuous-batching server).
 
-    python bench.py [--gpus N] [--steps K] [--warmup W] [--workload band|pair32k|pair1k|allpairs|serve]
+    python bench.py [--gpus N] [--steps K] [--warmup W]
+                    [--workload band|pair32k|pair1k|allpairs|centerstar|serve]
     python bench.py --impl reference ...   # the CPU oracle on the host cores
 
 Prints one JSON line.  The path does not shard: with --gpus N under
@@ -47,7 +49,7 @@ OPS_PER_CELL = 4             # algorithmic work of the textbook cell: s select, 
 W_OPS_PER_CELL = 3           # what the W-domain kernels issue for it: prmt + add-max + max
 PEAK_KINDS = (0, 2, 4)       # nw_peak_int kinds: DPX add-max, max, prmt (lane-ops/s each)
 CELL_KINDS = (5, 6, 7)       # nw_peak_int kinds: score-only cells in three instruction mixes (cells/s)
-STEPS_DEFAULT = {"pair32k": 100, "pair1k": 200, "allpairs": 20, "band": 3}
+STEPS_DEFAULT = {"pair32k": 100, "pair1k": 200, "allpairs": 20, "centerstar": 20, "band": 3}
 
 
 def code_only(text: str) -> str:
@@ -106,7 +108,8 @@ def parse():
                     help="timed steps (default per workload: pair32k 100, pair1k 200, allpairs 20, band 3)")
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--workload", default="band", choices=["band", "pair32k", "pair1k", "allpairs", "serve"])
+    ap.add_argument("--workload", default="band",
+                    choices=["band", "pair32k", "pair1k", "allpairs", "centerstar", "serve"])
     ap.add_argument("--rate", type=float, default=50000.0, help="serve: Poisson arrival rate (requests/s)")
     ap.add_argument("--duration", type=float, default=3.0, help="serve: seconds of arrivals")
     ap.add_argument("--serve-pool", type=int, default=1500, help="serve: distinct requests the stream cycles through")
@@ -163,6 +166,12 @@ def workload(name: str):
         return seqs, (f"all-vs-all scores of {nseq} mutants of one random 1,500-base root (lengths U{{500..1500}}, "
                       f"divergence U[0.05,0.30], 20% of mutations 1-bp indels), {nseq * (nseq - 1) // 2:,} pairs, int32 matrix "
                       "(seed 1003)")
+    if name == "centerstar":
+        nseq = WL_ARGS["nseq"]
+        seqs = seqgen.all_vs_all_family(1003, nseq=nseq)
+        return seqs, (f"center-star multiple alignment of {nseq} mutants of one random 1,500-base root (lengths "
+                      f"U{{500..1500}}, divergence U[0.05,0.30], 20% of mutations 1-bp indels; seed 1003): "
+                      f"{nseq * (nseq - 1) // 2:,} scored pairs, center, {nseq} alignments with CIGAR, merged rows")
     if name == "pair1k":
         p = seqgen.random_pair(1001, 1000, 1000)
         return p, "single pair 1,000 x 1,000 i.i.d. uniform ACGT, score + CIGAR (seed 1001)"
@@ -281,7 +290,7 @@ def run_reference(args):
     data, desc = workload(args.workload)
     import oracle
     oracle.build()
-    sample_fn = {"allpairs": allpairs_oracle_gcups,
+    sample_fn = {"allpairs": allpairs_oracle_gcups, "centerstar": allpairs_oracle_gcups,
                  "band": lambda d, budget_s: oracle_gcups_pairs([(p.a, p.b) for p in d[:400]], budget_s)}.get(
         args.workload, oracle_gcups)
     vals = []
@@ -371,6 +380,54 @@ class AllPairsWork:
 
     def result(self):
         return {"matrix_checksum": int(self.out.sum().item())}
+
+    def oracle_sample(self):
+        return allpairs_oracle_gcups(self.seqs)
+
+
+class CenterStarWork:
+    """Center-star multiple alignment (Sec. 3.2): scoring matrix, center,
+    alignments with the center, merged rows -- all on the device."""
+    dominant = "batch_score"
+
+    def __init__(self, nw, ctx, dev, name):
+        import torch
+        self.nw, self.ctx = nw, ctx
+        seqs, self.desc = workload(name)
+        self.seqs = seqs
+        pool, off, lens = nw.pool_of(seqs)
+        self.pool_host = torch.from_numpy(pool).pin_memory().numpy()
+        self.off, self.lens = off, lens
+        self.pool = torch.from_numpy(pool).to(dev)
+        n = len(seqs)
+        self.coff = nw._center_cigar_offsets(lens)
+        self.sums = torch.zeros(n, dtype=torch.int64, device=dev)
+        self.scores = torch.zeros(n, dtype=torch.int32, device=dev)
+        self.cpool = torch.zeros(int(self.coff[-1]), dtype=torch.uint8, device=dev)
+        self.clen = torch.zeros(n, dtype=torch.int64, device=dev)
+        self.ld = 2 * int(lens.max()) + 64
+        self.msa = torch.zeros(n * self.ld, dtype=torch.uint8, device=dev)
+        L = lens.astype(np.float64)
+        self.pair_cells = int((np.outer(L, L).sum() - (L * L).sum()) / 2)
+        self.center, self.cols, ok = nw.nw_center_star(ctx, self.pool, off, lens, SCORING, 0, self.sums, self.scores,
+                                                       self.cpool, self.coff, self.clen, self.msa, self.ld)
+        assert ok, "row stride below the merged column count"
+        self.cells = self.pair_cells + int((L * L[self.center]).sum())
+        self.config = {"nseq": n, "pairs": n * (n - 1) // 2, "center": self.center, "msa_columns": self.cols}
+
+    def step(self):
+        # the scoring stage replays the CUDA graph captured on the first call
+        self.nw.nw_center_star(self.ctx, self.pool, self.off, self.lens, SCORING, self.nw.NW_GRAPH, self.sums,
+                               self.scores, self.cpool, self.coff, self.clen, self.msa, self.ld)
+
+    def e2e(self):
+        res = self.nw.nw_center_star(self.ctx, self.pool_host, self.off, self.lens, SCORING)
+        out = res["scores"].nbytes + res["row_sums"].nbytes + sum(len(c) for c in res["cigars"]) + \
+            sum(len(r) for r in res["rows"])
+        return self.pool_host.nbytes, out
+
+    def result(self):
+        return {"score_checksum": int(self.scores.sum().item())}
 
     def oracle_sample(self):
         return allpairs_oracle_gcups(self.seqs)
@@ -598,7 +655,8 @@ def run_ours(args):
     stream = torch.cuda.current_stream(dev)
     ctx = nw.Context(local, stream)
     ctx.set_autotune(True)  # the warm-up steps time the candidate shapes
-    work = {"allpairs": AllPairsWork, "band": BandWork}.get(args.workload, PairWork)(nw, ctx, dev, args.workload)
+    work = {"allpairs": AllPairsWork, "band": BandWork, "centerstar": CenterStarWork}.get(args.workload, PairWork)(
+        nw, ctx, dev, args.workload)
     flush = torch.empty(L2_FLUSH_BYTES, dtype=torch.uint8, device=dev)
 
     # clock samples: nvidia-smi starts now (it takes a while to print its

@@ -269,6 +269,19 @@ int nw_align_batch(nw_ctx *ctx, const uint8_t *pool2b,
                    nw_scoring sc, uint32_t flags, int32_t *scores,
                    char *cigar_pool, const uint64_t *cigar_off, uint64_t *cigar_len);
 
+/* Partition of a pair list over `nranks` ranks (no GPU needed): the
+ * paper's Sec. 3.2 divides the alignments over MPI ranks and gathers the
+ * results; here each rank of a multi-GPU job aligns its share with
+ * nw_align_batch and the results are gathered.  Longest processing time
+ * first: pairs sorted by cells a_len*b_len, largest first (index order
+ * among equals), each given to the rank with the fewest cells so far (the
+ * lowest rank on ties); so the largest load is at most the mean load plus
+ * the largest pair.  rank_of[k] receives pair k's rank; load (optional,
+ * nranks entries) each rank's cells.  NW_ERR_ARG for nranks = 0 or null
+ * arrays. */
+int nw_shard_pairs(const uint32_t *a_len, const uint32_t *b_len, uint32_t npairs, uint32_t nranks, uint32_t *rank_of,
+                   uint64_t *load);
+
 /* The certified band with explicit starting half-widths (host array
  * band_w, one per pair): each pair is first aligned in the band of diagonals
  * d = j - i in [min(0,n-m) - w, max(0,n-m) + w].  The banded score S_b is

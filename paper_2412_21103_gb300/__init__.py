@@ -117,6 +117,7 @@ def load():
         "nw_band_certifies": (ctypes.c_int, [u64, u64, u64, ctypes.c_int32, Scoring, u32]),
         "nw_band_start_width": (u32, [ctypes.c_float, u64, u64]),
         "nw_route_stragglers": (ctypes.c_int64, [vp, vp, u32, vp]),
+        "nw_shard_pairs": (ctypes.c_int, [u32p, u32p, u32, u32, u32p, u64p]),
         "nw_band_next_width": (ctypes.c_int64, [u64, u64, u64, ctypes.c_int32, Scoring, u32]),
         "nw_band_model_save": (ctypes.c_int, [vp, ctypes.c_char_p]),
         "nw_band_model_load": (ctypes.c_int, [vp, ctypes.c_char_p]),

@@ -958,6 +958,28 @@ extern "C" int64_t nw_route_stragglers(const double *warp_cells, const double *f
     return (int64_t)r.size();
 }
 
+extern "C" int nw_shard_pairs(const uint32_t *a_len, const uint32_t *b_len, uint32_t npairs, uint32_t nranks,
+                              uint32_t *rank_of, uint64_t *load) {
+    if (nranks == 0 || (npairs && (!a_len || !b_len || !rank_of))) return NW_ERR_ARG;
+    // longest processing time first: pairs by cells, largest first (index
+    // order among equals), each to the least loaded rank (lowest on ties)
+    std::vector<uint32_t> order(npairs);
+    std::iota(order.begin(), order.end(), 0u);
+    auto cells = [&](uint32_t k) { return (uint64_t)a_len[k] * b_len[k]; };
+    std::stable_sort(order.begin(), order.end(), [&](uint32_t x, uint32_t y) { return cells(x) > cells(y); });
+    std::vector<uint64_t> ld(nranks, 0);
+    for (uint32_t k : order) {
+        uint32_t best = 0;
+        for (uint32_t r = 1; r < nranks; ++r)
+            if (ld[r] < ld[best]) best = r;
+        rank_of[k] = best;
+        ld[best] += cells(k);
+    }
+    if (load)
+        for (uint32_t r = 0; r < nranks; ++r) load[r] = ld[r];
+    return NW_OK;
+}
+
 extern "C" int nw_ctx_band_stats(nw_ctx *ctx, uint64_t *out, int cap) {
     if (!ctx) return -NW_ERR_ARG;
     for (int k = 0; k < cap && k < 8; ++k) out[k] = ctx->band_stats[k];
