@@ -17,6 +17,10 @@ Functions whose result the paper or mathematics pins (see ``tests/``):
                            brute force over in-band paths; the bound U is
                            checked against brute force over out-of-band paths.
   exit_bound (U0)       -- brute force over every path that leaves the band.
+  local_*               -- local alignment (Smith-Waterman, not in the paper):
+                           brute force over every pair of substrings and every
+                           alignment, longest common substring special case,
+                           invariants.
 """
 from __future__ import annotations
 
@@ -63,7 +67,12 @@ def _load():
             lib.nwo_banded.argtypes = [u8p, i64, u8p, i64, i32, i32, i32, i64, i32p, i32p, i32p]
             i64p = ctypes.POINTER(ctypes.c_int64)
             lib.nwo_region.argtypes = [u8p, i64, u8p, i64, i32, i32, i32, i64p, i64p, i64, i64, i32p]
-            for f in (lib.nwo_fill, lib.nwo_align, lib.nwo_score, lib.nwo_banded, lib.nwo_region):
+            lib.nwo_local_fill.argtypes = [u8p, i64, u8p, i64, i32, i32, i32, i32p]
+            lib.nwo_local_align.argtypes = [u8p, i64, u8p, i64, i32, i32, i32, i32p, i64p, ctypes.c_char_p,
+                                            ctypes.POINTER(i64)]
+            lib.nwo_local_score.argtypes = [u8p, i64, u8p, i64, i32, i32, i32, i32p]
+            for f in (lib.nwo_fill, lib.nwo_align, lib.nwo_score, lib.nwo_banded, lib.nwo_region, lib.nwo_local_fill,
+                      lib.nwo_local_align, lib.nwo_local_score):
                 f.restype = ctypes.c_int
             _lib = lib
     return _lib
@@ -212,6 +221,58 @@ def next_width(m: int, n: int, w: int, banded_score: int, want_cigar: bool, matc
     while wp <= max(m, n) and not certifies(m, n, wp, banded_score, want_cigar, match, gap):
         wp += 1
     return max(2 * w, wp)
+
+
+def local_fill(a, b, match: int = 1, mismatch: int = -1, gap: int = -1) -> np.ndarray:
+    """The full (m+1) x (n+1) local-alignment grid H (floor 0)."""
+    a, b = _codes(a), _codes(b)
+    H = np.empty((a.size + 1, b.size + 1), dtype=np.int32)
+    pa, ka = _ptr(a)
+    pb, kb = _ptr(b)
+    rc = _load().nwo_local_fill(pa, a.size, pb, b.size, match, mismatch, gap,
+                                H.ctypes.data_as(ctypes.POINTER(ctypes.c_int32)))
+    assert rc == 0, rc
+    return H
+
+
+def local_align(a, b, match: int = 1, mismatch: int = -1, gap: int = -1):
+    """(score, (i_start, j_start, i_end, j_end), op string): the local
+    alignment covers A[i_start:i_end] and B[j_start:j_end]."""
+    a, b = _codes(a), _codes(b)
+    out = ctypes.c_int32(0)
+    ends = (ctypes.c_int64 * 4)()
+    nops = ctypes.c_int64(0)
+    buf = ctypes.create_string_buffer(a.size + b.size + 1)
+    pa, ka = _ptr(a)
+    pb, kb = _ptr(b)
+    rc = _load().nwo_local_align(pa, a.size, pb, b.size, match, mismatch, gap, ctypes.byref(out), ends, buf,
+                                 ctypes.byref(nops))
+    if rc == -2:
+        raise MemoryError("oracle grid does not fit in host memory")
+    assert rc == 0, rc
+    return int(out.value), tuple(int(x) for x in ends), buf.raw[: nops.value].decode()
+
+
+def local_score(a, b, match: int = 1, mismatch: int = -1, gap: int = -1) -> int:
+    a, b = _codes(a), _codes(b)
+    out = ctypes.c_int32(0)
+    pa, ka = _ptr(a)
+    pb, kb = _ptr(b)
+    rc = _load().nwo_local_score(pa, a.size, pb, b.size, match, mismatch, gap, ctypes.byref(out))
+    assert rc == 0, rc
+    return int(out.value)
+
+
+def local_align_many(pairs, match: int = 1, mismatch: int = -1, gap: int = -1, threads: int | None = None):
+    threads = threads or os.cpu_count() or 1
+    with ThreadPoolExecutor(threads) as ex:
+        return list(ex.map(lambda p: local_align(p[0], p[1], match, mismatch, gap), pairs))
+
+
+def local_score_many(pairs, match: int = 1, mismatch: int = -1, gap: int = -1, threads: int | None = None):
+    threads = threads or os.cpu_count() or 1
+    with ThreadPoolExecutor(threads) as ex:
+        return list(ex.map(lambda p: local_score(p[0], p[1], match, mismatch, gap), pairs))
 
 
 def rle(ops: str) -> str:

@@ -254,3 +254,98 @@ int nwo_banded(const uint8_t *a, int64_t m, const uint8_t *b, int64_t n,
     if (!Hout) free(H);
     return NWO_OK;
 }
+
+/* ------------------------------------------------------------------------
+ * Local alignment (Smith-Waterman; not in the paper, the same grid with a
+ * floor of 0: an alignment may start and end anywhere).
+ *
+ *   H(i,0) = H(0,j) = 0
+ *   H(i,j) = max( 0, H(i-1,j-1) + s(A_i,B_j), H(i-1,j) + gap, H(i,j-1) + gap )
+ *
+ * The score is the largest H(i,j).  The alignment ends at the first cell in
+ * row-major order (smallest i, then smallest j) holding it, and is traced
+ * back from there with the priority diagonal > vertical > horizontal of the
+ * global walk, stopping at the first cell whose H is 0 (the alignment's
+ * start).  A score of 0 gives the empty alignment at (0,0).  Writes the
+ * score, the end cell (i_end, j_end) and the start cell (i_start, j_start)
+ * -- the alignment covers A[i_start .. i_end) and B[j_start .. j_end),
+ * 0-based -- and the ops in forward order.
+ * ---------------------------------------------------------------------- */
+static int32_t max4(int32_t a, int32_t b, int32_t c, int32_t d) { return max2(max2(a, b), max2(c, d)); }
+
+int nwo_local_fill(const uint8_t *a, int64_t m, const uint8_t *b, int64_t n,
+                   int32_t match, int32_t mismatch, int32_t gap, int32_t *H) {
+    if (m < 0 || n < 0 || !H) return NWO_ERR_ARG;
+    const int64_t w = n + 1;
+    for (int64_t j = 0; j <= n; ++j) H[j] = 0;
+    for (int64_t i = 1; i <= m; ++i) {
+        H[i * w] = 0;
+        for (int64_t j = 1; j <= n; ++j) {
+            int32_t diag = H[(i - 1) * w + (j - 1)] + subst(a[i - 1], b[j - 1], match, mismatch);
+            int32_t up = H[(i - 1) * w + j] + gap;
+            int32_t left = H[i * w + (j - 1)] + gap;
+            H[i * w + j] = max4(0, diag, up, left);
+        }
+    }
+    return NWO_OK;
+}
+
+int nwo_local_align(const uint8_t *a, int64_t m, const uint8_t *b, int64_t n,
+                    int32_t match, int32_t mismatch, int32_t gap, int32_t *score, int64_t *ends,
+                    char *ops, int64_t *nops) {
+    if (m < 0 || n < 0 || !score || !ends || !ops || !nops) return NWO_ERR_ARG;
+    const int64_t w = n + 1;
+    int32_t *H = (int32_t *)malloc((size_t)(m + 1) * (size_t)w * sizeof(int32_t));
+    if (!H) return NWO_ERR_OOM;
+    nwo_local_fill(a, m, b, n, match, mismatch, gap, H);
+    int64_t bi = 0, bj = 0;
+    for (int64_t i = 0; i <= m; ++i)           /* row-major: the first maximum */
+        for (int64_t j = 0; j <= n; ++j)
+            if (H[i * w + j] > H[bi * w + bj]) { bi = i; bj = j; }
+    int64_t i = bi, j = bj, k = 0;
+    while (H[i * w + j] > 0) {
+        int32_t here = H[i * w + j];
+        if (here == H[(i - 1) * w + (j - 1)] + subst(a[i - 1], b[j - 1], match, mismatch)) {
+            ops[k++] = (a[i - 1] == b[j - 1]) ? '=' : 'X';
+            --i; --j;
+        } else if (here == H[(i - 1) * w + j] + gap) {
+            ops[k++] = 'I';
+            --i;
+        } else {
+            ops[k++] = 'D';
+            --j;
+        }
+    }
+    for (int64_t x = 0, y = k - 1; x < y; ++x, --y) {
+        char t = ops[x]; ops[x] = ops[y]; ops[y] = t;
+    }
+    *nops = k;
+    *score = H[bi * w + bj];
+    ends[0] = i; ends[1] = j; ends[2] = bi; ends[3] = bj;
+    free(H);
+    return NWO_OK;
+}
+
+/* Local score only, two rolling rows. */
+int nwo_local_score(const uint8_t *a, int64_t m, const uint8_t *b, int64_t n,
+                    int32_t match, int32_t mismatch, int32_t gap, int32_t *score) {
+    if (m < 0 || n < 0 || !score) return NWO_ERR_ARG;
+    int32_t *prev = (int32_t *)calloc((size_t)(n + 1), sizeof(int32_t));
+    int32_t *cur = (int32_t *)calloc((size_t)(n + 1), sizeof(int32_t));
+    if (!prev || !cur) { free(prev); free(cur); return NWO_ERR_OOM; }
+    int32_t best = 0;
+    for (int64_t i = 1; i <= m; ++i) {
+        cur[0] = 0;
+        for (int64_t j = 1; j <= n; ++j) {
+            int32_t diag = prev[j - 1] + subst(a[i - 1], b[j - 1], match, mismatch);
+            int32_t up = prev[j] + gap;
+            int32_t left = cur[j - 1] + gap;
+            cur[j] = max4(0, diag, up, left);
+            best = max2(best, cur[j]);
+        }
+        int32_t *t = prev; prev = cur; cur = t;
+    }
+    *score = best;
+    free(prev); free(cur);
+    return NWO_OK;
+}
