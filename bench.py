@@ -13,10 +13,10 @@ score and CIGAR mismatches between the two.
 Other workloads: pair32k (one 32,768 x 32,768 pair), pair1k (one 1,000 x
 1,000 pair), allpairs (512 sequences, all 130,816 pairwise scores),
 centerstar (the center-star multiple alignment of the same 512 sequences),
-serve (Poisson request stream into the continuous-batching server).
+local (local alignment of 4,000 query/reference pairs), serve (Poisson request stream into the continuous-batching server).
 
     python bench.py [--gpus N] [--steps K] [--warmup W]
-                    [--workload band|pair32k|pair1k|allpairs|centerstar|serve]
+                    [--workload band|pair32k|pair1k|allpairs|centerstar|local|serve]
     python bench.py --impl reference ...   # the CPU oracle on the host cores
 
 Prints one JSON line.  The path does not shard: with --gpus N under
@@ -49,7 +49,7 @@ OPS_PER_CELL = 4             # algorithmic work of the textbook cell: s select, 
 W_OPS_PER_CELL = 3           # what the W-domain kernels issue for it: prmt + add-max + max
 PEAK_KINDS = (0, 2, 4)       # nw_peak_int kinds: DPX add-max, max, prmt (lane-ops/s each)
 CELL_KINDS = (5, 6, 7)       # nw_peak_int kinds: score-only cells in three instruction mixes (cells/s)
-STEPS_DEFAULT = {"pair32k": 100, "pair1k": 200, "allpairs": 20, "centerstar": 20, "band": 3}
+STEPS_DEFAULT = {"pair32k": 100, "pair1k": 200, "allpairs": 20, "centerstar": 20, "local": 10, "band": 3}
 
 
 def code_only(text: str) -> str:
@@ -109,7 +109,7 @@ def parse():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="band",
-                    choices=["band", "pair32k", "pair1k", "allpairs", "centerstar", "serve"])
+                    choices=["band", "pair32k", "pair1k", "allpairs", "centerstar", "local", "serve"])
     ap.add_argument("--rate", type=float, default=50000.0, help="serve: Poisson arrival rate (requests/s)")
     ap.add_argument("--duration", type=float, default=3.0, help="serve: seconds of arrivals")
     ap.add_argument("--serve-pool", type=int, default=1500, help="serve: distinct requests the stream cycles through")
@@ -172,6 +172,12 @@ def workload(name: str):
         return seqs, (f"center-star multiple alignment of {nseq} mutants of one random 1,500-base root (lengths "
                       f"U{{500..1500}}, divergence U[0.05,0.30], 20% of mutations 1-bp indels; seed 1003): "
                       f"{nseq * (nseq - 1) // 2:,} scored pairs, center, {nseq} alignments with CIGAR, merged rows")
+    if name == "local":
+        pairs = seqgen.local_pairs(1006, npairs=4000)
+        return pairs, ("local alignment (Smith-Waterman), 4,000 pairs: a reference of U[2,000, 10,000] random bases "
+                       "against a query made of a mutated window of it (U[200, 2,000] bases, divergence U[0.01,0.20], "
+                       "geometric indels) between random flanks of up to 500 bases (seed 1006); score, start, end "
+                       "and CIGAR")
     if name == "pair1k":
         p = seqgen.random_pair(1001, 1000, 1000)
         return p, "single pair 1,000 x 1,000 i.i.d. uniform ACGT, score + CIGAR (seed 1001)"
@@ -291,6 +297,7 @@ def run_reference(args):
     import oracle
     oracle.build()
     sample_fn = {"allpairs": allpairs_oracle_gcups, "centerstar": allpairs_oracle_gcups,
+                 "local": lambda d, budget_s: local_oracle_gcups([(p.a, p.b) for p in d[:400]], budget_s),
                  "band": lambda d, budget_s: oracle_gcups_pairs([(p.a, p.b) for p in d[:400]], budget_s)}.get(
         args.workload, oracle_gcups)
     vals = []
@@ -383,6 +390,64 @@ class AllPairsWork:
 
     def oracle_sample(self):
         return allpairs_oracle_gcups(self.seqs)
+
+
+class LocalWork:
+    """Local alignment of many pairs (score, start, end, CIGAR)."""
+    dominant = "local_fill_ptr"
+
+    def __init__(self, nw, ctx, dev, name):
+        import torch
+        self.nw, self.ctx = nw, ctx
+        pairs, self.desc = workload(name)
+        self.pairs = pairs
+        seqs = []
+        for p in pairs:
+            seqs += [p.a, p.b]
+        pool, off, lens = nw.pool_of(seqs)
+        self.pool_host = torch.from_numpy(pool).pin_memory().numpy()
+        self.pool = torch.from_numpy(pool).to(dev)
+        self.ao, self.al, self.bo, self.bl = off[0::2], lens[0::2], off[1::2], lens[1::2]
+        n = len(pairs)
+        self.coff = nw._cigar_offsets(self.al, self.bl)
+        self.scores = torch.zeros(n, dtype=torch.int32, device=dev)
+        self.ends = torch.zeros((n, 4), dtype=torch.int32, device=dev)
+        self.cpool = torch.zeros(int(self.coff[-1]), dtype=torch.uint8, device=dev)
+        self.clen = torch.zeros(n, dtype=torch.int64, device=dev)
+        self.cells = int(sum(int(x) * int(y) for x, y in zip(self.al, self.bl)))
+        self.config = {"npairs": n}
+
+    def step(self):
+        self.nw.nw_local_align_batch(self.ctx, self.pool, self.ao, self.al, self.bo, self.bl, SCORING,
+                                     self.nw.NW_CIGAR, self.scores, self.ends, self.cpool, self.coff, self.clen)
+
+    def e2e(self):
+        sc, ends, cig = self.nw.nw_local_align_batch(self.ctx, self.pool_host, self.ao, self.al, self.bo, self.bl,
+                                                     SCORING, self.nw.NW_CIGAR)
+        return self.pool_host.nbytes, sc.nbytes + ends.nbytes + sum(len(c) for c in cig) + 8 * len(cig)
+
+    def result(self):
+        return {"score_checksum": int(self.scores.sum().item())}
+
+    def oracle_sample(self):
+        return local_oracle_gcups([(p.a, p.b) for p in self.pairs[:400]])
+
+
+def local_oracle_gcups(pairs, budget_s: float = 12.0):
+    """The CPU oracle, as it stands, on local alignments (score, ends and
+    traceback) of pairs of the workload, on all host threads."""
+    import oracle
+    threads = len(os.sched_getaffinity(0))
+    t0 = time.perf_counter()
+    done, cells = 0, 0
+    while time.perf_counter() - t0 < budget_s and done < len(pairs):
+        chunk = pairs[done: done + threads]
+        oracle.local_align_many(chunk, *SCORING, threads=threads)
+        cells += sum(a.size * b.size for a, b in chunk)
+        done += len(chunk)
+    dt = time.perf_counter() - t0
+    return cells / dt / 1e9, threads, f"{done} pairs of the workload, local score + traceback ({cells:.3g} cells, " \
+                                      f"{dt:.1f} s)"
 
 
 class CenterStarWork:
@@ -655,7 +720,8 @@ def run_ours(args):
     stream = torch.cuda.current_stream(dev)
     ctx = nw.Context(local, stream)
     ctx.set_autotune(True)  # the warm-up steps time the candidate shapes
-    work = {"allpairs": AllPairsWork, "band": BandWork, "centerstar": CenterStarWork}.get(args.workload, PairWork)(
+    work = {"allpairs": AllPairsWork, "band": BandWork, "centerstar": CenterStarWork,
+            "local": LocalWork}.get(args.workload, PairWork)(
         nw, ctx, dev, args.workload)
     flush = torch.empty(L2_FLUSH_BYTES, dtype=torch.uint8, device=dev)
 

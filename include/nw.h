@@ -269,6 +269,31 @@ int nw_align_batch(nw_ctx *ctx, const uint8_t *pool2b,
                    nw_scoring sc, uint32_t flags, int32_t *scores,
                    char *cigar_pool, const uint64_t *cigar_off, uint64_t *cigar_len);
 
+/* Local alignment of many pairs (Smith-Waterman; not in the paper, which
+ * aligns globally): the grid of Sec. 2.3 with a floor of 0,
+ *     H(i,0) = H(0,j) = 0,
+ *     H(i,j) = max(0, H(i-1,j-1) + s(A_i,B_j), H(i-1,j) + gap, H(i,j-1) + gap),
+ * so the best alignment of any substring of A with any substring of B.
+ * scores[k] = the largest H(i,j) of pair k.  The alignment ends at the
+ * first cell in row-major order (smallest i, then smallest j) holding that
+ * value and is walked back with the priority diagonal > vertical >
+ * horizontal of nw_align until the first cell whose H is 0, its start; a
+ * score of 0 is the empty alignment at (0,0).  ends (4 entries per pair,
+ * may be NULL without NW_CIGAR): i_start, j_start, i_end, j_end -- the
+ * alignment covers A[i_start .. i_end) and B[j_start .. j_end), 0-based;
+ * without NW_CIGAR the start is not computed and reads 0xFFFFFFFF.  With
+ * NW_CIGAR (ends then required) pair k's CIGAR of the aligned part goes to
+ * cigar_pool + cigar_off[k] as in nw_align_batch (capacity at least
+ * nw_cigar_bound).  Pool, scores, ends and CIGAR buffers are device memory
+ * unless NW_HOST_IO; metadata arrays are host arrays.  Scoring as nw_align,
+ * with max(match, 0) * min(m, n) below 2^29; a pair whose one-warp sweep
+ * would exceed 2^31 stripe steps (about m*n/256 >= 2^31) is
+ * NW_ERR_UNSUPPORTED. */
+int nw_local_align_batch(nw_ctx *ctx, const uint8_t *pool2b, const uint64_t *a_off, const uint32_t *a_len,
+                         const uint64_t *b_off, const uint32_t *b_len, uint32_t npairs, nw_scoring sc,
+                         uint32_t flags, int32_t *scores, uint32_t *ends, char *cigar_pool,
+                         const uint64_t *cigar_off, uint64_t *cigar_len);
+
 /* Partition of a pair list over `nranks` ranks (no GPU needed): the
  * paper's Sec. 3.2 divides the alignments over MPI ranks and gathers the
  * results; here each rank of a multi-GPU job aligns its share with

@@ -118,6 +118,8 @@ def load():
         "nw_band_start_width": (u32, [ctypes.c_float, u64, u64]),
         "nw_route_stragglers": (ctypes.c_int64, [vp, vp, u32, vp]),
         "nw_shard_pairs": (ctypes.c_int, [u32p, u32p, u32, u32, u32p, u64p]),
+        "nw_local_align_batch": (ctypes.c_int, [vp, vp, u64p, u32p, u64p, u32p, u32, Scoring, u32, vp, vp, vp, u64p,
+                                                vp]),
         "nw_band_next_width": (ctypes.c_int64, [u64, u64, u64, ctypes.c_int32, Scoring, u32]),
         "nw_band_model_save": (ctypes.c_int, [vp, ctypes.c_char_p]),
         "nw_band_model_load": (ctypes.c_int, [vp, ctypes.c_char_p]),
@@ -371,6 +373,39 @@ def nw_align_batch(ctx: Context, pool2b, a_off, a_len, b_off, b_len, scoring=DEF
                           _ptr(cigar_pool) if want else None, cop, _ptr(cigar_len) if want else None)
     _check(ctx, rc)
     return scores, cigar_pool, cigar_len
+
+
+def nw_local_align_batch(ctx: Context, pool2b, a_off, a_len, b_off, b_len, scoring=DEFAULT_SCORING, flags: int = 0,
+                         scores=None, ends=None, cigar_pool=None, cigar_off=None, cigar_len=None):
+    """Local alignment (Smith-Waterman) of many pairs.  Host mode (pool2b
+    numpy) returns (scores, ends (npairs, 4): i_start, j_start, i_end, j_end,
+    CIGARs or None); device mode writes into the given tensors."""
+    L = load()
+    npairs = len(a_len)
+    ao, aop = _u64(a_off)
+    al, alp = _u32(a_len)
+    bo, bop = _u64(b_off)
+    bl, blp = _u32(b_len)
+    want = bool(flags & NW_CIGAR)
+    if cigar_off is None and want:
+        cigar_off = _cigar_offsets(al, bl)
+    co, cop = _u64(cigar_off) if want else (None, None)
+    if _is_host(pool2b):
+        flags |= NW_HOST_IO
+        sc_out = np.zeros(max(npairs, 1), np.int32)
+        e_out = np.zeros((max(npairs, 1), 4), np.uint32)
+        cpool = np.zeros(max(int(co[-1]) if want else 1, 1), np.uint8)
+        clen = np.zeros(max(npairs, 1), np.uint64)
+        rc = L.nw_local_align_batch(ctx.handle, _ptr(pool2b), aop, alp, bop, blp, npairs, _sc(scoring), flags,
+                                    _ptr(sc_out), _ptr(e_out), _ptr(cpool) if want else None, cop,
+                                    _ptr(clen) if want else None)
+        _check(ctx, rc)
+        return sc_out[:npairs], e_out[:npairs], (_cigars(cpool, co, clen, npairs) if want else None)
+    rc = L.nw_local_align_batch(ctx.handle, _ptr(pool2b), aop, alp, bop, blp, npairs, _sc(scoring), flags,
+                                _ptr(scores), _ptr(ends), _ptr(cigar_pool) if want else None, cop,
+                                _ptr(cigar_len) if want else None)
+    _check(ctx, rc)
+    return scores, ends, cigar_len
 
 
 def nw_align_batch_banded(ctx: Context, pool2b, a_off, a_len, b_off, b_len, band_w, scoring=DEFAULT_SCORING,

@@ -288,6 +288,8 @@ struct TraceTask {
     uint32_t s_lo;         // first stripe whose words `ptr` holds (0: all of them)
     uint32_t *state;       // null: walk from (m, n) to the end; else a walk resumed and
                            // paused in device memory: {i, j, k lo, k hi, done}
+    const uint32_t *origin;  // null: the moves start at (0, 0); else at (origin[0], origin[1])
+                             // (a local alignment's start cell, read by the CIGAR assembly)
 };
 constexpr int32_t kNoBand = INT32_MIN;
 // Traceback + CIGAR for `ntasks` tasks: `host` describes them on the host

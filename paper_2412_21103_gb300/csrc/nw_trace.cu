@@ -473,7 +473,8 @@ __global__ void __launch_bounds__(kFinThreads) k_finish(TraceTask one, const Tra
     __shared__ char first_op[kFinThreads + 1];
     const uint64_t L = *p.nmoves;
     const int tid = threadIdx.x;
-    uint64_t ci = 0, cj = 0;   // bases of A / B consumed before this chunk
+    // bases of A / B consumed before this chunk (from the start cell)
+    uint64_t ci = p.origin ? p.origin[0] : 0u, cj = p.origin ? p.origin[1] : 0u;
     long long last_end = -1;   // forward position of the last run end so far
     uint64_t out = 0;          // chars written so far
     const uint64_t CH = (uint64_t)kFinThreads * kFinPer;

@@ -276,3 +276,26 @@ def serving_stream(seed: int, rate: float = 50000.0, duration: float = 60.0, lmi
         b, tr = mutate_distinct(a, child, delta, indel_mean=3.0)
         yield Request(t, Pair(a, b, tr), bool(u[3] < 0.5))
         k += 1
+
+
+def local_pairs(seed: int, npairs: int = 4000, ref_min: int = 2000, ref_max: int = 10000, win_min: int = 200,
+                win_max: int = 2000, flank_max: int = 500, dmin: float = 0.01, dmax: float = 0.20) -> list[Pair]:
+    """Pairs for local alignment: B (the reference, columns) is random with a
+    length uniform in [ref_min, ref_max]; A (the query, rows) is a mutated
+    copy of a window of B (length uniform in [win_min, min(win_max, len B)],
+    divergence U[dmin, dmax], geometric indels of mean 3) between random
+    flanks of up to flank_max bases on each side."""
+    rs = Stream(seed, 6)
+    out = []
+    for k in range(npairs):
+        child = rs.child(k)
+        nb = int(child.integers(ref_min, ref_max, 1)[0])
+        b = child.bases(nb)
+        w = int(child.integers(min(win_min, nb), min(win_max, nb), 1)[0])
+        p0 = int(child.integers(0, nb - w, 1)[0])
+        core, _ = mutate_distinct(b[p0:p0 + w], child, float(dmin + (dmax - dmin) * child.uniform(1)[0]),
+                                  indel_mean=3.0)
+        left, right = (int(x) for x in child.integers(0, flank_max, 2))
+        a = np.concatenate([child.bases(left), core, child.bases(right)]).astype(np.uint8)
+        out.append(Pair(a, b, None))
+    return out
