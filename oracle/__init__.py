@@ -17,6 +17,10 @@ Functions whose result the paper or mathematics pins (see ``tests/``):
                            brute force over in-band paths; the bound U is
                            checked against brute force over out-of-band paths.
   exit_bound (U0)       -- brute force over every path that leaves the band.
+  affine_*              -- affine gaps (Gotoh, not in the paper): brute force
+                           over every alignment with gap runs scored open +
+                           length * extend, reduction to the linear oracle when
+                           the open cost is 0, closed forms.
   local_*               -- local alignment (Smith-Waterman, not in the paper):
                            brute force over every pair of substrings and every
                            alignment, longest common substring special case,
@@ -71,8 +75,13 @@ def _load():
             lib.nwo_local_align.argtypes = [u8p, i64, u8p, i64, i32, i32, i32, i32p, i64p, ctypes.c_char_p,
                                             ctypes.POINTER(i64)]
             lib.nwo_local_score.argtypes = [u8p, i64, u8p, i64, i32, i32, i32, i32p]
+            lib.nwo_affine_fill.argtypes = [u8p, i64, u8p, i64, i32, i32, i32, i32, i32p, i32p, i32p]
+            lib.nwo_affine_align.argtypes = [u8p, i64, u8p, i64, i32, i32, i32, i32, i32p, ctypes.c_char_p,
+                                             ctypes.POINTER(i64)]
+            lib.nwo_affine_score.argtypes = [u8p, i64, u8p, i64, i32, i32, i32, i32, i32p]
             for f in (lib.nwo_fill, lib.nwo_align, lib.nwo_score, lib.nwo_banded, lib.nwo_region, lib.nwo_local_fill,
-                      lib.nwo_local_align, lib.nwo_local_score):
+                      lib.nwo_local_align, lib.nwo_local_score, lib.nwo_affine_fill, lib.nwo_affine_align,
+                      lib.nwo_affine_score):
                 f.restype = ctypes.c_int
             _lib = lib
     return _lib
@@ -273,6 +282,59 @@ def local_score_many(pairs, match: int = 1, mismatch: int = -1, gap: int = -1, t
     threads = threads or os.cpu_count() or 1
     with ThreadPoolExecutor(threads) as ex:
         return list(ex.map(lambda p: local_score(p[0], p[1], match, mismatch, gap), pairs))
+
+
+def affine_fill(a, b, match: int = 1, mismatch: int = -1, gap_open: int = -2, gap_extend: int = -1):
+    """The three (m+1) x (n+1) grids H, E, F of affine-gap global alignment."""
+    a, b = _codes(a), _codes(b)
+    grids = [np.empty((a.size + 1, b.size + 1), dtype=np.int32) for _ in range(3)]
+    pa, ka = _ptr(a)
+    pb, kb = _ptr(b)
+    i32p = ctypes.POINTER(ctypes.c_int32)
+    rc = _load().nwo_affine_fill(pa, a.size, pb, b.size, match, mismatch, gap_open, gap_extend,
+                                 *[g.ctypes.data_as(i32p) for g in grids])
+    assert rc == 0, rc
+    return tuple(grids)
+
+
+def affine_align(a, b, match: int = 1, mismatch: int = -1, gap_open: int = -2, gap_extend: int = -1):
+    """(score, op string) of affine-gap global alignment."""
+    a, b = _codes(a), _codes(b)
+    out = ctypes.c_int32(0)
+    nops = ctypes.c_int64(0)
+    buf = ctypes.create_string_buffer(a.size + b.size + 1)
+    pa, ka = _ptr(a)
+    pb, kb = _ptr(b)
+    rc = _load().nwo_affine_align(pa, a.size, pb, b.size, match, mismatch, gap_open, gap_extend, ctypes.byref(out),
+                                  buf, ctypes.byref(nops))
+    if rc == -2:
+        raise MemoryError("oracle grids do not fit in host memory")
+    assert rc == 0, rc
+    return int(out.value), buf.raw[: nops.value].decode()
+
+
+def affine_score(a, b, match: int = 1, mismatch: int = -1, gap_open: int = -2, gap_extend: int = -1) -> int:
+    a, b = _codes(a), _codes(b)
+    out = ctypes.c_int32(0)
+    pa, ka = _ptr(a)
+    pb, kb = _ptr(b)
+    rc = _load().nwo_affine_score(pa, a.size, pb, b.size, match, mismatch, gap_open, gap_extend, ctypes.byref(out))
+    assert rc == 0, rc
+    return int(out.value)
+
+
+def affine_align_many(pairs, match: int = 1, mismatch: int = -1, gap_open: int = -2, gap_extend: int = -1,
+                      threads: int | None = None):
+    threads = threads or os.cpu_count() or 1
+    with ThreadPoolExecutor(threads) as ex:
+        return list(ex.map(lambda p: affine_align(p[0], p[1], match, mismatch, gap_open, gap_extend), pairs))
+
+
+def affine_score_many(pairs, match: int = 1, mismatch: int = -1, gap_open: int = -2, gap_extend: int = -1,
+                      threads: int | None = None):
+    threads = threads or os.cpu_count() or 1
+    with ThreadPoolExecutor(threads) as ex:
+        return list(ex.map(lambda p: affine_score(p[0], p[1], match, mismatch, gap_open, gap_extend), pairs))
 
 
 def rle(ops: str) -> str:

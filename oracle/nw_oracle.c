@@ -349,3 +349,120 @@ int nwo_local_score(const uint8_t *a, int64_t m, const uint8_t *b, int64_t n,
     free(prev); free(cur);
     return NWO_OK;
 }
+
+/* ------------------------------------------------------------------------
+ * Affine gaps (Gotoh; not in the paper, whose gap penalty is linear, but the
+ * center-star method it cites uses them).  A run of k gap moves of one kind
+ * scores go + k*ge (open plus extend, both <= 0).  Three grids:
+ *   E(i,j) best score of A[:i] vs B[:j] ending in a horizontal move (B_j alone):
+ *          max( E(i,j-1) + ge, H(i,j-1) + go + ge )
+ *   F(i,j) ending in a vertical move (A_i alone):
+ *          max( F(i-1,j) + ge, H(i-1,j) + go + ge )
+ *   H(i,j) best score: max( H(i-1,j-1) + s(A_i,B_j), E(i,j), F(i,j) )
+ * Boundary: H(0,0) = 0; H(0,j) = E(0,j) = go + j*ge and F(0,j) = -inf for
+ * j >= 1; H(i,0) = F(i,0) = go + i*ge and E(i,0) = -inf for i >= 1.
+ * Walk from (m,n) in state H: diagonal if H == H(i-1,j-1) + s, else the
+ * vertical gap if H == F, else the horizontal gap; in a gap state the move
+ * is emitted and the walk stays in the gap when extending is strictly
+ * better than opening (F(i-1,j) + ge > H(i-1,j) + go + ge), else returns to
+ * state H at the predecessor -- a tie closes the gap.  On row 0 only
+ * horizontal moves remain, on column 0 only vertical ones.  With go = 0
+ * this is the linear walk move for move.
+ * ---------------------------------------------------------------------- */
+#define NWO_AFF_NEG (INT32_MIN / 4)
+
+static int32_t aff_add(int32_t x, int32_t y) { return x <= NWO_AFF_NEG ? NWO_AFF_NEG : x + y; }
+
+int nwo_affine_fill(const uint8_t *a, int64_t m, const uint8_t *b, int64_t n, int32_t match, int32_t mismatch,
+                    int32_t go, int32_t ge, int32_t *H, int32_t *E, int32_t *F) {
+    if (m < 0 || n < 0 || !H || !E || !F) return NWO_ERR_ARG;
+    const int64_t w = n + 1;
+    H[0] = 0;
+    E[0] = F[0] = NWO_AFF_NEG;
+    for (int64_t j = 1; j <= n; ++j) {
+        H[j] = E[j] = go + (int32_t)j * ge;
+        F[j] = NWO_AFF_NEG;
+    }
+    for (int64_t i = 1; i <= m; ++i) {
+        H[i * w] = F[i * w] = go + (int32_t)i * ge;
+        E[i * w] = NWO_AFF_NEG;
+        for (int64_t j = 1; j <= n; ++j) {
+            const int64_t c = i * w + j;
+            E[c] = max2(aff_add(E[c - 1], ge), H[c - 1] + go + ge);
+            F[c] = max2(aff_add(F[c - w], ge), H[c - w] + go + ge);
+            H[c] = max2(H[c - w - 1] + subst(a[i - 1], b[j - 1], match, mismatch), max2(E[c], F[c]));
+        }
+    }
+    return NWO_OK;
+}
+
+int nwo_affine_align(const uint8_t *a, int64_t m, const uint8_t *b, int64_t n, int32_t match, int32_t mismatch,
+                     int32_t go, int32_t ge, int32_t *score, char *ops, int64_t *nops) {
+    if (m < 0 || n < 0 || !score || !ops || !nops) return NWO_ERR_ARG;
+    const int64_t w = n + 1;
+    const size_t cells = (size_t)(m + 1) * (size_t)w;
+    int32_t *H = (int32_t *)malloc(cells * sizeof(int32_t));
+    int32_t *E = (int32_t *)malloc(cells * sizeof(int32_t));
+    int32_t *F = (int32_t *)malloc(cells * sizeof(int32_t));
+    if (!H || !E || !F) { free(H); free(E); free(F); return NWO_ERR_OOM; }
+    nwo_affine_fill(a, m, b, n, match, mismatch, go, ge, H, E, F);
+    int64_t i = m, j = n, k = 0;
+    int state = 0;                                   /* 0: H, 1: F (vertical gap), 2: E (horizontal gap) */
+    while (i > 0 || j > 0) {
+        if (i == 0) { ops[k++] = 'D'; --j; continue; }
+        if (j == 0) { ops[k++] = 'I'; --i; continue; }
+        const int64_t c = i * w + j;
+        if (state == 0) {
+            if (H[c] == H[c - w - 1] + subst(a[i - 1], b[j - 1], match, mismatch)) {
+                ops[k++] = (a[i - 1] == b[j - 1]) ? '=' : 'X';
+                --i; --j;
+                continue;
+            }
+            state = H[c] == F[c] ? 1 : 2;
+        }
+        if (state == 1) {
+            ops[k++] = 'I';
+            state = aff_add(F[c - w], ge) > H[c - w] + go + ge ? 1 : 0;
+            --i;
+        } else {
+            ops[k++] = 'D';
+            state = aff_add(E[c - 1], ge) > H[c - 1] + go + ge ? 2 : 0;
+            --j;
+        }
+    }
+    for (int64_t x = 0, y = k - 1; x < y; ++x, --y) {
+        char t = ops[x]; ops[x] = ops[y]; ops[y] = t;
+    }
+    *nops = k;
+    *score = H[m * w + n];
+    free(H); free(E); free(F);
+    return NWO_OK;
+}
+
+/* Affine score only, rolling rows. */
+int nwo_affine_score(const uint8_t *a, int64_t m, const uint8_t *b, int64_t n, int32_t match, int32_t mismatch,
+                     int32_t go, int32_t ge, int32_t *score) {
+    if (m < 0 || n < 0 || !score) return NWO_ERR_ARG;
+    int32_t *Hp = (int32_t *)malloc((size_t)(n + 1) * sizeof(int32_t));
+    int32_t *Hc = (int32_t *)malloc((size_t)(n + 1) * sizeof(int32_t));
+    int32_t *Fp = (int32_t *)malloc((size_t)(n + 1) * sizeof(int32_t));
+    int32_t *Fc = (int32_t *)malloc((size_t)(n + 1) * sizeof(int32_t));
+    if (!Hp || !Hc || !Fp || !Fc) { free(Hp); free(Hc); free(Fp); free(Fc); return NWO_ERR_OOM; }
+    Hp[0] = 0;
+    Fp[0] = NWO_AFF_NEG;
+    for (int64_t j = 1; j <= n; ++j) { Hp[j] = go + (int32_t)j * ge; Fp[j] = NWO_AFF_NEG; }
+    for (int64_t i = 1; i <= m; ++i) {
+        Hc[0] = Fc[0] = go + (int32_t)i * ge;
+        int32_t e = NWO_AFF_NEG;                      /* E(i,0) */
+        for (int64_t j = 1; j <= n; ++j) {
+            e = max2(aff_add(e, ge), Hc[j - 1] + go + ge);
+            Fc[j] = max2(aff_add(Fp[j], ge), Hp[j] + go + ge);
+            Hc[j] = max2(Hp[j - 1] + subst(a[i - 1], b[j - 1], match, mismatch), max2(e, Fc[j]));
+        }
+        int32_t *t = Hp; Hp = Hc; Hc = t;
+        t = Fp; Fp = Fc; Fc = t;
+    }
+    *score = m == 0 && n == 0 ? 0 : Hp[n];
+    free(Hp); free(Hc); free(Fp); free(Fc);
+    return NWO_OK;
+}
