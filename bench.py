@@ -13,10 +13,11 @@ score and CIGAR mismatches between the two.
 Other workloads: pair32k (one 32,768 x 32,768 pair), pair1k (one 1,000 x
 1,000 pair), allpairs (512 sequences, all 130,816 pairwise scores),
 centerstar (the center-star multiple alignment of the same 512 sequences),
-local (local alignment of 4,000 query/reference pairs), serve (Poisson request stream into the continuous-batching server).
+local (local alignment of 4,000 query/reference pairs), affine (affine-gap
+global alignment of 2,000 pairs), serve (Poisson request stream into the continuous-batching server).
 
     python bench.py [--gpus N] [--steps K] [--warmup W]
-                    [--workload band|pair32k|pair1k|allpairs|centerstar|local|serve]
+                    [--workload band|pair32k|pair1k|allpairs|centerstar|local|affine|serve]
     python bench.py --impl reference ...   # the CPU oracle on the host cores
 
 Prints one JSON line.  The path does not shard: with --gpus N under
@@ -49,7 +50,7 @@ OPS_PER_CELL = 4             # algorithmic work of the textbook cell: s select, 
 W_OPS_PER_CELL = 3           # what the W-domain kernels issue for it: prmt + add-max + max
 PEAK_KINDS = (0, 2, 4)       # nw_peak_int kinds: DPX add-max, max, prmt (lane-ops/s each)
 CELL_KINDS = (5, 6, 7)       # nw_peak_int kinds: score-only cells in three instruction mixes (cells/s)
-STEPS_DEFAULT = {"pair32k": 100, "pair1k": 200, "allpairs": 20, "centerstar": 20, "local": 10, "band": 3}
+STEPS_DEFAULT = {"pair32k": 100, "pair1k": 200, "allpairs": 20, "centerstar": 20, "local": 10, "affine": 10, "band": 3}
 
 
 def code_only(text: str) -> str:
@@ -109,7 +110,7 @@ def parse():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="band",
-                    choices=["band", "pair32k", "pair1k", "allpairs", "centerstar", "local", "serve"])
+                    choices=["band", "pair32k", "pair1k", "allpairs", "centerstar", "local", "affine", "serve"])
     ap.add_argument("--rate", type=float, default=50000.0, help="serve: Poisson arrival rate (requests/s)")
     ap.add_argument("--duration", type=float, default=3.0, help="serve: seconds of arrivals")
     ap.add_argument("--serve-pool", type=int, default=1500, help="serve: distinct requests the stream cycles through")
@@ -178,6 +179,11 @@ def workload(name: str):
                        "against a query made of a mutated window of it (U[200, 2,000] bases, divergence U[0.01,0.20], "
                        "geometric indels) between random flanks of up to 500 bases (seed 1006); score, start, end "
                        "and CIGAR")
+    if name == "affine":
+        pairs = seqgen.band_pairs(1007, npairs=2000, lmin=1000, lmax=5000)
+        return pairs, ("affine-gap global alignment (Gotoh), 2,000 pairs: lengths log-uniform [1,000, 5,000], "
+                       "divergence U[0.01,0.25], geometric indels, indel bursts 50-500 bp w.p. 0.3 (seed 1007); "
+                       "match 2, mismatch -3, gap open -5, gap extend -2; score + CIGAR")
     if name == "pair1k":
         p = seqgen.random_pair(1001, 1000, 1000)
         return p, "single pair 1,000 x 1,000 i.i.d. uniform ACGT, score + CIGAR (seed 1001)"
@@ -298,6 +304,7 @@ def run_reference(args):
     oracle.build()
     sample_fn = {"allpairs": allpairs_oracle_gcups, "centerstar": allpairs_oracle_gcups,
                  "local": lambda d, budget_s: local_oracle_gcups([(p.a, p.b) for p in d[:400]], budget_s),
+                 "affine": lambda d, budget_s: affine_oracle_gcups([(p.a, p.b) for p in d[:400]], budget_s),
                  "band": lambda d, budget_s: oracle_gcups_pairs([(p.a, p.b) for p in d[:400]], budget_s)}.get(
         args.workload, oracle_gcups)
     vals = []
@@ -433,6 +440,66 @@ class LocalWork:
         return local_oracle_gcups([(p.a, p.b) for p in self.pairs[:400]])
 
 
+AFFINE_SCORING = (2, -3, -5, -2)
+
+
+class AffineWork:
+    """Affine-gap global alignment of many pairs (score + CIGAR)."""
+    dominant = "affine_fill_ptr"
+
+    def __init__(self, nw, ctx, dev, name):
+        import torch
+        self.nw, self.ctx = nw, ctx
+        pairs, self.desc = workload(name)
+        self.pairs = pairs
+        seqs = []
+        for p in pairs:
+            seqs += [p.a, p.b]
+        pool, off, lens = nw.pool_of(seqs)
+        self.pool_host = torch.from_numpy(pool).pin_memory().numpy()
+        self.pool = torch.from_numpy(pool).to(dev)
+        self.ao, self.al, self.bo, self.bl = off[0::2], lens[0::2], off[1::2], lens[1::2]
+        n = len(pairs)
+        self.coff = nw._cigar_offsets(self.al, self.bl)
+        self.scores = torch.zeros(n, dtype=torch.int32, device=dev)
+        self.cpool = torch.zeros(int(self.coff[-1]), dtype=torch.uint8, device=dev)
+        self.clen = torch.zeros(n, dtype=torch.int64, device=dev)
+        self.cells = int(sum(int(x) * int(y) for x, y in zip(self.al, self.bl)))
+        self.config = {"npairs": n, "affine_scoring": list(AFFINE_SCORING)}
+
+    def step(self):
+        self.nw.nw_affine_align_batch(self.ctx, self.pool, self.ao, self.al, self.bo, self.bl, AFFINE_SCORING,
+                                      self.nw.NW_CIGAR, self.scores, self.cpool, self.coff, self.clen)
+
+    def e2e(self):
+        sc, cig = self.nw.nw_affine_align_batch(self.ctx, self.pool_host, self.ao, self.al, self.bo, self.bl,
+                                                AFFINE_SCORING, self.nw.NW_CIGAR)
+        return self.pool_host.nbytes, sc.nbytes + sum(len(c) for c in cig) + 8 * len(cig)
+
+    def result(self):
+        return {"score_checksum": int(self.scores.sum().item())}
+
+    def oracle_sample(self):
+        return affine_oracle_gcups([(p.a, p.b) for p in self.pairs[:400]])
+
+
+def affine_oracle_gcups(pairs, budget_s: float = 12.0):
+    """The CPU oracle, as it stands, on affine-gap alignments (score +
+    traceback) of pairs of the workload, on all host threads."""
+    import oracle
+    threads = len(os.sched_getaffinity(0))
+    t0 = time.perf_counter()
+    done, cells = 0, 0
+    while time.perf_counter() - t0 < budget_s and done < len(pairs):
+        chunk = pairs[done: done + threads]
+        oracle.affine_align_many(chunk, *AFFINE_SCORING, threads=threads)
+        cells += sum(a.size * b.size for a, b in chunk)
+        done += len(chunk)
+    dt = time.perf_counter() - t0
+    return cells / dt / 1e9, threads, f"{done} pairs of the workload, affine score + traceback ({cells:.3g} " \
+                                      f"cells, {dt:.1f} s)"
+
+
 def local_oracle_gcups(pairs, budget_s: float = 12.0):
     """The CPU oracle, as it stands, on local alignments (score, ends and
     traceback) of pairs of the workload, on all host threads."""
@@ -470,13 +537,13 @@ class CenterStarWork:
         self.scores = torch.zeros(n, dtype=torch.int32, device=dev)
         self.cpool = torch.zeros(int(self.coff[-1]), dtype=torch.uint8, device=dev)
         self.clen = torch.zeros(n, dtype=torch.int64, device=dev)
-        self.ld = 2 * int(lens.max()) + 64
-        self.msa = torch.zeros(n * self.ld, dtype=torch.uint8, device=dev)
         L = lens.astype(np.float64)
         self.pair_cells = int((np.outer(L, L).sum() - (L * L).sum()) / 2)
+        # the merged column count first (no rows), then rows of that stride
         self.center, self.cols, ok = nw.nw_center_star(ctx, self.pool, off, lens, SCORING, 0, self.sums, self.scores,
-                                                       self.cpool, self.coff, self.clen, self.msa, self.ld)
-        assert ok, "row stride below the merged column count"
+                                                       self.cpool, self.coff, self.clen, None, 0)
+        self.ld = self.cols + 1
+        self.msa = torch.zeros(n * self.ld, dtype=torch.uint8, device=dev)
         self.cells = self.pair_cells + int((L * L[self.center]).sum())
         self.config = {"nseq": n, "pairs": n * (n - 1) // 2, "center": self.center, "msa_columns": self.cols}
 
@@ -721,7 +788,7 @@ def run_ours(args):
     ctx = nw.Context(local, stream)
     ctx.set_autotune(True)  # the warm-up steps time the candidate shapes
     work = {"allpairs": AllPairsWork, "band": BandWork, "centerstar": CenterStarWork,
-            "local": LocalWork}.get(args.workload, PairWork)(
+            "local": LocalWork, "affine": AffineWork}.get(args.workload, PairWork)(
         nw, ctx, dev, args.workload)
     flush = torch.empty(L2_FLUSH_BYTES, dtype=torch.uint8, device=dev)
 

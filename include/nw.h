@@ -89,6 +89,15 @@ typedef struct {
     int32_t gap;        /* score of a vertical or horizontal step (Sec. 2.3: -1)      */
 } nw_scoring;
 
+/* Affine gap scores (not in the paper): a run of k gap moves of one kind
+ * scores gap_open + k * gap_extend. */
+typedef struct {
+    int32_t match;
+    int32_t mismatch;
+    int32_t gap_open;     /* <= 0 */
+    int32_t gap_extend;   /* <= 0 */
+} nw_affine_scoring;
+
 typedef struct nw_ctx nw_ctx;
 
 /* ---------------------------------------------------------------- context */
@@ -293,6 +302,29 @@ int nw_local_align_batch(nw_ctx *ctx, const uint8_t *pool2b, const uint64_t *a_o
                          const uint64_t *b_off, const uint32_t *b_len, uint32_t npairs, nw_scoring sc,
                          uint32_t flags, int32_t *scores, uint32_t *ends, char *cigar_pool,
                          const uint64_t *cigar_off, uint64_t *cigar_len);
+
+/* Global alignment of many pairs with affine gaps (Gotoh; not in the paper,
+ * whose gap penalty is linear, though the center-star method it cites uses
+ * affine gaps).  A run of k gap moves of one kind scores go + k*ge:
+ *     E(i,j) = max(E(i,j-1) + ge, H(i,j-1) + go + ge)     (ends with 'D')
+ *     F(i,j) = max(F(i-1,j) + ge, H(i-1,j) + go + ge)     (ends with 'I')
+ *     H(i,j) = max(H(i-1,j-1) + s(A_i,B_j), E(i,j), F(i,j))
+ * from H(0,0) = 0, H(0,j) = go + j*ge, H(i,0) = go + i*ge.  scores[k] =
+ * H(m,n).  With NW_CIGAR the alignment is walked back from (m,n): in state
+ * H the diagonal when it gives H, else the vertical gap when F gives H,
+ * else the horizontal gap; in a gap the walk extends only when extending is
+ * strictly better than opening (a tie closes the gap); on row 0 / column 0
+ * only horizontal / vertical moves remain.  With gap_open = 0 the result
+ * equals nw_align_batch with gap = gap_extend, move for move.  Memory and
+ * arguments as nw_align_batch (NW_HOST_IO, NW_CIGAR, NW_CIGAR_M; pointer
+ * words take 0.5 byte per cell).  Scores in [-40, 40], both gap scores <=
+ * 0, mismatch <= match, max(match - 2*gap_extend, 0) * min(m,n) below 2^29;
+ * a pair whose one-warp sweep would exceed 2^31 stripe steps is
+ * NW_ERR_UNSUPPORTED. */
+int nw_affine_align_batch(nw_ctx *ctx, const uint8_t *pool2b, const uint64_t *a_off, const uint32_t *a_len,
+                          const uint64_t *b_off, const uint32_t *b_len, uint32_t npairs, nw_affine_scoring sc,
+                          uint32_t flags, int32_t *scores, char *cigar_pool, const uint64_t *cigar_off,
+                          uint64_t *cigar_len);
 
 /* Partition of a pair list over `nranks` ranks (no GPU needed): the
  * paper's Sec. 3.2 divides the alignments over MPI ranks and gathers the

@@ -53,6 +53,11 @@ class Scoring(ctypes.Structure):
     _fields_ = [("match", ctypes.c_int32), ("mismatch", ctypes.c_int32), ("gap", ctypes.c_int32)]
 
 
+class AffineScoring(ctypes.Structure):
+    _fields_ = [("match", ctypes.c_int32), ("mismatch", ctypes.c_int32), ("gap_open", ctypes.c_int32),
+                ("gap_extend", ctypes.c_int32)]
+
+
 class Completion(ctypes.Structure):
     _fields_ = [("ticket", ctypes.c_uint64), ("status", ctypes.c_int32), ("score", ctypes.c_int32),
                 ("cigar_len", ctypes.c_uint64), ("cigar_off", ctypes.c_uint64), ("latency_s", ctypes.c_double)]
@@ -118,6 +123,8 @@ def load():
         "nw_band_start_width": (u32, [ctypes.c_float, u64, u64]),
         "nw_route_stragglers": (ctypes.c_int64, [vp, vp, u32, vp]),
         "nw_shard_pairs": (ctypes.c_int, [u32p, u32p, u32, u32, u32p, u64p]),
+        "nw_affine_align_batch": (ctypes.c_int, [vp, vp, u64p, u32p, u64p, u32p, u32, AffineScoring, u32, vp, vp,
+                                                 u64p, vp]),
         "nw_local_align_batch": (ctypes.c_int, [vp, vp, u64p, u32p, u64p, u32p, u32, Scoring, u32, vp, vp, vp, u64p,
                                                 vp]),
         "nw_band_next_width": (ctypes.c_int64, [u64, u64, u64, ctypes.c_int32, Scoring, u32]),
@@ -406,6 +413,37 @@ def nw_local_align_batch(ctx: Context, pool2b, a_off, a_len, b_off, b_len, scori
                                 _ptr(cigar_len) if want else None)
     _check(ctx, rc)
     return scores, ends, cigar_len
+
+
+def nw_affine_align_batch(ctx: Context, pool2b, a_off, a_len, b_off, b_len, scoring=(1, -1, -2, -1), flags: int = 0,
+                          scores=None, cigar_pool=None, cigar_off=None, cigar_len=None):
+    """Global alignment with affine gaps; scoring = (match, mismatch,
+    gap_open, gap_extend).  Host mode (pool2b numpy) returns (scores, CIGARs
+    or None); device mode writes into the given tensors."""
+    L = load()
+    npairs = len(a_len)
+    ao, aop = _u64(a_off)
+    al, alp = _u32(a_len)
+    bo, bop = _u64(b_off)
+    bl, blp = _u32(b_len)
+    sc = scoring if isinstance(scoring, AffineScoring) else AffineScoring(*scoring)
+    want = bool(flags & NW_CIGAR)
+    if cigar_off is None and want:
+        cigar_off = _cigar_offsets(al, bl)
+    co, cop = _u64(cigar_off) if want else (None, None)
+    if _is_host(pool2b):
+        flags |= NW_HOST_IO
+        sc_out = np.zeros(max(npairs, 1), np.int32)
+        cpool = np.zeros(max(int(co[-1]) if want else 1, 1), np.uint8)
+        clen = np.zeros(max(npairs, 1), np.uint64)
+        rc = L.nw_affine_align_batch(ctx.handle, _ptr(pool2b), aop, alp, bop, blp, npairs, sc, flags, _ptr(sc_out),
+                                     _ptr(cpool) if want else None, cop, _ptr(clen) if want else None)
+        _check(ctx, rc)
+        return sc_out[:npairs], (_cigars(cpool, co, clen, npairs) if want else None)
+    rc = L.nw_affine_align_batch(ctx.handle, _ptr(pool2b), aop, alp, bop, blp, npairs, sc, flags, _ptr(scores),
+                                 _ptr(cigar_pool) if want else None, cop, _ptr(cigar_len) if want else None)
+    _check(ctx, rc)
+    return scores, cigar_pool, cigar_len
 
 
 def nw_align_batch_banded(ctx: Context, pool2b, a_off, a_len, b_off, b_len, band_w, scoring=DEFAULT_SCORING,

@@ -86,12 +86,16 @@ def test_full_family_device_buffers(ctx):
     scores = torch.zeros(n, dtype=torch.int32, device="cuda")
     cpool = torch.zeros(int(coff[-1]), dtype=torch.uint8, device="cuda")
     clen = torch.zeros(n, dtype=torch.int64, device="cuda")
-    ld = 4096
+    # first the column count (no rows), then the rows at that stride; the
+    # second call replays the captured scoring stage
+    center, cols, ok = nw.nw_center_star(ctx, dpool, off, lens, (1, -1, -1), nw.NW_GRAPH, sums, scores, cpool,
+                                         coff, clen, None, 0)
+    assert ok
+    ld = cols + 1
     msa = torch.zeros(n * ld, dtype=torch.uint8, device="cuda")
-    for _ in range(2):
-        center, cols, ok = nw.nw_center_star(ctx, dpool, off, lens, (1, -1, -1), nw.NW_GRAPH, sums, scores, cpool,
-                                             coff, clen, msa, ld)
-        assert ok
+    center, cols, ok = nw.nw_center_star(ctx, dpool, off, lens, (1, -1, -1), nw.NW_GRAPH, sums, scores, cpool,
+                                         coff, clen, msa, ld)
+    assert ok
     ctx.sync()
     c, want_sums, aligned, rows = cs.center_star(seqs)
     assert center == c and cols == len(rows[0])
