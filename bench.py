@@ -446,6 +446,7 @@ AFFINE_SCORING = (2, -3, -5, -2)
 class AffineWork:
     """Affine-gap global alignment of many pairs (score + CIGAR)."""
     dominant = "affine_fill_ptr"
+    scoring = AFFINE_SCORING
 
     def __init__(self, nw, ctx, dev, name):
         import torch
@@ -465,7 +466,7 @@ class AffineWork:
         self.cpool = torch.zeros(int(self.coff[-1]), dtype=torch.uint8, device=dev)
         self.clen = torch.zeros(n, dtype=torch.int64, device=dev)
         self.cells = int(sum(int(x) * int(y) for x, y in zip(self.al, self.bl)))
-        self.config = {"npairs": n, "affine_scoring": list(AFFINE_SCORING)}
+        self.config = {"npairs": n}
 
     def step(self):
         self.nw.nw_affine_align_batch(self.ctx, self.pool, self.ao, self.al, self.bo, self.bl, AFFINE_SCORING,
@@ -864,7 +865,8 @@ def run_ours(args):
         "metric": METRIC, "value": job_gcups(work.cells, world, ms), "unit": "GCUPS", "n_gpus": world,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "int32", "data": "synthetic",
-        "config": dict(workload=work.desc, scoring=list(SCORING), parallelism=f"replicas{world}",
+        "config": dict(workload=work.desc, scoring=list(getattr(work, "scoring", SCORING)),
+                       parallelism=f"replicas{world}",
                        tuning=ctx.tuning(), graphs=ctx.graph_stats(),
                        l2="flushed between timed steps (256 MB device write)", cells=work.cells,
                        **work.config, **work.result()),
