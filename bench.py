@@ -116,8 +116,11 @@ def parse():
     ap.add_argument("--serve-pool", type=int, default=1500, help="serve: distinct requests the stream cycles through")
     ap.add_argument("--serve-workers", type=int, default=8, help="serve: worker threads (contexts, streams)")
     ap.add_argument("--serve-batch", type=int, default=64, help="serve: most requests one admission takes")
-    ap.add_argument("--npairs", type=int, default=20000, help="band: evaluation pairs (20,000 = the full workload)")
+    ap.add_argument("--npairs", type=int, default=None,
+                    help="pairs of the band / local / affine workloads (full: 20,000 / 4,000 / 2,000)")
     ap.add_argument("--no-clocks", action="store_true")
+    ap.add_argument("--no-cpu-baseline", action="store_true",
+                    help="leave out the CPU oracle leg (outside the timed region; for profiling runs)")
     ap.add_argument("--nseq", type=int, default=512, help="allpairs: number of sequences (512 = the full workload)")
     ap.add_argument("--m", type=int, default=32768, help="pair32k: query length (32,768 = the full workload)")
     return ap.parse_args()
@@ -150,13 +153,14 @@ def dist_env():
     return rank, world, local
 
 
-WL_ARGS = {"nseq": 512, "m": 32768, "npairs": 20000}
+WL_ARGS = {"nseq": 512, "m": 32768, "npairs": None}
+NPAIRS_FULL = {"band": 20000, "local": 4000, "affine": 2000}
 LABELS = os.path.join(ROOT, "tests", "golden", "band_labels_seed9004.npz")
 
 
 def workload(name: str):
+    npairs = WL_ARGS["npairs"] or NPAIRS_FULL.get(name, 0)
     if name == "band":
-        npairs = WL_ARGS["npairs"]
         pairs = seqgen.band_pairs(1004, npairs=npairs)
         return pairs, (f"learned certified band, {npairs:,} pairs: lengths log-uniform [2,000, 20,000], divergence "
                        "U[0.01,0.25], geometric indels, indel bursts 50-500 bp w.p. 0.3 (seed 1004); score + CIGAR; "
@@ -174,14 +178,14 @@ def workload(name: str):
                       f"U{{500..1500}}, divergence U[0.05,0.30], 20% of mutations 1-bp indels; seed 1003): "
                       f"{nseq * (nseq - 1) // 2:,} scored pairs, center, {nseq} alignments with CIGAR, merged rows")
     if name == "local":
-        pairs = seqgen.local_pairs(1006, npairs=4000)
-        return pairs, ("local alignment (Smith-Waterman), 4,000 pairs: a reference of U[2,000, 10,000] random bases "
+        pairs = seqgen.local_pairs(1006, npairs=npairs)
+        return pairs, (f"local alignment (Smith-Waterman), {npairs:,} pairs: a reference of U[2,000, 10,000] random bases "
                        "against a query made of a mutated window of it (U[200, 2,000] bases, divergence U[0.01,0.20], "
                        "geometric indels) between random flanks of up to 500 bases (seed 1006); score, start, end "
                        "and CIGAR")
     if name == "affine":
-        pairs = seqgen.band_pairs(1007, npairs=2000, lmin=1000, lmax=5000)
-        return pairs, ("affine-gap global alignment (Gotoh), 2,000 pairs: lengths log-uniform [1,000, 5,000], "
+        pairs = seqgen.band_pairs(1007, npairs=npairs, lmin=1000, lmax=5000)
+        return pairs, (f"affine-gap global alignment (Gotoh), {npairs:,} pairs: lengths log-uniform [1,000, 5,000], "
                        "divergence U[0.01,0.25], geometric indels, indel bursts 50-500 bp w.p. 0.3 (seed 1007); "
                        "match 2, mismatch -3, gap open -5, gap extend -2; score + CIGAR")
     if name == "pair1k":
@@ -896,7 +900,7 @@ def run_ours(args):
     }
     if not args.no_clocks:
         line["clocks"] = clk.summary()
-    if rank == 0 and world == 1:
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
         g, cores, sample = work.oracle_sample()
         line["cpu_baseline"] = {"value": g, "unit": "GCUPS", "cores": cores, "kind": "oracle", "sample": sample}
     if rank == 0:
