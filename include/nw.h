@@ -62,7 +62,9 @@ typedef enum {
     NW_ERR_CIGAR_TRUNC = 4,   /* CIGAR capacity too small; length reported   */
     NW_ERR_TIMEOUT = 5,       /* a bounded device-side wait gave up          */
     NW_ERR_CUDA = 6,          /* a CUDA runtime call failed                   */
-    NW_ERR_UNSUPPORTED = 7    /* valid request this build cannot serve        */
+    NW_ERR_UNSUPPORTED = 7,   /* valid request this build cannot serve        */
+    NW_ERR_BOUNDS = 8         /* checked build (NW_CHECKS): a kernel index fell
+                                 outside its buffer; the store was skipped    */
 } nw_status;
 
 /* Flags (bitwise OR). */

@@ -27,6 +27,7 @@ NW_ERR_CIGAR_TRUNC = 4
 NW_ERR_TIMEOUT = 5
 NW_ERR_CUDA = 6
 NW_ERR_UNSUPPORTED = 7
+NW_ERR_BOUNDS = 8
 
 NW_SCORE_ONLY = 0
 NW_CIGAR = 1
@@ -64,7 +65,9 @@ class Completion(ctypes.Structure):
 
 
 def lib_path() -> str:
-    return _build.LIB
+    """libnw.so, or the bounds-checked libnw_checks.so when the environment
+    sets NW_CHECKS=1 before the first call."""
+    return _build.CHECKS_LIB if os.environ.get("NW_CHECKS") == "1" else _build.LIB
 
 
 def load():

@@ -12,6 +12,10 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 CSRC = os.path.join(HERE, "csrc")
 OUT_DIR = os.path.join(HERE, "_build")
 LIB = os.path.join(OUT_DIR, "libnw.so")
+# the bounds-checked debug build (-DNW_CHECKS): every checked kernel store
+# compares its index with its buffer's capacity and reports NW_ERR_BOUNDS
+CHECKS_DIR = os.path.join(HERE, "_build_checks")
+CHECKS_LIB = os.path.join(CHECKS_DIR, "libnw_checks.so")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 NVCC_FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC,-O2", "--expt-relaxed-constexpr",
               "-Xptxas", "-warn-spills"]
@@ -35,16 +39,19 @@ def _stale(target: str, deps: list[str]) -> bool:
     return any(os.path.getmtime(d) > t for d in deps)
 
 
-def build(force: bool = False, verbose: bool = False, extra: list[str] | None = None) -> str:
-    os.makedirs(OUT_DIR, exist_ok=True)
+def build(force: bool = False, verbose: bool = False, extra: list[str] | None = None, checks: bool = False) -> str:
+    """Compile libnw.so (or, with checks, the bounds-checked
+    libnw_checks.so) in-tree; returns the library's path."""
+    out_dir, lib = (CHECKS_DIR, CHECKS_LIB) if checks else (OUT_DIR, LIB)
+    os.makedirs(out_dir, exist_ok=True)
     nvcc = _nvcc()
     headers = [os.path.join(CSRC, f) for f in os.listdir(CSRC) if f.endswith((".cuh", ".h"))]
     headers.append(os.path.join(os.path.dirname(HERE), "include", "nw.h"))
-    flags = NVCC_FLAGS + (extra or [])
+    flags = NVCC_FLAGS + (["-DNW_CHECKS"] if checks else []) + (extra or [])
     jobs = []
     objs = []
     for src in sources():
-        obj = os.path.join(OUT_DIR, os.path.basename(src)[:-3] + ".o")
+        obj = os.path.join(out_dir, os.path.basename(src)[:-3] + ".o")
         objs.append(obj)
         if force or _stale(obj, [src] + headers):
             jobs.append([nvcc, *ARCH, *flags, "-c", src, "-o", obj])
@@ -59,13 +66,14 @@ def build(force: bool = False, verbose: bool = False, extra: list[str] | None = 
 
     with ThreadPoolExecutor(max(1, min(len(jobs), os.cpu_count() or 4))) as ex:
         list(ex.map(run, jobs))
-    if jobs or force or _stale(LIB, objs):
-        tmp = LIB + f".tmp{os.getpid()}"
+    if jobs or force or _stale(lib, objs):
+        tmp = lib + f".tmp{os.getpid()}"
         run([nvcc, *ARCH, "-shared", "-o", tmp, *objs])
-        os.replace(tmp, LIB)
-    return LIB
+        os.replace(tmp, lib)
+    return lib
 
 
 if __name__ == "__main__":
     import sys
-    print(build(force="--force" in sys.argv, verbose=True, extra=["-Xptxas", "-v"] if "-v" in sys.argv else None))
+    print(build(force="--force" in sys.argv, verbose=True, extra=["-Xptxas", "-v"] if "-v" in sys.argv else None,
+                checks="--checks" in sys.argv))

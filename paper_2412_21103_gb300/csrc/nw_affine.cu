@@ -55,6 +55,9 @@ struct AffArgs {
     int32_t *scores;
     uint32_t *ptr;
     uint64_t ext_off;    // words from a pointer word to its extension word
+    uint32_t *err;
+    uint32_t out_cap;    // pairs at scores (checked build; the pointer words
+                         // of a launch are 2 * ext_off)
 };
 
 template <int R>
@@ -97,7 +100,8 @@ __global__ void __launch_bounds__(kAffWarps * 32) k_affine(AffArgs p) {
         const uint8_t *B = p.pool + tk.b_off;
         const uint32_t m = tk.m, n = tk.n;
         if (m == 0 || n == 0) {
-            if (lane == 0) p.scores[tk.out] = m + n ? go + p.ge * (int32_t)(m + n) : 0;
+            if (lane == 0 && in_range(tk.out, p.out_cap, p.err, kSiteAffScore))
+                p.scores[tk.out] = m + n ? go + p.ge * (int32_t)(m + n) : 0;
             continue;
         }
         const uint32_t S = (m + SH - 1) / SH;
@@ -196,14 +200,16 @@ __global__ void __launch_bounds__(kAffWarps * 32) k_affine(AffArgs p) {
                         fout = o.y;
                         const uint32_t col = (uint32_t)c + uu;
                         if constexpr (PTR) {
-                            if (cc == CPW - 1) {
+                            if (cc == CPW - 1 &&
+                                in_range((uint64_t)(prow - p.ptr) + col / CPW, p.ext_off, p.err, kSiteAffPtr)) {
                                 prow[col / CPW] = ptr_word(accL, accH);
                                 prow[p.ext_off + col / CPW] = ptr_word(accF, accE);
                             }
                             cc = (cc + 1) & (CPW - 1);
                         }
-                        aff_st_if(ring_out, ringW + col, xout);
-                        aff_st_if(ring_out, ringF + col, (uint32_t)fout);
+                        const bool rok = ring_out && in_range(col, p.ring_stride, p.err, kSiteAffRing);
+                        aff_st_if(rok, ringW + col, xout);
+                        aff_st_if(rok, ringF + col, (uint32_t)fout);
                     }
                     c += 32;
                     t += 31;
@@ -229,12 +235,14 @@ __global__ void __launch_bounds__(kAffWarps * 32) k_affine(AffArgs p) {
                     const uint32_t cc = (uint32_t)c % CPW;
                     if (cc == CPW - 1 || c == (int32_t)n - 1) {
                         const uint32_t miss = (CPW - 1 - cc) * R;
-                        uint32_t *w = pbase + (size_t)(s * 32u + lane) * tk.ncg + (uint32_t)c / CPW;
-                        w[0] = ptr_word(accL << miss, accH << miss);
-                        w[p.ext_off] = ptr_word(accF << miss, accE << miss);
+                        const size_t wi = (size_t)(s * 32u + lane) * tk.ncg + (uint32_t)c / CPW;
+                        if (in_range(tk.ptr_off + wi, p.ext_off, p.err, kSiteAffPtr)) {
+                            pbase[wi] = ptr_word(accL << miss, accH << miss);
+                            pbase[p.ext_off + wi] = ptr_word(accF << miss, accE << miss);
+                        }
                     }
                 }
-                if (lane == 31 && s + 1 < S) {
+                if (lane == 31 && s + 1 < S && in_range((uint64_t)c, p.ring_stride, p.err, kSiteAffRing)) {
                     ringW[c] = xout;
                     ringF[c] = (uint32_t)fout;
                 }
@@ -243,7 +251,8 @@ __global__ void __launch_bounds__(kAffWarps * 32) k_affine(AffArgs p) {
 #pragma unroll
                     for (int r = 0; r < R; ++r)
                         if ((uint32_t)r == rM) wmn = Wl[r];
-                    p.scores[tk.out] = wmn + p.ge * (int32_t)(m + n);
+                    if (in_range(tk.out, p.out_cap, p.err, kSiteAffScore))
+                        p.scores[tk.out] = wmn + p.ge * (int32_t)(m + n);
                 }
             }
             if (++c == (int32_t)P) {
@@ -267,7 +276,7 @@ __global__ void __launch_bounds__(kAffWarps * 32) k_affine(AffArgs p) {
 // diagonal, 1 vertical, 2 horizontal).
 template <int R>
 __global__ void k_affine_walk(const AffTask *tasks, uint32_t ntasks, const uint32_t *ptr, uint64_t ext_off,
-                              uint8_t *moves, const uint64_t *move_off, uint64_t *nmoves) {
+                              uint8_t *moves, const uint64_t *move_off, uint64_t *nmoves, uint32_t *err) {
     constexpr uint32_t SH = 32u * R, CPW = 16u / R;
     for (uint32_t q = blockIdx.x * blockDim.x + threadIdx.x; q < ntasks; q += gridDim.x * blockDim.x) {
         const AffTask tk = tasks[q];
@@ -277,6 +286,7 @@ __global__ void k_affine_walk(const AffTask *tasks, uint32_t ntasks, const uint3
         uint64_t k = 0;
         int state = 0;   // 0 H, 1 F (vertical gap), 2 E (horizontal gap)
         while (i > 0 && j > 0) {
+            if (!in_range(k, (uint64_t)tk.m + tk.n, err, kSiteAffMoves)) break;
             const uint32_t i1 = i - 1, j1 = j - 1;
             const size_t wi = (size_t)((i1 / SH) * 32u + (i1 % SH) / R) * tk.ncg + j1 / CPW;
             const uint32_t o = (j1 % CPW) * R + (i1 % R);
@@ -368,6 +378,8 @@ int affine_device(nw_ctx *ctx, const uint8_t *pool, const uint64_t *a_off, const
     aa.go = sc.gap_open;
     aa.ge = sc.gap_extend;
     aa.scores = scores;
+    aa.err = ctx->d_err;
+    aa.out_cap = npairs;
     std::vector<AffTask> all(npairs);
     for (uint32_t k = 0; k < npairs; ++k) {
         AffTask &t = all[k];
@@ -427,13 +439,13 @@ int affine_device(nw_ctx *ctx, const uint8_t *pool, const uint64_t *a_off, const
             const uint32_t blocks = std::max<uint32_t>(1, ((uint32_t)wave.size() + 127) / 128);
             if (R == 4)
                 k_affine_walk<4><<<blocks, 128, 0, ctx->stream>>>(dt, (uint32_t)wave.size(), (const uint32_t *)pv,
-                                                                  words, (uint8_t *)mv, dmoff, (uint64_t *)nm);
+                                                                  words, (uint8_t *)mv, dmoff, (uint64_t *)nm, ctx->d_err);
             else if (R == 16)
                 k_affine_walk<16><<<blocks, 128, 0, ctx->stream>>>(dt, (uint32_t)wave.size(), (const uint32_t *)pv,
-                                                                   words, (uint8_t *)mv, dmoff, (uint64_t *)nm);
+                                                                   words, (uint8_t *)mv, dmoff, (uint64_t *)nm, ctx->d_err);
             else
                 k_affine_walk<8><<<blocks, 128, 0, ctx->stream>>>(dt, (uint32_t)wave.size(), (const uint32_t *)pv,
-                                                                  words, (uint8_t *)mv, dmoff, (uint64_t *)nm);
+                                                                  words, (uint8_t *)mv, dmoff, (uint64_t *)nm, ctx->d_err);
         }
         std::vector<TraceTask> tt(wave.size());
         for (size_t q = 0; q < wave.size(); ++q) {

@@ -14,6 +14,17 @@
 namespace nw {
 
 // ------------------------------------------------------------------- host
+// Score slots the tasks of a launch may write (the checked build compares
+// every score store against it).
+static uint32_t score_slots(const BatchTask *host, uint32_t n) {
+    uint32_t cap = 0;
+    for (uint32_t k = 0; k < n; ++k) {
+        cap = std::max(cap, host[k].out0 + 1);
+        if (host[k].out1 != ~0u) cap = std::max(cap, host[k].out1 + 1);
+    }
+    return cap;
+}
+
 template <int R, bool PTR, int BAND>
 static int launch_batch_R(nw_ctx *ctx, BatchArgs &ba, uint32_t max_n, const std::string &prefix) {
     int occ = 0;
@@ -458,6 +469,8 @@ static int band_rounds(nw_ctx *ctx, const uint8_t *pool, const uint64_t *a_off, 
             ba.tasks = dt;
             ba.ntasks = (uint32_t)fill.size();
             ba.ptr = (uint32_t *)pv;
+            ba.ptr_cap = words;
+            ba.score_cap = score_slots(fill.data(), (uint32_t)fill.size());
             if ((rc = launch_batch(ctx, R, want, ba, max_n, 2))) return rc;
             // certificate on the banded scores: one gather, one copy back
             {
@@ -575,6 +588,7 @@ static int band_raw(nw_ctx *ctx, const uint8_t *pool, const uint64_t *a_off, con
     ba.err = ctx->d_err;
     ba.tasks = dt;
     ba.ntasks = npairs;
+    ba.score_cap = npairs;
     return launch_batch(ctx, R, false, ba, max_n, 1);
 }
 
@@ -712,6 +726,7 @@ int batch_device_impl(nw_ctx *ctx, const uint8_t *pool, const uint64_t *a_off, c
         BatchArgs bs = ba;
         bs.tasks = dt;
         bs.ntasks = npairs;
+        bs.score_cap = score_slots(lpt.data(), npairs);
         if ((rc = tune_rows(ctx, lpt, R, [&](int r) { return launch_batch(ctx, r, false, bs, max_n, 0, pre); },
                             &R)))
             return rc;
@@ -803,6 +818,8 @@ int batch_device_impl(nw_ctx *ctx, const uint8_t *pool, const uint64_t *a_off, c
         ba.tasks = dt;
         ba.ntasks = (uint32_t)fill.size();
         ba.ptr = (uint32_t *)pv;
+        ba.ptr_cap = words;
+        ba.score_cap = score_slots(fill.data(), (uint32_t)fill.size());
         uint32_t wave_max_n = 1;
         for (const auto &t : wave) wave_max_n = std::max(wave_max_n, t.n);
         if ((rc = launch_batch(ctx, R, true, ba, wave_max_n))) return rc;
@@ -1062,6 +1079,7 @@ extern "C" int nw_score_all_pairs(nw_ctx *ctx, const uint8_t *pool2b, const uint
     if ((rc = upload(ctx, (pre + "_tasks").c_str(), tasks, &dt))) return rc;
     ba.tasks = dt;
     ba.ntasks = (uint32_t)tasks.size();
+    ba.score_cap = nseq * nseq;
     std::vector<uint32_t> lens(len, len + nseq);
     uint32_t *dlen = nullptr;
     if ((rc = upload(ctx, (pre + "_len").c_str(), lens, &dlen))) return rc;

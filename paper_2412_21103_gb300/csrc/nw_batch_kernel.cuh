@@ -48,6 +48,8 @@ struct BatchArgs {
     int32_t *scores;
     uint32_t *ptr;
     uint32_t *err;
+    uint64_t ptr_cap;    // words at ptr; score slots at scores (checked build)
+    uint32_t score_cap;
 };
 
 // One predicated 32-bit global store (no branch around it).
@@ -107,8 +109,9 @@ __global__ void __launch_bounds__(kBatchWarps * 32) k_batch(BatchArgs p) {
         if (m == 0 || n == 0) {
             if (lane == 0) {
                 const int32_t sc = p.gap * (int32_t)(m + n);
-                p.scores[tk.out0] = sc;
-                if (tk.out1 != ~0u) p.scores[tk.out1] = sc;
+                if (in_range(tk.out0, p.score_cap, p.err, kSiteBatchScore)) p.scores[tk.out0] = sc;
+                if (tk.out1 != ~0u && in_range(tk.out1, p.score_cap, p.err, kSiteBatchScore))
+                    p.scores[tk.out1] = sc;
             }
             continue;
         }
@@ -207,10 +210,13 @@ __global__ void __launch_bounds__(kBatchWarps * 32) k_batch(BatchArgs p) {
                         xout = ((uint32_t)uv << 2) | (x & 3u);
                         const uint32_t cu = (uint32_t)c + u;
                         if constexpr (PTR) {
-                            if (cc == CPW - 1) prow[cu / CPW] = ptr_word(accL, accH);
+                            if (cc == CPW - 1 &&
+                                in_range((uint64_t)(prow - p.ptr) + cu / CPW, p.ptr_cap, p.err, kSiteBatchPtr))
+                                prow[cu / CPW] = ptr_word(accL, accH);
                             cc = (cc + 1) & (CPW - 1);
                         }
-                        st_global_if(ring_out, ring + cb + cu, xout);
+                        st_global_if(ring_out && in_range((uint64_t)cb + cu, p.ring_stride, p.err, kSiteBatchRing),
+                                     ring + cb + cu, xout);
                     }
                     c += 32;
                     t += 31;
@@ -256,19 +262,22 @@ __global__ void __launch_bounds__(kBatchWarps * 32) k_batch(BatchArgs p) {
                     const uint32_t cc = (uint32_t)c % CPW;
                     if (cc == CPW - 1 || col == ce) {
                         const uint32_t miss = (CPW - 1 - cc) * R;  // cells a row's last word lacks
-                        pbase[(size_t)(s * 32u + lane) * tk.ncg + (uint32_t)c / CPW] =
-                            ptr_word(accL << miss, accH << miss);
+                        const size_t wi = (size_t)(s * 32u + lane) * tk.ncg + (uint32_t)c / CPW;
+                        if (in_range(tk.ptr_off + wi, p.ptr_cap, p.err, kSiteBatchPtr))
+                            pbase[wi] = ptr_word(accL << miss, accH << miss);
                     }
                 }
-                if (lane == 31 && s + 1 < S) ring[col] = xout;
+                if (lane == 31 && s + 1 < S && in_range((uint64_t)col, p.ring_stride, p.err, kSiteBatchRing))
+                    ring[col] = xout;
                 if (s == sM && (uint32_t)lane == lM && col == (int32_t)n - 1) {
                     int32_t wmn = 0;
 #pragma unroll
                     for (int r = 0; r < R; ++r)
                         if ((uint32_t)r == rM) wmn = Wl[r];
                     const int32_t sc = wmn + p.gap * (int32_t)(m + n);
-                    p.scores[tk.out0] = sc;
-                    if (tk.out1 != ~0u) p.scores[tk.out1] = sc;
+                    if (in_range(tk.out0, p.score_cap, p.err, kSiteBatchScore)) p.scores[tk.out0] = sc;
+                    if (tk.out1 != ~0u && in_range(tk.out1, p.score_cap, p.err, kSiteBatchScore))
+                        p.scores[tk.out1] = sc;
                 }
             }
             if (++c == (int32_t)P) {

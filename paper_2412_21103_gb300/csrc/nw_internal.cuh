@@ -69,6 +69,31 @@ __device__ __forceinline__ bool wait_geq(const uint32_t *flag, uint32_t target, 
     }
 }
 
+// Checked build (compiled with -DNW_CHECKS): the kernels' global stores go
+// through in_range(), which compares the index with the buffer's capacity;
+// out of range it records NW_ERR_BOUNDS in the error word (detail: the
+// store site in the top 8 bits, the low 24 bits of the index) and the store
+// is skipped.  In the normal build in_range() is constant true and costs
+// nothing.
+#ifdef NW_CHECKS
+constexpr bool kChecks = true;
+#else
+constexpr bool kChecks = false;
+#endif
+enum CheckSite : uint32_t {
+    kSiteBatchPtr = 1, kSiteBatchRing, kSiteBatchScore, kSiteLocalPtr, kSiteLocalRing, kSiteLocalOut,
+    kSiteLocalMoves, kSiteAffPtr, kSiteAffRing, kSiteAffScore, kSiteAffMoves, kSiteMsaRow, kSiteMsaSlot
+};
+__device__ __forceinline__ bool in_range(uint64_t idx, uint64_t cap, uint32_t *err, uint32_t site) {
+    if constexpr (kChecks) {
+        if (idx >= cap) {
+            raise_error(err, NW_ERR_BOUNDS, (site << 24) | (uint32_t)(idx & 0xffffffu));
+            return false;
+        }
+    }
+    return true;
+}
+
 // Byte permute: output byte 0 = byte (sel & 7) of {hi:lo}, etc. (PTX prmt).
 __device__ __forceinline__ uint32_t prmt(uint32_t lo, uint32_t hi, uint32_t sel) {
     uint32_t d;

@@ -54,6 +54,9 @@ struct LocalArgs {
     int32_t *scores;     // [out]
     uint32_t *ends;      // [4*out]: i_start, j_start, i_end, j_end (POS)
     uint32_t *ptr;
+    uint32_t *err;
+    uint64_t ptr_cap;    // words at ptr, pairs at scores / ends (checked build)
+    uint32_t out_cap;
 };
 
 template <int R>
@@ -101,7 +104,7 @@ __global__ void __launch_bounds__(kLocalWarps * 32) k_local(LocalArgs p) {
         const uint8_t *B = p.pool + tk.b_off;
         const uint32_t m = tk.m, n = tk.n;
         if (m == 0 || n == 0) {
-            if (lane == 0) {
+            if (lane == 0 && in_range(tk.out, p.out_cap, p.err, kSiteLocalOut)) {
                 p.scores[tk.out] = 0;
                 if (POS)
                     for (int q = 0; q < 4; ++q) p.ends[4 * (size_t)tk.out + q] = (PTR || q >= 2) ? 0u : ~0u;
@@ -216,10 +219,13 @@ __global__ void __launch_bounds__(kLocalWarps * 32) k_local(LocalArgs p) {
                         dtop = up;
                         xout = ((uint32_t)uv << 2) | (x & 3u);
                         if constexpr (PTR) {
-                            if (cc == CPW - 1) prow[(uint32_t)col / CPW] = ptr_word(accL, accH);
+                            if (cc == CPW - 1 && in_range((uint64_t)(prow - p.ptr) + (uint32_t)col / CPW, p.ptr_cap,
+                                                          p.err, kSiteLocalPtr))
+                                prow[(uint32_t)col / CPW] = ptr_word(accL, accH);
                             cc = (cc + 1) & (CPW - 1);
                         }
-                        st_if(ring_out, ring + col, xout);
+                        st_if(ring_out && in_range((uint64_t)col, p.ring_stride, p.err, kSiteLocalRing), ring + col,
+                              xout);
                     }
                     c += 32;
                     t += 31;
@@ -247,11 +253,13 @@ __global__ void __launch_bounds__(kLocalWarps * 32) k_local(LocalArgs p) {
                     const uint32_t cc = (uint32_t)c % CPW;
                     if (cc == CPW - 1 || c == (int32_t)n - 1) {
                         const uint32_t miss = (CPW - 1 - cc) * R;  // cells a row's last word lacks
-                        pbase[(size_t)(s * 32u + lane) * tk.ncg + (uint32_t)c / CPW] =
-                            ptr_word(accL << miss, accH << miss);
+                        const size_t wi = (size_t)(s * 32u + lane) * tk.ncg + (uint32_t)c / CPW;
+                        if (in_range(tk.ptr_off + wi, p.ptr_cap, p.err, kSiteLocalPtr))
+                            pbase[wi] = ptr_word(accL << miss, accH << miss);
                     }
                 }
-                if (lane == 31 && s + 1 < S) ring[c] = xout;
+                if (lane == 31 && s + 1 < S && in_range((uint64_t)c, p.ring_stride, p.err, kSiteLocalRing))
+                    ring[c] = xout;
             }
             if (++c == (int32_t)P) {
                 fold(s);
@@ -274,7 +282,7 @@ __global__ void __launch_bounds__(kLocalWarps * 32) k_local(LocalArgs p) {
                 bj = j2;
             }
         }
-        if (lane == 0) {
+        if (lane == 0 && in_range(tk.out, p.out_cap, p.err, kSiteLocalOut)) {
             p.scores[tk.out] = best;
             if (POS) {
                 p.ends[4 * (size_t)tk.out + 2] = bi;
@@ -297,7 +305,7 @@ template <int R>
 __global__ void k_local_walk(const LocalTask *tasks, uint32_t ntasks, const uint8_t *pool, const uint32_t *ptr,
                              const int32_t *scores, uint32_t *ends, uint8_t *moves, const uint64_t *move_off,
                              uint64_t *nmoves, uint32_t prof0, uint32_t prof1, uint32_t prof2, uint32_t prof3,
-                             int32_t gap) {
+                             int32_t gap, uint32_t *err) {
     constexpr uint32_t SH = 32u * R, CPW = 16u / R;
     for (uint32_t q = blockIdx.x * blockDim.x + threadIdx.x; q < ntasks; q += gridDim.x * blockDim.x) {
         const LocalTask tk = tasks[q];
@@ -312,6 +320,7 @@ __global__ void k_local_walk(const LocalTask *tasks, uint32_t ntasks, const uint
             const uint32_t i1 = i - 1, j1 = j - 1;
             const uint32_t word = __ldg(pw + (size_t)((i1 / SH) * 32u + (i1 % SH) / R) * tk.ncg + j1 / CPW);
             const uint32_t d = ptr_move(word, (j1 % CPW) * R + (i1 % R));
+            if (!in_range(k, (uint64_t)tk.m + tk.n, err, kSiteLocalMoves)) break;
             mv[k++] = (uint8_t)d;
             if (d == 0) {
                 const uint32_t ca = base_at(A, i1), cb = base_at(B, j1);
@@ -399,6 +408,8 @@ int local_device(nw_ctx *ctx, const uint8_t *pool, const uint64_t *a_off, const 
     la.gap = sc.gap;
     la.scores = scores;
     la.ends = ends;
+    la.err = ctx->d_err;
+    la.out_cap = npairs;
     std::vector<LocalTask> all(npairs);
     for (uint32_t k = 0; k < npairs; ++k) {
         LocalTask &t = all[k];
@@ -453,6 +464,7 @@ int local_device(nw_ctx *ctx, const uint8_t *pool, const uint64_t *a_off, const 
         la.tasks = dt;
         la.ntasks = (uint32_t)wave.size();
         la.ptr = (uint32_t *)pv;
+        la.ptr_cap = words;
         if ((rc = launch_local(ctx, R, true, true, la, max_n))) return rc;
         {
             LaunchTimer t(ctx, "local_walk");
@@ -460,7 +472,7 @@ int local_device(nw_ctx *ctx, const uint8_t *pool, const uint64_t *a_off, const 
 #define NW_WALK(RV)                                                                                               \
     k_local_walk<RV><<<blocks, 128, 0, ctx->stream>>>(dt, (uint32_t)wave.size(), pool, (const uint32_t *)pv, scores, \
                                                       ends, (uint8_t *)mv, dmoff, (uint64_t *)nm, la.prof[0],       \
-                                                      la.prof[1], la.prof[2], la.prof[3], sc.gap)
+                                                      la.prof[1], la.prof[2], la.prof[3], sc.gap, ctx->d_err)
             if (R == 4) NW_WALK(4);
             else if (R == 16) NW_WALK(16);
             else NW_WALK(8);

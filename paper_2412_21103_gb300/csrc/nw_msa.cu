@@ -158,7 +158,7 @@ __global__ void k_slot_scan(const uint32_t *G, uint32_t count, uint64_t *start, 
 __global__ void k_merge_rows(const uint8_t *pool, const uint64_t *off, const uint32_t *len, const char *cigar_pool,
                              const uint64_t *cigar_off, const uint64_t *cigar_len, uint32_t nseq, const uint32_t *G,
                              const uint64_t *start, const uint64_t *ncols, char *msa, uint64_t ld,
-                             const uint32_t *err) {
+                             uint32_t *err) {
     if (*(volatile const uint32_t *)err) return;  // a CIGAR failed its check
     const uint64_t cols = *ncols;
     for (uint32_t k = blockIdx.x * blockDim.x + threadIdx.x; k < nseq; k += gridDim.x * blockDim.x) {
@@ -168,12 +168,16 @@ __global__ void k_merge_rows(const uint8_t *pool, const uint64_t *off, const uin
         for_runs(cigar_pool + cigar_off[k], cigar_len[k], [&](char op, uint64_t cnt) {
             for (uint64_t r = 0; r < cnt; ++r) {
                 if (op == 'I') {
-                    row[start[p] + used++] = "ACGT"[base_at(s, i++)];
+                    const uint64_t col = start[p] + used++;
+                    if (in_range(col, cols, err, kSiteMsaRow)) row[col] = "ACGT"[base_at(s, i)];
+                    ++i;
                 } else if (op == 'D') {
                     ++p;
                     used = 0;
                 } else {
-                    row[start[p] + G[p]] = "ACGT"[base_at(s, i++)];
+                    const uint64_t col = start[p] + G[p];
+                    if (in_range(col, cols, err, kSiteMsaRow)) row[col] = "ACGT"[base_at(s, i)];
+                    ++i;
                     ++p;
                     used = 0;
                 }

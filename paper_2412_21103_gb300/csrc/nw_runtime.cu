@@ -263,6 +263,7 @@ const char *nw_strerror(int status) {
         case NW_ERR_TIMEOUT: return "device-side wait timed out";
         case NW_ERR_CUDA: return "CUDA runtime error";
         case NW_ERR_UNSUPPORTED: return "unsupported request";
+        case NW_ERR_BOUNDS: return "index out of range (checked build)";
         default: return "unknown status";
     }
 }

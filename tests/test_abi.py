@@ -99,3 +99,13 @@ def test_plain_c_program_uses_the_abi(lib, tmp_path):
 
 def load_strerror(code: int) -> str:
     return nw.load().nw_strerror(code).decode()
+
+
+def test_checked_build_exports_the_same_boundary():
+    """The bounds-checked debug build (-DNW_CHECKS, selected with NW_CHECKS=1)
+    compiles and exports every symbol the header declares."""
+    path = nwbuild.build(checks=True)
+    checked = ctypes.CDLL(path)
+    missing = [s for s in nw.exported_symbols() if not hasattr(checked, s)]
+    assert not missing, missing
+    assert checked.nw_strerror is not None
