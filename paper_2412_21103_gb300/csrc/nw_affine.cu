@@ -20,9 +20,18 @@
 // index the extension bits of the cell's gap states -- F: F'(i-1,j) >
 // W(i-1,j) + go, E: E'(i,j-1) > W(i,j-1) + go (a tie closes the gap).
 //
-// Batched like the global kernel: one warp per pair from an atomic queue,
-// lane k owns R rows of a 32R-row stripe, stripes back to back; a step
-// hands the lane below two values (W with the base code, and F').
+// Batched by stripe jobs: every 32R-row stripe of every pair is one job,
+// jobs queued pair by pair (longest pairs first) and stripes in order, so a
+// long pair's stripes run on many warps at once as a wavefront instead of
+// one after another on one warp (which left a batch waiting on its longest
+// pair).  A warp takes the next job from an atomic counter; lane k owns R
+// rows of the stripe and a step hands the lane below two values (W with the
+// base code, and F').  Lane 31 writes the stripe's bottom row (W and F')
+// to the job's row buffer and publishes every 32 columns with a release
+// store to the job's progress word; the warp of the next stripe waits (a
+// bounded spin) on that word before it reads each chunk of 32 columns.
+// The job it waits on was taken earlier by a warp of the same persistent,
+// fully resident grid, so every wait ends.
 #include <algorithm>
 #include <vector>
 
@@ -41,17 +50,27 @@ struct AffTask {
     uint32_t out;
     uint32_t ncg;        // pointer words per lane row
     uint64_t ptr_off;    // word offset (the extension words follow at + ext_off)
+    uint64_t row_off;    // word offset of the pair's stripe rows: stripe s (< S-1) at row_off + 2*s*nr
+    uint32_t nr;         // words per row half (n rounded up to 32)
+    uint32_t pad;
+};
+
+struct AffJob {
+    uint32_t task;       // index into the launch's tasks
+    uint32_t stripe;
 };
 
 struct AffArgs {
     const uint8_t *pool;
     const AffTask *tasks;
-    uint32_t ntasks;
+    const AffJob *jobs;
+    uint32_t njobs;
     uint32_t *counter;
     uint32_t prof[4];    // byte d of prof[c] = s(c, d) - 2*ge as int8
     int32_t go, ge;
-    uint32_t *ring;      // per warp: W words, then F' words
-    uint32_t ring_stride;
+    uint32_t *rows;      // stripe rows of every pair (W words, then F' words)
+    uint64_t rows_cap;
+    uint32_t *progress;  // per job: columns of its bottom row published
     int32_t *scores;
     uint32_t *ptr;
     uint64_t ext_off;    // words from a pointer word to its extension word
@@ -79,44 +98,59 @@ __device__ __forceinline__ void aff_st_if(bool p, uint32_t *dst, uint32_t v) {
                  : "memory");
 }
 
+// Warp-uniform bounded wait until *flag >= target (lane 0 spins; then every
+// lane acquires, so its following loads see what the producer published).
+__device__ __forceinline__ bool aff_wait(const uint32_t *flag, uint32_t target, uint32_t *err, uint32_t where) {
+    int ok = 1;
+    if ((threadIdx.x & 31) == 0) ok = wait_geq(flag, target, err, where) ? 1 : 0;
+    ok = __shfl_sync(kFull, ok, 0);
+    if (ok) (void)ld_acquire(flag);
+    return ok != 0;
+}
+
 template <int R, bool PTR>
 __global__ void __launch_bounds__(kAffWarps * 32) k_affine(AffArgs p) {
     constexpr uint32_t SH = 32u * R;
     constexpr uint32_t CPW = PTR ? 16u / R : 1u;
     const int lane = threadIdx.x & 31;
-    const uint32_t gw = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-    uint32_t *ringW = p.ring + (size_t)gw * 2 * p.ring_stride;
-    uint32_t *ringF = ringW + p.ring_stride;
     const int32_t go = p.go;
     const uint32_t P0 = p.prof[0], P1 = p.prof[1], P2 = p.prof[2], P3 = p.prof[3];
 
     for (;;) {
-        uint32_t idx = 0;
-        if (lane == 0) idx = atomicAdd(p.counter, 1u);
-        idx = __shfl_sync(kFull, idx, 0);
-        if (idx >= p.ntasks) break;
-        const AffTask tk = p.tasks[idx];
+        uint32_t jidx = 0;
+        if (lane == 0) jidx = atomicAdd(p.counter, 1u);
+        jidx = __shfl_sync(kFull, jidx, 0);
+        if (jidx >= p.njobs) break;
+        const AffJob jb = p.jobs[jidx];
+        const AffTask tk = p.tasks[jb.task];
+        const uint32_t s = jb.stripe;
         const uint8_t *A = p.pool + tk.a_off;
         const uint8_t *B = p.pool + tk.b_off;
         const uint32_t m = tk.m, n = tk.n;
-        if (m == 0 || n == 0) {
+        if (m == 0 || n == 0) {   // a single job
             if (lane == 0 && in_range(tk.out, p.out_cap, p.err, kSiteAffScore))
                 p.scores[tk.out] = m + n ? go + p.ge * (int32_t)(m + n) : 0;
             continue;
         }
         const uint32_t S = (m + SH - 1) / SH;
-        const uint32_t P = max(n, kAffMinPeriod);
-        const uint32_t T = S * P + 31;
-        const uint32_t sM = (m - 1) / SH, lM = ((m - 1) % SH) / R, rM = (m - 1) % R;
+        const uint32_t T = n + 31;
+        const uint32_t lM = ((m - 1) % SH) / R, rM = (m - 1) % R;
         uint32_t *pbase = PTR ? p.ptr + tk.ptr_off : nullptr;
+        // the previous stripe's row (s > 0) and this stripe's (s < S - 1)
+        const uint32_t *inW = s ? p.rows + tk.row_off + (size_t)(s - 1) * 2 * tk.nr : nullptr;
+        const uint32_t *inF = s ? inW + tk.nr : nullptr;
+        uint32_t *outW = s + 1 < S ? p.rows + tk.row_off + (size_t)s * 2 * tk.nr : nullptr;
+        uint32_t *outF = s + 1 < S ? outW + tk.nr : nullptr;
+        const uint32_t *prev = s ? p.progress + (jidx - 1) : nullptr;   // stripe s-1 is the job before
+        uint32_t *mine = p.progress + jidx;
 
         uint32_t prof[R];
         int32_t Wl[R], El[R];
-        int32_t dtop = 0;
         uint32_t xout = 0, accL = 0, accH = 0, accF = 0, accE = 0;
         int32_t fout = kAffNeg;
-        auto init_rows = [&](uint32_t codes, uint32_t st) {
-            const uint32_t i0 = st * SH + (uint32_t)lane * R;   // rows i0+1 .. i0+R (1-based)
+        const uint32_t i0 = s * SH + (uint32_t)lane * R;   // rows i0+1 .. i0+R (1-based)
+        {
+            const uint32_t codes = aff_rows<R>(A, i0, m);
 #pragma unroll
             for (int r = 0; r < R; ++r) {
                 const uint32_t c = (codes >> (2 * r)) & 3u;
@@ -124,28 +158,23 @@ __global__ void __launch_bounds__(kAffWarps * 32) k_affine(AffArgs p) {
                 Wl[r] = go;        // W(i, 0)
                 El[r] = kAffNeg;   // E'(i, 0)
             }
-            dtop = i0 == 0 ? 0 : go;   // W(i0, 0)
-        };
-        init_rows(aff_rows<R>(A, (uint32_t)lane * R, m), 0);
-        uint32_t next_rows = S > 1 ? aff_rows<R>(A, SH + (uint32_t)lane * R, m) : 0u;
+        }
+        int32_t dtop = i0 == 0 ? 0 : go;   // W(i0, 0)
         int32_t c = -lane;
-        uint32_t s = 0;
-        // lane 0's inputs for global index gi: row 0 (W = go, F' = -inf) in
-        // stripe 0, the previous stripe's bottom row (lane 31 wrote it at
-        // least P - 94 steps earlier, past the fences below) in later ones
-        auto chunk_w = [&](uint32_t gi) -> uint32_t {
-            const uint32_t sg = gi / P, tg = gi - sg * P;
-            if (sg >= S || tg >= n) return 0u;
-            if (sg == 0) return ((uint32_t)go << 2) | base_at(B, tg);
-            return __ldcg(ringW + tg);
+        // lane 0's inputs for column col: row 0 (W = go, F' = -inf) in stripe
+        // 0, the previous stripe's bottom row (published, see the waits) after
+        auto chunk_w = [&](uint32_t col) -> uint32_t {
+            if (col >= n) return 0u;
+            if (!s) return ((uint32_t)go << 2) | base_at(B, col);
+            return __ldcg(inW + col);
         };
-        auto chunk_f = [&](uint32_t gi) -> int32_t {
-            const uint32_t sg = gi / P, tg = gi - sg * P;
-            if (sg == 0 || sg >= S || tg >= n) return kAffNeg;
-            return (int32_t)__ldcg(ringF + tg);
+        auto chunk_f = [&](uint32_t col) -> int32_t {
+            if (!s || col >= n) return kAffNeg;
+            return (int32_t)__ldcg(inF + col);
         };
-        uint32_t stage = 0, stage_next = chunk_w((uint32_t)lane);
-        int32_t fstage = kAffNeg, fstage_next = chunk_f((uint32_t)lane);
+        bool alive = !s || aff_wait(prev, min(32u, n), p.err, jidx);
+        uint32_t stage = 0, stage_next = alive ? chunk_w((uint32_t)lane) : 0u;
+        int32_t fstage = kAffNeg, fstage_next = alive ? chunk_f((uint32_t)lane) : kAffNeg;
 
         // the R cells of one column; u / fu: W and F' of the row above
         auto column = [&](int32_t d, int32_t u, int32_t fu, uint32_t sel) {
@@ -170,17 +199,23 @@ __global__ void __launch_bounds__(kAffWarps * 32) k_affine(AffArgs p) {
             }
             return make_int2(u, fu);
         };
+        // lane 31: this stripe's bottom row out, published every 32 columns
+        auto row_out = [&](uint32_t col) {
+            if (lane == 31 && outW && in_range((size_t)(outW - p.rows) + tk.nr + col, p.rows_cap, p.err, kSiteAffRing)) {
+                outW[col] = xout;
+                outF[col] = (uint32_t)fout;
+                if (((col + 1) & 31u) == 0 || col + 1 == n) st_release(mine, col + 1);
+            }
+        };
 
-        for (uint32_t t = 0; t < T; ++t) {
+        for (uint32_t t = 0; t < T && alive; ++t) {
             if ((t & 31u) == 0) {
                 stage = stage_next;
                 fstage = fstage_next;
-                __threadfence_block();
-                __syncwarp();
+                if (s && t + 32 < n && !(alive = aff_wait(prev, min(t + 64u, n), p.err, jidx))) break;
                 stage_next = chunk_w(t + 32u + (uint32_t)lane);
                 fstage_next = chunk_f(t + 32u + (uint32_t)lane);
-                if (__all_sync(kFull, c >= 0 && s < S && c + 32 <= (int32_t)n - 1)) {
-                    const bool ring_out = lane == 31 && s + 1 < S;
+                if (__all_sync(kFull, c >= 0 && c + 32 <= (int32_t)n - 1)) {
                     uint32_t cc = (uint32_t)c % CPW;
                     uint32_t *prow = PTR ? pbase + (size_t)(s * 32u + lane) * tk.ncg : nullptr;
 #pragma unroll 4
@@ -207,9 +242,7 @@ __global__ void __launch_bounds__(kAffWarps * 32) k_affine(AffArgs p) {
                             }
                             cc = (cc + 1) & (CPW - 1);
                         }
-                        const bool rok = ring_out && in_range(col, p.ring_stride, p.err, kSiteAffRing);
-                        aff_st_if(rok, ringW + col, xout);
-                        aff_st_if(rok, ringF + col, (uint32_t)fout);
+                        row_out(col);
                     }
                     c += 32;
                     t += 31;
@@ -224,8 +257,7 @@ __global__ void __launch_bounds__(kAffWarps * 32) k_affine(AffArgs p) {
                 x = x0;
                 fx = f0;
             }
-            const bool act = c >= 0 && c < (int32_t)n && s < S;
-            if (act) {
+            if (c >= 0 && c < (int32_t)n) {
                 const int32_t up = (int32_t)x >> 2;
                 const int2 o = column(dtop, up, fx, sext_selector(x & 3u));
                 dtop = up;
@@ -242,11 +274,8 @@ __global__ void __launch_bounds__(kAffWarps * 32) k_affine(AffArgs p) {
                         }
                     }
                 }
-                if (lane == 31 && s + 1 < S && in_range((uint64_t)c, p.ring_stride, p.err, kSiteAffRing)) {
-                    ringW[c] = xout;
-                    ringF[c] = (uint32_t)fout;
-                }
-                if (s == sM && (uint32_t)lane == lM && c == (int32_t)n - 1) {
+                row_out((uint32_t)c);
+                if (s + 1 == S && (uint32_t)lane == lM && c == (int32_t)n - 1) {
                     int32_t wmn = 0;
 #pragma unroll
                     for (int r = 0; r < R; ++r)
@@ -255,16 +284,10 @@ __global__ void __launch_bounds__(kAffWarps * 32) k_affine(AffArgs p) {
                         p.scores[tk.out] = wmn + p.ge * (int32_t)(m + n);
                 }
             }
-            if (++c == (int32_t)P) {
-                c = 0;
-                ++s;
-                if (s < S) {
-                    init_rows(next_rows, s);
-                    next_rows = s + 1 < S ? aff_rows<R>(A, (s + 1) * SH + (uint32_t)lane * R, m) : 0u;
-                }
-            }
+            ++c;
         }
         __syncwarp();
+        if (!alive) return;   // a wait gave up (NW_ERR_TIMEOUT is raised): leave
     }
 }
 
@@ -318,19 +341,17 @@ __global__ void k_affine_walk(const AffTask *tasks, uint32_t ntasks, const uint3
 }
 
 template <int R, bool PTR>
-int launch_affine_R(nw_ctx *ctx, AffArgs &aa, uint32_t max_n) {
+int launch_affine_R(nw_ctx *ctx, AffArgs &aa) {
     int occ = 0;
     cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_affine<R, PTR>, kAffWarps * 32, 0);
     if (occ < 1) occ = 1;
+    // every CTA resident: a job's warp may wait on an earlier job's warp
     uint32_t blocks = (uint32_t)occ * (uint32_t)ctx->sm_count;
-    const uint32_t need = (aa.ntasks + kAffWarps - 1) / kAffWarps;
+    const uint32_t need = (aa.njobs + kAffWarps - 1) / kAffWarps;
     if (blocks > need) blocks = need ? need : 1;
-    aa.ring_stride = ((max_n + 31) / 32) * 32 + 32;
     void *v = nullptr;
-    int rc = scratch(ctx, "affine_ring", (size_t)blocks * kAffWarps * 2 * aa.ring_stride * 4, &v);
+    int rc = scratch(ctx, "affine_counter", 16, &v);
     if (rc) return rc;
-    aa.ring = (uint32_t *)v;
-    if ((rc = scratch(ctx, "affine_counter", 16, &v))) return rc;
     aa.counter = (uint32_t *)v;
     cudaMemsetAsync(aa.counter, 0, 4, ctx->stream);
     LaunchTimer t(ctx, PTR ? "affine_fill_ptr" : "affine_score");
@@ -338,15 +359,15 @@ int launch_affine_R(nw_ctx *ctx, AffArgs &aa, uint32_t max_n) {
     return NW_OK;
 }
 
-int launch_affine(nw_ctx *ctx, int R, bool ptr, AffArgs &aa, uint32_t max_n) {
+int launch_affine(nw_ctx *ctx, int R, bool ptr, AffArgs &aa) {
     if (ptr) {
-        if (R == 4) return launch_affine_R<4, true>(ctx, aa, max_n);
-        if (R == 16) return launch_affine_R<16, true>(ctx, aa, max_n);
-        return launch_affine_R<8, true>(ctx, aa, max_n);
+        if (R == 4) return launch_affine_R<4, true>(ctx, aa);
+        if (R == 16) return launch_affine_R<16, true>(ctx, aa);
+        return launch_affine_R<8, true>(ctx, aa);
     }
-    if (R == 4) return launch_affine_R<4, false>(ctx, aa, max_n);
-    if (R == 16) return launch_affine_R<16, false>(ctx, aa, max_n);
-    return launch_affine_R<8, false>(ctx, aa, max_n);
+    if (R == 4) return launch_affine_R<4, false>(ctx, aa);
+    if (R == 16) return launch_affine_R<16, false>(ctx, aa);
+    return launch_affine_R<8, false>(ctx, aa);
 }
 
 template <typename T>
@@ -357,6 +378,39 @@ int aff_upload(nw_ctx *ctx, const char *slot, const std::vector<T> &v, T **dev) 
     cudaError_t e = cudaStreamSynchronize(ctx->stream);  // the host vector may be freed right after
     if (e != cudaSuccess) return cuda_fail(ctx, e, "task upload sync");
     *dev = (T *)d;
+    return NW_OK;
+}
+
+// Stripe jobs of a launch's tasks (in order, stripes in order), the tasks'
+// row-buffer offsets, and the row buffers and progress words in scratch.
+int affine_jobs(nw_ctx *ctx, std::vector<AffTask> &tasks, int R, AffArgs &aa) {
+    const uint32_t SH = 32u * R;
+    std::vector<AffJob> jobs;
+    uint64_t rows = 0;
+    for (uint32_t q = 0; q < tasks.size(); ++q) {
+        AffTask &t = tasks[q];
+        const uint32_t S = (t.m && t.n) ? (t.m + SH - 1) / SH : 1;
+        t.nr = (t.n + 31) / 32 * 32;
+        t.row_off = rows;
+        rows += (uint64_t)(S - 1) * 2 * t.nr;
+        for (uint32_t s = 0; s < S; ++s) jobs.push_back(AffJob{q, s});
+    }
+    int rc;
+    void *rv = nullptr, *pv = nullptr;
+    if ((rc = scratch(ctx, "affine_rows", rows * 4 + 16, &rv))) return rc;
+    if ((rc = scratch(ctx, "affine_progress", jobs.size() * 4 + 16, &pv))) return rc;
+    cudaError_t e = cudaMemsetAsync(pv, 0, jobs.size() * 4, ctx->stream);
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "affine progress reset");
+    AffTask *dt = nullptr;
+    AffJob *dj = nullptr;
+    if ((rc = aff_upload(ctx, "affine_tasks", tasks, &dt))) return rc;
+    if ((rc = aff_upload(ctx, "affine_jobs", jobs, &dj))) return rc;
+    aa.tasks = dt;
+    aa.jobs = dj;
+    aa.njobs = (uint32_t)jobs.size();
+    aa.rows = (uint32_t *)rv;
+    aa.rows_cap = rows;
+    aa.progress = (uint32_t *)pv;
     return NW_OK;
 }
 
@@ -383,23 +437,17 @@ int affine_device(nw_ctx *ctx, const uint8_t *pool, const uint64_t *a_off, const
     std::vector<AffTask> all(npairs);
     for (uint32_t k = 0; k < npairs; ++k) {
         AffTask &t = all[k];
-        t = AffTask{a_off[k], b_off[k], a_len[k], b_len[k], k, 0, 0};
-        if ((uint64_t)((t.m + SH - 1) / SH) * std::max(t.n, kAffMinPeriod) >= (1ull << 31))
-            return fail(ctx, NW_ERR_UNSUPPORTED, "pair %u too large for one warp (m*n/%u >= 2^31)", k, SH);
-        if (want) t.ncg = ptr_words_per_lane_row(std::max(t.n, kAffMinPeriod), R);
+        t = AffTask{a_off[k], b_off[k], a_len[k], b_len[k], k, 0, 0, 0, 0, 0};
+        if (want) t.ncg = ptr_words_per_lane_row(std::max(t.n, 1u), R);
     }
+    // longest pairs first: their stripe jobs start first
     std::stable_sort(all.begin(), all.end(), [](const AffTask &x, const AffTask &y) {
         return (uint64_t)x.m * x.n > (uint64_t)y.m * y.n;
     });
     int rc;
     if (!want) {
-        uint32_t max_n = 1;
-        for (const AffTask &t : all) max_n = std::max(max_n, t.n);
-        AffTask *dt = nullptr;
-        if ((rc = aff_upload(ctx, "affine_tasks", all, &dt))) return rc;
-        aa.tasks = dt;
-        aa.ntasks = npairs;
-        return launch_affine(ctx, R, false, aa, max_n);
+        if ((rc = affine_jobs(ctx, all, R, aa))) return rc;
+        return launch_affine(ctx, R, false, aa);
     }
     // waves whose pointer words (two arrays) fit half the free budget
     const uint64_t wave_budget = (ctx->budget - std::min(ctx->budget, ctx->used)) / 2;
@@ -408,7 +456,6 @@ int affine_device(nw_ctx *ctx, const uint8_t *pool, const uint64_t *a_off, const
         std::vector<AffTask> wave;
         std::vector<uint64_t> moff;
         uint64_t words = 0, mbytes = 0;
-        uint32_t max_n = 1;
         size_t k = k0;
         for (; k < all.size(); ++k) {
             AffTask t = all[k];
@@ -418,24 +465,21 @@ int affine_device(nw_ctx *ctx, const uint8_t *pool, const uint64_t *a_off, const
             words += wds;
             moff.push_back(mbytes);
             mbytes += (uint64_t)t.m + t.n + 16;
-            max_n = std::max(max_n, t.n);
             wave.push_back(t);
         }
         void *pv = nullptr, *mv = nullptr, *nm = nullptr;
         if ((rc = scratch(ctx, "affine_ptr", words * 8 + 16, &pv))) return rc;
         if ((rc = scratch(ctx, "affine_moves", mbytes + 16, &mv))) return rc;
         if ((rc = scratch(ctx, "affine_nmoves", wave.size() * 8 + 16, &nm))) return rc;
-        AffTask *dt = nullptr;
+        if ((rc = affine_jobs(ctx, wave, R, aa))) return rc;
         uint64_t *dmoff = nullptr;
-        if ((rc = aff_upload(ctx, "affine_tasks", wave, &dt))) return rc;
         if ((rc = aff_upload(ctx, "affine_move_off", moff, &dmoff))) return rc;
-        aa.tasks = dt;
-        aa.ntasks = (uint32_t)wave.size();
         aa.ptr = (uint32_t *)pv;
         aa.ext_off = words;
-        if ((rc = launch_affine(ctx, R, true, aa, max_n))) return rc;
+        if ((rc = launch_affine(ctx, R, true, aa))) return rc;
         {
             LaunchTimer t(ctx, "affine_walk");
+            const AffTask *dt = aa.tasks;
             const uint32_t blocks = std::max<uint32_t>(1, ((uint32_t)wave.size() + 127) / 128);
             if (R == 4)
                 k_affine_walk<4><<<blocks, 128, 0, ctx->stream>>>(dt, (uint32_t)wave.size(), (const uint32_t *)pv,

@@ -24,6 +24,12 @@
 namespace nw {
 
 constexpr int kBatchWarps = 8;   // warps per CTA
+// CTAs per SM the register allocation must allow.  1: the R = 16 pointer
+// kernel takes 159 registers and an SM holds 8 warps.  Capping it at 128
+// registers for 2 CTAs per SM (16 warps, no spills) measured slower on
+// GB300 -- 162 ms against 128 ms per banded launch on 20,000 pairs --
+// because the fewer registers cost the unrolled step its overlap.
+constexpr int kBatchMinBlocks = 1;
 constexpr uint32_t kMinPeriod = 96;
 
 struct BatchTask {
@@ -89,7 +95,7 @@ constexpr int32_t kNegW = -(1 << 27);
 // the same certificate (every path leaving the band is bounded).  The
 // stripe period is the task's fixed `period`.
 template <int R, bool PTR, int BAND>
-__global__ void __launch_bounds__(kBatchWarps * 32) k_batch(BatchArgs p) {
+__global__ void __launch_bounds__(kBatchWarps * 32, kBatchMinBlocks) k_batch(BatchArgs p) {
     constexpr uint32_t SH = 32u * R;
     constexpr uint32_t CPW = PTR ? 16u / R : 1u;
     const int lane = threadIdx.x & 31;
