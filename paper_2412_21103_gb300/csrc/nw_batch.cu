@@ -9,6 +9,7 @@
 #include <vector>
 
 #include "nw_batch_kernel.cuh"
+#include "nw_bits.cuh"
 #include "nw_internal.cuh"
 
 namespace nw {
@@ -93,8 +94,12 @@ static int pick_rows(const std::vector<BatchTask> &tasks) {
 // two) runs the launch with each candidate, times it with CUDA events and
 // keeps the fastest; later calls of the signature take the kept choice.
 // Every candidate computes the same scores, so the timed runs are real work.
+// Rows per lane 32 names the bit-sliced score-only kernel (one 32-row word
+// per lane, nw_bits.cu); it is a candidate only where `bits` allows it (a
+// score-only launch whose scoring fits two bit planes).
 template <typename F>
-static int tune_rows(nw_ctx *ctx, const std::vector<BatchTask> &tasks, int fallback, F launch, int *R) {
+static int tune_rows(nw_ctx *ctx, const std::vector<BatchTask> &tasks, int fallback, F launch, int *R,
+                     bool bits = false) {
     *R = fallback;
     if (!ctx->autotune || tasks.empty()) return NW_OK;
     double sm = 0, sn = 0;
@@ -106,8 +111,9 @@ static int tune_rows(nw_ctx *ctx, const std::vector<BatchTask> &tasks, int fallb
                             size_bucket((uint64_t)(sn / tasks.size())) + ":p" + size_bucket(tasks.size());
     uint32_t c = 0;
     if (tuned(ctx, key, &c)) {
-        if (c != 4 && c != 8 && c != 16) return fail(ctx, NW_ERR_ARG, "tuning %s: rows per lane %u", key.c_str(), c);
-        *R = (int)c;
+        if (c != 4 && c != 8 && c != 16 && c != 32)
+            return fail(ctx, NW_ERR_ARG, "tuning %s: rows per lane %u", key.c_str(), c);
+        *R = c == 32 && !bits ? 16 : (int)c;  // a pointer fill has no 32-row kernel
         return NW_OK;
     }
     cudaEvent_t a, b;
@@ -115,7 +121,8 @@ static int tune_rows(nw_ctx *ctx, const std::vector<BatchTask> &tasks, int fallb
     cudaEventCreate(&b);
     float best = 1e30f;
     int rc = NW_OK;
-    for (int r : {4, 8, 16}) {
+    for (int r : {4, 8, 16, 32}) {
+        if (r == 32 && !bits) continue;
         cudaEventRecord(a, ctx->stream);
         if ((rc = launch(r))) break;
         cudaEventRecord(b, ctx->stream);
@@ -727,13 +734,21 @@ int batch_device_impl(nw_ctx *ctx, const uint8_t *pool, const uint64_t *a_off, c
         bs.tasks = dt;
         bs.ntasks = npairs;
         bs.score_cap = score_slots(lpt.data(), npairs);
-        if ((rc = tune_rows(ctx, lpt, R, [&](int r) { return launch_batch(ctx, r, false, bs, max_n, 0, pre); },
-                            &R)))
-            return rc;
+        // score-only: the bit-sliced kernel (rows per lane 32) where the
+        // scoring fits two bit planes
+        const bool bits = !want && bits_scoring_ok(sc);
+        BitsPlan bp;
+        if (bits) {
+            std::vector<BatchTask> bt = lpt;
+            if ((rc = bits_prepare(ctx, pool, bits_pool_bytes(bt), bt, sc, scores, bs.score_cap, pre, &bp))) return rc;
+        }
+        auto run = [&](int r) { return r == 32 ? bits_launch(ctx, bp) : launch_batch(ctx, r, false, bs, max_n, 0, pre); };
+        if ((rc = tune_rows(ctx, lpt, bits ? 32 : R, run, &R, bits))) return rc;
         if (!want) {
-            auto launches = [&]() -> int { return launch_batch(ctx, R, false, bs, max_n, 0, pre); };
+            auto launches = [&]() -> int { return run(R); };
             if ((rc = launches())) return rc;
-            if (graph) return capture_graph(ctx, gkey, pre, "batch_score", 1, launches);
+            if (graph)
+                return capture_graph(ctx, gkey, pre, R == 32 ? "bits_score" : "batch_score", R == 32 ? 2 : 1, launches);
             return NW_OK;
         }
     }
@@ -1075,20 +1090,27 @@ extern "C" int nw_score_all_pairs(nw_ctx *ctx, const uint8_t *pool2b, const uint
     ba.gap = pf.gap;
     ba.scores = dout;
     ba.err = ctx->d_err;
-    BatchTask *dt = nullptr;
-    if ((rc = upload(ctx, (pre + "_tasks").c_str(), tasks, &dt))) return rc;
-    ba.tasks = dt;
     ba.ntasks = (uint32_t)tasks.size();
     ba.score_cap = nseq * nseq;
     std::vector<uint32_t> lens(len, len + nseq);
     uint32_t *dlen = nullptr;
     if ((rc = upload(ctx, (pre + "_len").c_str(), lens, &dlen))) return rc;
+    // the bit-sliced kernel where the scoring fits two bit planes (rows per
+    // lane 32), else -- or as the autotuner finds -- the scalar batch kernel
+    const bool bits = bits_scoring_ok(sc);
+    BitsPlan bp;
+    if (bits) {
+        std::vector<BatchTask> bt = tasks;
+        if ((rc = bits_prepare(ctx, pool, bits_pool_bytes(bt), bt, sc, dout, nseq * nseq, pre, &bp))) return rc;
+    }
+    BatchTask *dt = nullptr;
+    if ((rc = upload(ctx, (pre + "_tasks").c_str(), tasks, &dt))) return rc;
+    ba.tasks = dt;
+    auto run = [&](int r) { return r == 32 ? bits_launch(ctx, bp) : launch_batch(ctx, r, false, ba, max_n, 0, pre); };
     int R = 16;
-    if ((rc = tune_rows(ctx, tasks, pick_rows(tasks), [&](int r) { return launch_batch(ctx, r, false, ba, max_n, 0, pre); },
-                        &R)))
-        return rc;
+    if ((rc = tune_rows(ctx, tasks, bits ? 32 : pick_rows(tasks), run, &R, bits))) return rc;
     auto launches = [&]() -> int {
-        int r = launch_batch(ctx, R, false, ba, max_n, 0, pre);
+        int r = run(R);
         if (r) return r;
         {
             LaunchTimer t(ctx, "diag");
@@ -1098,7 +1120,9 @@ extern "C" int nw_score_all_pairs(nw_ctx *ctx, const uint8_t *pool2b, const uint
         return e == cudaSuccess ? NW_OK : cuda_fail(ctx, e, "all-pairs launch");
     };
     if ((rc = launches())) return rc;
-    if (graph && (rc = capture_graph(ctx, gkey, pre, "batch_score", 2, launches))) return rc;
+    if (graph && (rc = capture_graph(ctx, gkey, pre, R == 32 ? "bits_score" : "batch_score", R == 32 ? 3 : 2,
+                                     launches)))
+        return rc;
     cudaError_t e = cudaSuccess;
     if (flags & NW_HOST_IO) {
         e = cudaMemcpyAsync(out, dout, (size_t)nseq * nseq * 4, cudaMemcpyDeviceToHost, ctx->stream);

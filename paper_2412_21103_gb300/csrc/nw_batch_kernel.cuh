@@ -32,16 +32,6 @@ constexpr int kBatchWarps = 8;   // warps per CTA
 constexpr int kBatchMinBlocks = 1;
 constexpr uint32_t kMinPeriod = 96;
 
-struct BatchTask {
-    uint64_t a_off, b_off;  // byte offsets in the pool
-    uint32_t m, n;          // rows (A) and columns (B)
-    uint32_t out0, out1;    // score destinations (out1 == ~0u: none)
-    uint64_t ptr_off;       // word offset of the pair's pointer words
-    uint32_t ncg;           // pointer words per lane row
-    uint32_t period;        // steps per stripe (banded: fixed band width)
-    int32_t lo, hi;         // banded: diagonals j - i kept, [lo, hi]
-};
-
 struct BatchArgs {
     const uint8_t *pool;
     const BatchTask *tasks;

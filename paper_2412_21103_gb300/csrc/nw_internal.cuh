@@ -298,6 +298,17 @@ inline uint32_t ptr_words_per_lane_row(uint32_t n, int R) {
     return (((n + cpw - 1) / cpw + kTileWords - 1) / kTileWords) * kTileWords;
 }
 
+// One pair of a batched launch (nw_batch_kernel.cuh, nw_bits.cu).
+struct BatchTask {
+    uint64_t a_off, b_off;  // byte offsets in the pool
+    uint32_t m, n;          // rows (A) and columns (B)
+    uint32_t out0, out1;    // score destinations (out1 == ~0u: none)
+    uint64_t ptr_off;       // word offset of the pair's pointer words
+    uint32_t ncg;           // pointer words per lane row
+    uint32_t period;        // steps per stripe (banded: fixed band width)
+    int32_t lo, hi;         // banded: diagonals j - i kept, [lo, hi]
+};
+
 // One traceback + CIGAR job (see nw_trace.cu).
 struct TraceTask {
     const uint32_t *ptr;   // pointer words of the pair

@@ -170,13 +170,17 @@ int graph_launch(nw_ctx *ctx, const std::string &key, const char *label, uint32_
     if (it == ctx->graphs.end()) return NW_OK;
     cudaError_t e;
     {
-        // timed under the dominant kernel's name (one launch of it); the
-        // graph's other kernels are counted, untimed, under their own entry
-        LaunchTimer t(ctx, label, 1);
+        // timed under the dominant kernel's name (one launch of it), as
+        // recorded when the graph was captured; the graph's other kernels
+        // are counted, untimed, under their own entry
+        LaunchTimer t(ctx, it->second.label, 1);
         e = cudaGraphLaunch(it->second.exec, ctx->stream);
     }
+    (void)label;
+    (void)kernels;
     if (e != cudaSuccess) return cuda_fail(ctx, e, "cudaGraphLaunch");
-    if (ctx->profiling && kernels > 1) ctx->stats["graph_other_kernels"].launches += kernels - 1;
+    if (ctx->profiling && it->second.kernels > 1)
+        ctx->stats["graph_other_kernels"].launches += it->second.kernels - 1;
     it->second.last_use = ++ctx->graph_seq;
     ++ctx->graph_replays;
     *replayed = true;
