@@ -50,6 +50,17 @@ OPS_PER_CELL = 4             # algorithmic work of the textbook cell: s select, 
 W_OPS_PER_CELL = 3           # what the W-domain kernels issue for it: prmt + add-max + max
 PEAK_KINDS = (0, 2, 4)       # nw_peak_int kinds: DPX add-max, max, prmt (lane-ops/s each)
 CELL_KINDS = (5, 6, 7)       # nw_peak_int kinds: score-only cells in three instruction mixes (cells/s)
+# The bit-sliced kernels (bits_score, bband_*) update 32 cells of an anti-diagonal
+# with whole-word operations.  Their algorithmic work per 32 cells: 14 logic
+# ops of the difference update (match word 2, T = max(s', a, b) 6, dV 3, dH 3)
+# and 2 funnel shifts that bring the upper neighbour's difference into line;
+# the pointer planes add 2 (L, Hb).
+BITS_OPS_PER_32 = 16
+BITS_PTR_OPS_PER_32 = 18
+BITS_PEAK_KINDS = (8, 10)    # nw_peak_int kinds: 3-input logic op, funnel shift (lane-ops/s)
+BITS_CELL_KIND = 11          # nw_peak_int kind: one bit-sliced step, 32 cells (cells/s)
+BITS_KERNELS = ("bits_score", "bband_fill_ptr", "bband_score")
+HBM_PEAK_FALLBACK = 6800.0   # GB/s, when MEASURED_PEAKS.json is absent
 STEPS_DEFAULT = {"pair32k": 100, "pair1k": 200, "allpairs": 20, "centerstar": 20, "local": 10, "affine": 10, "band": 3}
 
 
@@ -371,7 +382,7 @@ class PairWork:
 
 class AllPairsWork:
     """All-vs-all int32 score matrix of 512 sequences (130,816 pairs)."""
-    dominant = "batch_score"
+    dominant = "bits_score"
 
     def __init__(self, nw, ctx, dev, name):
         import torch
@@ -525,7 +536,7 @@ def local_oracle_gcups(pairs, budget_s: float = 12.0):
 class CenterStarWork:
     """Center-star multiple alignment (Sec. 3.2): scoring matrix, center,
     alignments with the center, merged rows -- all on the device."""
-    dominant = "batch_score"
+    dominant = "bits_score"
 
     def __init__(self, nw, ctx, dev, name):
         import torch
@@ -598,7 +609,7 @@ def train_band_model(nw, ctx, dev, epochs: int = 60, batch: int = 512, lr: float
 class BandWork:
     """Certified learned band over many pairs (score + CIGAR); the plain
     full-grid batch runs on the same pairs for comparison."""
-    dominant = "band_fill_ptr"
+    dominant = "bband_fill_ptr"
 
     def __init__(self, nw, ctx, dev, name):
         import torch
@@ -811,6 +822,13 @@ def run_ours(args):
     # measured score-only cell rates (GCUPS) of three instruction mixes of the
     # cell update on every SM: the cell roofline as a measured number
     cell_rates = {f"kind{k}": nw.nw_peak_int(ctx, k, 1 << 15) for k in CELL_KINDS}
+    bits_kernel = work.dominant in BITS_KERNELS
+    if bits_kernel:
+        # the bit-sliced kernels' instructions (LOP3, funnel shift) and their
+        # step on independent chains, measured the same way
+        bits_rates = {f"kind{k}": nw.nw_peak_int(ctx, k, 1 << 15) for k in BITS_PEAK_KINDS}
+        bits_peak = min(bits_rates.values())
+        bits_cell_peak = nw.nw_peak_int(ctx, BITS_CELL_KIND, 1 << 13)
 
     band0 = nw.nw_ctx_band_stats(ctx)["band_cells"]
     ctx.reset_stats()
@@ -858,8 +876,8 @@ def run_ours(args):
     dl, dms = stats.get(work.dominant, (0, 0.0))
     dom_avg_ms = dms / max(dl, 1)
     # cells the dominant kernel computed per launch: the full grid, or for
-    # the banded kernel the band cells it actually swept
-    kcells = (band_cells / max(dl, 1)) if work.dominant.startswith("band") else work.cells
+    # the banded kernels the band (window) cells they actually swept
+    kcells = (band_cells / max(dl, 1)) if "band" in work.dominant else work.cells
     achieved = kcells * OPS_PER_CELL / (dom_avg_ms * 1e-3) / 1e9 if dom_avg_ms else None
     kernel_gcups = kcells / (dom_avg_ms * 1e-3) / 1e9 if dom_avg_ms else None
     cell_peak = max(cell_rates.values())
@@ -898,6 +916,13 @@ def run_ours(args):
                 "ms_per_step": statistics.mean(e2e_ms)},
         "wall_s_timed": wall,
     }
+    if bits_kernel:
+        line["roofline"] = bits_roofline(work.dominant, args.workload, kcells, dom_avg_ms, bits_peak, bits_cell_peak,
+                                         peak_ops)
+        line["roofline"].setdefault("alu", {}).setdefault("rates", bits_rates)
+        if line["roofline"]["bound"] == "alu":
+            line["roofline"]["rates"] = bits_rates
+            line["roofline"].pop("alu")
     if not args.no_clocks:
         line["clocks"] = clk.summary()
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
@@ -908,6 +933,55 @@ def run_ours(args):
     ctx.close()
     if world > 1:
         dist.destroy_process_group()
+
+
+def measured_hbm_gbs():
+    """The driver's measured copy bandwidth (GB/s) and where it came from."""
+    try:
+        v = float(json.load(open(os.path.join(HERE, "MEASURED_PEAKS.json")))["hbm_gbs"])
+        return v, "MEASURED_PEAKS.json hbm_gbs (STREAM-style copy, measured on this pool's GB300)"
+    except (OSError, KeyError, ValueError):
+        return HBM_PEAK_FALLBACK, "fallback 6.8 TB/s (no MEASURED_PEAKS.json)"
+
+
+def bits_roofline(kernel, workload, cells, kernel_ms, bits_peak, bits_cell_peak, scalar_peak):
+    """Roofline of a bit-sliced kernel.  Score-only (bits_score): bound by the
+    ALU issue of its word operations, 16 per 32 cells, against the slowest of
+    the measured LOP3 / funnel-shift rates.  With pointers (bband_fill_ptr): it
+    also writes 0.25 B per window cell, so the line reports the HBM side as
+    the bound (pointer bytes per launch over the kernel's time against the
+    measured copy bandwidth) with the ALU side beside it."""
+    if not kernel_ms or not cells:
+        return {"bound": "alu", "kernel": kernel, "achieved": None, "peak": bits_peak, "unit": "Gop/s",
+                "frac": None, "traffic": dram_traffic(kernel, workload)}
+    sec = kernel_ms * 1e-3
+    ptr = kernel == "bband_fill_ptr"
+    ops32 = BITS_PTR_OPS_PER_32 if ptr else BITS_OPS_PER_32
+    alu_achieved = cells * ops32 / 32.0 / sec / 1e9
+    gcups = cells / sec / 1e9
+    alu = {"bound": "alu", "achieved": alu_achieved, "peak": bits_peak, "unit": "Gop/s",
+           "frac": alu_achieved / bits_peak, "ops_per_32_cells": ops32,
+           "peak_source": "measured live: slowest of nw_peak_int kinds 8/10 (LOP3, funnel shift; independent "
+                          "chains on every SM)"}
+    cell = {"unit": "GCUPS", "value": bits_cell_peak, "kernel_gcups": gcups, "frac": gcups / bits_cell_peak,
+            "source": "measured live: nw_peak_int kind 11, one bit-sliced anti-diagonal step (32 cells) on "
+                      "independent chains on every SM"}
+    scalar = {"ops_per_cell": OPS_PER_CELL, "achieved": gcups * OPS_PER_CELL, "peak": scalar_peak,
+              "frac": gcups * OPS_PER_CELL / scalar_peak,
+              "note": "the scalar unit (4 int32 ops per cell against the DPX/max/prmt peak): above 1 because one "
+                      "word op here updates a bit of 32 cells"}
+    base = {"kernel": kernel, "kernel_ms": kernel_ms, "cells_per_launch": cells,
+            "traffic": dram_traffic(kernel, workload),
+            "traffic_note": "DRAM bytes per launch (ncu, profiles/dram_traffic.json); algorithmic: 0.25 B per "
+                            "window cell of pointers for bband_fill_ptr, ~0 for score-only"}
+    if not ptr:
+        return {**alu, **base, "cell_peak": cell, "scalar_unit": scalar}
+    hbm, src = measured_hbm_gbs()
+    bytes_ = cells * 0.25
+    achieved = bytes_ / sec / 1e9
+    return {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s", "frac": achieved / hbm,
+            "bytes_per_launch": bytes_, "peak_source": src, **base, "alu": alu, "cell_peak": cell,
+            "scalar_unit": scalar}
 
 
 class _Null:

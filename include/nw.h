@@ -557,12 +557,14 @@ void nw_server_destroy(nw_server *srv);
 /* Integer-pipe peak microbenchmark used as the roofline denominator: every
  * SM runs independent dependency chains of one kind of work for `iters`
  * iterations; *gops receives the measured rate in 1e9 units per second,
- * where a unit is one lane-instruction for kinds 0-4, 8, 9 and one
- * score-only cell for kinds 5-7.  kind: 0 = add-then-max (__viaddmax_s32),
- * 1 = 3-input max (__vimax3_s32), 2 = 2-input max, 3 = 3-input add,
- * 4 = byte permute (prmt), 5 = cell as prmt + add-max + max, 6 = cell as
- * prmt + add + 3-input max, 7 = cell as prmt + add + max + max,
- * 8 = 3-input logic op, 9 = integer multiply-add.  Not in the paper. */
+ * where a unit is one lane-instruction for kinds 0-4, 8-10 and one
+ * score-only cell for kinds 5-7 and 11.  kind: 0 = add-then-max
+ * (__viaddmax_s32), 1 = 3-input max (__vimax3_s32), 2 = 2-input max,
+ * 3 = 3-input add, 4 = byte permute (prmt), 5 = cell as prmt + add-max +
+ * max, 6 = cell as prmt + add + 3-input max, 7 = cell as prmt + add + max +
+ * max, 8 = 3-input logic op, 9 = integer multiply-add, 10 = funnel shift,
+ * 11 = one anti-diagonal step of the bit-sliced difference update (32
+ * cells).  Not in the paper. */
 int nw_peak_int(nw_ctx *ctx, int kind, uint64_t iters, double *gops);
 
 #ifdef __cplusplus

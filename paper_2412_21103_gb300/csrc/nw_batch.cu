@@ -213,7 +213,8 @@ constexpr double kWarpRate = 2e9, kBatchRate = 3.5e12, kPairRate = 2e11, kPairFi
 
 // warp_cells[k]: cells pair k costs on one warp (scaled for slower
 // kernels), full_cells[k]: its full grid.  Returns the indices to route.
-static std::vector<size_t> pick_stragglers(const std::vector<double> &warp_cells, const std::vector<double> &full_cells) {
+static std::vector<size_t> pick_stragglers(const std::vector<double> &warp_cells, const std::vector<double> &full_cells,
+                                           double batch_rate = kBatchRate) {
     std::vector<size_t> order(warp_cells.size());
     std::iota(order.begin(), order.end(), (size_t)0);
     std::sort(order.begin(), order.end(), [&](size_t x, size_t y) { return warp_cells[x] > warp_cells[y]; });
@@ -223,7 +224,7 @@ static std::vector<size_t> pick_stragglers(const std::vector<double> &warp_cells
     size_t best_k = 0;
     for (size_t k = 0; k <= order.size(); ++k) {
         const double tail = k < order.size() ? warp_cells[order[k]] / kWarpRate : 0.0;
-        const double est = routed + std::max(rest / kBatchRate, tail);
+        const double est = routed + std::max(rest / batch_rate, tail);
         if (est < best) {
             best = est;
             best_k = k;
@@ -340,6 +341,101 @@ int batch_device_impl(nw_ctx *ctx, const uint8_t *pool, const uint64_t *a_off, c
                       const nw_scoring &sc, uint32_t flags, int32_t *scores, char *cigar_pool,
                       const uint64_t *cigar_off, uint64_t *cigar_len);
 
+// One banded round on the bit-sliced window kernel (nw_bits_band.cu) for
+// the items (half-widths iw): pairs that would keep the GPU waiting on one
+// warp go to `rest` (the full kernels), the others run in waves bounded by
+// pointer memory; each wave's certified pairs are walked into CIGARs, the
+// others return in next / nextw with their next widths.
+static int bits_round(nw_ctx *ctx, const uint8_t *pool, const uint32_t *pl0, const uint32_t *pl1, uint32_t plane_words,
+                      std::vector<BandBitsItem> &items, std::vector<uint32_t> &iw, int round, const nw_scoring &sc,
+                      uint32_t flags, int32_t *scores, uint32_t score_cap, char *cigar_pool, const uint64_t *cigar_off,
+                      uint64_t *cigar_len, std::vector<uint32_t> &next, std::vector<uint32_t> &nextw,
+                      std::vector<uint32_t> &rest) {
+    const bool want = flags & NW_CIGAR;
+    int rc;
+    {
+        // one warp of this kernel runs its pair at about the scalar batch
+        // kernel's per-warp rate; the whole kernel fills the GPU's 4 x 152
+        // schedulers
+        std::vector<double> wc(items.size()), fc(items.size());
+        for (size_t q = 0; q < items.size(); ++q) {
+            wc[q] = band_bits_seconds(items[q].shape) * kWarpRate;
+            fc[q] = (double)items[q].m * items[q].n;
+        }
+        const std::vector<size_t> strag = pick_stragglers(wc, fc, kWarpRate * 4.0 * ctx->sm_count);
+        if (!strag.empty()) {
+            std::vector<char> routed(items.size(), 0);
+            for (size_t q : strag) {
+                routed[q] = 1;
+                rest.push_back(items[q].out0);
+            }
+            std::vector<BandBitsItem> keep;
+            std::vector<uint32_t> keep_w;
+            for (size_t q = 0; q < items.size(); ++q)
+                if (!routed[q]) {
+                    keep.push_back(items[q]);
+                    keep_w.push_back(iw[q]);
+                }
+            items.swap(keep);
+            iw.swap(keep_w);
+        }
+    }
+    if (round == 0) ctx->band_stats[0] += items.size();
+    const uint64_t wave_budget = (ctx->budget - std::min(ctx->budget, ctx->used)) / 2;
+    size_t k0 = 0;
+    while (k0 < items.size()) {
+        std::vector<BandBitsItem> wave;
+        std::vector<uint32_t> ww;
+        uint64_t recs = 0;
+        size_t k = k0;
+        for (; k < items.size(); ++k) {
+            BandBitsItem it = items[k];
+            const uint64_t r = band_bits_records(it.shape);
+            if (want) {
+                if (!wave.empty() && (recs + r) * 16 > wave_budget) break;
+                it.ptr_off = recs;
+                recs += r;
+            }
+            ctx->band_stats[6] += r * 64u;  // cells: 2 anti-diagonals x 32 rows per record
+            wave.push_back(it);
+            ww.push_back(iw[k]);
+        }
+        void *pv = nullptr;
+        if (want && (rc = scratch(ctx, "bband_ptr", recs * 16 + 16, &pv))) return rc;
+        std::vector<int32_t> hs;
+        if ((rc = band_bits_fill(ctx, pl0, pl1, plane_words, wave, want, sc.gap, scores, score_cap, pv, recs, hs)))
+            return rc;
+        std::vector<uint32_t> cert;
+        for (size_t q = 0; q < wave.size(); ++q) {
+            const BandBitsItem &it = wave[q];
+            const uint32_t w = ww[q];
+            if (!band_certifies(it.m, it.n, w, hs[q], sc, want)) {
+                // the next round's width, kept within the window kernel's
+                // reach while this round was below it: a narrower band than
+                // the guaranteed one often certifies too, and a failed round
+                // on this kernel costs less than the scalar banded kernel
+                uint32_t nwid = band_next_width(it.m, it.n, w, hs[q], sc, want);
+                const uint32_t cap = band_bits_max_width(it.m, it.n);
+                if (nwid > cap && w < cap) nwid = cap;
+                next.push_back(it.out0);
+                nextw.push_back(nwid);
+                continue;
+            }
+            ctx->band_stats[1 + round] += 1;
+            if (it.out0 < ctx->band_round.size()) {
+                ctx->band_round[it.out0] = (uint8_t)(round + 1);
+                ctx->band_w_cert[it.out0] = w;
+            }
+            cert.push_back((uint32_t)q);
+        }
+        if (want && (rc = band_bits_walk(ctx, pv, wave, cert, pool, cigar_pool, cigar_off, cigar_len,
+                                         (flags & NW_CIGAR_M) ? 1u : 0u)))
+            return rc;
+        k0 = k;
+    }
+    return NW_OK;
+}
+
 // Banded rounds for the pairs in `ids` with starting half-widths w0[k]; the
 // pairs no round certifies are appended to `rest` for the full kernel.
 static int band_rounds(nw_ctx *ctx, const uint8_t *pool, const uint64_t *a_off, const uint32_t *a_len,
@@ -368,11 +464,36 @@ static int band_rounds(nw_ctx *ctx, const uint8_t *pool, const uint64_t *a_off, 
         free_prefix(ctx, "batch_ptr");
         free_prefix(ctx, "ptr");
     }
+    // the paper's scoring (s' = 3 on a match, 1 on a mismatch) runs on the
+    // bit-sliced window kernel, from a planar copy of the pool;
+    // NW_BAND_SCALAR=1 keeps every round on the scalar banded kernel (for
+    // comparisons)
+    const bool use_bits = sc.match - 2 * sc.gap == 3 && sc.mismatch - 2 * sc.gap == 1 && !getenv("NW_BAND_SCALAR");
+    const uint32_t *pl0 = nullptr, *pl1 = nullptr;
+    uint32_t plane_words = 0;
+    uint32_t score_cap_all = 0;
+    if (use_bits) {
+        uint64_t pool_bytes = 16;
+        for (uint32_t id : ids) {
+            pool_bytes = std::max<uint64_t>(pool_bytes, a_off[id] + (a_len[id] + 3) / 4);
+            pool_bytes = std::max<uint64_t>(pool_bytes, b_off[id] + (b_len[id] + 3) / 4);
+            score_cap_all = std::max(score_cap_all, id + 1);
+        }
+        plane_words = planes_words(pool_bytes);
+        void *v = nullptr;
+        if ((rc = scratch(ctx, "bband_planes", (size_t)plane_words * 8, &v))) return rc;
+        pl0 = (const uint32_t *)v;
+        pl1 = pl0 + plane_words;
+        if ((rc = launch_planes(ctx, pool, pool_bytes, plane_words, (uint32_t *)pl0, (uint32_t *)pl1))) return rc;
+    }
     for (int round = 0; round < kRounds && !pending.empty(); ++round) {
         size_t routed_full = 0;
         // the previous round's pointer words are traced already (stream
         // order): their slot does not count against this round's waves
-        if (want) free_prefix(ctx, "band_ptr");
+        if (want) {
+            free_prefix(ctx, "band_ptr");
+            free_prefix(ctx, "bband_ptr");
+        }
         // pairs whose band would cover most of the grid go straight to full
         std::vector<BatchTask> tasks;
         std::vector<uint32_t> tw;  // width used per task
@@ -402,7 +523,36 @@ static int band_rounds(nw_ctx *ctx, const uint8_t *pool, const uint64_t *a_off, 
             tasks.push_back(t);
             tw.push_back(width[q]);
         }
-        if (tasks.empty()) break;
+        if (use_bits && !tasks.empty()) {
+            // every pair whose band fits the window kernel (at most 8,192 rows)
+            std::vector<BandBitsItem> items;
+            std::vector<uint32_t> iw, keep_w;
+            std::vector<BatchTask> keep;
+            for (size_t q = 0; q < tasks.size(); ++q) {
+                const BatchTask &t = tasks[q];
+                BandBitsShape sh;
+                BatchTask tb = t;
+                uint32_t wq = tw[q];
+                const uint32_t cap = band_bits_max_width(t.m, t.n);
+                if (wq > cap && cap > 0) {  // a start wider than the window: start at the window's width
+                    wq = cap;
+                    band_task(tb, R, wq);
+                }
+                if (band_bits_shape(tb.m, tb.n, tb.lo, tb.hi, &sh)) {
+                    items.push_back(BandBitsItem{tb.a_off, tb.b_off, 0, tb.m, tb.n, tb.out0, sh});
+                    iw.push_back(wq);
+                } else {
+                    keep.push_back(t);
+                    keep_w.push_back(tw[q]);
+                }
+            }
+            tasks.swap(keep);
+            tw.swap(keep_w);
+            if (!items.empty() &&
+                (rc = bits_round(ctx, pool, pl0, pl1, plane_words, items, iw, round, sc, flags, scores, score_cap_all,
+                                 cigar_pool, cigar_off, cigar_len, next, nextw, rest)))
+                return rc;
+        }
         {
             // banded pairs that would leave the GPU idle on one warp run full
             // on the single-pair kernel instead (counted as fallbacks); a
@@ -430,7 +580,6 @@ static int band_rounds(nw_ctx *ctx, const uint8_t *pool, const uint64_t *a_off, 
                 tasks.swap(keep);
                 tw.swap(keep_w);
             }
-            if (tasks.empty()) break;
         }
         ctx->band_stats[0] += round == 0 ? tasks.size() : 0;
         // waves bounded by pointer memory (score-only: one wave)

@@ -41,35 +41,6 @@
 
 namespace nw {
 
-// Three-input logic operation with the truth table LUT (PTX lop3).
-template <uint32_t LUT>
-__device__ __forceinline__ uint32_t lop3(uint32_t a, uint32_t b, uint32_t c) {
-    uint32_t d;
-    asm("lop3.b32 %0, %1, %2, %3, %4;" : "=r"(d) : "r"(a), "r"(b), "r"(c), "n"(LUT));
-    return d;
-}
-// Truth tables from the canonical inputs a = 0xF0, b = 0xCC, c = 0xAA.
-constexpr uint32_t kA = 0xF0, kB = 0xCC, kC = 0xAA;
-constexpr uint32_t lut(uint32_t v) { return v & 0xFFu; }
-constexpr uint32_t kLutXorOrNotC = lut((kA ^ kB) | ~kC);     // (a ^ b) | ~c
-constexpr uint32_t kLutEq = lut(~(kA ^ kB) & ~kC);           // ~(a ^ b) & ~c
-constexpr uint32_t kLutAndOrNot = lut(kA & (kB | ~kC));      // a & (b | ~c)
-constexpr uint32_t kLutCOrNor = lut(kC | (~kA & ~kB));       // c | ~(a | b)
-constexpr uint32_t kLutOrAnd = lut(kA | (kB & kC));          // a | (b & c)
-constexpr uint32_t kLutOr3 = lut(kA | kB | kC);              // a | b | c
-constexpr uint32_t kLutXor3 = lut(kA ^ kB ^ kC);             // a ^ b ^ c
-constexpr uint32_t kLutAndNot = lut(kA & ~kB);               // a & ~b
-constexpr uint32_t kLutXorAnd = lut((kA ^ kB) & kC);         // (a ^ b) & c
-constexpr uint32_t kLutSel = lut((kA & kB) | (~kA & kC));    // a ? b : c
-constexpr uint32_t kLutAndNotOr = lut(kA & (~kB | kC));      // a & (~b | c)
-
-// 32 bits of a planar sequence plane starting at global base index g.
-__device__ __forceinline__ uint32_t plane_window(const uint32_t *pl, int64_t g) {
-    const uint64_t x = (uint64_t)(g + kPlanePad);
-    return __funnelshift_r(__ldg(pl + (x >> 5)), __ldg(pl + (x >> 5) + 1), (uint32_t)x & 31u);
-}
-
-
 // One anti-diagonal step of the 32 cells of a lane.  (H, V): the dH, dV
 // planes of the previous anti-diagonal; Q: the shift register of the stripe
 // boundary (bit 31 = the input bit of this step, the output bit enters at
@@ -223,6 +194,18 @@ __global__ void k_planes(const uint8_t *pool, uint64_t nbytes, uint32_t nwords, 
 }
 
 // ------------------------------------------------------------------ host
+int launch_planes(nw_ctx *ctx, const uint8_t *pool, uint64_t pool_bytes, uint32_t nwords, uint32_t *pl0,
+                  uint32_t *pl1) {
+    {
+        LaunchTimer t(ctx, "planes");
+        k_planes<<<(nwords + 255) / 256, 256, 0, ctx->stream>>>(pool, pool_bytes, nwords, pl0, pl1);
+    }
+    const cudaError_t e = cudaGetLastError();
+    return e == cudaSuccess ? NW_OK : cuda_fail(ctx, e, "planar pool launch");
+}
+
+uint32_t planes_words(uint64_t pool_bytes) { return (uint32_t)((pool_bytes * 4 + kPlanePad + 256) / 32); }
+
 bool bits_scoring_ok(const nw_scoring &sc) {
     const int32_t sm = sc.match - 2 * sc.gap, sx = sc.mismatch - 2 * sc.gap;
     return sx >= 0 && sx <= sm && sm <= 3;
@@ -289,7 +272,7 @@ int bits_prepare(nw_ctx *ctx, const uint8_t *pool, uint64_t pool_bytes, std::vec
                      [](const BitsJob &x, const BitsJob &y) { return (uint64_t)x.S * x.C > (uint64_t)y.S * y.C; });
 
     void *v = nullptr;
-    plan->nwords = (uint32_t)((pool_bytes * 4 + kPlanePad + 256) / 32);
+    plan->nwords = planes_words(pool_bytes);
     if ((rc = scratch(ctx, (prefix + "_planes").c_str(), (size_t)plan->nwords * 8, &v))) return rc;
     BitsArgs &ba = plan->ba;
     ba.pl0 = (const uint32_t *)v;
@@ -334,10 +317,7 @@ int bits_launch(nw_ctx *ctx, const BitsPlan &plan) {
     if (plan.ba.njobs == 0) return NW_OK;
     cudaMemsetAsync(plan.ba.counter, 0, 4, ctx->stream);
     uint32_t *pl0 = const_cast<uint32_t *>(plan.ba.pl0), *pl1 = const_cast<uint32_t *>(plan.ba.pl1);
-    {
-        LaunchTimer t(ctx, "planes");
-        k_planes<<<(plan.nwords + 255) / 256, 256, 0, ctx->stream>>>(plan.pool, plan.pool_bytes, plan.nwords, pl0, pl1);
-    }
+    if (int rc = launch_planes(ctx, plan.pool, plan.pool_bytes, plan.nwords, pl0, pl1)) return rc;
     {
         LaunchTimer t(ctx, "bits_score");
         if (plan.gen) k_bits_score<true><<<plan.blocks, kBitsWarps * 32, 0, ctx->stream>>>(plan.ba);

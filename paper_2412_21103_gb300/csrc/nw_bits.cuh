@@ -1,4 +1,5 @@
-// Bit-sliced score-only fill (nw_bits.cu): shared declarations.
+// Bit-sliced fills (nw_bits.cu: score-only batches; nw_bits_band.cu: the
+// certified band with pointers): shared declarations and device helpers.
 #pragma once
 
 #include <string>
@@ -10,6 +11,34 @@ namespace nw {
 
 constexpr int64_t kPlanePad = 64;  // bases of padding in front of base 0 of the planar pool
 constexpr int kBitsWarps = 8;      // warps per CTA
+
+// Three-input logic operation with the truth table LUT (PTX lop3).
+template <uint32_t LUT>
+__device__ __forceinline__ uint32_t lop3(uint32_t a, uint32_t b, uint32_t c) {
+    uint32_t d;
+    asm("lop3.b32 %0, %1, %2, %3, %4;" : "=r"(d) : "r"(a), "r"(b), "r"(c), "n"(LUT));
+    return d;
+}
+// Truth tables from the canonical inputs a = 0xF0, b = 0xCC, c = 0xAA.
+constexpr uint32_t kA = 0xF0, kB = 0xCC, kC = 0xAA;
+constexpr uint32_t lut(uint32_t v) { return v & 0xFFu; }
+constexpr uint32_t kLutXorOrNotC = lut((kA ^ kB) | ~kC);     // (a ^ b) | ~c
+constexpr uint32_t kLutEq = lut(~(kA ^ kB) & ~kC);           // ~(a ^ b) & ~c
+constexpr uint32_t kLutAndOrNot = lut(kA & (kB | ~kC));      // a & (b | ~c)
+constexpr uint32_t kLutCOrNor = lut(kC | (~kA & ~kB));       // c | ~(a | b)
+constexpr uint32_t kLutOrAnd = lut(kA | (kB & kC));          // a | (b & c)
+constexpr uint32_t kLutOr3 = lut(kA | kB | kC);              // a | b | c
+constexpr uint32_t kLutXor3 = lut(kA ^ kB ^ kC);             // a ^ b ^ c
+constexpr uint32_t kLutAndNot = lut(kA & ~kB);               // a & ~b
+constexpr uint32_t kLutXorAnd = lut((kA ^ kB) & kC);         // (a ^ b) & c
+constexpr uint32_t kLutSel = lut((kA & kB) | (~kA & kC));    // a ? b : c
+constexpr uint32_t kLutAndNotOr = lut(kA & (~kB | kC));      // a & (~b | c)
+
+// 32 bits of a planar sequence plane starting at global base index g.
+__device__ __forceinline__ uint32_t plane_window(const uint32_t *pl, int64_t g) {
+    const uint64_t x = (uint64_t)(g + kPlanePad);
+    return __funnelshift_r(__ldg(pl + (x >> 5)), __ldg(pl + (x >> 5) + 1), (uint32_t)x & 31u);
+}
 
 // The two planes of s' for a general scoring with 0 <= s'x <= s'm <= 3:
 // bit k of s'(match) / s'(mismatch) as all-ones or zero words.
@@ -47,6 +76,11 @@ struct BitsPlan {
     bool gen = false;
 };
 
+// Planar copy of the packed pool (words of the two planes: planes_words).
+uint32_t planes_words(uint64_t pool_bytes);
+int launch_planes(nw_ctx *ctx, const uint8_t *pool, uint64_t pool_bytes, uint32_t nwords, uint32_t *pl0,
+                  uint32_t *pl1);
+
 // 0 <= s'(mismatch) <= s'(match) <= 3, s' = s - 2*gap: every difference fits two bits.
 bool bits_scoring_ok(const nw_scoring &sc);
 // Bytes of the pool the tasks read.
@@ -58,5 +92,38 @@ int bits_prepare(nw_ctx *ctx, const uint8_t *pool, uint64_t pool_bytes, std::vec
 // Enqueues the planar copy of the pool and the fill (no host copies: it can
 // be captured into a graph).
 int bits_launch(nw_ctx *ctx, const BitsPlan &plan);
+
+// ---- the certified band on the bit-sliced window (nw_bits_band.cu)
+// Window of one pair: g lanes (a power of two) x Q words of 32 rows, its
+// anchor diagonal hi (the band's upper diagonal raised to the parity of
+// m+n), and its anti-diagonals a_first .. m+n in chunks of 64.
+struct BandBitsShape {
+    uint32_t g = 1, Q = 1, nchunks = 0;
+    int32_t hi = 0, a_first = 0;
+};
+// One banded pair of a round: pool offsets, sizes, score slot, window, and
+// its first pointer record (16 bytes per word and pair of anti-diagonals).
+struct BandBitsItem {
+    uint64_t a_off, b_off, ptr_off;
+    uint32_t m, n, out0;
+    BandBitsShape shape;
+};
+// The window of the band of diagonals [lo, hi]; false when it needs more
+// than 128 words (4,096 rows).
+bool band_bits_shape(uint32_t m, uint32_t n, int32_t lo, int32_t hi, BandBitsShape *s);
+uint64_t band_bits_records(const BandBitsShape &s);  // pointer records of the pair
+// The widest half-width whose band fits the window of an m x n pair.
+uint32_t band_bits_max_width(uint32_t m, uint32_t n);
+double band_bits_seconds(const BandBitsShape &s);    // estimated time of the pair on one warp
+// Fills the items (the paper's scoring: s' = 3 on a match, 1 on a
+// mismatch), writes scores[out0], returns the banded scores in item order,
+// and with `want` the pointer records at ptr + ptr_off.
+int band_bits_fill(nw_ctx *ctx, const uint32_t *pl0, const uint32_t *pl1, uint32_t plane_words,
+                   const std::vector<BandBitsItem> &items, bool want, int32_t gap, int32_t *scores, uint32_t score_cap,
+                   void *ptr, uint64_t ptr_records, std::vector<int32_t> &banded);
+// Walks the items `which` of a filled wave and writes their CIGARs.
+int band_bits_walk(nw_ctx *ctx, const void *ptr, const std::vector<BandBitsItem> &items,
+                   const std::vector<uint32_t> &which, const uint8_t *pool, char *cigar_pool,
+                   const uint64_t *cigar_off, uint64_t *cigar_len, uint32_t mflag);
 
 }  // namespace nw

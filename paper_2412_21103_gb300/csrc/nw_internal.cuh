@@ -82,7 +82,7 @@ constexpr bool kChecks = false;
 #endif
 enum CheckSite : uint32_t {
     kSiteBatchPtr = 1, kSiteBatchRing, kSiteBatchScore, kSiteLocalPtr, kSiteLocalRing, kSiteLocalOut,
-    kSiteLocalMoves, kSiteAffPtr, kSiteAffRing, kSiteAffScore, kSiteAffMoves, kSiteMsaRow, kSiteMsaSlot
+    kSiteLocalMoves, kSiteAffPtr, kSiteAffRing, kSiteAffScore, kSiteAffMoves, kSiteMsaRow, kSiteMsaSlot, kSiteBandBitsPtr
 };
 __device__ __forceinline__ bool in_range(uint64_t idx, uint64_t cap, uint32_t *err, uint32_t site) {
     if constexpr (kChecks) {
