@@ -126,7 +126,7 @@ def parse():
     ap.add_argument("--duration", type=float, default=3.0, help="serve: seconds of arrivals")
     ap.add_argument("--serve-pool", type=int, default=1500, help="serve: distinct requests the stream cycles through")
     ap.add_argument("--serve-workers", type=int, default=8, help="serve: worker threads (contexts, streams)")
-    ap.add_argument("--serve-batch", type=int, default=64, help="serve: most requests one admission takes")
+    ap.add_argument("--serve-batch", type=int, default=1024, help="serve: most requests one admission takes")
     ap.add_argument("--npairs", type=int, default=None,
                     help="pairs of the band / local / affine workloads (full: 20,000 / 4,000 / 2,000)")
     ap.add_argument("--no-clocks", action="store_true")

@@ -346,13 +346,22 @@ int batch_device_impl(nw_ctx *ctx, const uint8_t *pool, const uint64_t *a_off, c
 // warp go to `rest` (the full kernels), the others run in waves bounded by
 // pointer memory; each wave's certified pairs are walked into CIGARs, the
 // others return in next / nextw with their next widths.
-static int bits_round(nw_ctx *ctx, const uint8_t *pool, const uint32_t *pl0, const uint32_t *pl1, uint32_t plane_words,
-                      std::vector<BandBitsItem> &items, std::vector<uint32_t> &iw, int round, const nw_scoring &sc,
+static int bits_round(nw_ctx *ctx, const uint8_t *pool, const PlaneSet &planes, std::vector<BandBitsItem> &items, std::vector<uint32_t> &iw, int round, const nw_scoring &sc,
                       uint32_t flags, int32_t *scores, uint32_t score_cap, char *cigar_pool, const uint64_t *cigar_off,
                       uint64_t *cigar_len, std::vector<uint32_t> &next, std::vector<uint32_t> &nextw,
                       std::vector<uint32_t> &rest) {
     const bool want = flags & NW_CIGAR;
     int rc;
+    {
+        // pairs that would take longer on their warp than the whole round
+        // ideally takes (the GPU's 4 x 152 schedulers busy) spread their
+        // window over more lanes
+        double total = 0;
+        for (const auto &it : items) total += band_bits_seconds(it.shape);
+        const double ideal = total / (4.0 * ctx->sm_count);
+        for (auto &it : items)
+            if (band_bits_seconds(it.shape) > ideal) band_bits_fast(&it.shape);
+    }
     {
         // one warp of this kernel runs its pair at about the scalar batch
         // kernel's per-warp rate; the whole kernel fills the GPU's 4 x 152
@@ -403,7 +412,7 @@ static int bits_round(nw_ctx *ctx, const uint8_t *pool, const uint32_t *pl0, con
         void *pv = nullptr;
         if (want && (rc = scratch(ctx, "bband_ptr", recs * 16 + 16, &pv))) return rc;
         std::vector<int32_t> hs;
-        if ((rc = band_bits_fill(ctx, pl0, pl1, plane_words, wave, want, sc.gap, scores, score_cap, pv, recs, hs)))
+        if ((rc = band_bits_fill(ctx, planes, wave, want, sc.gap, scores, score_cap, pv, recs, hs)))
             return rc;
         std::vector<uint32_t> cert;
         for (size_t q = 0; q < wave.size(); ++q) {
@@ -469,22 +478,22 @@ static int band_rounds(nw_ctx *ctx, const uint8_t *pool, const uint64_t *a_off, 
     // NW_BAND_SCALAR=1 keeps every round on the scalar banded kernel (for
     // comparisons)
     const bool use_bits = sc.match - 2 * sc.gap == 3 && sc.mismatch - 2 * sc.gap == 1 && !getenv("NW_BAND_SCALAR");
-    const uint32_t *pl0 = nullptr, *pl1 = nullptr;
-    uint32_t plane_words = 0;
+    PlaneSet planes;
+    std::vector<int64_t> a_slot, b_slot;  // by position in ids
     uint32_t score_cap_all = 0;
+    std::vector<uint32_t> pos_of;         // pair id -> position in ids
     if (use_bits) {
-        uint64_t pool_bytes = 16;
-        for (uint32_t id : ids) {
-            pool_bytes = std::max<uint64_t>(pool_bytes, a_off[id] + (a_len[id] + 3) / 4);
-            pool_bytes = std::max<uint64_t>(pool_bytes, b_off[id] + (b_len[id] + 3) / 4);
+        a_slot.resize(ids.size());
+        b_slot.resize(ids.size());
+        for (size_t q = 0; q < ids.size(); ++q) {
+            const uint32_t id = ids[q];
+            a_slot[q] = planes.add(a_off[id], a_len[id]);
+            b_slot[q] = planes.add(b_off[id], b_len[id]);
             score_cap_all = std::max(score_cap_all, id + 1);
         }
-        plane_words = planes_words(pool_bytes);
-        void *v = nullptr;
-        if ((rc = scratch(ctx, "bband_planes", (size_t)plane_words * 8, &v))) return rc;
-        pl0 = (const uint32_t *)v;
-        pl1 = pl0 + plane_words;
-        if ((rc = launch_planes(ctx, pool, pool_bytes, plane_words, (uint32_t *)pl0, (uint32_t *)pl1))) return rc;
+        pos_of.assign(score_cap_all, 0u);
+        for (size_t q = 0; q < ids.size(); ++q) pos_of[ids[q]] = (uint32_t)q;
+        if ((rc = planes.launch(ctx, pool, "bband"))) return rc;
     }
     for (int round = 0; round < kRounds && !pending.empty(); ++round) {
         size_t routed_full = 0;
@@ -534,12 +543,21 @@ static int band_rounds(nw_ctx *ctx, const uint8_t *pool, const uint64_t *a_off, 
                 BatchTask tb = t;
                 uint32_t wq = tw[q];
                 const uint32_t cap = band_bits_max_width(t.m, t.n);
-                if (wq > cap && cap > 0) {  // a start wider than the window: start at the window's width
+                if (wq > cap && cap > 0) {
+                    if (round == 0) {
+                        // a starting width beyond the window (a prediction that
+                        // the pair needs a wider band): straight to the full kernel
+                        rest.push_back(t.out0);
+                        continue;
+                    }
+                    // a next width beyond it: the window's widest band first
+                    // (the guaranteed width is often wider than needed)
                     wq = cap;
                     band_task(tb, R, wq);
                 }
                 if (band_bits_shape(tb.m, tb.n, tb.lo, tb.hi, &sh)) {
-                    items.push_back(BandBitsItem{tb.a_off, tb.b_off, 0, tb.m, tb.n, tb.out0, sh});
+                    const uint32_t pq = pos_of[tb.out0];
+                    items.push_back(BandBitsItem{tb.a_off, tb.b_off, 0, a_slot[pq], b_slot[pq], tb.m, tb.n, tb.out0, sh});
                     iw.push_back(wq);
                 } else {
                     keep.push_back(t);
@@ -549,7 +567,7 @@ static int band_rounds(nw_ctx *ctx, const uint8_t *pool, const uint64_t *a_off, 
             tasks.swap(keep);
             tw.swap(keep_w);
             if (!items.empty() &&
-                (rc = bits_round(ctx, pool, pl0, pl1, plane_words, items, iw, round, sc, flags, scores, score_cap_all,
+                (rc = bits_round(ctx, pool, planes, items, iw, round, sc, flags, scores, score_cap_all,
                                  cigar_pool, cigar_off, cigar_len, next, nextw, rest)))
                 return rc;
         }
@@ -889,7 +907,7 @@ int batch_device_impl(nw_ctx *ctx, const uint8_t *pool, const uint64_t *a_off, c
         BitsPlan bp;
         if (bits) {
             std::vector<BatchTask> bt = lpt;
-            if ((rc = bits_prepare(ctx, pool, bits_pool_bytes(bt), bt, sc, scores, bs.score_cap, pre, &bp))) return rc;
+            if ((rc = bits_prepare(ctx, pool, bt, sc, scores, bs.score_cap, pre, &bp))) return rc;
         }
         auto run = [&](int r) { return r == 32 ? bits_launch(ctx, bp) : launch_batch(ctx, r, false, bs, max_n, 0, pre); };
         if ((rc = tune_rows(ctx, lpt, bits ? 32 : R, run, &R, bits))) return rc;
@@ -1250,7 +1268,7 @@ extern "C" int nw_score_all_pairs(nw_ctx *ctx, const uint8_t *pool2b, const uint
     BitsPlan bp;
     if (bits) {
         std::vector<BatchTask> bt = tasks;
-        if ((rc = bits_prepare(ctx, pool, bits_pool_bytes(bt), bt, sc, dout, nseq * nseq, pre, &bp))) return rc;
+        if ((rc = bits_prepare(ctx, pool, bt, sc, dout, nseq * nseq, pre, &bp))) return rc;
     }
     BatchTask *dt = nullptr;
     if ((rc = upload(ctx, (pre + "_tasks").c_str(), tasks, &dt))) return rc;

@@ -113,7 +113,7 @@ __global__ void __launch_bounds__(kBitsWarps * 32) k_bits_score(BitsArgs p) {
         const uint32_t S = job.S, C = job.C;
         int32_t W = 0;
         if (S > 0) {
-            const int64_t Ag = (int64_t)tk.a_off * 4, Bg = (int64_t)tk.b_off * 4;
+            const int64_t Ag = (int64_t)tk.a_off, Bg = (int64_t)tk.b_off;  // planar slots
             const int32_t top0 = (int32_t)m - 32 * (int32_t)S;  // row above bit 0 of stripe 0
             for (uint32_t s = 0; s < S; ++s) {
                 const int32_t pad = min(max(-top0 - 32 * (int32_t)s, 0), 32);  // padding rows of this stripe
@@ -173,51 +173,84 @@ __device__ __forceinline__ uint32_t even_bits(uint64_t x) {
     return (uint32_t)x;
 }
 
-// Planar copy of a packed pool: word w of plane k holds bit k of the codes
-// of global bases 32w-64 .. 32w-33+32 (bases outside the pool read as 0).
-__global__ void k_planes(const uint8_t *pool, uint64_t nbytes, uint32_t nwords, uint32_t *pl0, uint32_t *pl1) {
-    for (uint32_t w = blockIdx.x * blockDim.x + threadIdx.x; w < nwords; w += gridDim.x * blockDim.x) {
-        const int64_t b0 = ((int64_t)w * 32 - kPlanePad) / 4;  // first byte (kPlanePad is a multiple of 32)
-        uint64_t v = 0;
-        if (b0 >= 0 && (uint64_t)b0 + 8 <= nbytes) {
+// Planar copy of the launch's sequences: one warp per sequence; word w of
+// its slot holds bit k of the codes of its bases 32w .. 32w+31 (bases past
+// its end read as 0).
+__global__ void k_planes(const uint8_t *pool, const PlaneSeg *segs, uint32_t nsegs, uint32_t *pl0, uint32_t *pl1) {
+    const uint32_t lane = threadIdx.x & 31u;
+    for (uint32_t sg = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; sg < nsegs; sg += (gridDim.x * blockDim.x) >> 5) {
+        const PlaneSeg seg = segs[sg];
+        const uint8_t *src = pool + seg.src;
+        const uint32_t words = (seg.nbytes + 7) / 8;
+        for (uint32_t w = lane; w < words; w += 32) {
+            uint64_t v = 0;
+            const uint32_t b0 = 8 * w;
+            if (b0 + 8 <= seg.nbytes) {
 #pragma unroll
-            for (int k = 0; k < 8; ++k) v |= (uint64_t)pool[b0 + k] << (8 * k);
-        } else {
-            for (int k = 0; k < 8; ++k) {
-                const int64_t b = b0 + k;
-                if (b >= 0 && (uint64_t)b < nbytes) v |= (uint64_t)pool[b] << (8 * k);
+                for (int k = 0; k < 8; ++k) v |= (uint64_t)src[b0 + k] << (8 * k);
+            } else {
+                for (uint32_t k = 0; b0 + k < seg.nbytes; ++k) v |= (uint64_t)src[b0 + k] << (8 * k);
             }
+            pl0[seg.dst + w] = even_bits(v);
+            pl1[seg.dst + w] = even_bits(v >> 1);
         }
-        pl0[w] = even_bits(v);
-        pl1[w] = even_bits(v >> 1);
     }
 }
 
 // ------------------------------------------------------------------ host
-int launch_planes(nw_ctx *ctx, const uint8_t *pool, uint64_t pool_bytes, uint32_t nwords, uint32_t *pl0,
-                  uint32_t *pl1) {
-    {
-        LaunchTimer t(ctx, "planes");
-        k_planes<<<(nwords + 255) / 256, 256, 0, ctx->stream>>>(pool, pool_bytes, nwords, pl0, pl1);
-    }
-    const cudaError_t e = cudaGetLastError();
-    return e == cudaSuccess ? NW_OK : cuda_fail(ctx, e, "planar pool launch");
+int64_t PlaneSet::add(uint64_t off, uint32_t len) {
+    const Key k{off, len};
+    auto it = slots_.find(k);
+    if (it != slots_.end()) return it->second;
+    const uint32_t nbytes = (len + 3) / 4;
+    const int64_t slot = (int64_t)words_ * 32 - kPlanePad;
+    segs_.push_back(PlaneSeg{off, nbytes, (uint32_t)words_});
+    words_ += (nbytes + 7) / 8 + 2;
+    slots_.emplace(k, slot);
+    return slot;
 }
 
-uint32_t planes_words(uint64_t pool_bytes) { return (uint32_t)((pool_bytes * 4 + kPlanePad + 256) / 32); }
+int PlaneSet::prepare(nw_ctx *ctx, const std::string &prefix) {
+    int rc;
+    void *v = nullptr;
+    const uint64_t words = words_ + 4;  // room for the last window's second word
+    if (words >= (1ull << 32)) return fail(ctx, NW_ERR_ARG, "planar copy of more than 2^37 bases");
+    if ((rc = scratch(ctx, (prefix + "_planes").c_str(), (size_t)words * 8, &v))) return rc;
+    planes_ = (uint32_t *)v;
+    pl0 = planes_;
+    pl1 = planes_ + words;
+    max_base = (int64_t)words * 32 - kPlanePad - 64;
+    if ((rc = scratch(ctx, (prefix + "_plane_segs").c_str(), segs_.size() * sizeof(PlaneSeg) + 16, &v))) return rc;
+    dsegs_ = (PlaneSeg *)v;
+    if (!segs_.empty()) {
+        cudaError_t e = cudaMemcpyAsync(dsegs_, segs_.data(), segs_.size() * sizeof(PlaneSeg), cudaMemcpyHostToDevice,
+                                        ctx->stream);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(ctx->stream);  // the table is host memory of this object
+        if (e != cudaSuccess) return cuda_fail(ctx, e, "planar segments H2D");
+    }
+    return NW_OK;
+}
+
+int PlaneSet::enqueue(nw_ctx *ctx, const uint8_t *pool) const {
+    if (segs_.empty()) return NW_OK;
+    {
+        LaunchTimer t(ctx, "planes");
+        const uint32_t blocks = (uint32_t)std::min<size_t>((segs_.size() + 7) / 8, 4096);
+        k_planes<<<blocks, 256, 0, ctx->stream>>>(pool, dsegs_, (uint32_t)segs_.size(), planes_,
+                                                  planes_ + (words_ + 4));
+    }
+    const cudaError_t e = cudaGetLastError();
+    return e == cudaSuccess ? NW_OK : cuda_fail(ctx, e, "planar copy launch");
+}
+
+int PlaneSet::launch(nw_ctx *ctx, const uint8_t *pool, const std::string &prefix) {
+    const int rc = prepare(ctx, prefix);
+    return rc ? rc : enqueue(ctx, pool);
+}
 
 bool bits_scoring_ok(const nw_scoring &sc) {
     const int32_t sm = sc.match - 2 * sc.gap, sx = sc.mismatch - 2 * sc.gap;
     return sx >= 0 && sx <= sm && sm <= 3;
-}
-
-uint64_t bits_pool_bytes(const std::vector<BatchTask> &tasks) {
-    uint64_t b = 16;
-    for (const auto &t : tasks) {
-        b = std::max<uint64_t>(b, t.a_off + (t.m + 3) / 4);
-        b = std::max<uint64_t>(b, t.b_off + (t.n + 3) / 4);
-    }
-    return b;
 }
 
 template <typename T>
@@ -234,8 +267,8 @@ static int bits_upload(nw_ctx *ctx, const std::string &slot, const std::vector<T
     return NW_OK;
 }
 
-int bits_prepare(nw_ctx *ctx, const uint8_t *pool, uint64_t pool_bytes, std::vector<BatchTask> &tasks,
-                 const nw_scoring &sc, int32_t *scores, uint32_t score_cap, const std::string &prefix, BitsPlan *plan) {
+int bits_prepare(nw_ctx *ctx, const uint8_t *pool, std::vector<BatchTask> &tasks, const nw_scoring &sc,
+                 int32_t *scores, uint32_t score_cap, const std::string &prefix, BitsPlan *plan) {
     int rc;
     *plan = BitsPlan{};
     if (tasks.empty()) return NW_OK;
@@ -272,11 +305,16 @@ int bits_prepare(nw_ctx *ctx, const uint8_t *pool, uint64_t pool_bytes, std::vec
                      [](const BitsJob &x, const BitsJob &y) { return (uint64_t)x.S * x.C > (uint64_t)y.S * y.C; });
 
     void *v = nullptr;
-    plan->nwords = planes_words(pool_bytes);
-    if ((rc = scratch(ctx, (prefix + "_planes").c_str(), (size_t)plan->nwords * 8, &v))) return rc;
+    // the tasks address their sequences by planar slot
+    for (auto &t : tasks) {
+        if (!t.m || !t.n) continue;
+        t.a_off = (uint64_t)plan->planes.add(t.a_off, t.m);
+        t.b_off = (uint64_t)plan->planes.add(t.b_off, t.n);
+    }
+    if ((rc = plan->planes.prepare(ctx, prefix))) return rc;
     BitsArgs &ba = plan->ba;
-    ba.pl0 = (const uint32_t *)v;
-    ba.pl1 = (const uint32_t *)v + plan->nwords;
+    ba.pl0 = plan->planes.pl0;
+    ba.pl1 = plan->planes.pl1;
     BatchTask *dt = nullptr;
     BitsJob *dj = nullptr;
     if ((rc = bits_upload(ctx, prefix + "_bits_tasks", tasks, &dt))) return rc;
@@ -309,15 +347,13 @@ int bits_prepare(nw_ctx *ctx, const uint8_t *pool, uint64_t pool_bytes, std::vec
     if ((rc = scratch(ctx, (prefix + "_bits_counter").c_str(), 16, &v))) return rc;
     ba.counter = (uint32_t *)v;
     plan->pool = pool;
-    plan->pool_bytes = pool_bytes;
     return NW_OK;
 }
 
 int bits_launch(nw_ctx *ctx, const BitsPlan &plan) {
     if (plan.ba.njobs == 0) return NW_OK;
     cudaMemsetAsync(plan.ba.counter, 0, 4, ctx->stream);
-    uint32_t *pl0 = const_cast<uint32_t *>(plan.ba.pl0), *pl1 = const_cast<uint32_t *>(plan.ba.pl1);
-    if (int rc = launch_planes(ctx, plan.pool, plan.pool_bytes, plan.nwords, pl0, pl1)) return rc;
+    if (int rc = plan.planes.enqueue(ctx, plan.pool)) return rc;
     {
         LaunchTimer t(ctx, "bits_score");
         if (plan.gen) k_bits_score<true><<<plan.blocks, kBitsWarps * 32, 0, ctx->stream>>>(plan.ba);

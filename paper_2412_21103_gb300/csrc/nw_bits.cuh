@@ -3,6 +3,7 @@
 #pragma once
 
 #include <string>
+#include <unordered_map>
 #include <vector>
 
 #include "nw_internal.cuh"
@@ -52,8 +53,8 @@ struct BitsJob {
 };
 
 struct BitsArgs {
-    const uint32_t *pl0, *pl1;  // planar pool: bit k of global base g at word (g+64)>>5, bit (g+64)&31
-    const BatchTask *tasks;
+    const uint32_t *pl0, *pl1;  // planar sequences: bit k of global base g at word (g+64)>>5, bit (g+64)&31
+    const BatchTask *tasks;     // a_off / b_off: the sequences' slots (global base indices)
     const BitsJob *jobs;
     uint32_t njobs;
     uint32_t *counter;
@@ -66,28 +67,62 @@ struct BitsArgs {
     uint32_t *err;
 };
 
+// Planar copy of the sequences a launch reads.  Each distinct sequence
+// (pool byte offset, length) gets a slot of whole 32-base words, two words
+// apart; a kernel addresses base i of the sequence as global base index
+// slot + i.  Only the launch's own sequences are copied, wherever they lie
+// in the pool.
+struct PlaneSeg {
+    uint64_t src;      // pool byte offset of the sequence
+    uint32_t nbytes;   // its packed bytes
+    uint32_t dst;      // first word of its slot
+};
+class PlaneSet {
+  public:
+    // Slot (global base index of base 0) of the sequence at pool byte `off`
+    // with `len` bases, added on first use.
+    int64_t add(uint64_t off, uint32_t len);
+    // Enqueues the copy (one H2D table, one kernel); pl0 / pl1 receive the
+    // two planes, max_base the largest base index a 32-bit window may start at.
+    int launch(nw_ctx *ctx, const uint8_t *pool, const std::string &prefix);
+    // Uploads the segment table and sizes the planes without copying (the
+    // copy can then be enqueued, also into a graph, by enqueue()).
+    int prepare(nw_ctx *ctx, const std::string &prefix);
+    int enqueue(nw_ctx *ctx, const uint8_t *pool) const;
+    const uint32_t *pl0 = nullptr, *pl1 = nullptr;
+    int64_t max_base = 0;
+
+  private:
+    struct Key {
+        uint64_t off;
+        uint32_t len;
+        bool operator==(const Key &o) const { return off == o.off && len == o.len; }
+    };
+    struct KeyHash {
+        size_t operator()(const Key &k) const { return std::hash<uint64_t>()(k.off * 0x9E3779B97F4A7C15ull ^ k.len); }
+    };
+    std::unordered_map<Key, int64_t, KeyHash> slots_;
+    std::vector<PlaneSeg> segs_;
+    uint64_t words_ = 2;  // kPlanePad bases in front of the first slot
+    PlaneSeg *dsegs_ = nullptr;
+    uint32_t *planes_ = nullptr;
+};
+
 // Everything a launch needs, prepared (sorted, uploaded, scratch sized)
 // ahead of the launch so that the launch itself only enqueues kernels.
 struct BitsPlan {
     BitsArgs ba{};
-    uint32_t blocks = 0, nwords = 0;
+    uint32_t blocks = 0;
     const uint8_t *pool = nullptr;
-    uint64_t pool_bytes = 0;
+    PlaneSet planes;
     bool gen = false;
 };
 
-// Planar copy of the packed pool (words of the two planes: planes_words).
-uint32_t planes_words(uint64_t pool_bytes);
-int launch_planes(nw_ctx *ctx, const uint8_t *pool, uint64_t pool_bytes, uint32_t nwords, uint32_t *pl0,
-                  uint32_t *pl1);
-
 // 0 <= s'(mismatch) <= s'(match) <= 3, s' = s - 2*gap: every difference fits two bits.
 bool bits_scoring_ok(const nw_scoring &sc);
-// Bytes of the pool the tasks read.
-uint64_t bits_pool_bytes(const std::vector<BatchTask> &tasks);
 // Orients, groups and uploads the tasks (reordered in place), sizes the
 // scratch; scores[out0] (and scores[out1]) receive each task's score.
-int bits_prepare(nw_ctx *ctx, const uint8_t *pool, uint64_t pool_bytes, std::vector<BatchTask> &tasks,
+int bits_prepare(nw_ctx *ctx, const uint8_t *pool, std::vector<BatchTask> &tasks,
                  const nw_scoring &sc, int32_t *scores, uint32_t score_cap, const std::string &prefix, BitsPlan *plan);
 // Enqueues the planar copy of the pool and the fill (no host copies: it can
 // be captured into a graph).
@@ -100,17 +135,22 @@ int bits_launch(nw_ctx *ctx, const BitsPlan &plan);
 struct BandBitsShape {
     uint32_t g = 1, Q = 1, nchunks = 0;
     int32_t hi = 0, a_first = 0;
+    uint32_t words = 1;  // the band needs this many 32-row words (g * Q >= words)
 };
 // One banded pair of a round: pool offsets, sizes, score slot, window, and
 // its first pointer record (16 bytes per word and pair of anti-diagonals).
 struct BandBitsItem {
-    uint64_t a_off, b_off, ptr_off;
+    uint64_t a_off, b_off, ptr_off;  // pool byte offsets (the walk), first pointer record
+    int64_t a_slot, b_slot;          // the sequences' planar slots (the fill)
     uint32_t m, n, out0;
     BandBitsShape shape;
 };
 // The window of the band of diagonals [lo, hi]; false when it needs more
 // than 128 words (4,096 rows).
 bool band_bits_shape(uint32_t m, uint32_t n, int32_t lo, int32_t hi, BandBitsShape *s);
+// The same window spread over as many lanes as it has words (up to 32):
+// fewer instructions per lane and step, so a shorter time for the pair.
+void band_bits_fast(BandBitsShape *s);
 uint64_t band_bits_records(const BandBitsShape &s);  // pointer records of the pair
 // The widest half-width whose band fits the window of an m x n pair.
 uint32_t band_bits_max_width(uint32_t m, uint32_t n);
@@ -118,8 +158,7 @@ double band_bits_seconds(const BandBitsShape &s);    // estimated time of the pa
 // Fills the items (the paper's scoring: s' = 3 on a match, 1 on a
 // mismatch), writes scores[out0], returns the banded scores in item order,
 // and with `want` the pointer records at ptr + ptr_off.
-int band_bits_fill(nw_ctx *ctx, const uint32_t *pl0, const uint32_t *pl1, uint32_t plane_words,
-                   const std::vector<BandBitsItem> &items, bool want, int32_t gap, int32_t *scores, uint32_t score_cap,
+int band_bits_fill(nw_ctx *ctx, const PlaneSet &planes, const std::vector<BandBitsItem> &items, bool want, int32_t gap, int32_t *scores, uint32_t score_cap,
                    void *ptr, uint64_t ptr_records, std::vector<int32_t> &banded);
 // Walks the items `which` of a filled wave and writes their CIGARs.
 int band_bits_walk(nw_ctx *ctx, const void *ptr, const std::vector<BandBitsItem> &items,

@@ -53,7 +53,7 @@ constexpr int kWalkWarps = 4;
 constexpr int kBandWarps = 4;
 
 struct BandBitsTask {
-    uint64_t a_off, b_off;  // pool byte offsets of A (rows) and B (columns)
+    int64_t a_slot, b_slot; // planar slots of A (rows) and B (columns)
     uint64_t ptr_off;       // first pointer record of the pair (16-byte units)
     uint32_t m, n;
     int32_t hi;             // window anchor: the band's upper diagonal, raised to the parity of m+n
@@ -125,7 +125,7 @@ __device__ __forceinline__ void band_job(const BandBitsArgs &p, const BandBitsJo
     const int32_t gq = (int32_t)g * Q, Hw = 32 * gq;
     const int32_t a0 = t.a_first;
     const int32_t R = (a0 - t.hi - 1) >> 1;  // r0(a_first); a_first - hi is odd
-    const int64_t Ag = (int64_t)t.a_off * 4, Bg = (int64_t)t.b_off * 4;
+    const int64_t Ag = t.a_slot, Bg = t.b_slot;
     auto ld = [&](const uint32_t *pl, int64_t gidx) {
         return plane_window(pl, min(max(gidx, -kPlanePad), p.max_base));  // outside: bases of no cell that matters
     };
@@ -336,14 +336,21 @@ bool band_bits_shape(uint32_t m, uint32_t n, int32_t lo, int32_t hi, BandBitsSha
     const int32_t hip = hi + (int32_t)(((int64_t)m + n - hi) & 1);
     const int64_t words = ((int64_t)hip - lo + 4 + 63) / 64;
     if (words > kBandBitsMaxWords) return false;
-    // the fewest lanes with at most kBandBitsMaxQ words each (longer pairs
-    // get more lanes and fewer words per lane: less time per step)
+    // throughput shape: the fewest lanes with at most kBandBitsMaxQ words
+    // each (a lane's fixed work per step is shared by more words)
     s->g = std::min<uint32_t>(32, next_pow2((uint32_t)((words + kBandBitsMaxQ - 1) / kBandBitsMaxQ)));
     s->Q = (uint32_t)((words + s->g - 1) / s->g);
+    s->words = (uint32_t)words;
     s->hi = hip;
     s->nchunks = (uint32_t)(((uint64_t)m + n + 1 + 63) / 64);
     s->a_first = (int32_t)((int64_t)m + n + 1 - 64 * (int64_t)s->nchunks);
     return true;
+}
+
+void band_bits_fast(BandBitsShape *s) {
+    // latency shape: one word per lane while 32 lanes suffice, else 32 lanes
+    s->g = std::min<uint32_t>(32, next_pow2(s->words));
+    s->Q = (s->words + s->g - 1) / s->g;
 }
 
 uint32_t band_bits_max_width(uint32_t m, uint32_t n) {
@@ -361,8 +368,7 @@ double band_bits_seconds(const BandBitsShape &s) {
     return (double)s.nchunks * 64.0 * (20.0 * s.Q + 14.0) * 2.0 / 2.07e9;
 }
 
-int band_bits_fill(nw_ctx *ctx, const uint32_t *pl0, const uint32_t *pl1, uint32_t plane_words,
-                   const std::vector<BandBitsItem> &items, bool want, int32_t gap, int32_t *scores, uint32_t score_cap,
+int band_bits_fill(nw_ctx *ctx, const PlaneSet &planes, const std::vector<BandBitsItem> &items, bool want, int32_t gap, int32_t *scores, uint32_t score_cap,
                    void *ptr, uint64_t ptr_records, std::vector<int32_t> &banded) {
     int rc;
     banded.assign(items.size(), 0);
@@ -386,8 +392,8 @@ int band_bits_fill(nw_ctx *ctx, const uint32_t *pl0, const uint32_t *pl1, uint32
                items[order[k]].shape.Q == s0.Q) {
             const BandBitsItem &it = items[order[k]];
             BandBitsTask &t = tasks[k];
-            t.a_off = it.a_off;
-            t.b_off = it.b_off;
+            t.a_slot = it.a_slot;
+            t.b_slot = it.b_slot;
             t.ptr_off = it.ptr_off;
             t.m = it.m;
             t.n = it.n;
@@ -421,9 +427,9 @@ int band_bits_fill(nw_ctx *ctx, const uint32_t *pl0, const uint32_t *pl1, uint32
     if (e == cudaSuccess) e = cudaMemsetAsync(cnt, 0, 4, ctx->stream);
     if (e != cudaSuccess) return cuda_fail(ctx, e, "banded bit-sliced tasks H2D");
     BandBitsArgs a{};
-    a.pl0 = pl0;
-    a.pl1 = pl1;
-    a.max_base = (int64_t)plane_words * 32 - kPlanePad - 64;
+    a.pl0 = planes.pl0;
+    a.pl1 = planes.pl1;
+    a.max_base = planes.max_base;
     a.tasks = dt;
     a.jobs = dj;
     a.njobs = (uint32_t)jobs.size();
