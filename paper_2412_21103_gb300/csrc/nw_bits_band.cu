@@ -266,10 +266,13 @@ struct BitsWalkTask {
 // words around the walk's position into shared memory, then lane 0 walks
 // from (m, n) while the cells stay inside them; moves are written in walk
 // order (0 diagonal, 1 vertical, 2 horizontal), as the CIGAR assembly reads.
+// While lane 0 walks one block, the loads of the 32 records before it (the
+// same words) are in flight; they fill the second buffer, which the walk
+// continues in unless it left those words (then a new block is staged).
 __global__ void __launch_bounds__(kWalkWarps * 32) k_bits_walk(const uint4 *ptr, const BitsWalkTask *tasks,
                                                                uint32_t ntasks, uint8_t *moves, uint64_t *nmoves,
                                                                uint32_t *err) {
-    __shared__ uint4 tile[kWalkWarps][32][3];
+    __shared__ uint4 tile[kWalkWarps][2][32][3];
     const uint32_t lane = threadIdx.x & 31u, wb = threadIdx.x >> 5;
     const uint32_t nw = gridDim.x * kWalkWarps;
     for (uint32_t ti = blockIdx.x * kWalkWarps + wb; ti < ntasks; ti += nw) {
@@ -279,36 +282,50 @@ __global__ void __launch_bounds__(kWalkWarps * 32) k_bits_walk(const uint4 *ptr,
         int32_t i = (int32_t)tk.m, j = (int32_t)tk.n;
         uint64_t k = 0;
         const int32_t gq = (int32_t)tk.gq;
-        bool ok = true;
+        bool ok = true, have = false;
+        int32_t ds_lo = 0, w_lo = 0, cur = 0;
         while (ok && i > 0 && j > 0) {
             const int32_t a = i + j, ds = (a - tk.a_first) >> 1;
             const int32_t W = (i - ((a - tk.hi) >> 1)) >> 5;
-            const int32_t ds_lo = max(ds - 31, 0), w_lo = max(min(W - 1, gq - 3), 0);
-            __syncwarp();
-            if (ds_lo + (int32_t)lane <= ds) {
+            bool staged = false;
+            if (!have || ds < ds_lo || ds > ds_lo + 31 || W < w_lo || W > w_lo + 2) {
+                // the 32 records ending at the walk's position, staged now
+                ds_lo = max(ds - 31, 0);
+                w_lo = max(min(W - 1, gq - 3), 0);
+                __syncwarp();
+                if (ds_lo + (int32_t)lane <= ds) {
 #pragma unroll
-                for (int x = 0; x < 3; ++x)
-                    if (w_lo + x < gq) tile[wb][lane][x] = __ldcg(pp + (uint64_t)(ds_lo + (int32_t)lane) * gq + w_lo + x);
+                    for (int x = 0; x < 3; ++x)
+                        if (w_lo + x < gq)
+                            tile[wb][cur][lane][x] = __ldcg(pp + (uint64_t)(ds_lo + (int32_t)lane) * gq + w_lo + x);
+                }
+                __syncwarp();
+                have = staged = true;
             }
-            __syncwarp();
+            // the 32 records before the block: loads issued now, stored after the walk
+            const int32_t nds = ds_lo - 32, rec = nds + (int32_t)lane;
+            uint4 r[3];
+#pragma unroll
+            for (int x = 0; x < 3; ++x)
+                r[x] = (rec >= 0 && w_lo + x < gq) ? __ldcg(pp + (uint64_t)rec * gq + w_lo + x) : make_uint4(0, 0, 0, 0);
             if (lane == 0) {
                 uint32_t steps = 0;
                 while (i > 0 && j > 0) {
                     const int32_t a2 = i + j, rel = a2 - tk.a_first, d2 = rel >> 1;
                     const int32_t P = i - ((a2 - tk.hi) >> 1), W2 = P >> 5;
-                    if (d2 < ds_lo || W2 < w_lo || W2 > w_lo + 2 || W2 >= gq || P < 0) break;
-                    const uint4 rec = tile[wb][d2 - ds_lo][W2 - w_lo];
+                    if (d2 < ds_lo || d2 > ds_lo + 31 || W2 < w_lo || W2 > w_lo + 2 || W2 >= gq || P < 0) break;
+                    const uint4 rc = tile[wb][cur][d2 - ds_lo][W2 - w_lo];
                     const uint32_t bit = (uint32_t)P & 31u;
-                    const uint32_t L = (rel & 1) ? rec.z : rec.x, Hb = (rel & 1) ? rec.w : rec.y;
+                    const uint32_t L = (rel & 1) ? rc.z : rc.x, Hb = (rel & 1) ? rc.w : rc.y;
                     const uint32_t mvc = !((L >> bit) & 1u) ? 0u : !((Hb >> bit) & 1u) ? 1u : 2u;
                     mv[k++] = (uint8_t)mvc;
                     i -= mvc != 2u;
                     j -= mvc != 1u;
                     ++steps;
                 }
-                // the staged block held the walk's own cell: no progress means
-                // the walk left the window, which a certified band excludes
-                if (steps == 0) {
+                // a block staged at the walk's own cell: no progress means the
+                // walk left the window, which a certified band excludes
+                if (staged && steps == 0) {
                     raise_error(err, NW_ERR_ARG, 0x50000u + ti);
                     ok = false;
                 }
@@ -317,6 +334,19 @@ __global__ void __launch_bounds__(kWalkWarps * 32) k_bits_walk(const uint4 *ptr,
             j = __shfl_sync(kFull, j, 0);
             k = __shfl_sync(kFull, k, 0);
             ok = __shfl_sync(kFull, ok, 0);
+            if (nds + 31 >= 0) {
+                // the prefetched block becomes the current one
+                __syncwarp();
+                if (rec >= 0) {
+#pragma unroll
+                    for (int x = 0; x < 3; ++x) tile[wb][cur ^ 1][lane][x] = r[x];
+                }
+                __syncwarp();
+                cur ^= 1;
+                ds_lo = nds;
+            } else {
+                have = false;
+            }
         }
         const uint32_t rest = (uint32_t)(max(i, 0) + max(j, 0));
         const uint8_t mvr = i > 0 ? 1 : 2;
@@ -469,16 +499,21 @@ int band_bits_walk(nw_ctx *ctx, const void *ptr, const std::vector<BandBitsItem>
                    const uint64_t *cigar_off, uint64_t *cigar_len, uint32_t mflag) {
     if (which.empty()) return NW_OK;
     int rc;
+    // longest walks first: the kernel's warps take pairs in order
+    std::vector<uint32_t> order(which);
+    std::stable_sort(order.begin(), order.end(), [&](uint32_t x, uint32_t y) {
+        return (uint64_t)items[x].m + items[x].n > (uint64_t)items[y].m + items[y].n;
+    });
     uint64_t mbytes = 0;
-    for (uint32_t k : which) mbytes += (uint64_t)items[k].m + items[k].n + 16;
+    for (uint32_t k : order) mbytes += (uint64_t)items[k].m + items[k].n + 16;
     void *mv = nullptr, *nm = nullptr, *v = nullptr;
     if ((rc = scratch(ctx, "bband_moves", mbytes + 16, &mv))) return rc;
     if ((rc = scratch(ctx, "bband_nmoves", which.size() * 8 + 16, &nm))) return rc;
     std::vector<BitsWalkTask> wt(which.size());
     std::vector<TraceTask> tt(which.size());
     uint64_t mpos = 0;
-    for (size_t q = 0; q < which.size(); ++q) {
-        const BandBitsItem &it = items[which[q]];
+    for (size_t q = 0; q < order.size(); ++q) {
+        const BandBitsItem &it = items[order[q]];
         wt[q] = BitsWalkTask{it.ptr_off, mpos, it.m, it.n, it.shape.g * it.shape.Q, it.shape.hi, it.shape.a_first,
                              (uint32_t)q};
         TraceTask x{};
