@@ -77,10 +77,13 @@ typedef enum {
                                  banded score itself, no certificate or
                                  fallback (score only; for inspection)      */
 #define NW_GRAPH        64u   /* nw_score_all_pairs / score-only nw_align_batch
-                                 on device buffers: capture the launches into a
-                                 CUDA graph kept on the context, keyed by every
-                                 pointer, size and host metadata of the call;
-                                 a repeated call replays it (see below)     */
+                                 on device buffers (nw_score_all_pairs also
+                                 with NW_HOST_IO: the pool is copied to the
+                                 context's device slot first): capture the
+                                 launches into a CUDA graph kept on the
+                                 context, keyed by every pointer, size and host
+                                 metadata of the call; a repeated call replays
+                                 it (see below)                             */
 #define NW_RECOMPUTE    32u   /* nw_align with NW_CIGAR: take the stripe-
                                  checkpoint recompute path even when the
                                  pointer matrix fits (see nw_align)         */

@@ -217,6 +217,7 @@ class Context:
         self.device = device
 
     def close(self):
+        self._cigar_host = None
         if getattr(self, "handle", None):
             load().nw_ctx_destroy(self.handle)
             self.handle = None
@@ -346,6 +347,19 @@ def _cigar_offsets(a_len, b_len) -> np.ndarray:
     return out
 
 
+def _host_cigar_pool(ctx: "Context", nbytes: int) -> np.ndarray:
+    """A host CIGAR pool of at least nbytes, kept on the context and reused
+    by later host-mode calls (the library writes each pair's bytes at its
+    offset; the strings returned are copies, so reuse is safe).  Reuse
+    avoids faulting in a fresh buffer sized by the worst-case bound on every
+    call."""
+    buf = getattr(ctx, "_cigar_host", None)
+    if buf is None or buf.size < nbytes:
+        buf = np.empty(max(nbytes, 1), np.uint8)
+        ctx._cigar_host = buf
+    return buf
+
+
 def _cigars(cpool: np.ndarray, off, length, npairs: int) -> list[str]:
     mv = memoryview(cpool)
     return [str(mv[o:o + n], "ascii") for o, n in zip(np.asarray(off[:npairs]).tolist(),
@@ -370,7 +384,7 @@ def nw_align_batch(ctx: Context, pool2b, a_off, a_len, b_off, b_len, scoring=DEF
     if _is_host(pool2b):
         flags |= NW_HOST_IO
         sc_out = np.zeros(max(npairs, 1), np.int32)
-        cpool = np.zeros(max(int(co[-1]) if want else 1, 1), np.uint8)
+        cpool = _host_cigar_pool(ctx, int(co[-1]) if want else 1)
         clen = np.zeros(max(npairs, 1), np.uint64)
         rc = L.nw_align_batch(ctx.handle, _ptr(pool2b), aop, alp, bop, blp, npairs, _sc(scoring), flags,
                               _ptr(sc_out), _ptr(cpool) if want else None, cop, _ptr(clen) if want else None)
@@ -404,7 +418,7 @@ def nw_local_align_batch(ctx: Context, pool2b, a_off, a_len, b_off, b_len, scori
         flags |= NW_HOST_IO
         sc_out = np.zeros(max(npairs, 1), np.int32)
         e_out = np.zeros((max(npairs, 1), 4), np.uint32)
-        cpool = np.zeros(max(int(co[-1]) if want else 1, 1), np.uint8)
+        cpool = _host_cigar_pool(ctx, int(co[-1]) if want else 1)
         clen = np.zeros(max(npairs, 1), np.uint64)
         rc = L.nw_local_align_batch(ctx.handle, _ptr(pool2b), aop, alp, bop, blp, npairs, _sc(scoring), flags,
                                     _ptr(sc_out), _ptr(e_out), _ptr(cpool) if want else None, cop,
@@ -437,7 +451,7 @@ def nw_affine_align_batch(ctx: Context, pool2b, a_off, a_len, b_off, b_len, scor
     if _is_host(pool2b):
         flags |= NW_HOST_IO
         sc_out = np.zeros(max(npairs, 1), np.int32)
-        cpool = np.zeros(max(int(co[-1]) if want else 1, 1), np.uint8)
+        cpool = _host_cigar_pool(ctx, int(co[-1]) if want else 1)
         clen = np.zeros(max(npairs, 1), np.uint64)
         rc = L.nw_affine_align_batch(ctx.handle, _ptr(pool2b), aop, alp, bop, blp, npairs, sc, flags, _ptr(sc_out),
                                      _ptr(cpool) if want else None, cop, _ptr(clen) if want else None)
@@ -467,7 +481,7 @@ def nw_align_batch_banded(ctx: Context, pool2b, a_off, a_len, b_off, b_len, band
     if _is_host(pool2b):
         flags |= NW_HOST_IO
         sc_out = np.zeros(max(npairs, 1), np.int32)
-        cpool = np.zeros(max(int(co[-1]) if want else 1, 1), np.uint8)
+        cpool = _host_cigar_pool(ctx, int(co[-1]) if want else 1)
         clen = np.zeros(max(npairs, 1), np.uint64)
         rc = L.nw_align_batch_banded(ctx.handle, _ptr(pool2b), aop, alp, bop, blp, npairs, wwp, _sc(scoring), flags,
                                      _ptr(sc_out), _ptr(cpool) if want else None, cop, _ptr(clen) if want else None)

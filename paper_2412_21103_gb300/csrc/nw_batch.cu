@@ -1067,12 +1067,13 @@ static int with_host_io(nw_ctx *ctx, const uint8_t *pool2b, const uint64_t *a_of
                                                        (const uint64_t *)dlen, (const uint64_t *)ddst, npairs,
                                                        (char *)dpk);
     }
-    std::vector<char> host(packed[npairs]);
-    if (packed[npairs])
-        cudaMemcpyAsync(host.data(), dpk, packed[npairs], cudaMemcpyDeviceToHost, ctx->stream);
+    void *hv = nullptr;  // the packed bytes land in pinned staging (one DMA, no zero fill)
+    if ((rc = pinned_host(ctx, packed[npairs] + 16, &hv))) return rc;
+    const char *host = (const char *)hv;
+    if (packed[npairs]) cudaMemcpyAsync(hv, dpk, packed[npairs], cudaMemcpyDeviceToHost, ctx->stream);
     if ((rc = nw_ctx_sync(ctx))) return rc;
     for (uint32_t k = 0; k < npairs; ++k) {
-        memcpy(cigar_pool + cigar_off[k], host.data() + packed[k], cigar_len[k]);
+        memcpy(cigar_pool + cigar_off[k], host + packed[k], cigar_len[k]);
         if (cigar_off[k] + cigar_len[k] < cigar_off[k + 1]) cigar_pool[cigar_off[k] + cigar_len[k]] = '\0';
     }
     return NW_OK;
@@ -1207,19 +1208,11 @@ extern "C" int nw_score_all_pairs(nw_ctx *ctx, const uint8_t *pool2b, const uint
     for (uint32_t i = 0; i < nseq; ++i)
         if ((rc = check_len(ctx, sc, len[i], len[i]))) return rc;
     const bool graph = flags & NW_GRAPH;
-    if (graph && (flags & NW_HOST_IO)) return fail(ctx, NW_ERR_ARG, "NW_GRAPH needs device buffers");
-    std::string gkey, pre = "batch";
-    if (graph) {
-        // a repeated call replays its captured launches
-        const uint64_t h = hash_bytes(len, (size_t)nseq * 4, hash_bytes(off, (size_t)nseq * 8, 1469598103934665603ull));
-        gkey = batch_key("allpairs", pool2b, out, nseq, sc, flags, h);
-        bool replayed = false;
-        if ((rc = graph_launch(ctx, gkey, "batch_score", 2, &replayed)) || replayed) return rc;
-        pre = "g" + std::to_string(++ctx->graph_seq);
-    }
     const uint8_t *pool = pool2b;
     int32_t *dout = out;
     if (flags & NW_HOST_IO) {
+        // host buffers: the pool goes to a device slot first (also before a
+        // graph replay, which reads that slot), the matrix comes back at the end
         uint64_t pool_bytes = 16;
         for (uint32_t i = 0; i < nseq; ++i) pool_bytes = std::max<uint64_t>(pool_bytes, off[i] + (len[i] + 3) / 4);
         void *dp = nullptr, *dq = nullptr;
@@ -1227,6 +1220,23 @@ extern "C" int nw_score_all_pairs(nw_ctx *ctx, const uint8_t *pool2b, const uint
         if ((rc = scratch(ctx, "hio_matrix", (size_t)nseq * nseq * 4, &dq))) return rc;
         pool = (const uint8_t *)dp;
         dout = (int32_t *)dq;
+    }
+    auto copy_back = [&]() -> int {
+        if (!(flags & NW_HOST_IO)) return NW_OK;
+        cudaError_t e = cudaMemcpyAsync(out, dout, (size_t)nseq * nseq * 4, cudaMemcpyDeviceToHost, ctx->stream);
+        if (e != cudaSuccess) return cuda_fail(ctx, e, "matrix D2H");
+        return nw_ctx_sync(ctx);
+    };
+    std::string gkey, pre = "batch";
+    if (graph) {
+        // a repeated call replays its captured launches (keyed by the device
+        // buffers they read and write)
+        const uint64_t h = hash_bytes(len, (size_t)nseq * 4, hash_bytes(off, (size_t)nseq * 8, 1469598103934665603ull));
+        gkey = batch_key("allpairs", pool, dout, nseq, sc, flags, h);
+        bool replayed = false;
+        if ((rc = graph_launch(ctx, gkey, "batch_score", 2, &replayed))) return rc;
+        if (replayed) return copy_back();
+        pre = "g" + std::to_string(++ctx->graph_seq);
     }
     // n(n-1)/2 pairs (Eq. 2), each written to both triangle entries
     std::vector<BatchTask> tasks;
@@ -1290,11 +1300,5 @@ extern "C" int nw_score_all_pairs(nw_ctx *ctx, const uint8_t *pool2b, const uint
     if (graph && (rc = capture_graph(ctx, gkey, pre, R == 32 ? "bits_score" : "batch_score", R == 32 ? 3 : 2,
                                      launches)))
         return rc;
-    cudaError_t e = cudaSuccess;
-    if (flags & NW_HOST_IO) {
-        e = cudaMemcpyAsync(out, dout, (size_t)nseq * nseq * 4, cudaMemcpyDeviceToHost, ctx->stream);
-        if (e != cudaSuccess) return cuda_fail(ctx, e, "matrix D2H");
-        return nw_ctx_sync(ctx);
-    }
-    return NW_OK;
+    return copy_back();
 }

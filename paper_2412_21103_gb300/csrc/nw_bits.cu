@@ -180,7 +180,7 @@ __global__ void k_planes(const uint8_t *pool, const PlaneSeg *segs, uint32_t nse
     const uint32_t lane = threadIdx.x & 31u;
     for (uint32_t sg = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; sg < nsegs; sg += (gridDim.x * blockDim.x) >> 5) {
         const PlaneSeg seg = segs[sg];
-        const uint8_t *src = pool + seg.src;
+        const uint8_t *src = pool ? pool + seg.src : reinterpret_cast<const uint8_t *>(seg.src);  // offset or address
         const uint32_t words = (seg.nbytes + 7) / 8;
         for (uint32_t w = lane; w < words; w += 32) {
             uint64_t v = 0;

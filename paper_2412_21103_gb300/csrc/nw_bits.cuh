@@ -73,7 +73,7 @@ struct BitsArgs {
 // slot + i.  Only the launch's own sequences are copied, wherever they lie
 // in the pool.
 struct PlaneSeg {
-    uint64_t src;      // pool byte offset of the sequence
+    uint64_t src;      // pool byte offset of the sequence (its device address when the pool is null)
     uint32_t nbytes;   // its packed bytes
     uint32_t dst;      // first word of its slot
 };
@@ -84,6 +84,7 @@ class PlaneSet {
     int64_t add(uint64_t off, uint32_t len);
     // Enqueues the copy (one H2D table, one kernel); pl0 / pl1 receive the
     // two planes, max_base the largest base index a 32-bit window may start at.
+    // With a null pool the offsets given to add() are device addresses.
     int launch(nw_ctx *ctx, const uint8_t *pool, const std::string &prefix);
     // Uploads the segment table and sizes the planes without copying (the
     // copy can then be enqueued, also into a graph, by enqueue()).
@@ -127,6 +128,14 @@ int bits_prepare(nw_ctx *ctx, const uint8_t *pool, std::vector<BatchTask> &tasks
 // Enqueues the planar copy of the pool and the fill (no host copies: it can
 // be captured into a graph).
 int bits_launch(nw_ctx *ctx, const BitsPlan &plan);
+
+// ---- one long pair on the bit-sliced stripes (nw_bits_pair.cu)
+// Whether the pair runs there (the paper's scoring, long enough to spread
+// over several warps, every warp co-resident, pointers within the budget).
+bool bits_pair_takes(nw_ctx *ctx, uint32_t m, uint32_t n, const nw_scoring &sc, bool want);
+// Score (and with `want` the CIGAR, written by the CIGAR assembly) of one pair.
+int bits_pair(nw_ctx *ctx, const uint8_t *a2b, uint32_t m, const uint8_t *b2b, uint32_t n, const nw_scoring &sc,
+              bool want, uint32_t mflag, int32_t *score, char *cigar, uint64_t *cigar_len);
 
 // ---- the certified band on the bit-sliced window (nw_bits_band.cu)
 // Window of one pair: g lanes (a power of two) x Q words of 32 rows, its

@@ -284,6 +284,9 @@ int capture_graph(nw_ctx *ctx, const std::string &key, const std::string &prefix
 
 // Copy helpers for NW_HOST_IO.
 int to_device(nw_ctx *ctx, const void *host, size_t bytes, const char *slot, void **dev);
+// Pinned host staging of at least `bytes` owned by the context (grown on
+// demand, kept until nw_ctx_destroy); one user at a time per context.
+int pinned_host(nw_ctx *ctx, size_t bytes, void **out);
 
 }  // namespace nw
 

@@ -212,6 +212,23 @@ int graph_store(nw_ctx *ctx, const std::string &key, const std::string &prefix, 
     return NW_OK;
 }
 
+int pinned_host(nw_ctx *ctx, size_t bytes, void **out) {
+    if (bytes > ctx->pinned_cap) {
+        if (ctx->pinned) cudaFreeHost(ctx->pinned);
+        ctx->pinned = nullptr;
+        ctx->pinned_cap = 0;
+        const size_t cap = std::max<size_t>(bytes + bytes / 4, 1u << 20);
+        const cudaError_t e = cudaHostAlloc(&ctx->pinned, cap, cudaHostAllocDefault);
+        if (e != cudaSuccess) {
+            ctx->pinned = nullptr;
+            return cuda_fail(ctx, e, "pinned staging");
+        }
+        ctx->pinned_cap = cap;
+    }
+    *out = ctx->pinned;
+    return NW_OK;
+}
+
 int to_device(nw_ctx *ctx, const void *host, size_t bytes, const char *slot, void **dev) {
     int rc = scratch(ctx, slot, bytes, dev);
     if (rc) return rc;

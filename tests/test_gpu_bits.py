@@ -164,3 +164,24 @@ def test_preloaded_bits_choice_maps_to_a_pointer_kernel_for_cigars(ctx):
     want = oracle.align_many(pairs)
     assert s1.tolist() == [s for s, _ in want] and s2.tolist() == [s for s, _ in want]
     assert cig == [oracle.rle(ops) for _, ops in want]
+
+
+def test_host_buffers_graph_replay(ctx):
+    """All-pairs with host buffers under NW_GRAPH: the pool is copied to the
+    context's device slot before every call, so a replay of the captured
+    launches reads the new contents; results stay exact."""
+    import paper_2412_21103_gb300 as nw
+    rs = seqgen.Stream(450)
+    seqs = [rs.bases(int(L)) for L in rs.integers(40, 350, 20)]
+    pool, off, ln = nw.pool_of(seqs)
+    before = ctx.graph_stats()
+    for _ in range(2):
+        M = nw.nw_score_all_pairs(ctx, pool, off, ln, (1, -1, -1), nw.NW_GRAPH)
+        assert np.array_equal(M, _oracle_matrix(seqs, (1, -1, -1)))
+    seqs2 = [rs.bases(int(L)) for L in ln]
+    pool2, off2, ln2 = nw.pool_of(seqs2)
+    assert np.array_equal(off2, off) and np.array_equal(ln2, ln)
+    M2 = nw.nw_score_all_pairs(ctx, pool2, off, ln, (1, -1, -1), nw.NW_GRAPH)
+    assert np.array_equal(M2, _oracle_matrix(seqs2, (1, -1, -1)))
+    after = ctx.graph_stats()
+    assert after["replays"] >= before["replays"] + 2
