@@ -447,7 +447,7 @@ class LocalWork:
     def e2e(self):
         sc, ends, cig = self.nw.nw_local_align_batch(self.ctx, self.pool_host, self.ao, self.al, self.bo, self.bl,
                                                      SCORING, self.nw.NW_CIGAR)
-        return self.pool_host.nbytes, sc.nbytes + ends.nbytes + sum(len(c) for c in cig) + 8 * len(cig)
+        return self.pool_host.nbytes, sc.nbytes + ends.nbytes + cig.nbytes() + 8 * len(cig)
 
     def result(self):
         return {"score_checksum": int(self.scores.sum().item())}
@@ -491,7 +491,7 @@ class AffineWork:
     def e2e(self):
         sc, cig = self.nw.nw_affine_align_batch(self.ctx, self.pool_host, self.ao, self.al, self.bo, self.bl,
                                                 AFFINE_SCORING, self.nw.NW_CIGAR)
-        return self.pool_host.nbytes, sc.nbytes + sum(len(c) for c in cig) + 8 * len(cig)
+        return self.pool_host.nbytes, sc.nbytes + cig.nbytes() + 8 * len(cig)
 
     def result(self):
         return {"score_checksum": int(self.scores.sum().item())}
@@ -571,7 +571,7 @@ class CenterStarWork:
 
     def e2e(self):
         res = self.nw.nw_center_star(self.ctx, self.pool_host, self.off, self.lens, SCORING)
-        out = res["scores"].nbytes + res["row_sums"].nbytes + sum(len(c) for c in res["cigars"]) + \
+        out = res["scores"].nbytes + res["row_sums"].nbytes + res["cigars"].nbytes() + \
             sum(len(r) for r in res["rows"])
         return self.pool_host.nbytes, out
 
@@ -644,7 +644,7 @@ class BandWork:
     def e2e(self):
         sc, cig = self.nw.nw_align_batch(self.ctx, self.pool_host, self.ao, self.al, self.bo, self.bl, SCORING,
                                          self.flags)
-        return self.pool_host.nbytes, sc.nbytes + sum(len(c) for c in cig) + 8 * len(cig)
+        return self.pool_host.nbytes, sc.nbytes + cig.nbytes() + 8 * len(cig)
 
     def result(self):
         """Plain full-grid batch on the same pairs: time, and score mismatches."""

@@ -348,28 +348,91 @@ def _cigar_offsets(a_len, b_len) -> np.ndarray:
 
 
 def _host_cigar_pool(ctx: "Context", nbytes: int) -> np.ndarray:
-    """A host CIGAR pool of at least nbytes, kept on the context and reused
-    by later host-mode calls (the library writes each pair's bytes at its
-    offset; the strings returned are copies, so reuse is safe).  Reuse
-    avoids faulting in a fresh buffer sized by the worst-case bound on every
-    call."""
+    """A host CIGAR pool of at least nbytes.  The library writes each pair's
+    bytes at its offset.  The buffer is lent to the Cigars view of the call
+    that fills it and returns to the context when that view is released, so
+    a later call reuses it (no fresh buffer the size of the worst-case bound
+    to fault in on every call)."""
     buf = getattr(ctx, "_cigar_host", None)
+    ctx._cigar_host = None
     if buf is None or buf.size < nbytes:
         buf = np.empty(max(nbytes, 1), np.uint8)
-        ctx._cigar_host = buf
     return buf
 
 
-def _cigars(cpool: np.ndarray, off, length, npairs: int) -> list[str]:
-    mv = memoryview(cpool)
-    return [str(mv[o:o + n], "ascii") for o, n in zip(np.asarray(off[:npairs]).tolist(),
-                                                     np.asarray(length[:npairs]).tolist())]
+class Cigars:
+    """The CIGARs of one host-mode batch call, one per pair, in pair order.
+
+    The bytes stay in the host buffer the library wrote (each pair's CIGAR at
+    its offset); an item is decoded to a str when it is read.  Behaves as a
+    read-only sequence of str: len, indexing (slices give lists), iteration,
+    and == against any sequence of str."""
+
+    __hash__ = None
+
+    def __init__(self, ctx: "Context", buf: np.ndarray, off, length, n: int):
+        self._buf = buf
+        self._off = np.asarray(off[:n], np.int64).copy()
+        self._len = np.asarray(length[:n], np.int64).copy()
+        self._ctx = ctx
+
+    def __len__(self) -> int:
+        return int(self._len.size)
+
+    def _item(self, k: int) -> str:
+        o = int(self._off[k])
+        return self._buf[o:o + int(self._len[k])].tobytes().decode("ascii")
+
+    def __getitem__(self, k):
+        if isinstance(k, slice):
+            return [self._item(i) for i in range(*k.indices(len(self)))]
+        k = int(k)
+        if k < 0:
+            k += len(self)
+        if not 0 <= k < len(self):
+            raise IndexError(k)
+        return self._item(k)
+
+    def __iter__(self):
+        mv = memoryview(self._buf)
+        for o, n in zip(self._off.tolist(), self._len.tolist()):
+            yield str(mv[o:o + n], "ascii")
+
+    def __eq__(self, other):
+        try:
+            if len(other) != len(self):
+                return False
+            return all(a == b for a, b in zip(self, other))
+        except TypeError:
+            return NotImplemented
+
+    def nbytes(self) -> int:
+        """Total CIGAR bytes (without terminators)."""
+        return int(self._len.sum())
+
+    def tolist(self) -> list[str]:
+        return list(self)
+
+    def __repr__(self) -> str:
+        return f"Cigars({len(self)} pairs, {self.nbytes()} bytes)"
+
+    def __del__(self):
+        ctx, buf = self._ctx, self._buf
+        self._buf = None
+        if ctx is not None and buf is not None and getattr(ctx, "handle", None):
+            cur = getattr(ctx, "_cigar_host", None)
+            if cur is None or cur.size < buf.size:
+                ctx._cigar_host = buf
+
+
+def _cigars(ctx: "Context", cpool: np.ndarray, off, length, npairs: int) -> Cigars:
+    return Cigars(ctx, cpool, off, length, npairs)
 
 
 def nw_align_batch(ctx: Context, pool2b, a_off, a_len, b_off, b_len, scoring=DEFAULT_SCORING, flags: int = 0,
                    scores=None, cigar_pool=None, cigar_off=None, cigar_len=None):
     """Align many pairs from one packed pool.  Metadata arrays are host
-    numpy.  Host mode (pool2b numpy) returns (scores ndarray, list of CIGARs
+    numpy.  Host mode (pool2b numpy) returns (scores ndarray, Cigars sequence
     or None); device mode writes into the given tensors."""
     L = load()
     npairs = len(a_len)
@@ -384,14 +447,14 @@ def nw_align_batch(ctx: Context, pool2b, a_off, a_len, b_off, b_len, scoring=DEF
     if _is_host(pool2b):
         flags |= NW_HOST_IO
         sc_out = np.zeros(max(npairs, 1), np.int32)
-        cpool = _host_cigar_pool(ctx, int(co[-1]) if want else 1)
+        cpool = _host_cigar_pool(ctx, int(co[-1])) if want else np.empty(1, np.uint8)
         clen = np.zeros(max(npairs, 1), np.uint64)
         rc = L.nw_align_batch(ctx.handle, _ptr(pool2b), aop, alp, bop, blp, npairs, _sc(scoring), flags,
                               _ptr(sc_out), _ptr(cpool) if want else None, cop, _ptr(clen) if want else None)
         _check(ctx, rc)
         cigars = None
         if want:
-            cigars = _cigars(cpool, co, clen, npairs)
+            cigars = _cigars(ctx, cpool, co, clen, npairs)
         return sc_out[:npairs], cigars
     rc = L.nw_align_batch(ctx.handle, _ptr(pool2b), aop, alp, bop, blp, npairs, _sc(scoring), flags, _ptr(scores),
                           _ptr(cigar_pool) if want else None, cop, _ptr(cigar_len) if want else None)
@@ -418,13 +481,13 @@ def nw_local_align_batch(ctx: Context, pool2b, a_off, a_len, b_off, b_len, scori
         flags |= NW_HOST_IO
         sc_out = np.zeros(max(npairs, 1), np.int32)
         e_out = np.zeros((max(npairs, 1), 4), np.uint32)
-        cpool = _host_cigar_pool(ctx, int(co[-1]) if want else 1)
+        cpool = _host_cigar_pool(ctx, int(co[-1])) if want else np.empty(1, np.uint8)
         clen = np.zeros(max(npairs, 1), np.uint64)
         rc = L.nw_local_align_batch(ctx.handle, _ptr(pool2b), aop, alp, bop, blp, npairs, _sc(scoring), flags,
                                     _ptr(sc_out), _ptr(e_out), _ptr(cpool) if want else None, cop,
                                     _ptr(clen) if want else None)
         _check(ctx, rc)
-        return sc_out[:npairs], e_out[:npairs], (_cigars(cpool, co, clen, npairs) if want else None)
+        return sc_out[:npairs], e_out[:npairs], (_cigars(ctx, cpool, co, clen, npairs) if want else None)
     rc = L.nw_local_align_batch(ctx.handle, _ptr(pool2b), aop, alp, bop, blp, npairs, _sc(scoring), flags,
                                 _ptr(scores), _ptr(ends), _ptr(cigar_pool) if want else None, cop,
                                 _ptr(cigar_len) if want else None)
@@ -451,12 +514,12 @@ def nw_affine_align_batch(ctx: Context, pool2b, a_off, a_len, b_off, b_len, scor
     if _is_host(pool2b):
         flags |= NW_HOST_IO
         sc_out = np.zeros(max(npairs, 1), np.int32)
-        cpool = _host_cigar_pool(ctx, int(co[-1]) if want else 1)
+        cpool = _host_cigar_pool(ctx, int(co[-1])) if want else np.empty(1, np.uint8)
         clen = np.zeros(max(npairs, 1), np.uint64)
         rc = L.nw_affine_align_batch(ctx.handle, _ptr(pool2b), aop, alp, bop, blp, npairs, sc, flags, _ptr(sc_out),
                                      _ptr(cpool) if want else None, cop, _ptr(clen) if want else None)
         _check(ctx, rc)
-        return sc_out[:npairs], (_cigars(cpool, co, clen, npairs) if want else None)
+        return sc_out[:npairs], (_cigars(ctx, cpool, co, clen, npairs) if want else None)
     rc = L.nw_affine_align_batch(ctx.handle, _ptr(pool2b), aop, alp, bop, blp, npairs, sc, flags, _ptr(scores),
                                  _ptr(cigar_pool) if want else None, cop, _ptr(cigar_len) if want else None)
     _check(ctx, rc)
@@ -481,14 +544,14 @@ def nw_align_batch_banded(ctx: Context, pool2b, a_off, a_len, b_off, b_len, band
     if _is_host(pool2b):
         flags |= NW_HOST_IO
         sc_out = np.zeros(max(npairs, 1), np.int32)
-        cpool = _host_cigar_pool(ctx, int(co[-1]) if want else 1)
+        cpool = _host_cigar_pool(ctx, int(co[-1])) if want else np.empty(1, np.uint8)
         clen = np.zeros(max(npairs, 1), np.uint64)
         rc = L.nw_align_batch_banded(ctx.handle, _ptr(pool2b), aop, alp, bop, blp, npairs, wwp, _sc(scoring), flags,
                                      _ptr(sc_out), _ptr(cpool) if want else None, cop, _ptr(clen) if want else None)
         _check(ctx, rc)
         cigars = None
         if want:
-            cigars = _cigars(cpool, co, clen, npairs)
+            cigars = _cigars(ctx, cpool, co, clen, npairs)
         return sc_out[:npairs], cigars
     rc = L.nw_align_batch_banded(ctx.handle, _ptr(pool2b), aop, alp, bop, blp, npairs, wwp, _sc(scoring), flags,
                                  _ptr(scores), _ptr(cigar_pool) if want else None, cop,
@@ -791,7 +854,7 @@ def nw_center_star(ctx: Context, pool2b, off, lens, scoring=DEFAULT_SCORING, fla
         ncols = int(cols.value)
         text = rows[: nseq * ld].reshape(nseq, ld)[:, :ncols] if nseq else rows[:0]
         return {"center": int(center.value), "row_sums": sums[:nseq], "scores": sc_out[:nseq],
-                "cigars": _cigars(cpool, co, clen, nseq), "rows": [bytes(r).decode() for r in text],
+                "cigars": _cigars(ctx, cpool, co, clen, nseq), "rows": [bytes(r).decode() for r in text],
                 "columns": ncols}
     rc = L.nw_center_star(ctx.handle, _ptr(pool2b), oop, llp, nseq, _sc(scoring), flags, ctypes.byref(center),
                           _ptr(row_sums), _ptr(scores), _ptr(cigar_pool), cop, _ptr(cigar_len), _ptr(msa), msa_ld,

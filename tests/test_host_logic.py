@@ -56,7 +56,30 @@ def test_binding_cigar_decoding(nw):
     pool = np.zeros(32, np.uint8)
     pool[0:4] = np.frombuffer(b"3=1X", np.uint8)
     pool[20:22] = np.frombuffer(b"5D", np.uint8)
-    assert nw._cigars(pool, np.array([0, 10, 20], np.uint64), np.array([4, 0, 2], np.uint64), 3) == ["3=1X", "", "5D"]
+    c = nw._cigars(None, pool, np.array([0, 10, 20], np.uint64), np.array([4, 0, 2], np.uint64), 3)
+    assert c == ["3=1X", "", "5D"] and ["3=1X", "", "5D"] == c and c != ["3=1X", "", "5E"] and c != ["3=1X"]
+    assert len(c) == 3 and c[0] == "3=1X" and c[-1] == "5D" and c[1:] == ["", "5D"] and list(c) == c.tolist()
+    assert c.nbytes() == 6
+    with pytest.raises(IndexError):
+        c[3]
+
+
+def test_host_cigar_buffer_returns_to_the_context(nw):
+    """The host CIGAR buffer a call fills is lent to its Cigars view and
+    comes back to the context when the view is released, so a later call
+    reuses it; a view still alive keeps its bytes."""
+    class Ctx:
+        handle = 1
+    ctx = Ctx()
+    buf = nw._host_cigar_pool(ctx, 100)
+    buf[:2] = np.frombuffer(b"7=", np.uint8)
+    c = nw._cigars(ctx, buf, np.array([0], np.uint64), np.array([2], np.uint64), 1)
+    other = nw._host_cigar_pool(ctx, 50)          # the first view is alive: a new buffer
+    assert other is not buf
+    other[:2] = np.frombuffer(b"9I", np.uint8)
+    assert c[0] == "7=" and nw._cigars(ctx, other, [0], [2], 1)[0] == "9I"
+    del c
+    assert nw._host_cigar_pool(ctx, 80) is buf    # released: the larger buffer comes back
 
 
 def test_certificate_and_next_width_match_the_oracle(nw):
