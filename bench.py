@@ -59,7 +59,13 @@ BITS_OPS_PER_32 = 16
 BITS_PTR_OPS_PER_32 = 18
 BITS_PEAK_KINDS = (8, 10)    # nw_peak_int kinds: 3-input logic op, funnel shift (lane-ops/s)
 BITS_CELL_KIND = 11          # nw_peak_int kind: one bit-sliced step, 32 cells (cells/s)
-BITS_KERNELS = ("bits_score", "bband_fill_ptr", "bband_score")
+BITS_KERNELS = ("bits_score", "bband_fill_ptr", "bband_score", "bpair_fill_ptr")
+# The single-pair kernel (bpair_fill_ptr) keeps 31 rows per word (bit 31 is a
+# spare row) and runs one anti-diagonal step of a stripe after another: its
+# time is the wavefront's chain of m + n + m/31 steps, each 24 logic ops of
+# one warp (the 16-lane logic pipe of one scheduler: 2 cycles each).
+PAIR_ROWS = 31
+PAIR_ALU_OPS_PER_STEP = 24
 HBM_PEAK_FALLBACK = 6800.0   # GB/s, when MEASURED_PEAKS.json is absent
 STEPS_DEFAULT = {"pair32k": 100, "pair1k": 200, "allpairs": 20, "centerstar": 20, "local": 10, "affine": 10, "band": 3}
 
@@ -342,7 +348,7 @@ def run_reference(args):
 class PairWork:
     """One pair: pack both sequences on the device, fill with pointers,
     trace back, build the CIGAR."""
-    dominant = "fill_ptr"
+    dominant = "bpair_fill_ptr"
 
     def __init__(self, nw, ctx, dev, name):
         import torch
@@ -926,6 +932,8 @@ def run_ours(args):
             line["roofline"].pop("alu")
     if not args.no_clocks:
         line["clocks"] = clk.summary()
+    if work.dominant == "bpair_fill_ptr" and dom_avg_ms:
+        line["roofline"]["chain"] = pair_chain(work.m, work.n, dom_avg_ms, line.get("clocks", {}).get("sm_mhz"))
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         g, cores, sample = work.oracle_sample()
         line["cpu_baseline"] = {"value": g, "unit": "GCUPS", "cores": cores, "kind": "oracle", "sample": sample}
@@ -934,6 +942,29 @@ def run_ours(args):
     ctx.close()
     if world > 1:
         dist.destroy_process_group()
+
+
+def pair_chain(m, n, kernel_ms, sm_mhz):
+    """The single-pair kernel against its own bound: the steps on its
+    critical path (stripes of 31 rows, one per lane, 32 steps behind the
+    previous one; the next warp's first lane 34 chunks of 32 steps behind a
+    warp's), the time per step, and the floor of a step (its logic ops on
+    one scheduler's 16-lane pipe, 2 cycles each, at the sampled SM clock)."""
+    S = -(-m // PAIR_ROWS)
+    C = -(-(n + PAIR_ROWS - 1) // 32)
+    nwarps = -(-S // 32)
+    steps = 32 * ((nwarps - 1) * 34 + C + min(31, S - 1 - 32 * (nwarps - 1)))
+    ns = kernel_ms * 1e6 / steps
+    out = {"critical_steps": steps, "ns_per_step": ns, "warps": nwarps,
+           "alu_ops_per_step": PAIR_ALU_OPS_PER_STEP,
+           "note": "a wavefront: each anti-diagonal step of a stripe waits for the previous one; the whole-GPU "
+                   "ALU fraction above is small because only one warp per scheduler on ~m/992 schedulers can "
+                   "work at a time"}
+    if sm_mhz:
+        cyc = ns * sm_mhz / 1e3
+        floor = 2.0 * PAIR_ALU_OPS_PER_STEP
+        out.update({"cycles_per_step": cyc, "floor_cycles_per_step": floor, "frac": floor / cyc})
+    return out
 
 
 def measured_hbm_gbs():
@@ -956,9 +987,10 @@ def bits_roofline(kernel, workload, cells, kernel_ms, bits_peak, bits_cell_peak,
         return {"bound": "alu", "kernel": kernel, "achieved": None, "peak": bits_peak, "unit": "Gop/s",
                 "frac": None, "traffic": dram_traffic(kernel, workload)}
     sec = kernel_ms * 1e-3
-    ptr = kernel == "bband_fill_ptr"
+    ptr = kernel in ("bband_fill_ptr", "bpair_fill_ptr")
     ops32 = BITS_PTR_OPS_PER_32 if ptr else BITS_OPS_PER_32
-    alu_achieved = cells * ops32 / 32.0 / sec / 1e9
+    rows = PAIR_ROWS if kernel == "bpair_fill_ptr" else 32  # grid cells per word step
+    alu_achieved = cells * ops32 / rows / sec / 1e9
     gcups = cells / sec / 1e9
     alu = {"bound": "alu", "achieved": alu_achieved, "peak": bits_peak, "unit": "Gop/s",
            "frac": alu_achieved / bits_peak, "ops_per_32_cells": ops32,
@@ -976,6 +1008,8 @@ def bits_roofline(kernel, workload, cells, kernel_ms, bits_peak, bits_cell_peak,
             "traffic_note": "DRAM bytes per launch (ncu, profiles/dram_traffic.json); algorithmic: 0.25 B per "
                             "window cell of pointers for bband_fill_ptr, ~0 for score-only"}
     if not ptr:
+        return {**alu, **base, "cell_peak": cell, "scalar_unit": scalar}
+    if kernel == "bpair_fill_ptr":
         return {**alu, **base, "cell_peak": cell, "scalar_unit": scalar}
     hbm, src = measured_hbm_gbs()
     bytes_ = cells * 0.25

@@ -204,6 +204,10 @@ struct nw_ctx {
     // reserved in it (release threshold: never), so regrowing is cheap
     cudaMemPool_t mempool = nullptr;
     uint32_t test_hook = 0;            // NW_TEST_DROP_PROGRESS (one use)
+    // ring of the bit-sliced single-pair fill: its buffer and the tag of its
+    // last launch (entries carry the tag of the launch that wrote them)
+    void *bits_ring = nullptr;
+    uint32_t bits_epoch = 0;
 };
 
 namespace nw {
@@ -216,6 +220,13 @@ int cuda_fail(nw_ctx *ctx, cudaError_t e, const char *what);
 // (stream-ordered) under the context budget.  Returns NW_OK or NW_ERR_OOM /
 // NW_ERR_CUDA.
 int scratch(nw_ctx *ctx, const char *name, size_t bytes, void **out);
+// Bytes the scratch slot `name` may still grow to under the budget.
+inline uint64_t scratch_headroom(nw_ctx *ctx, const char *name) {
+    const auto it = ctx->bufs.find(name);
+    const uint64_t mine = it == ctx->bufs.end() ? 0 : it->second.cap;
+    const uint64_t others = ctx->used - mine;
+    return ctx->budget > others ? ctx->budget - others : 0;
+}
 
 // Validate scoring and sizes shared by all entry points.
 int check_scoring(nw_ctx *ctx, const nw_scoring &sc);
@@ -336,6 +347,10 @@ constexpr int32_t kNoBand = INT32_MIN;
 // passed by value).  Pairs of kParMinStripes stripes or more walk their
 // stripes in parallel (see nw_trace.cu).
 int launch_trace(nw_ctx *ctx, int R, const TraceTask *host, const TraceTask *dev, uint32_t ntasks, uint32_t mflag);
+// The same on the bit-sliced single-pair records (ptr: (L, Hb) word pairs,
+// [warp][step pair][lane] with ncg step pairs per warp; stripes of 31 rows
+// from the top, see nw_bits_pair.cu).
+int launch_trace_bits(nw_ctx *ctx, const TraceTask *host, const TraceTask *dev, uint32_t ntasks, uint32_t mflag);
 // The two halves of launch_trace: the walk (resumable through `state`) and
 // the CIGAR assembly from the finished move list.
 int launch_traceback(nw_ctx *ctx, int R, const TraceTask &one, const TraceTask *many, uint32_t ntasks);

@@ -24,7 +24,7 @@
 #include <cstdlib>
 #include <string>
 
-#include "nw_internal.cuh"
+#include "nw_bits.cuh"
 
 namespace nw {
 
@@ -186,13 +186,7 @@ __global__ void k_walk_init(uint32_t *state, uint32_t m, uint32_t n) {
     state[4] = 0;
 }
 
-// Bytes a scratch slot may still grow to under the budget.
-static uint64_t headroom(nw_ctx *ctx, const char *slot) {
-    const auto it = ctx->bufs.find(slot);
-    const uint64_t mine = it == ctx->bufs.end() ? 0 : it->second.cap;
-    const uint64_t others = ctx->used - mine;
-    return ctx->budget > others ? ctx->budget - others : 0;
-}
+static uint64_t headroom(nw_ctx *ctx, const char *slot) { return scratch_headroom(ctx, slot); }
 
 // Stripe-checkpoint recompute (a6), for pairs whose pointer matrix exceeds
 // the memory budget.  A score-only fill keeps the bottom W row of every
@@ -412,6 +406,12 @@ int align_single(nw_ctx *ctx, const uint8_t *a2b, uint64_t m, const uint8_t *b2b
         LaunchTimer t(ctx, "trivial");
         k_trivial<<<1, 1, 0, ctx->stream>>>((uint32_t)m, (uint32_t)n, sc.gap, score, want ? cigar : nullptr,
                                             want ? cigar_len : nullptr);
+    } else if (!(ctx->test_hook & NW_TEST_DROP_PROGRESS) && !(flags & NW_RECOMPUTE) &&
+               bits_pair_takes(ctx, (uint32_t)m, (uint32_t)n, sc, want)) {
+        // the paper's scoring (any with 0 <= s'x <= s'm <= 3): bit-sliced stripes
+        const int rc = bits_pair(ctx, a2b, (uint32_t)m, b2b, (uint32_t)n, sc, want, (flags & NW_CIGAR_M) ? 1u : 0u,
+                                 score, cigar, cigar_len);
+        if (rc) return rc;
     } else {
         const int rc = run_pair(ctx, a2b, (uint32_t)m, b2b, (uint32_t)n, pf, flags, score, cigar, cigar_len);
         if (rc) return rc;

@@ -152,29 +152,106 @@ __device__ __forceinline__ StripeJob job_of(const StripeJob *jobs, uint32_t g, u
     return j;
 }
 
-// Walk from (i, j) inside stripe s (rows s*SH+1 .. s*SH+SH) until the walk
-// leaves the stripe or reaches row / column 0 (kWalkDone), steps on a cell
-// of the spec path in `arow` (kWalkJoined; JOIN only; a_from = the spec's
-// move count there), has made `cap` moves (kWalkFull) or would read a column
-// left of the stored band (kWalkBand).  RECORD writes the row records
-// {entry column, (entry - exit column) | moves-before-entry << 16}.  Moves
-// go to out[k..].  Lane 0 walks, the warp stages 8-lane x 32-word pointer
-// tiles; i, j, k and the status are valid in every lane on return.
-template <int R, bool RECORD, bool JOIN>
+// Pointer layouts the walks read.  A layout splits the rows into stripes of
+// at most SH rows (stripe s: rows top(s)+1 .. bot(s)), names the staged tile
+// that holds a cell (key), stages it (load, the whole warp) and decodes the
+// move of a cell from it.  Cells are (a1, b1) = (i-1, j-1).
+//
+// Scalar fills: stripes of 32R rows from the top, words of R rows x 16/R
+// columns in [stripe][lane][column group] order, optionally banded (stripe s
+// keeps the columns from max(0, s*32R + band_lo)); a tile is 8 lane rows x
+// 32 words.
+template <int R>
+struct ScalarLayout {
+    static constexpr uint32_t SH = 32u * R, CPW = 16u / R;
+    __device__ static uint32_t stripes(const TraceTask &p) { return (p.m + SH - 1) / SH; }
+    __device__ static uint32_t top(const TraceTask &, uint32_t s) { return s * SH; }
+    __device__ static uint32_t bot(const TraceTask &p, uint32_t s) { return min(p.m, (s + 1) * SH); }
+    __device__ static uint32_t stripe_of(const TraceTask &, uint32_t a1) { return a1 / SH; }
+    __device__ static uint32_t cbeg(const TraceTask &p, uint32_t s) {
+        if (p.band_lo == kNoBand) return 0u;
+        const int64_t v = (int64_t)s * SH + p.band_lo;
+        return v > 0 ? (uint32_t)v : 0u;
+    }
+    __device__ static uint32_t cend(const TraceTask &p, uint32_t s) {
+        return p.band_lo == kNoBand ? p.n : min(p.n, cbeg(p, s) + p.ncg * CPW);
+    }
+    __device__ static uint32_t key(const TraceTask &, uint32_t top, uint32_t cb, uint32_t a1, uint32_t b1) {
+        return (((b1 - cb) / CPW) / kTileWords) * 4u + ((a1 - top) / R) / kTileLanes;
+    }
+    __device__ static void load(const TraceTask &p, uint32_t s, uint32_t key, uint32_t *tile, uint32_t lane) {
+        const uint32_t kt = key & 3u, ct = key >> 2;
+        const uint32_t rl = lane >> 2, part = lane & 3u;
+        const size_t base = (size_t)((s - p.s_lo) * 32u + kt * kTileLanes + rl) * p.ncg + ct * kTileWords + part * 8u;
+        const uint4 v0 = __ldcg(reinterpret_cast<const uint4 *>(p.ptr + base));
+        const uint4 v1 = __ldcg(reinterpret_cast<const uint4 *>(p.ptr + base + 4));
+        uint4 *dst = reinterpret_cast<uint4 *>(tile + rl * kTileWords + part * 8u);
+        dst[0] = v0;
+        dst[1] = v1;
+    }
+    __device__ static uint32_t move(const TraceTask &, const uint32_t *tile, uint32_t top, uint32_t cb, uint32_t a1,
+                                    uint32_t b1) {
+        const uint32_t kk = (a1 - top) / R, cg = (b1 - cb) / CPW;
+        const uint32_t word = tile[(kk % kTileLanes) * kTileWords + cg % kTileWords];
+        return ptr_move(word, ((b1 - cb) % CPW) * R + (a1 % R));
+    }
+};
+
+// Bit-sliced single-pair fill: bit stripes of 31 rows from the top (bit
+// stripe s: rows 31s + 1 .. 31s + 31).  Bit stripe s is lane l = s % 32 of
+// warp w = s / 32, and its step t is the warp's step tau = t + 32l; one
+// record (L, Hb) per bit stripe and step, laid out [warp][tau / 2][lane] in
+// 16-byte pairs of steps (ncg = pairs per warp).  Bit p of the step-t
+// record is the cell of row 31s + p + 1 and column t + 1 - p; L = 0 where
+// the diagonal predecessor attains the maximum, Hb = 0 where the upper one
+// does.  The walk's stripes are G bit stripes each, so that a speculative
+// walk has room to meet the true path; a tile is 64 consecutive steps of
+// one bit stripe.
+template <uint32_t G>
+struct BitsLayout {
+    static constexpr uint32_t RS = 31u, SH = RS * G;
+    __device__ static uint32_t stripes(const TraceTask &p) { return (p.m + SH - 1) / SH; }
+    __device__ static uint32_t top(const TraceTask &, uint32_t g) { return g * SH; }
+    __device__ static uint32_t bot(const TraceTask &p, uint32_t g) { return min(p.m, (g + 1) * SH); }
+    __device__ static uint32_t stripe_of(const TraceTask &, uint32_t a1) { return a1 / SH; }
+    __device__ static uint32_t cbeg(const TraceTask &, uint32_t) { return 0u; }
+    __device__ static uint32_t cend(const TraceTask &p, uint32_t) { return p.n; }
+    __device__ static uint32_t key(const TraceTask &, uint32_t, uint32_t, uint32_t a1, uint32_t b1) {
+        const uint32_t s = a1 / RS, bit = a1 - s * RS;
+        return ((s % G) << 24) | ((b1 + bit) >> 6);  // bit stripe within the walk stripe, 64-step tile
+    }
+    __device__ static void load(const TraceTask &p, uint32_t g, uint32_t key, uint32_t *tile, uint32_t lane) {
+        const uint32_t s = g * G + (key >> 24);
+        const uint32_t w = s >> 5, l = s & 31u;
+        const size_t row = (size_t)w * p.ncg + (size_t)(key & 0xffffffu) * 32u + 16u * l;  // tau = 64 tile + 32 l
+        reinterpret_cast<uint4 *>(tile)[lane] = __ldcg(reinterpret_cast<const uint4 *>(p.ptr) + (row + lane) * 32u + l);
+    }
+    __device__ static uint32_t move(const TraceTask &, const uint32_t *tile, uint32_t, uint32_t, uint32_t a1,
+                                    uint32_t b1) {
+        const uint32_t bit = a1 % RS, t = (b1 + bit) & 63u;
+        const uint32_t L = (tile[2 * t] >> bit) & 1u, H = (tile[2 * t + 1] >> bit) & 1u;
+        return L ? (H ? 2u : 1u) : 0u;
+    }
+};
+constexpr uint32_t kBitsWalkGroup = 8;  // bit stripes per walk stripe (248 rows)
+
+// Walk from (i, j) inside stripe s until the walk leaves the stripe or
+// reaches row / column 0 (kWalkDone), steps on a cell of the spec path in
+// `arow` (kWalkJoined; JOIN only; a_from = the spec's move count there), has
+// made `cap` moves (kWalkFull) or would read a column left of the stored
+// band (kWalkBand).  RECORD writes the row records {entry column,
+// (entry - exit column) | moves-before-entry << 16}, indexed by row - top.
+// Moves go to out[k..].  Lane 0 walks, the warp stages the layout's tiles;
+// i, j, k and the status are valid in every lane on return.
+template <class LY, bool RECORD, bool JOIN>
 __device__ uint32_t walk_stripe(const TraceTask &p, uint32_t s, uint32_t &i, uint32_t &j, uint32_t &k, uint32_t cap,
                                 uint8_t *out, uint2 *rec, const uint2 *arow, uint32_t &a_from, uint32_t *tile) {
-    constexpr uint32_t SH = 32u * R, CPW = 16u / R;
     const uint32_t lane = threadIdx.x & 31u;
-    const uint32_t top = s * SH;
-    uint32_t cb = 0;
-    if (p.band_lo != kNoBand) {
-        const int64_t v = (int64_t)top + p.band_lo;
-        cb = v > 0 ? (uint32_t)v : 0u;
-    }
-    uint32_t ckt = 0xffffffffu, cct = 0xffffffffu;
+    const uint32_t top = LY::top(p, s), cb = LY::cbeg(p, s);
+    uint32_t ckey = 0xffffffffu;
     uint32_t status = kWalkDone, rjhi = j, ridx = k;
     for (;;) {
-        uint32_t need = 0, nkt = 0, nct = 0;
+        uint32_t need = 0, nkey = 0;
         if (lane == 0) {
             for (;;) {
                 if (i == 0 || j == 0 || i <= top) {
@@ -198,15 +275,13 @@ __device__ uint32_t walk_stripe(const TraceTask &p, uint32_t s, uint32_t &i, uin
                     status = kWalkBand;
                     break;
                 }
-                const uint32_t kk = (a1 - top) / R, cg = (b1 - cb) / CPW;
-                if (kk / kTileLanes != ckt || cg / kTileWords != cct) {
+                const uint32_t key = LY::key(p, top, cb, a1, b1);
+                if (key != ckey) {
                     need = 1;
-                    nkt = kk / kTileLanes;
-                    nct = cg / kTileWords;
+                    nkey = key;
                     break;
                 }
-                const uint32_t word = tile[(kk % kTileLanes) * kTileWords + cg % kTileWords];
-                const uint32_t mv = ptr_move(word, ((b1 - cb) % CPW) * R + (a1 % R));
+                const uint32_t mv = LY::move(p, tile, top, cb, a1, b1);
                 out[k] = (uint8_t)mv;
                 ++k;
                 if (RECORD && mv != 2u) {  // leaving row i
@@ -220,20 +295,11 @@ __device__ uint32_t walk_stripe(const TraceTask &p, uint32_t s, uint32_t &i, uin
         }
         need = __shfl_sync(kFull, need, 0);
         if (!need) break;
-        nkt = __shfl_sync(kFull, nkt, 0);
-        nct = __shfl_sync(kFull, nct, 0);
+        nkey = __shfl_sync(kFull, nkey, 0);
         __syncwarp();
-        const uint32_t rl = lane >> 2, part = lane & 3u;
-        const size_t base =
-            (size_t)((s - p.s_lo) * 32u + nkt * kTileLanes + rl) * p.ncg + nct * kTileWords + part * 8u;
-        const uint4 v0 = __ldcg(reinterpret_cast<const uint4 *>(p.ptr + base));
-        const uint4 v1 = __ldcg(reinterpret_cast<const uint4 *>(p.ptr + base + 4));
-        uint4 *dst = reinterpret_cast<uint4 *>(tile + rl * kTileWords + part * 8u);
-        dst[0] = v0;
-        dst[1] = v1;
+        LY::load(p, s, nkey, tile, lane);
         __syncwarp();
-        ckt = nkt;
-        cct = nct;
+        ckey = nkey;
     }
     if (RECORD && lane == 0 && status == kWalkDone && j == 0 && i > top)
         rec[i - 1 - top] = make_uint2(rjhi, rjhi | (ridx << 16));
@@ -245,11 +311,11 @@ __device__ uint32_t walk_stripe(const TraceTask &p, uint32_t s, uint32_t &i, uin
 }
 
 // Spec (LINK = false) or link (LINK = true) walks, one warp per stripe job.
-template <int R, bool LINK>
+template <class LY, bool LINK>
 __global__ void __launch_bounds__(kWalkWarps * 32, 1) k_tb_stripes(TraceTask one, const TraceTask *many,
                                                                 const StripeJob *jobs, uint32_t njobs, uint32_t lcap,
                                                                 uint8_t *mbuf, uint2 *rows, uint4 *asum, uint4 *bsum) {
-    constexpr uint32_t SH = 32u * R, CPW = 16u / R;
+    constexpr uint32_t SH = LY::SH;
     __shared__ __align__(16) uint32_t tiles[kWalkWarps][kTileLanes * kTileWords];
     __shared__ uint2 arows[LINK ? kWalkWarps : 1][LINK ? SH : 1];
     const uint32_t lane = threadIdx.x & 31u, wi = threadIdx.x >> 5;
@@ -257,8 +323,8 @@ __global__ void __launch_bounds__(kWalkWarps * 32, 1) k_tb_stripes(TraceTask one
     if (g >= njobs) return;
     const StripeJob jb = job_of(jobs, g, lcap, SH);
     const TraceTask &p = many ? many[jb.task] : one;
-    const uint32_t s = jb.s, top = s * SH;
-    const uint32_t S = (p.m + SH - 1) / SH;
+    const uint32_t s = jb.s;
+    const uint32_t S = LY::stripes(p);
     uint2 *rec = rows + jb.roff;
     uint32_t a_from = 0, k = 0;
     if (!LINK) {
@@ -267,29 +333,24 @@ __global__ void __launch_bounds__(kWalkWarps * 32, 1) k_tb_stripes(TraceTask one
         // guess for the bottom row of stripe q: the proportional diagonal,
         // kept inside the stored columns
         auto guess = [&](uint32_t q, uint32_t row) -> uint32_t {
-            uint32_t g = (uint32_t)(((uint64_t)row * p.n + p.m / 2) / p.m), lo = 1, hi = p.n;
-            if (p.band_lo != kNoBand) {
-                const int64_t v = (int64_t)q * SH + p.band_lo;
-                const uint32_t cb = v > 0 ? (uint32_t)v : 0u;
-                lo = cb + 1;
-                hi = min(hi, cb + p.ncg * CPW);
-            }
+            const uint32_t g = (uint32_t)(((uint64_t)row * p.n + p.m / 2) / p.m);
+            const uint32_t lo = LY::cbeg(p, q) + 1, hi = LY::cend(p, q);
             return max(lo, min(g, hi));
         };
-        uint32_t i = min(p.m, top + SH), j = p.n;
+        uint32_t i = LY::bot(p, s), j = p.n;
         if (s + 1 < S) {
             j = guess(s, i);
             // burn-in: start one stripe lower and walk up to this stripe's
             // bottom row unrecorded; walks from different cells merge, so the
             // entry it reaches is usually the true path's
-            uint32_t bi = min(p.m, top + 2 * SH), bj = s + 2 < S ? guess(s + 1, bi) : p.n;
+            uint32_t bi = LY::bot(p, s + 1), bj = s + 2 < S ? guess(s + 1, bi) : p.n;
             uint32_t bk = 0, bf = 0;
-            const uint32_t bst = walk_stripe<R, false, false>(p, s + 1, bi, bj, bk, jb.lcap, mbuf + jb.moff, nullptr,
-                                                              nullptr, bf, tiles[wi]);
+            const uint32_t bst = walk_stripe<LY, false, false>(p, s + 1, bi, bj, bk, jb.lcap, mbuf + jb.moff, nullptr,
+                                                               nullptr, bf, tiles[wi]);
             if (bst == kWalkDone && bi == i && bj > 0) j = bj;
         }
-        const uint32_t st = walk_stripe<R, true, false>(p, s, i, j, k, jb.lcap, mbuf + jb.moff, rec, nullptr, a_from,
-                                                        tiles[wi]);
+        const uint32_t st = walk_stripe<LY, true, false>(p, s, i, j, k, jb.lcap, mbuf + jb.moff, rec, nullptr, a_from,
+                                                         tiles[wi]);
         if (lane == 0) asum[g] = make_uint4(i, j, k, st);
     } else {
         uint32_t si = p.m, sj = p.n;
@@ -309,8 +370,8 @@ __global__ void __launch_bounds__(kWalkWarps * 32, 1) k_tb_stripes(TraceTask one
         for (uint32_t r = lane; r < SH; r += 32) arows[wi][r] = av ? rec[r] : make_uint2(0u, 0u);
         __syncwarp();
         uint32_t i = si, j = sj;
-        const uint32_t st = walk_stripe<R, false, true>(p, s, i, j, k, jb.lcap, mbuf + jb.moff + jb.lcap, nullptr,
-                                                        arows[wi], a_from, tiles[wi]);
+        const uint32_t st = walk_stripe<LY, false, true>(p, s, i, j, k, jb.lcap, mbuf + jb.moff + jb.lcap, nullptr,
+                                                         arows[wi], a_from, tiles[wi]);
         if (lane == 0) {
             bsum[2 * (size_t)g] = make_uint4(si, sj, i, j);
             bsum[2 * (size_t)g + 1] = make_uint4(k, a_from, st, 0u);
@@ -322,12 +383,12 @@ __global__ void __launch_bounds__(kWalkWarps * 32, 1) k_tb_stripes(TraceTask one
 // the copies in `seg`) and walks the stripes no piece resolves, writing
 // those moves in place.  Pairs without stripe jobs (job_base ~0) walk every
 // stripe here.  Ends with the row-0 / column-0 moves and the move count.
-template <int R>
+template <class LY>
 __global__ void __launch_bounds__(32) k_tb_stitch(TraceTask one, const TraceTask *many, const uint32_t *job_base,
                                                   const StripeJob *jobs, uint32_t njobs, uint32_t lcap,
                                                   const uint2 *rows, const uint4 *asum, const uint4 *bsum, uint4 *seg,
                                                   uint32_t *err) {
-    constexpr uint32_t SH = 32u * R;
+    constexpr uint32_t SH = LY::SH;
     __shared__ __align__(16) uint32_t tile[kTileLanes * kTileWords];
     __shared__ uint2 arow[SH];
     __shared__ uint4 win[32][3];  // summaries of stripes [wlo, wlo + 32)
@@ -335,13 +396,13 @@ __global__ void __launch_bounds__(32) k_tb_stitch(TraceTask one, const TraceTask
     const uint32_t lane = threadIdx.x;
     const uint32_t gb = job_base ? job_base[blockIdx.x] : (njobs ? 0u : 0xffffffffu);
     const bool par = gb != 0xffffffffu;
-    const uint32_t S = (p.m + SH - 1) / SH;
+    const uint32_t S = LY::stripes(p);
     if (par)
         for (uint32_t s = lane; s < S; s += 32) seg[gb + s] = make_uint4(0xffffffffu, 0u, 0u, 0u);
     __syncwarp();
     uint32_t i = p.m, j = p.n, k = 0, wlo = 0xffffffffu;
     while (i > 0 && j > 0) {
-        const uint32_t s = (i - 1) / SH;
+        const uint32_t s = LY::stripe_of(p, i - 1);
         uint4 A = make_uint4(0u, 0u, 0u, kWalkNone), B0 = make_uint4(0u, 0u, 0u, 0u),
               B1 = make_uint4(0u, 0u, kWalkNone, 0u);
         if (par) {
@@ -381,7 +442,7 @@ __global__ void __launch_bounds__(32) k_tb_stitch(TraceTask one, const TraceTask
         __syncwarp();
         uint32_t a_from = 0;
         const uint32_t st =
-            walk_stripe<R, false, true>(p, s, i, j, k, 0xffffffffu, p.moves, nullptr, arow, a_from, tile);
+            walk_stripe<LY, false, true>(p, s, i, j, k, 0xffffffffu, p.moves, nullptr, arow, a_from, tile);
         if (st == kWalkJoined) {
             if (lane == 0) seg[gb + s] = make_uint4(k, 0u, a_from, A.z - a_from);
             k += A.z - a_from;
@@ -400,11 +461,11 @@ __global__ void __launch_bounds__(32) k_tb_stitch(TraceTask one, const TraceTask
 }
 
 // Copies of the linked pieces into the move list, one warp per stripe job.
-template <int R>
+template <class LY>
 __global__ void __launch_bounds__(kWalkWarps * 32) k_tb_copy(TraceTask one, const TraceTask *many,
                                                              const StripeJob *jobs, uint32_t njobs, uint32_t lcap,
                                                              const uint8_t *mbuf, const uint4 *seg) {
-    constexpr uint32_t SH = 32u * R;
+    constexpr uint32_t SH = LY::SH;
     const uint32_t lane = threadIdx.x & 31u;
     const uint32_t g = blockIdx.x * kWalkWarps + (threadIdx.x >> 5);
     if (g >= njobs) return;
@@ -612,9 +673,9 @@ int launch_finish(nw_ctx *ctx, const TraceTask &one, const TraceTask *many, uint
 
 // Stripe jobs of the pairs with at least kParMinStripes stripes, scratch
 // for their walks, and the four walk kernels.
-template <int R>
+template <class LY>
 static int launch_walks(nw_ctx *ctx, const TraceTask *host, const TraceTask *dev, uint32_t ntasks) {
-    constexpr uint32_t SH = 32u * R;
+    constexpr uint32_t SH = LY::SH;
     HostTimer ht(ctx, "trace_plan");
     static const char *min_env = getenv("NW_TB_MIN_MOVES");  // sweep knob
     const uint64_t min_moves = min_env ? (uint64_t)atoll(min_env) : ntasks == 1 ? kParMinMovesOne : kParMinMoves;
@@ -674,24 +735,24 @@ static int launch_walks(nw_ctx *ctx, const TraceTask *host, const TraceTask *dev
     if (njobs) {
         {
             LaunchTimer t(ctx, "tb_spec");
-            k_tb_stripes<R, false><<<blocks, kWalkWarps * 32, 0, ctx->stream>>>(
+            k_tb_stripes<LY, false><<<blocks, kWalkWarps * 32, 0, ctx->stream>>>(
                 one, dev, dj, njobs, lcap, (uint8_t *)vm, (uint2 *)vr, (uint4 *)va, (uint4 *)vb);
         }
         {
             LaunchTimer t(ctx, "tb_link");
-            k_tb_stripes<R, true><<<blocks, kWalkWarps * 32, 0, ctx->stream>>>(
+            k_tb_stripes<LY, true><<<blocks, kWalkWarps * 32, 0, ctx->stream>>>(
                 one, dev, dj, njobs, lcap, (uint8_t *)vm, (uint2 *)vr, (uint4 *)va, (uint4 *)vb);
         }
     }
     {
         LaunchTimer t(ctx, "tb_stitch");
-        k_tb_stitch<R><<<ntasks, 32, 0, ctx->stream>>>(one, dev, (const uint32_t *)vbase, dj, njobs, lcap,
+        k_tb_stitch<LY><<<ntasks, 32, 0, ctx->stream>>>(one, dev, (const uint32_t *)vbase, dj, njobs, lcap,
                                                        (const uint2 *)vr, (const uint4 *)va, (const uint4 *)vb,
                                                        (uint4 *)vs, ctx->d_err);
     }
     if (njobs) {
         LaunchTimer t(ctx, "tb_copy");
-        k_tb_copy<R><<<blocks, kWalkWarps * 32, 0, ctx->stream>>>(one, dev, dj, njobs, lcap, (const uint8_t *)vm,
+        k_tb_copy<LY><<<blocks, kWalkWarps * 32, 0, ctx->stream>>>(one, dev, dj, njobs, lcap, (const uint8_t *)vm,
                                                                   (const uint4 *)vs);
     }
     cudaError_t e = cudaGetLastError();
@@ -702,12 +763,18 @@ int launch_trace(nw_ctx *ctx, int R, const TraceTask *host, const TraceTask *dev
     if (ntasks == 0) return NW_OK;
     int rc;
     switch (R) {
-        case 2: rc = launch_walks<2>(ctx, host, dev, ntasks); break;
-        case 4: rc = launch_walks<4>(ctx, host, dev, ntasks); break;
-        case 8: rc = launch_walks<8>(ctx, host, dev, ntasks); break;
-        case 16: rc = launch_walks<16>(ctx, host, dev, ntasks); break;
+        case 2: rc = launch_walks<ScalarLayout<2>>(ctx, host, dev, ntasks); break;
+        case 4: rc = launch_walks<ScalarLayout<4>>(ctx, host, dev, ntasks); break;
+        case 8: rc = launch_walks<ScalarLayout<8>>(ctx, host, dev, ntasks); break;
+        case 16: rc = launch_walks<ScalarLayout<16>>(ctx, host, dev, ntasks); break;
         default: return fail(ctx, NW_ERR_ARG, "unsupported rows per lane %d", R);
     }
+    return rc ? rc : launch_finish(ctx, host[0], dev, ntasks, mflag);
+}
+
+int launch_trace_bits(nw_ctx *ctx, const TraceTask *host, const TraceTask *dev, uint32_t ntasks, uint32_t mflag) {
+    if (ntasks == 0) return NW_OK;
+    const int rc = launch_walks<BitsLayout<kBitsWalkGroup>>(ctx, host, dev, ntasks);
     return rc ? rc : launch_finish(ctx, host[0], dev, ntasks, mflag);
 }
 
