@@ -416,6 +416,10 @@ int nw_band_model_load(nw_ctx *ctx, const char *path);
  * first k costs the sum of their single-pair times plus the larger of the
  * rest's batch time and the (k+1)-th pair's one-warp time; the k with the
  * lowest estimate is taken (pairs under 1e7 full cells are never routed).
+ * Here a single-pair time is full_cells / 2e11 s + 1 ms (the scalar
+ * single-pair kernel); inside the batched paths, pairs whose scoring the
+ * bit-sliced single-pair kernel takes are costed by its chain instead,
+ * (m + n + m/31) x 40 ns + 0.3 ms.
  * Writes the indices, costliest first, to out (n entries of room) and
  * returns how many, or -NW_ERR_ARG. */
 int64_t nw_route_stragglers(const double *warp_cells, const double *full_cells, uint32_t n, uint32_t *out);

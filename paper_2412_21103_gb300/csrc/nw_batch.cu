@@ -207,14 +207,25 @@ static int check_band_scoring(nw_ctx *ctx, const nw_scoring &sc) {
 // one-warp time, routing the first k costs sum(single-pair times) +
 // max(the rest's ideal batch time, the (k+1)-th one-warp time), and the k
 // with the lowest estimate is taken.  Rates are GB300 measurements (cells/s):
-// one warp of the batched kernels, the whole batched kernel, and the
-// single-pair kernel on a long pair.
+// one warp of the batched kernels, the whole batched kernel, and the scalar
+// single-pair kernel on a long pair; the bit-sliced single-pair kernel runs
+// a chain of m + n + m/31 steps of about 40 ns, then its walk.
 constexpr double kWarpRate = 2e9, kBatchRate = 3.5e12, kPairRate = 2e11, kPairFixed = 1e-3;
+constexpr double kBitsStepSeconds = 40e-9, kBitsPairFixed = 0.3e-3;
+
+// Seconds the single-pair path takes on an m x n pair.
+static double single_pair_seconds(uint32_t m, uint32_t n, const nw_scoring &sc) {
+    if (bits_scoring_ok(sc) && std::min(m, n) >= 64)
+        return ((double)m + n + m / 31.0) * kBitsStepSeconds + kBitsPairFixed;
+    return (double)m * n / kPairRate + kPairFixed;
+}
 
 // warp_cells[k]: cells pair k costs on one warp (scaled for slower
-// kernels), full_cells[k]: its full grid.  Returns the indices to route.
+// kernels), full_cells[k]: its full grid, pair_secs[k] (or, when empty,
+// full_cells[k] / kPairRate + kPairFixed): its time on the single-pair path.
+// Returns the indices to route.
 static std::vector<size_t> pick_stragglers(const std::vector<double> &warp_cells, const std::vector<double> &full_cells,
-                                           double batch_rate = kBatchRate) {
+                                           const std::vector<double> &pair_secs, double batch_rate = kBatchRate) {
     std::vector<size_t> order(warp_cells.size());
     std::iota(order.begin(), order.end(), (size_t)0);
     std::sort(order.begin(), order.end(), [&](size_t x, size_t y) { return warp_cells[x] > warp_cells[y]; });
@@ -230,7 +241,7 @@ static std::vector<size_t> pick_stragglers(const std::vector<double> &warp_cells
             best_k = k;
         }
         if (k == order.size() || full_cells[order[k]] < 1e7) break;
-        routed += full_cells[order[k]] / kPairRate + kPairFixed;
+        routed += pair_secs.empty() ? full_cells[order[k]] / kPairRate + kPairFixed : pair_secs[order[k]];
         rest -= warp_cells[order[k]];
     }
     return std::vector<size_t>(order.begin(), order.begin() + best_k);
@@ -243,6 +254,30 @@ static int run_straggler(nw_ctx *ctx, const uint8_t *pool, uint64_t a_off, uint3
     LaunchTimer t(ctx, "straggler", 0);  // spans the single-pair kernels, which count themselves
     return align_single(ctx, pool + a_off, m, pool + b_off, n, sc, flags & (NW_CIGAR | NW_CIGAR_M | NW_RECOMPUTE), score,
                         (flags & NW_CIGAR) ? cigar : nullptr, cigar_cap, (flags & NW_CIGAR) ? cigar_len : nullptr);
+}
+
+// Runs tasks on the single-pair path, writing into the batch outputs: the
+// pairs the bit-sliced single-pair kernel takes run together, each on its
+// own warps, in waves; the others one after another.
+static int run_stragglers(nw_ctx *ctx, const uint8_t *pool, const std::vector<BatchTask> &ts, const nw_scoring &sc,
+                          uint32_t flags, int32_t *scores, char *cigar_pool, const uint64_t *cigar_off,
+                          uint64_t *cigar_len) {
+    const bool want = flags & NW_CIGAR;
+    std::vector<PairJob> jobs;
+    for (const BatchTask &t : ts) {
+        const uint32_t id = t.out0;
+        if (!(flags & NW_RECOMPUTE) && bits_pair_takes(ctx, t.m, t.n, sc, want)) {
+            jobs.push_back(PairJob{t.a_off, t.b_off, t.m, t.n, scores + id, want ? cigar_pool + cigar_off[id] : nullptr,
+                                   want ? cigar_len + id : nullptr});
+            continue;
+        }
+        const int rc = run_straggler(ctx, pool, t.a_off, t.m, t.b_off, t.n, sc, flags, scores + id,
+                                     want ? cigar_pool + cigar_off[id] : nullptr,
+                                     want ? cigar_off[id + 1] - cigar_off[id] : 0, want ? cigar_len + id : nullptr);
+        if (rc) return rc;
+    }
+    LaunchTimer t(ctx, "straggler", 0);  // spans the single-pair kernels, which count themselves
+    return bits_pairs(ctx, pool, jobs, sc, want, (flags & NW_CIGAR_M) ? 1u : 0u);
 }
 
 // ------------------------------------------------------- certified band
@@ -366,12 +401,13 @@ static int bits_round(nw_ctx *ctx, const uint8_t *pool, const PlaneSet &planes, 
         // one warp of this kernel runs its pair at about the scalar batch
         // kernel's per-warp rate; the whole kernel fills the GPU's 4 x 152
         // schedulers
-        std::vector<double> wc(items.size()), fc(items.size());
+        std::vector<double> wc(items.size()), fc(items.size()), ps(items.size());
         for (size_t q = 0; q < items.size(); ++q) {
             wc[q] = band_bits_seconds(items[q].shape) * kWarpRate;
             fc[q] = (double)items[q].m * items[q].n;
+            ps[q] = single_pair_seconds(items[q].m, items[q].n, sc);
         }
-        const std::vector<size_t> strag = pick_stragglers(wc, fc, kWarpRate * 4.0 * ctx->sm_count);
+        const std::vector<size_t> strag = pick_stragglers(wc, fc, ps, kWarpRate * 4.0 * ctx->sm_count);
         if (!strag.empty()) {
             std::vector<char> routed(items.size(), 0);
             for (size_t q : strag) {
@@ -575,12 +611,13 @@ static int band_rounds(nw_ctx *ctx, const uint8_t *pool, const uint64_t *a_off, 
             // banded pairs that would leave the GPU idle on one warp run full
             // on the single-pair kernel instead (counted as fallbacks); a
             // banded warp is ~1.5x slower per cell than a full-grid one
-            std::vector<double> wc(tasks.size()), fc(tasks.size());
+            std::vector<double> wc(tasks.size()), fc(tasks.size()), ps(tasks.size());
             for (size_t q = 0; q < tasks.size(); ++q) {
                 wc[q] = 1.5 * (double)band_cells(tasks[q], R);
                 fc[q] = (double)tasks[q].m * tasks[q].n;
+                ps[q] = single_pair_seconds(tasks[q].m, tasks[q].n, sc);
             }
-            const std::vector<size_t> strag = pick_stragglers(wc, fc);
+            const std::vector<size_t> strag = pick_stragglers(wc, fc, ps);
             routed_full = strag.size();
             if (!strag.empty()) {
                 std::vector<char> routed(tasks.size(), 0);
@@ -851,9 +888,12 @@ int batch_device_impl(nw_ctx *ctx, const uint8_t *pool, const uint64_t *a_off, c
     // kernel, and so do pairs whose pointer matrix alone exceeds half the
     // remaining budget (the single-pair path recomputes from checkpoints)
     {
-        std::vector<double> wc(tasks.size()), fc(tasks.size());
-        for (size_t q = 0; q < tasks.size(); ++q) wc[q] = fc[q] = (double)tasks[q].m * tasks[q].n;
-        std::vector<size_t> strag = pick_stragglers(wc, fc);
+        std::vector<double> wc(tasks.size()), fc(tasks.size()), ps(tasks.size());
+        for (size_t q = 0; q < tasks.size(); ++q) {
+            wc[q] = fc[q] = (double)tasks[q].m * tasks[q].n;
+            ps[q] = single_pair_seconds(tasks[q].m, tasks[q].n, sc);
+        }
+        std::vector<size_t> strag = pick_stragglers(wc, fc, ps);
         if (want) {
             const uint64_t room = (ctx->budget - std::min(ctx->budget, ctx->used)) / 2;
             std::vector<char> in(tasks.size(), 0);
@@ -863,15 +903,12 @@ int batch_device_impl(nw_ctx *ctx, const uint8_t *pool, const uint64_t *a_off, c
         }
         if (!strag.empty()) {
             std::vector<char> routed(tasks.size(), 0);
+            std::vector<BatchTask> st;
             for (size_t q : strag) {
-                const BatchTask &t = tasks[q];
-                const uint32_t id = t.out0;
-                if ((rc = run_straggler(ctx, pool, t.a_off, t.m, t.b_off, t.n, sc, flags, scores + id,
-                                        want ? cigar_pool + cigar_off[id] : nullptr,
-                                        want ? cigar_off[id + 1] - cigar_off[id] : 0, want ? cigar_len + id : nullptr)))
-                    return rc;
+                st.push_back(tasks[q]);
                 routed[q] = 1;
             }
+            if ((rc = run_stragglers(ctx, pool, st, sc, flags, scores, cigar_pool, cigar_off, cigar_len))) return rc;
             std::vector<BatchTask> keep;
             for (size_t q = 0; q < tasks.size(); ++q)
                 if (!routed[q]) keep.push_back(tasks[q]);
@@ -951,20 +988,21 @@ int batch_device_impl(nw_ctx *ctx, const uint8_t *pool, const uint64_t *a_off, c
             ids_w.push_back(t.out0);
         }
         if (k < npairs || k0 > 0) {  // a true wave (not the whole batch): route its stragglers
-            std::vector<double> wc(wave.size());
-            for (size_t q = 0; q < wave.size(); ++q) wc[q] = (double)wave[q].m * wave[q].n;
-            const std::vector<size_t> strag = pick_stragglers(wc, wc);
+            std::vector<double> wc(wave.size()), ps(wave.size());
+            for (size_t q = 0; q < wave.size(); ++q) {
+                wc[q] = (double)wave[q].m * wave[q].n;
+                ps[q] = single_pair_seconds(wave[q].m, wave[q].n, sc);
+            }
+            const std::vector<size_t> strag = pick_stragglers(wc, wc, ps);
             if (!strag.empty() && strag.size() < wave.size()) {
                 std::vector<char> routed(wave.size(), 0);
+                std::vector<BatchTask> st;
                 for (size_t q : strag) {
-                    const BatchTask &t = wave[q];
-                    const uint32_t id = t.out0;
-                    if ((rc = run_straggler(ctx, pool, t.a_off, t.m, t.b_off, t.n, sc, flags, scores + id,
-                                            cigar_pool + cigar_off[id], cigar_off[id + 1] - cigar_off[id],
-                                            cigar_len + id)))
-                        return rc;
+                    st.push_back(wave[q]);
                     routed[q] = 1;
                 }
+                if ((rc = run_stragglers(ctx, pool, st, sc, flags, scores, cigar_pool, cigar_off, cigar_len)))
+                    return rc;
                 std::vector<BatchTask> keep;
                 std::vector<uint32_t> keep_ids;
                 for (size_t q = 0; q < wave.size(); ++q)
@@ -1153,7 +1191,7 @@ extern "C" int64_t nw_route_stragglers(const double *warp_cells, const double *f
                                        uint32_t *out) {
     if (n && (!warp_cells || !full_cells || !out)) return -NW_ERR_ARG;
     const std::vector<size_t> r = pick_stragglers(std::vector<double>(warp_cells, warp_cells + n),
-                                                  std::vector<double>(full_cells, full_cells + n));
+                                                  std::vector<double>(full_cells, full_cells + n), {});
     for (size_t k = 0; k < r.size(); ++k) out[k] = (uint32_t)r[k];
     return (int64_t)r.size();
 }

@@ -136,6 +136,19 @@ bool bits_pair_takes(nw_ctx *ctx, uint32_t m, uint32_t n, const nw_scoring &sc, 
 // Score (and with `want` the CIGAR, written by the CIGAR assembly) of one pair.
 int bits_pair(nw_ctx *ctx, const uint8_t *a2b, uint32_t m, const uint8_t *b2b, uint32_t n, const nw_scoring &sc,
               bool want, uint32_t mflag, int32_t *score, char *cigar, uint64_t *cigar_len);
+// Many pairs, each on its own warps: waves of pairs whose warps are all
+// resident at once, longest chains first.  a_off / b_off: byte offsets into
+// `pool` (device addresses when it is null).  Every job must pass
+// bits_pair_takes.
+struct PairJob {
+    uint64_t a_off, b_off;
+    uint32_t m, n;
+    int32_t *score;
+    char *cigar;
+    uint64_t *cigar_len;
+};
+int bits_pairs(nw_ctx *ctx, const uint8_t *pool, const std::vector<PairJob> &jobs, const nw_scoring &sc, bool want,
+               uint32_t mflag);
 
 // ---- the certified band on the bit-sliced window (nw_bits_band.cu)
 // Window of one pair: g lanes (a power of two) x Q words of 32 rows, its

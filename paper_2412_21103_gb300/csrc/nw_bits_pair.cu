@@ -35,6 +35,8 @@
 // steps per 16-byte store, so a warp's stores are contiguous.
 #include <algorithm>
 #include <cstdlib>
+#include <numeric>
+#include <vector>
 
 #include "nw_bits.cuh"
 
@@ -48,16 +50,44 @@ constexpr uint32_t kLutAndNand = lut(kA & ~(kB & kC));   // a & !(b & c)
 constexpr uint32_t kLutOrAndNot = lut((kA | kB) & ~kC);  // (a | b) & !c
 constexpr uint32_t kLutXorAndNot = lut(kA ^ (kB & ~kC)); // a ^ (b & !c)
 
-struct PairBitsArgs {
-    const uint32_t *pl0, *pl1;  // planar sequences
+// One pair of a launch (device array).
+struct PairDesc {
     int64_t Ag, Bg;             // slots of a (rows) and b (columns)
     uint32_t m, n, S, C;        // stripes, chunks of 32 steps per stripe
     uint32_t nwarps;
     uint32_t pm;                // bit of row m in the last stripe
-    uint4 *rec;                 // records [warp][rec_rows][32 lanes] (two steps each), or null
     uint32_t rec_rows;          // step pairs per warp: the last lane's steps and a walk tile's overhang
-    uint64_t *ring;             // [warp][C][2] tagged outgoing words of lane 31
+    uint32_t pad;
+    uint64_t rec_off;           // the pair's records: rec + rec_off (uint4 units)
+    uint64_t ring_off;          // the pair's ring: ring + ring_off (64-bit words)
+    int32_t *score;
+};
+// A CTA's pair and the index of its first warp in that pair.
+struct PairBlock {
+    uint32_t pair, w0;
+};
+// A launch: several pairs at once, each on its own warps, every warp of
+// every pair resident (cooperative launch).
+struct PairLaunch {
+    const uint32_t *pl0, *pl1;  // planar sequences
+    const PairDesc *pairs;
+    const PairBlock *blocks;
+    uint4 *rec;                 // records, per pair [warp][rec_rows][32 lanes] (two steps each), or null
+    uint64_t *ring;             // per pair [warp][C][2] tagged outgoing words of lane 31
     uint32_t epoch;             // tag of this launch (never 0)
+    int32_t gap;
+    BitsScoring g;
+    uint32_t *err;
+};
+// What one warp sees of its pair.
+struct PairBitsArgs {
+    const uint32_t *pl0, *pl1;
+    int64_t Ag, Bg;
+    uint32_t m, n, S, C, nwarps, pm;
+    uint4 *rec;
+    uint32_t rec_rows;
+    uint64_t *ring;
+    uint32_t epoch;
     int32_t *score;
     int32_t gap;
     BitsScoring g;
@@ -211,10 +241,15 @@ __device__ __forceinline__ void pair_chunk(PairState &st, uint32_t A0, uint32_t 
 }
 
 template <bool GEN, bool PTR>
-__global__ void __launch_bounds__(kPairWarps * 32, 1) k_bits_pair(PairBitsArgs p) {
+__global__ void __launch_bounds__(kPairWarps * 32, 1) k_bits_pair(PairLaunch L) {
     const uint32_t lane = threadIdx.x & 31u;
-    const uint32_t w = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
-    if (w >= p.nwarps) return;
+    const PairBlock bk = L.blocks[blockIdx.x];
+    const PairDesc pd = L.pairs[bk.pair];
+    const uint32_t w = bk.w0 + (threadIdx.x >> 5);
+    if (w >= pd.nwarps) return;
+    const PairBitsArgs p{L.pl0, L.pl1, pd.Ag, pd.Bg, pd.m, pd.n, pd.S, pd.C, pd.nwarps, pd.pm,
+                         PTR ? L.rec + pd.rec_off : nullptr, pd.rec_rows, L.ring + pd.ring_off, L.epoch, pd.score,
+                         L.gap, L.g, L.err};
     const uint32_t S = p.S, C = p.C;
     const uint32_t s = 32u * w + lane;
     const bool valid = s < S;
@@ -295,30 +330,45 @@ __global__ void __launch_bounds__(kPairWarps * 32, 1) k_bits_pair(PairBitsArgs p
 // ------------------------------------------------------------------ host
 namespace {
 struct PairGeom {
-    uint32_t S, C, nwarps, per_cta, blocks, rec_rows;
+    uint32_t S, C, nwarps, rec_rows;
     uint64_t rec_bytes, ring_bytes;
 };
 
-PairGeom pair_geom(uint32_t m, uint32_t n, int sms) {
+PairGeom pair_geom(uint32_t m, uint32_t n) {
     PairGeom g;
     g.S = (m + kPairRows - 1) / kPairRows;
     g.C = (uint32_t)(((uint64_t)n + kPairRows - 1 + 31u) / 32u);  // steps 0 .. n + 29
     g.nwarps = (g.S + 31u) / 32u;
-    // a warp per SM while they fit (no warp shares an SM's memory pipes or
-    // instruction cache), else kPairWarps per SM
-    g.per_cta = g.nwarps <= (uint32_t)sms ? 1u : (uint32_t)kPairWarps;
-    g.blocks = (g.nwarps + g.per_cta - 1) / g.per_cta;
     // the last lane's steps end at warp step 32 (C + 31); a walk tile of 64
     // steps may start up to 63 steps before a stripe's last step
     g.rec_rows = 16u * (g.C + 33u);
     g.rec_bytes = (uint64_t)g.nwarps * g.rec_rows * 32u * 16u;
-    g.ring_bytes = (uint64_t)g.nwarps * g.C * 16u + 64;
+    g.ring_bytes = (uint64_t)g.nwarps * g.C * 16u;
     return g;
 }
 
 bool env_on(const char *name) {
     const char *v = getenv(name);
     return v && *v && *v != '0';
+}
+
+const void *pair_kernel(bool gen, bool want) {
+    return want ? (gen ? (const void *)k_bits_pair<true, true> : (const void *)k_bits_pair<false, true>)
+                : (gen ? (const void *)k_bits_pair<true, false> : (const void *)k_bits_pair<false, false>);
+}
+
+// Most warps of the kernel (one per CTA) that the device holds at once.
+uint32_t resident_warps(nw_ctx *ctx, bool gen, bool want) {
+    int occ = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, pair_kernel(gen, want), 32, 0) != cudaSuccess) {
+        cudaGetLastError();
+        occ = 1;
+    }
+    return (uint32_t)std::max(occ, 1) * (uint32_t)ctx->sm_count;
+}
+
+bool gen_of(const nw_scoring &sc) {
+    return !(sc.match - 2 * sc.gap == 3 && sc.mismatch - 2 * sc.gap == 1);
 }
 }  // namespace
 
@@ -327,72 +377,155 @@ bool bits_pair_takes(nw_ctx *ctx, uint32_t m, uint32_t n, const nw_scoring &sc, 
     const char *mn = getenv("NW_BITS_PAIR_MIN");  // smallest side taken (test and sweep knob)
     const uint32_t min_side = mn ? (uint32_t)atoi(mn) : 64u;
     if (std::min(m, n) < min_side) return false;
-    const PairGeom g = pair_geom(m, n, ctx->sm_count);
-    if (g.blocks > (uint32_t)ctx->sm_count) return false;  // one CTA per SM is always co-resident
-    uint64_t need = g.ring_bytes;
+    const PairGeom g = pair_geom(m, n);
+    if (g.nwarps > resident_warps(ctx, gen_of(sc), want)) return false;
+    uint64_t need = g.ring_bytes + 64;
     if (want) need += g.rec_bytes + (uint64_t)m + n + 64;
     return need <= scratch_headroom(ctx, "bpair_rec");
 }
 
+int bits_pairs(nw_ctx *ctx, const uint8_t *pool, const std::vector<PairJob> &jobs, const nw_scoring &sc, bool want,
+               uint32_t mflag) {
+    if (jobs.empty()) return NW_OK;
+    int rc;
+    const bool gen = gen_of(sc);
+    PlaneSet ps;
+    std::vector<int64_t> ag(jobs.size()), bg(jobs.size());
+    for (size_t k = 0; k < jobs.size(); ++k) {
+        ag[k] = ps.add(jobs[k].a_off, jobs[k].m);
+        bg[k] = ps.add(jobs[k].b_off, jobs[k].n);
+    }
+    if ((rc = ps.launch(ctx, pool, "bpair"))) return rc;
+    PairLaunch L{};
+    L.pl0 = ps.pl0;
+    L.pl1 = ps.pl1;
+    L.gap = sc.gap;
+    L.err = ctx->d_err;
+    const int32_t sm = sc.match - 2 * sc.gap, sx = sc.mismatch - 2 * sc.gap;
+    L.g.M1 = (sm & 2) ? ~0u : 0u;
+    L.g.M0 = (sm & 1) ? ~0u : 0u;
+    L.g.X1 = (sx & 2) ? ~0u : 0u;
+    L.g.X0 = (sx & 1) ? ~0u : 0u;
+    // longest chains first; a wave takes pairs while their warps are all
+    // resident at once and their records fit the budget
+    std::vector<size_t> order(jobs.size());
+    std::iota(order.begin(), order.end(), (size_t)0);
+    auto steps = [&](size_t k) { return (double)jobs[k].m + jobs[k].n + jobs[k].m / 31.0; };
+    std::sort(order.begin(), order.end(), [&](size_t x, size_t y) { return steps(x) > steps(y); });
+    const uint32_t cap_warps = resident_warps(ctx, gen, want);
+    const uint64_t room = scratch_headroom(ctx, "bpair_rec");
+    size_t next = 0;
+    while (next < order.size()) {
+        std::vector<size_t> wave;
+        uint64_t warps = 0, rec = 0, ring = 0, moves = 0;
+        while (next < order.size()) {
+            const size_t k = order[next];
+            const PairGeom g = pair_geom(jobs[k].m, jobs[k].n);
+            const uint64_t r = want ? g.rec_bytes : 0;
+            if (!wave.empty() && (warps + g.nwarps > cap_warps || rec + r > room)) break;
+            if (g.nwarps > cap_warps)
+                return fail(ctx, NW_ERR_ARG, "pair of %u rows needs %u resident warps", jobs[k].m, g.nwarps);
+            wave.push_back(k);
+            warps += g.nwarps;
+            rec += r;
+            ring += g.ring_bytes;
+            moves += (uint64_t)jobs[k].m + jobs[k].n + 16;
+            ++next;
+        }
+        // pair table and block table
+        std::vector<PairDesc> descs;
+        std::vector<PairBlock> blocks;
+        uint64_t rec_off = 0, ring_off = 0;
+        for (size_t q = 0; q < wave.size(); ++q) {
+            const PairJob &j = jobs[wave[q]];
+            const PairGeom g = pair_geom(j.m, j.n);
+            PairDesc d{};
+            d.Ag = ag[wave[q]];
+            d.Bg = bg[wave[q]];
+            d.m = j.m;
+            d.n = j.n;
+            d.S = g.S;
+            d.C = g.C;
+            d.nwarps = g.nwarps;
+            d.pm = (j.m - 1) - kPairRows * (g.S - 1);
+            d.rec_rows = g.rec_rows;
+            d.rec_off = rec_off;
+            d.ring_off = ring_off;
+            d.score = j.score;
+            descs.push_back(d);
+            for (uint32_t w = 0; w < g.nwarps; ++w) blocks.push_back(PairBlock{(uint32_t)q, w});
+            rec_off += want ? (uint64_t)g.nwarps * g.rec_rows * 32u : 0;
+            ring_off += (uint64_t)g.nwarps * g.C * 2u;
+        }
+        void *v = nullptr;
+        const size_t dbytes = descs.size() * sizeof(PairDesc), bbytes = blocks.size() * sizeof(PairBlock);
+        if ((rc = scratch(ctx, "bpair_desc", dbytes + bbytes + 16, &v))) return rc;
+        {
+            cudaError_t e = cudaMemcpyAsync(v, descs.data(), dbytes, cudaMemcpyHostToDevice, ctx->stream);
+            if (e == cudaSuccess)
+                e = cudaMemcpyAsync((char *)v + dbytes, blocks.data(), bbytes, cudaMemcpyHostToDevice, ctx->stream);
+            if (e == cudaSuccess) e = cudaStreamSynchronize(ctx->stream);  // the tables are host memory of this call
+            if (e != cudaSuccess) return cuda_fail(ctx, e, "pair table upload");
+        }
+        L.pairs = (const PairDesc *)v;
+        L.blocks = (const PairBlock *)((char *)v + dbytes);
+        if ((rc = scratch(ctx, "bpair_ring", ring + 64, &v))) return rc;
+        if (v != ctx->bits_ring || ctx->bits_epoch == 0xffffffffu) {
+            // a new ring may hold anything, also tags of an earlier context:
+            // clear it and start the epochs again
+            const cudaError_t e = cudaMemsetAsync(v, 0, ring + 64, ctx->stream);
+            if (e != cudaSuccess) return cuda_fail(ctx, e, "ring clear");
+            ctx->bits_ring = v;
+            ctx->bits_epoch = 0;
+        }
+        L.ring = (uint64_t *)v;
+        L.epoch = ++ctx->bits_epoch;
+        L.rec = nullptr;
+        if (want) {
+            if ((rc = scratch(ctx, "bpair_rec", rec + 16, &v))) return rc;
+            L.rec = (uint4 *)v;
+        }
+        void *args[] = {&L};
+        {
+            LaunchTimer t(ctx, want ? "bpair_fill_ptr" : "bpair_fill");
+            const cudaError_t e = cudaLaunchCooperativeKernel(pair_kernel(gen, want), dim3((uint32_t)blocks.size()),
+                                                              dim3(32), args, 0, ctx->stream);
+            if (e != cudaSuccess) return cuda_fail(ctx, e, "bit-sliced pair launch");
+        }
+        if (!want) continue;
+        void *mv = nullptr, *nm = nullptr, *dt = nullptr;
+        if ((rc = scratch(ctx, "bpair_moves", moves + 16, &mv))) return rc;
+        if ((rc = scratch(ctx, "bpair_nmoves", wave.size() * 8 + 16, &nm))) return rc;
+        std::vector<TraceTask> tts;
+        uint64_t moff = 0;
+        for (size_t q = 0; q < wave.size(); ++q) {
+            const PairJob &j = jobs[wave[q]];
+            const uint8_t *a = pool ? pool + j.a_off : (const uint8_t *)(uintptr_t)j.a_off;
+            const uint8_t *b = pool ? pool + j.b_off : (const uint8_t *)(uintptr_t)j.b_off;
+            tts.push_back(TraceTask{(const uint32_t *)(L.rec + descs[q].rec_off), descs[q].rec_rows, j.m, j.n,
+                                    (uint8_t *)mv + moff, (uint64_t *)nm + q, a, b, j.cigar, j.cigar_len, kNoBand, 0,
+                                    nullptr, nullptr});
+            moff += (uint64_t)j.m + j.n + 16;
+        }
+        if (tts.size() > 1) {
+            if ((rc = scratch(ctx, "bpair_tt", tts.size() * sizeof(TraceTask), &dt))) return rc;
+            cudaError_t e = cudaMemcpyAsync(dt, tts.data(), tts.size() * sizeof(TraceTask), cudaMemcpyHostToDevice,
+                                            ctx->stream);
+            if (e == cudaSuccess) e = cudaStreamSynchronize(ctx->stream);
+            if (e != cudaSuccess) return cuda_fail(ctx, e, "pair trace upload");
+        }
+        if ((rc = launch_trace_bits(ctx, tts.data(), tts.size() > 1 ? (const TraceTask *)dt : nullptr,
+                                    (uint32_t)tts.size(), mflag)))
+            return rc;
+    }
+    return NW_OK;
+}
+
 int bits_pair(nw_ctx *ctx, const uint8_t *a2b, uint32_t m, const uint8_t *b2b, uint32_t n, const nw_scoring &sc,
               bool want, uint32_t mflag, int32_t *score, char *cigar, uint64_t *cigar_len) {
-    int rc;
-    const PairGeom g = pair_geom(m, n, ctx->sm_count);
-    PlaneSet ps;
-    PairBitsArgs pa{};
-    pa.Ag = ps.add((uint64_t)(uintptr_t)a2b, m);
-    pa.Bg = ps.add((uint64_t)(uintptr_t)b2b, n);
-    if ((rc = ps.launch(ctx, nullptr, "bpair"))) return rc;
-    pa.pl0 = ps.pl0;
-    pa.pl1 = ps.pl1;
-    pa.m = m;
-    pa.n = n;
-    pa.S = g.S;
-    pa.C = g.C;
-    pa.nwarps = g.nwarps;
-    pa.pm = (m - 1) - kPairRows * (g.S - 1);
-    pa.rec_rows = g.rec_rows;
-    pa.score = score;
-    pa.gap = sc.gap;
-    pa.err = ctx->d_err;
-    const int32_t sm = sc.match - 2 * sc.gap, sx = sc.mismatch - 2 * sc.gap;
-    pa.g.M1 = (sm & 2) ? ~0u : 0u;
-    pa.g.M0 = (sm & 1) ? ~0u : 0u;
-    pa.g.X1 = (sx & 2) ? ~0u : 0u;
-    pa.g.X0 = (sx & 1) ? ~0u : 0u;
-    const bool gen = !(sm == 3 && sx == 1);
-    void *v = nullptr;
-    if ((rc = scratch(ctx, "bpair_ring", g.ring_bytes, &v))) return rc;
-    if (v != ctx->bits_ring || ctx->bits_epoch == 0xffffffffu) {
-        // a new ring may hold anything, also tags of an earlier context:
-        // clear it and start the epochs again
-        const cudaError_t e = cudaMemsetAsync(v, 0, g.ring_bytes, ctx->stream);
-        if (e != cudaSuccess) return cuda_fail(ctx, e, "ring clear");
-        ctx->bits_ring = v;
-        ctx->bits_epoch = 0;
-    }
-    pa.ring = (uint64_t *)v;
-    pa.epoch = ++ctx->bits_epoch;
-    if (want) {
-        if ((rc = scratch(ctx, "bpair_rec", g.rec_bytes, &v))) return rc;
-        pa.rec = (uint4 *)v;
-    }
-    void *args[] = {&pa};
-    const void *fn = want ? (gen ? (const void *)k_bits_pair<true, true> : (const void *)k_bits_pair<false, true>)
-                          : (gen ? (const void *)k_bits_pair<true, false> : (const void *)k_bits_pair<false, false>);
-    {
-        LaunchTimer t(ctx, want ? "bpair_fill_ptr" : "bpair_fill");
-        const cudaError_t e = cudaLaunchCooperativeKernel(fn, dim3(g.blocks), dim3(g.per_cta * 32), args, 0,
-                                                          ctx->stream);
-        if (e != cudaSuccess) return cuda_fail(ctx, e, "bit-sliced pair launch");
-    }
-    if (!want) return NW_OK;
-    void *mv = nullptr, *nm = nullptr;
-    if ((rc = scratch(ctx, "moves", (size_t)m + n + 16, &mv))) return rc;
-    if ((rc = scratch(ctx, "nmoves", 16, &nm))) return rc;
-    TraceTask tt{(const uint32_t *)pa.rec, g.rec_rows, m, n, (uint8_t *)mv, (uint64_t *)nm, a2b, b2b, cigar,
-                 cigar_len, kNoBand, 0, nullptr, nullptr};
-    return launch_trace_bits(ctx, &tt, nullptr, 1, mflag);
+    const std::vector<PairJob> jobs{PairJob{(uint64_t)(uintptr_t)a2b, (uint64_t)(uintptr_t)b2b, m, n, score,
+                                            want ? cigar : nullptr, want ? cigar_len : nullptr}};
+    return bits_pairs(ctx, nullptr, jobs, sc, want, mflag);
 }
 
 }  // namespace nw
