@@ -753,6 +753,7 @@ def run_serve(args):
     t0 = time.perf_counter()
     k = 0
     ticket_req = {}
+    ticket_lag = {}  # submission minus scheduled arrival (the server's intake can push back)
     done = []
     while k < arrivals.size:
         now = time.perf_counter() - t0
@@ -760,8 +761,9 @@ def run_serve(args):
         if j > k:
             sel = idx[k:j]
             tick = srv.submit_many(pool, ao[sel], al[sel], bo[sel], bl[sel], want[sel])
-            for tt, q in zip(tick, sel):
+            for tt, q, arr in zip(tick, sel, arrivals[k:j]):
                 ticket_req[int(tt)] = int(q)
+                ticket_lag[int(tt)] = now - float(arr)
             k = j
         else:
             time.sleep(0.0005)
@@ -772,8 +774,15 @@ def run_serve(args):
     done += srv.poll_all()
     wall = time.perf_counter() - t0
     lat = np.array([d[4] for d in done]) if done else np.zeros(1)
+    # from the scheduled arrival: the server's latency plus the time the
+    # request waited to be submitted
+    lat_arr = np.array([d[4] + ticket_lag.get(d[0], 0.0) for d in done]) if done else np.zeros(1)
     cells = float(sum(cells_of[ticket_req[d[0]]] for d in done if d[0] in ticket_req))
     ok = sum(1 for d in done if d[1] == nw.NW_OK)
+    failed = {}
+    for d in done:
+        if d[1] != nw.NW_OK:
+            failed[int(d[1])] = failed.get(int(d[1]), 0) + 1
     offered = float(cells_of[idx].sum()) / args.duration
     line = {
         "metric": METRIC, "value": cells / wall / 1e9, "unit": "GCUPS", "n_gpus": 1, "steps": 1, "warmup": 1,
@@ -784,11 +793,15 @@ def run_serve(args):
                                 f"score+CIGAR, requests cycled from {len(reqs)} drawn from seed 1005; certified learned "
                                 f"band, {args.serve_workers} workers, batches of at most {args.serve_batch}, "
                                 "64 GiB traceback budget"),
-                   "requests": int(arrivals.size), "completed": len(done), "ok": ok, "drained": drained,
+                   "requests": int(arrivals.size), "completed": len(done), "ok": ok, "failed_by_status": failed,
+                   "last_failure": srv.last_message(),
+                   "drained": drained,
                    "offered_gcups": offered / 1e9, "backlog_at_end_of_arrivals": backlog["waiting"] + backlog["running"],
                    "arrival_window_s": submit_end, "train_loss": train_loss},
         "latency_s": {"p50": float(np.percentile(lat, 50)), "p99": float(np.percentile(lat, 99)),
-                      "max": float(lat.max())},
+                      "max": float(lat.max()), "from": "submission"},
+        "latency_from_arrival_s": {"p50": float(np.percentile(lat_arr, 50)), "p99": float(np.percentile(lat_arr, 99)),
+                                   "max": float(lat_arr.max())},
         "gpu_launches": None,
     }
     print(json.dumps(line), flush=True)

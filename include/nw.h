@@ -547,6 +547,12 @@ int nw_server_submit_many(nw_server *srv, const uint8_t *pool2b, const uint64_t 
  * returns NW_ERR_CIGAR_TRUNC. */
 int nw_server_poll(nw_server *srv, nw_completion *out, uint32_t cap, uint32_t *count, char *cigar_buf,
                    uint64_t cigar_cap, uint64_t *cigar_used);
+/* The status text and context message of the last batch that failed, with
+ * its request count ("" while none has), copied NUL-terminated into buf
+ * (cap bytes; truncated to fit).  Returns the full length without the NUL,
+ * or -NW_ERR_ARG.  Every request of a failed batch completes with that
+ * batch's status. */
+int64_t nw_server_last_message(nw_server *srv, char *buf, uint64_t cap);
 /* Wait until nothing is queued or running (NW_ERR_TIMEOUT after timeout_s). */
 int nw_server_drain(nw_server *srv, double timeout_s);
 /* [0] submitted, [1] completed, [2] waiting, [3] running, [4] full-grid

@@ -143,6 +143,7 @@ def load():
         "nw_server_submit_many": (ctypes.c_int, [vp, vp, u64p, u32p, u64p, u32p, vp, u32, u64p]),
         "nw_server_poll": (ctypes.c_int, [vp, ctypes.POINTER(Completion), u32, u32p, vp, u64, u64p]),
         "nw_server_drain": (ctypes.c_int, [vp, ctypes.c_double]),
+        "nw_server_last_message": (ctypes.c_int64, [vp, ctypes.c_char_p, ctypes.c_uint64]),
         "nw_server_stats": (ctypes.c_int, [vp, u64p, ctypes.c_int]),
         "nw_server_destroy": (None, [vp]),
     }
@@ -772,6 +773,12 @@ class Server:
 
     def drain(self, timeout_s: float = 600.0) -> bool:
         return load().nw_server_drain(self.handle, timeout_s) == NW_OK
+
+    def last_message(self) -> str:
+        """Status and message of the last batch that failed ("" while none has)."""
+        buf = ctypes.create_string_buffer(1024)
+        n = load().nw_server_last_message(self.handle, buf, len(buf))
+        return buf.value.decode(errors="replace") if n > 0 else ""
 
     def stats(self) -> dict:
         out = (ctypes.c_uint64 * 8)()

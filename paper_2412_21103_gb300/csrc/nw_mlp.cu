@@ -279,6 +279,19 @@ static int gradients(nw_ctx *ctx, BandModel *bm, const float *x, const float *t,
 
 using namespace nw;
 
+// The feature kernel keeps B in dynamic shared memory (one byte per base).
+// Its limit above the default 48 KiB is a per-function attribute of the
+// process, which concurrent callers (the server's workers) share: it is
+// always set to the one value that covers every accepted B, never to a
+// call's own need, so a launch never meets a smaller limit set by another
+// thread.
+constexpr uint32_t kFeatMaxB = 200000;
+static int features_smem(nw_ctx *ctx, uint32_t maxn) {
+    if (maxn <= 48 * 1024) return NW_OK;
+    const cudaError_t e = cudaFuncSetAttribute(k_features, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kFeatMaxB);
+    return e == cudaSuccess ? NW_OK : cuda_fail(ctx, e, "feature kernel shared memory");
+}
+
 // Features -> network -> half-widths (with a safety factor), on the host.
 uint32_t band_start_width(float y, uint32_t m, uint32_t n, double margin, double probe_cap, bool skip);
 
@@ -313,14 +326,14 @@ int learned_band_widths(nw_ctx *ctx, const uint8_t *pool, const uint64_t *a_off,
     if ((rc = scratch(ctx, "lb_feat", (size_t)npairs * kF * 4 + 64, &f))) return rc;
     uint32_t maxn = 4;
     for (uint32_t k = 0; k < npairs; ++k) maxn = std::max(maxn, b_len[k]);
-    if (maxn > 200000) return NW_OK;  // features need B <= 200,000 bases: keep the fixed start
-    if (maxn > 48 * 1024)
-        cudaFuncSetAttribute(k_features, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)maxn);
+    if (maxn > kFeatMaxB) return NW_OK;  // features need B <= 200,000 bases: keep the fixed start
+    if ((rc = features_smem(ctx, maxn))) return rc;
     {
         LaunchTimer t(ctx, "features");
         k_features<<<std::min<uint32_t>(npairs, (uint32_t)ctx->sm_count * 8), kAnchors, maxn, ctx->stream>>>(
             pool, dao, dal, dbo, dbl, npairs, (float *)f);
     }
+    if (const cudaError_t e = cudaGetLastError(); e != cudaSuccess) return cuda_fail(ctx, e, "features launch");
     Acts a;
     if ((rc = forward(ctx, bm, (const float *)f, npairs, a))) return rc;
     std::vector<float> y(npairs);
@@ -369,9 +382,8 @@ int nw_band_features(nw_ctx *ctx, const uint8_t *pool2b, const uint64_t *a_off, 
     cudaMemcpyAsync(dbl, b_len, (size_t)npairs * 4, cudaMemcpyHostToDevice, ctx->stream);
     uint32_t maxn = 4;
     for (uint32_t k = 0; k < npairs; ++k) maxn = std::max(maxn, b_len[k]);
-    if (maxn > 200000) return fail(ctx, NW_ERR_ARG, "features need B <= 200,000 bases");
-    if (maxn > 48 * 1024)
-        cudaFuncSetAttribute(k_features, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)maxn);
+    if (maxn > kFeatMaxB) return fail(ctx, NW_ERR_ARG, "features need B <= 200,000 bases");
+    if (int rc2 = features_smem(ctx, maxn)) return rc2;
     {
         LaunchTimer t(ctx, "features");
         k_features<<<std::min<uint32_t>(npairs, (uint32_t)ctx->sm_count * 8), kAnchors, maxn, ctx->stream>>>(

@@ -174,6 +174,9 @@ struct nw_server {
     uint64_t reserved = 0, inflight = 0;
     uint64_t submitted = 0, completed = 0, cells_done = 0, batches = 0;
     bool stop = false;
+    // the last batch that failed: its status and its context's message
+    uint64_t failed_batches = 0;
+    std::string last_error;
 };
 
 static uint64_t trace_reserve(uint32_t m, uint32_t n, bool cigar) {
@@ -280,6 +283,12 @@ static void worker_loop(nw_server *srv, nw_ctx *ctx) {
                     cudaMemcpyAsync(cig.data(), dcig, coff.back(), cudaMemcpyDeviceToHost, ctx->stream);
                 }
                 rc = nw_ctx_sync(ctx);
+            }
+            if (rc != NW_OK) {
+                std::lock_guard<std::mutex> lk(srv->mu);
+                srv->failed_batches += 1;
+                srv->last_error = std::string(nw_strerror(rc)) + ": " + nw_ctx_last_message(ctx) + " (" +
+                                  std::to_string(np) + " requests)";
             }
             for (uint32_t q = 0; q < np; ++q) {
                 Done &d = out[idx[q]];
@@ -548,6 +557,18 @@ int nw_server_poll(nw_server *srv, nw_completion *out, uint32_t cap, uint32_t *c
     *count = k;
     if (cigar_used) *cigar_used = used;
     return NW_OK;
+}
+
+int64_t nw_server_last_message(nw_server *srv, char *buf, uint64_t cap) {
+    if (!srv || (cap && !buf)) return -NW_ERR_ARG;
+    std::lock_guard<std::mutex> lk(srv->mu);
+    const uint64_t len = srv->last_error.size();
+    if (cap) {
+        const uint64_t k = std::min<uint64_t>(len, cap - 1);
+        memcpy(buf, srv->last_error.data(), k);
+        buf[k] = '\0';
+    }
+    return (int64_t)len;
 }
 
 int nw_server_drain(nw_server *srv, double timeout_s) {

@@ -146,3 +146,26 @@ def test_small_arena_and_ring_wrap_and_wait():
         srv.submit(nw.pack_codes(big), big.size, nw.pack_codes(big), big.size, False)
     srv.close()
     ctx.close()
+
+
+def test_failed_batch_reports_its_status_and_message():
+    """A batch the worker cannot run (its context's memory budget is far too
+    small for the batch's scratch: a failure made on the host) completes
+    every request of it with the batch's status, and the server keeps that
+    status's text and the context's message."""
+    import torch
+    import paper_2412_21103_gb300 as nw
+    ctx = nw.Context(0, torch.cuda.current_stream(), mem_budget=64 << 10)  # 16 KiB per worker
+    srv = nw.Server(ctx, workers=3, max_batch=8, trace_budget=1 << 30)
+    assert srv.last_message() == ""
+    rs = seqgen.Stream(41)
+    tickets = [srv.submit(nw.pack_codes(a), a.size, nw.pack_codes(b), b.size, True)
+               for a, b in ((rs.bases(3000), rs.bases(3100)), (rs.bases(2000), rs.bases(1900)))]
+    assert srv.drain(60.0)
+    res = {t: st for t, st, sc, cg, lat in srv.poll()}
+    st = {res[t] for t in tickets}
+    assert len(res) == 2 and nw.NW_OK not in st
+    msg = srv.last_message()
+    assert any(msg.startswith(nw.load().nw_strerror(x).decode()) for x in st) and "requests)" in msg
+    srv.close()
+    ctx.close()
