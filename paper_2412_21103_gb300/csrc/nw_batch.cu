@@ -387,6 +387,7 @@ static int bits_round(nw_ctx *ctx, const uint8_t *pool, const PlaneSet &planes, 
                       std::vector<uint32_t> &rest) {
     const bool want = flags & NW_CIGAR;
     int rc;
+    HostTimer ht_prep(ctx, "bband_round_prep");
     {
         // pairs that would take longer on their warp than the whole round
         // ideally takes (the GPU's 4 x 152 schedulers busy) spread their
@@ -426,7 +427,8 @@ static int bits_round(nw_ctx *ctx, const uint8_t *pool, const PlaneSet &planes, 
         }
     }
     if (round == 0) ctx->band_stats[0] += items.size();
-    const uint64_t wave_budget = (ctx->budget - std::min(ctx->budget, ctx->used)) / 2;
+    ht_prep.stop();
+    const uint64_t wave_budget = scratch_headroom(ctx, "bband_ptr") / 2;
     size_t k0 = 0;
     while (k0 < items.size()) {
         std::vector<BandBitsItem> wave;
@@ -519,6 +521,7 @@ static int band_rounds(nw_ctx *ctx, const uint8_t *pool, const uint64_t *a_off, 
     uint32_t score_cap_all = 0;
     std::vector<uint32_t> pos_of;         // pair id -> position in ids
     if (use_bits) {
+        HostTimer htp(ctx, "bband_planes");
         a_slot.resize(ids.size());
         b_slot.resize(ids.size());
         for (size_t q = 0; q < ids.size(); ++q) {
@@ -534,12 +537,14 @@ static int band_rounds(nw_ctx *ctx, const uint8_t *pool, const uint64_t *a_off, 
     for (int round = 0; round < kRounds && !pending.empty(); ++round) {
         size_t routed_full = 0;
         // the previous round's pointer words are traced already (stream
-        // order): their slot does not count against this round's waves
-        if (want) {
-            free_prefix(ctx, "band_ptr");
-            free_prefix(ctx, "bband_ptr");
-        }
+        // order): the scalar kernel's slot does not count against this
+        // round's waves.  The window kernel's slot is kept and reused: its
+        // waves budget it by its own headroom, and freeing it while the last
+        // walk still reads it would have the pool map fresh memory for the
+        // next round instead of reusing it.
+        if (want) free_prefix(ctx, "band_ptr");
         // pairs whose band would cover most of the grid go straight to full
+        HostTimer hti(ctx, "bband_items");
         std::vector<BatchTask> tasks;
         std::vector<uint32_t> tw;  // width used per task
         std::vector<uint32_t> next, nextw;  // rejected pairs and their next widths
@@ -602,6 +607,7 @@ static int band_rounds(nw_ctx *ctx, const uint8_t *pool, const uint64_t *a_off, 
             }
             tasks.swap(keep);
             tw.swap(keep_w);
+            hti.stop();
             if (!items.empty() &&
                 (rc = bits_round(ctx, pool, planes, items, iw, round, sc, flags, scores, score_cap_all,
                                  cigar_pool, cigar_off, cigar_len, next, nextw, rest)))

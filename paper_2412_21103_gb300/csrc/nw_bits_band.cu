@@ -403,6 +403,7 @@ int band_bits_fill(nw_ctx *ctx, const PlaneSet &planes, const std::vector<BandBi
     int rc;
     banded.assign(items.size(), 0);
     if (items.empty()) return NW_OK;
+    HostTimer ht(ctx, "bband_fill_host");
     // jobs: pairs of equal shape (g, Q), similar lengths, 32/g per warp
     std::vector<uint32_t> order(items.size());
     for (uint32_t k = 0; k < order.size(); ++k) order[k] = k;
@@ -499,6 +500,7 @@ int band_bits_walk(nw_ctx *ctx, const void *ptr, const std::vector<BandBitsItem>
                    const uint64_t *cigar_off, uint64_t *cigar_len, uint32_t mflag) {
     if (which.empty()) return NW_OK;
     int rc;
+    HostTimer ht(ctx, "bband_walk_host");
     // longest walks first: the kernel's warps take pairs in order
     std::vector<uint32_t> order(which);
     std::stable_sort(order.begin(), order.end(), [&](uint32_t x, uint32_t y) {
@@ -537,6 +539,10 @@ int band_bits_walk(nw_ctx *ctx, const void *ptr, const std::vector<BandBitsItem>
                                     ctx->stream);
     if (e == cudaSuccess)
         e = cudaMemcpyAsync(dtt, tt.data(), tt.size() * sizeof(TraceTask), cudaMemcpyHostToDevice, ctx->stream);
+    // the host task arrays go out of scope: wait for their copies (the fill
+    // before them has finished already; its scores were read back), not for
+    // the walk, so the caller prepares its next round while the GPU walks
+    if (e == cudaSuccess) e = cudaStreamSynchronize(ctx->stream);
     if (e != cudaSuccess) return cuda_fail(ctx, e, "walk tasks H2D");
     {
         LaunchTimer t(ctx, "bband_walk");
@@ -546,10 +552,7 @@ int band_bits_walk(nw_ctx *ctx, const void *ptr, const std::vector<BandBitsItem>
     }
     e = cudaGetLastError();
     if (e != cudaSuccess) return cuda_fail(ctx, e, "walk launch");
-    if ((rc = launch_finish(ctx, TraceTask{}, dtt, (uint32_t)tt.size(), mflag))) return rc;
-    // the host task arrays go out of scope: their copies must have left
-    e = cudaStreamSynchronize(ctx->stream);
-    return e == cudaSuccess ? NW_OK : cuda_fail(ctx, e, "walk sync");
+    return launch_finish(ctx, TraceTask{}, dtt, (uint32_t)tt.size(), mflag);
 }
 
 }  // namespace nw

@@ -247,8 +247,10 @@ struct HostTimer {
     nw_ctx *ctx;
     const char *name;
     double t0;
+    bool done = false;
     HostTimer(nw_ctx *c, const char *n);
-    ~HostTimer();
+    ~HostTimer() { stop(); }
+    void stop();  // ends the section early (once)
 };
 
 // Autotuning keys and the graph cache (nw_runtime.cu).

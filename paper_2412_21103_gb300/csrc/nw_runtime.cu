@@ -119,7 +119,9 @@ static double wall_ms() {
 
 HostTimer::HostTimer(nw_ctx *c, const char *n) : ctx(c), name(n), t0(c->profiling ? wall_ms() : 0.0) {}
 
-HostTimer::~HostTimer() {
+void HostTimer::stop() {
+    if (done) return;
+    done = true;
     if (!ctx->profiling) return;
     KernelStat &st = ctx->stats[std::string("host:") + name];
     st.ms += wall_ms() - t0;
