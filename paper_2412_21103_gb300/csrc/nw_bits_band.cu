@@ -473,8 +473,17 @@ int band_bits_fill(nw_ctx *ctx, const PlaneSet &planes, const std::vector<BandBi
     a.gap = gap;
     a.err = ctx->d_err;
     auto kern = want ? k_bits_band<true> : k_bits_band<false>;
+    // Two CTAs per SM (two warps per scheduler), not the five the registers
+    // allow: the jobs are taken longest first, and a long job that shares
+    // its scheduler with four others runs at a fifth of its speed and ends
+    // the launch alone.  Measured on GB300 (config 4, 20,000 pairs, CTAs per
+    // SM 5 / 4 / 3 / 2 / 1): the fills took 54.4 / 48.1 / 41.2 / 37.7 /
+    // 45.0 ms.  NW_BBAND_OCC overrides (sweeps).
     int occ = 0;
     cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kern, kBandWarps * 32, 0);
+    int cap = 2;
+    if (const char *e = getenv("NW_BBAND_OCC")) cap = std::max(1, atoi(e));
+    occ = std::min(occ, cap);
     uint32_t blocks = (uint32_t)std::max(occ, 1) * (uint32_t)ctx->sm_count;
     blocks = std::max(1u, std::min(blocks, (a.njobs + kBandWarps - 1) / kBandWarps));
     {
