@@ -335,6 +335,14 @@ int bits_prepare(nw_ctx *ctx, const uint8_t *pool, std::vector<BatchTask> &tasks
     int occ = 0;
     cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, plan->gen ? k_bits_score<true> : k_bits_score<false>,
                                                   kBitsWarps * 32, 0);
+    // One CTA of 8 warps per SM (two warps per scheduler), not the most the
+    // registers allow: with more, the longest jobs -- taken first -- share
+    // their scheduler with the rest and finish the launch alone.  Measured on
+    // GB300 (all-vs-all of 512 sequences, CTAs per SM 8 / 3 / 2 / 1): 17.6k /
+    // 17.7k / 22.4k / 23.7k GCUPS.  NW_BITS_OCC overrides (sweeps).
+    int cap = 1;
+    if (const char *e = getenv("NW_BITS_OCC")) cap = std::max(1, atoi(e));
+    occ = std::min(occ, cap);
     if (occ < 1) occ = 1;
     uint32_t blocks = (uint32_t)occ * (uint32_t)ctx->sm_count;
     const uint32_t need = (ba.njobs + kBitsWarps - 1) / kBitsWarps;
