@@ -469,7 +469,8 @@ int nw_score_all_pairs(nw_ctx *ctx, const uint8_t *pool2b, const uint64_t *off, 
  * rows later from the CIGARs); msa_ld below the column count returns
  * NW_ERR_CIGAR_TRUNC with every other output written.  Buffers are device
  * memory on the context's device unless NW_HOST_IO; NW_GRAPH applies to the
- * scoring stage; NW_CIGAR_M is passed to the alignments.  Synchronises the
+ * scoring stage (with NW_HOST_IO too: it runs on the copied pool);
+ * NW_CIGAR_M is passed to the alignments.  Synchronises the
  * context's stream (the center and the column count come to the host).
  * 1..65535 sequences. */
 int nw_center_star(nw_ctx *ctx, const uint8_t *pool2b, const uint64_t *off, const uint32_t *len, uint32_t nseq,
