@@ -522,7 +522,10 @@ typedef struct {
  * queue_bytes >= 4096, queue_slots a power of two in 2..2^30; or device
  * memory).  The context must outlive the server.  The arena and the ring
  * are allocated on the context's device outside its scratch budget
- * (queue_bytes + 40 * queue_slots bytes). */
+ * (queue_bytes + 40 * queue_slots bytes).  Each worker's context gets a
+ * scratch budget of 1/(workers+1) of what is available at creation: the
+ * creating context's unused budget, capped at 90 % of the device's free
+ * memory. */
 nw_server *nw_server_create_ex(nw_ctx *ctx, uint32_t workers, uint32_t max_batch, uint64_t trace_budget,
                                uint64_t queue_bytes, uint32_t queue_slots, nw_scoring sc, uint32_t flags);
 /* nw_server_create_ex with a 1 GiB arena and 2^20 slots. */

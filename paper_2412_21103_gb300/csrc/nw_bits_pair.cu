@@ -413,7 +413,9 @@ int bits_pairs(nw_ctx *ctx, const uint8_t *pool, const std::vector<PairJob> &job
     auto steps = [&](size_t k) { return (double)jobs[k].m + jobs[k].n + jobs[k].m / 31.0; };
     std::sort(order.begin(), order.end(), [&](size_t x, size_t y) { return steps(x) > steps(y); });
     const uint32_t cap_warps = resident_warps(ctx, gen, want);
-    const uint64_t room = scratch_headroom(ctx, "bpair_rec");
+    // half of what the records' slot may grow to: the walks and the rest of
+    // a batch still need scratch after the waves (a lone pair may take more)
+    const uint64_t room = scratch_headroom(ctx, "bpair_rec") / 2;
     size_t next = 0;
     while (next < order.size()) {
         std::vector<size_t> wave;
@@ -422,7 +424,7 @@ int bits_pairs(nw_ctx *ctx, const uint8_t *pool, const std::vector<PairJob> &job
             const size_t k = order[next];
             const PairGeom g = pair_geom(jobs[k].m, jobs[k].n);
             const uint64_t r = want ? g.rec_bytes : 0;
-            if (!wave.empty() && (warps + g.nwarps > cap_warps || rec + r > room)) break;
+            if (!wave.empty() && (warps + g.nwarps > cap_warps || rec + r > room)) break;  // a first pair always goes
             if (g.nwarps > cap_warps)
                 return fail(ctx, NW_ERR_ARG, "pair of %u rows needs %u resident warps", jobs[k].m, g.nwarps);
             wave.push_back(k);

@@ -24,6 +24,7 @@
 // results.  Batches of different workers run on different streams, so
 // requests that arrive while others are on the GPU are admitted as soon as
 // a worker and memory are free, and their kernels overlap on the device.
+#include <algorithm>
 #include <chrono>
 #include <condition_variable>
 #include <cstring>
@@ -464,7 +465,14 @@ nw_server *nw_server_create_ex(nw_ctx *ctx, uint32_t workers, uint32_t max_batch
         params.resize(nw_band_model_size());
         if (nw_band_model_get(ctx, params.data(), params.size()) != NW_OK) params.clear();
     }
-    const uint64_t per = ctx->budget / (workers + 1);
+    // each worker's scratch budget: a share of what is really available --
+    // the creating context's unused budget, and at most 90 % of the device's
+    // free memory (the creating context may hold scratch of earlier calls)
+    size_t free_b = 0, total_b = 0;
+    uint64_t avail = ctx->budget - std::min(ctx->budget, ctx->used);
+    if (cudaMemGetInfo(&free_b, &total_b) == cudaSuccess) avail = std::min<uint64_t>(avail, (uint64_t)(free_b * 0.9));
+    else cudaGetLastError();
+    const uint64_t per = avail / (workers + 1);
     for (uint32_t w = 0; w < workers; ++w) {
         cudaStream_t st = nullptr;
         if (cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking) != cudaSuccess) {

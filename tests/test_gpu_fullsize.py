@@ -125,13 +125,17 @@ def test_config5_two_thousand_requests(trained_ctx):
     srv = nw.Server(trained_ctx, workers=8, max_batch=64, trace_budget=64 << 30, flags=nw.NW_LEARNED_BAND)
     pool, ao, al, bo, bl = _pool([(r.pair.a, r.pair.b) for r in reqs])
     tickets = srv.submit_many(pool, ao, al, bo, bl, [r.want_cigar for r in reqs])
-    assert srv.drain(300.0)
+    assert srv.drain(300.0), srv.stats()
     got = {t: (st, sc, cg) for t, st, sc, cg, lat in srv.poll_all()}
+    failure = srv.last_message()
     srv.close()
-    assert len(got) == 2000 and all(st == nw.NW_OK for st, _, _ in got.values())
+    assert len(got) == 2000, len(got)
+    bad = {st for st, _, _ in got.values() if st != nw.NW_OK}
+    assert not bad, (bad, failure)
     res = [got[int(t)] for t in tickets]
     want = oracle.score_many([(r.pair.a, r.pair.b) for r in reqs])
-    assert [sc for _, sc, _ in res] == want
+    wrong = [k for k in range(len(reqs)) if res[k][1] != want[k]]
+    assert not wrong, [(k, reqs[k].pair.a.size, reqs[k].pair.b.size, res[k][1], want[k]) for k in wrong[:10]]
     small = [k for k, r in enumerate(reqs) if r.want_cigar and r.pair.a.size * r.pair.b.size <= 3e7]
     big = [k for k, r in enumerate(reqs) if r.want_cigar and r.pair.a.size * r.pair.b.size > 3e7]
     for k, (s, ops) in zip(small, oracle.align_many([(reqs[k].pair.a, reqs[k].pair.b) for k in small])):
