@@ -69,8 +69,17 @@ __global__ void __launch_bounds__(kAnchors) k_features(const uint8_t *pool, cons
             const int32_t W = max(1, (int32_t)(L / 8));
             const int32_t c0 = (int32_t)i + e;
             const int32_t jlo = max(0, c0 - W), jhi = min((int32_t)nk - 1, c0 + W);
-            for (int32_t j = jlo; j <= jhi; ++j) {
-                if (bcode[j] == ac) {
+            // four codes per 32-bit load; a byte of x is zero exactly where
+            // the code equals ac (hi: its high bit set for every nonzero byte)
+            const uint32_t acx4 = ac * 0x01010101u;
+            const uint32_t *bw = reinterpret_cast<const uint32_t *>(bcode);
+            for (int32_t w = jlo >> 2; w <= (jhi >> 2); ++w) {
+                const uint32_t x = bw[w] ^ acx4;
+                uint32_t zero = ~((((x & 0x7F7F7F7Fu) + 0x7F7F7F7Fu) | x) & 0x80808080u) & 0x80808080u;
+                while (zero) {
+                    const int32_t j = 4 * w + ((__ffs(zero) - 1) >> 3);
+                    zero &= zero - 1;
+                    if (j < jlo || j > jhi) continue;
                     const int32_t bin = (int32_t)(((int64_t)(j - c0 + W) * kBins) / (2 * W + 1));
                     atomicAdd(&hist[min(max(bin, 0), kBins - 1)], 1u);
                 }
