@@ -522,6 +522,7 @@ static int band_rounds(nw_ctx *ctx, const uint8_t *pool, const uint64_t *a_off, 
     std::vector<uint32_t> pos_of;         // pair id -> position in ids
     if (use_bits) {
         HostTimer htp(ctx, "bband_planes");
+        planes.reserve(2 * ids.size());
         a_slot.resize(ids.size());
         b_slot.resize(ids.size());
         for (size_t q = 0; q < ids.size(); ++q) {

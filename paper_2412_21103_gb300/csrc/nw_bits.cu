@@ -198,15 +198,44 @@ __global__ void k_planes(const uint8_t *pool, const PlaneSeg *segs, uint32_t nse
 }
 
 // ------------------------------------------------------------------ host
+static size_t plane_hash(uint64_t off, uint32_t len) {
+    uint64_t z = off * 0x9E3779B97F4A7C15ull ^ ((uint64_t)len << 17);
+    z ^= z >> 31;
+    z *= 0xBF58476D1CE4E5B9ull;
+    return (size_t)(z ^ (z >> 29));
+}
+
+void PlaneSet::rehash(size_t size) {
+    std::vector<Entry> old;
+    old.swap(table_);
+    table_.assign(size, Entry{0, 0, 0, 0});
+    for (const Entry &e : old) {
+        if (!e.used) continue;
+        size_t h = plane_hash(e.off, e.len) & (size - 1);
+        while (table_[h].used) h = (h + 1) & (size - 1);
+        table_[h] = e;
+    }
+}
+
+void PlaneSet::reserve(size_t n) {
+    size_t size = 64;
+    while (size < 2 * n) size *= 2;
+    if (size > table_.size()) rehash(size);
+    segs_.reserve(n);
+}
+
 int64_t PlaneSet::add(uint64_t off, uint32_t len) {
-    const Key k{off, len};
-    auto it = slots_.find(k);
-    if (it != slots_.end()) return it->second;
+    if (2 * (count_ + 1) > table_.size()) rehash(std::max<size_t>(64, 2 * table_.size()));
+    const size_t mask = table_.size() - 1;
+    size_t h = plane_hash(off, len) & mask;
+    for (; table_[h].used; h = (h + 1) & mask)
+        if (table_[h].off == off && table_[h].len == len) return table_[h].slot;
     const uint32_t nbytes = (len + 3) / 4;
     const int64_t slot = (int64_t)words_ * 32 - kPlanePad;
     segs_.push_back(PlaneSeg{off, nbytes, (uint32_t)words_});
     words_ += (nbytes + 7) / 8 + 2;
-    slots_.emplace(k, slot);
+    table_[h] = Entry{off, len, 1, slot};
+    ++count_;
     return slot;
 }
 

@@ -3,7 +3,6 @@
 #pragma once
 
 #include <string>
-#include <unordered_map>
 #include <vector>
 
 #include "nw_internal.cuh"
@@ -79,6 +78,8 @@ struct PlaneSeg {
 };
 class PlaneSet {
   public:
+    // Room for n sequences without regrowing.
+    void reserve(size_t n);
     // Slot (global base index of base 0) of the sequence at pool byte `off`
     // with `len` bases, added on first use.
     int64_t add(uint64_t off, uint32_t len);
@@ -94,15 +95,16 @@ class PlaneSet {
     int64_t max_base = 0;
 
   private:
-    struct Key {
+    // open addressing (linear probing, at most half full): one table of
+    // entries instead of a node per sequence
+    struct Entry {
         uint64_t off;
-        uint32_t len;
-        bool operator==(const Key &o) const { return off == o.off && len == o.len; }
+        uint32_t len, used;
+        int64_t slot;
     };
-    struct KeyHash {
-        size_t operator()(const Key &k) const { return std::hash<uint64_t>()(k.off * 0x9E3779B97F4A7C15ull ^ k.len); }
-    };
-    std::unordered_map<Key, int64_t, KeyHash> slots_;
+    std::vector<Entry> table_;
+    size_t count_ = 0;
+    void rehash(size_t size);
     std::vector<PlaneSeg> segs_;
     uint64_t words_ = 2;  // kPlanePad bases in front of the first slot
     PlaneSeg *dsegs_ = nullptr;

@@ -404,6 +404,7 @@ int band_bits_fill(nw_ctx *ctx, const PlaneSet &planes, const std::vector<BandBi
     banded.assign(items.size(), 0);
     if (items.empty()) return NW_OK;
     HostTimer ht(ctx, "bband_fill_host");
+    HostTimer htp(ctx, "bband_fill_prep");
     // jobs: pairs of equal shape (g, Q), similar lengths, 32/g per warp
     std::vector<uint32_t> order(items.size());
     for (uint32_t k = 0; k < order.size(); ++k) order[k] = k;
@@ -473,6 +474,7 @@ int band_bits_fill(nw_ctx *ctx, const PlaneSet &planes, const std::vector<BandBi
     a.gap = gap;
     a.err = ctx->d_err;
     auto kern = want ? k_bits_band<true> : k_bits_band<false>;
+    htp.stop();
     // Two CTAs per SM (two warps per scheduler), not the five the registers
     // allow: the jobs are taken longest first, and a long job that shares
     // its scheduler with four others runs at a fifth of its speed and ends
