@@ -2,6 +2,7 @@
 // (the kernel is in nw_batch_kernel.cuh), straggler routing, the certified
 // banded rounds (a8), CUDA graphs, and the C entry points.
 #include <algorithm>
+#include <cmath>
 #include <chrono>
 #include <cstdlib>
 #include <cstring>
@@ -203,45 +204,64 @@ static int check_band_scoring(nw_ctx *ctx, const nw_scoring &sc) {
 // One warp per pair is efficient while the batch fills the GPU, but a pair
 // much longer than the rest (or a long pair in a small batch) leaves the GPU
 // idle while one warp grinds through it.  The longest pairs go to the
-// multi-warp single-pair kernel, one after another: with pairs sorted by
-// one-warp time, routing the first k costs sum(single-pair times) +
-// max(the rest's ideal batch time, the (k+1)-th one-warp time), and the k
-// with the lowest estimate is taken.  Rates are GB300 measurements (cells/s):
-// one warp of the batched kernels, the whole batched kernel, and the scalar
-// single-pair kernel on a long pair; the bit-sliced single-pair kernel runs
-// a chain of m + n + m/31 steps of about 40 ns, then its walk.
+// multi-warp single-pair kernels instead: with pairs sorted by one-warp
+// time, routing the first k costs the routed pairs' time + max(the rest's
+// ideal batch time, the (k+1)-th one-warp time), and the k with the lowest
+// estimate is taken.  Routed pairs on the bit-sliced single-pair kernel run
+// together, each on its own warps (m/992 of them), so they cost the larger
+// of their longest chain and their warp-seconds spread over the GPU's
+// schedulers (1.5 warps at full speed on each); pairs on the scalar kernel
+// run one after another.  Rates are GB300 measurements (cells/s): one warp
+// of the batched kernels, the whole batched kernel, and the scalar
+// single-pair kernel on a long pair; the bit-sliced one runs a chain of
+// m + n + m/31 steps of about 40 ns, then its walk.
 constexpr double kWarpRate = 2e9, kBatchRate = 3.5e12, kPairRate = 2e11, kPairFixed = 1e-3;
 constexpr double kBitsStepSeconds = 40e-9, kBitsPairFixed = 0.3e-3;
 
-// Seconds the single-pair path takes on an m x n pair.
-static double single_pair_seconds(uint32_t m, uint32_t n, const nw_scoring &sc) {
+struct PairCost {
+    double secs;   // time of the pair on the single-pair path
+    double warps;  // its warps on the bit-sliced kernel (0: the scalar kernel, one pair at a time)
+};
+
+static PairCost single_pair_cost(uint32_t m, uint32_t n, const nw_scoring &sc) {
     if (bits_scoring_ok(sc) && std::min(m, n) >= 64)
-        return ((double)m + n + m / 31.0) * kBitsStepSeconds + kBitsPairFixed;
-    return (double)m * n / kPairRate + kPairFixed;
+        return PairCost{((double)m + n + m / 31.0) * kBitsStepSeconds + kBitsPairFixed,
+                        std::ceil(std::ceil(m / 31.0) / 32.0)};
+    return PairCost{(double)m * n / kPairRate + kPairFixed, 0.0};
 }
 
 // warp_cells[k]: cells pair k costs on one warp (scaled for slower
-// kernels), full_cells[k]: its full grid, pair_secs[k] (or, when empty,
-// full_cells[k] / kPairRate + kPairFixed): its time on the single-pair path.
-// Returns the indices to route.
+// kernels), full_cells[k]: its full grid, costs[k] (or, when empty,
+// full_cells[k] / kPairRate + kPairFixed on the scalar kernel): its cost on
+// the single-pair path; sms: the GPU's SMs.  Returns the indices to route.
 static std::vector<size_t> pick_stragglers(const std::vector<double> &warp_cells, const std::vector<double> &full_cells,
-                                           const std::vector<double> &pair_secs, double batch_rate = kBatchRate) {
+                                           const std::vector<PairCost> &costs, int sms,
+                                           double batch_rate = kBatchRate) {
     std::vector<size_t> order(warp_cells.size());
     std::iota(order.begin(), order.end(), (size_t)0);
     std::sort(order.begin(), order.end(), [&](size_t x, size_t y) { return warp_cells[x] > warp_cells[y]; });
     double rest = 0;
     for (double c : warp_cells) rest += c;
-    double routed = 0, best = 1e300;
+    const double lanes = 6.0 * std::max(sms, 1);  // warps at full speed on the GPU's schedulers
+    double serial = 0, conc_sum = 0, conc_max = 0, best = 1e300;
     size_t best_k = 0;
     for (size_t k = 0; k <= order.size(); ++k) {
         const double tail = k < order.size() ? warp_cells[order[k]] / kWarpRate : 0.0;
-        const double est = routed + std::max(rest / batch_rate, tail);
+        const double est = serial + std::max(conc_max, conc_sum / lanes) + std::max(rest / batch_rate, tail);
         if (est < best) {
             best = est;
             best_k = k;
         }
-        if (k == order.size() || full_cells[order[k]] < 1e7) break;
-        routed += pair_secs.empty() ? full_cells[order[k]] / kPairRate + kPairFixed : pair_secs[order[k]];
+        if (k == order.size()) break;
+        const PairCost c = costs.empty() ? PairCost{full_cells[order[k]] / kPairRate + kPairFixed, 0.0}
+                                         : costs[order[k]];
+        if (c.warps > 0) {
+            conc_sum += c.secs * c.warps;
+            conc_max = std::max(conc_max, c.secs);
+        } else {
+            if (full_cells[order[k]] < 1e7) break;  // small pairs are not worth the scalar kernel's launches
+            serial += c.secs;
+        }
         rest -= warp_cells[order[k]];
     }
     return std::vector<size_t>(order.begin(), order.begin() + best_k);
@@ -402,13 +422,14 @@ static int bits_round(nw_ctx *ctx, const uint8_t *pool, const PlaneSet &planes, 
         // one warp of this kernel runs its pair at about the scalar batch
         // kernel's per-warp rate; the whole kernel fills the GPU's 4 x 152
         // schedulers
-        std::vector<double> wc(items.size()), fc(items.size()), ps(items.size());
+        std::vector<double> wc(items.size()), fc(items.size());
+        std::vector<PairCost> ps(items.size());
         for (size_t q = 0; q < items.size(); ++q) {
             wc[q] = band_bits_seconds(items[q].shape) * kWarpRate;
             fc[q] = (double)items[q].m * items[q].n;
-            ps[q] = single_pair_seconds(items[q].m, items[q].n, sc);
+            ps[q] = single_pair_cost(items[q].m, items[q].n, sc);
         }
-        const std::vector<size_t> strag = pick_stragglers(wc, fc, ps, kWarpRate * 4.0 * ctx->sm_count);
+        const std::vector<size_t> strag = pick_stragglers(wc, fc, ps, ctx->sm_count, kWarpRate * 4.0 * ctx->sm_count);
         if (!strag.empty()) {
             std::vector<char> routed(items.size(), 0);
             for (size_t q : strag) {
@@ -618,13 +639,14 @@ static int band_rounds(nw_ctx *ctx, const uint8_t *pool, const uint64_t *a_off, 
             // banded pairs that would leave the GPU idle on one warp run full
             // on the single-pair kernel instead (counted as fallbacks); a
             // banded warp is ~1.5x slower per cell than a full-grid one
-            std::vector<double> wc(tasks.size()), fc(tasks.size()), ps(tasks.size());
+            std::vector<double> wc(tasks.size()), fc(tasks.size());
+            std::vector<PairCost> ps(tasks.size());
             for (size_t q = 0; q < tasks.size(); ++q) {
                 wc[q] = 1.5 * (double)band_cells(tasks[q], R);
                 fc[q] = (double)tasks[q].m * tasks[q].n;
-                ps[q] = single_pair_seconds(tasks[q].m, tasks[q].n, sc);
+                ps[q] = single_pair_cost(tasks[q].m, tasks[q].n, sc);
             }
-            const std::vector<size_t> strag = pick_stragglers(wc, fc, ps);
+            const std::vector<size_t> strag = pick_stragglers(wc, fc, ps, ctx->sm_count);
             routed_full = strag.size();
             if (!strag.empty()) {
                 std::vector<char> routed(tasks.size(), 0);
@@ -895,12 +917,13 @@ int batch_device_impl(nw_ctx *ctx, const uint8_t *pool, const uint64_t *a_off, c
     // kernel, and so do pairs whose pointer matrix alone exceeds half the
     // remaining budget (the single-pair path recomputes from checkpoints)
     {
-        std::vector<double> wc(tasks.size()), fc(tasks.size()), ps(tasks.size());
+        std::vector<double> wc(tasks.size()), fc(tasks.size());
+        std::vector<PairCost> ps(tasks.size());
         for (size_t q = 0; q < tasks.size(); ++q) {
             wc[q] = fc[q] = (double)tasks[q].m * tasks[q].n;
-            ps[q] = single_pair_seconds(tasks[q].m, tasks[q].n, sc);
+            ps[q] = single_pair_cost(tasks[q].m, tasks[q].n, sc);
         }
-        std::vector<size_t> strag = pick_stragglers(wc, fc, ps);
+        std::vector<size_t> strag = pick_stragglers(wc, fc, ps, ctx->sm_count);
         if (want) {
             const uint64_t room = (ctx->budget - std::min(ctx->budget, ctx->used)) / 2;
             std::vector<char> in(tasks.size(), 0);
@@ -995,12 +1018,13 @@ int batch_device_impl(nw_ctx *ctx, const uint8_t *pool, const uint64_t *a_off, c
             ids_w.push_back(t.out0);
         }
         if (k < npairs || k0 > 0) {  // a true wave (not the whole batch): route its stragglers
-            std::vector<double> wc(wave.size()), ps(wave.size());
+            std::vector<double> wc(wave.size());
+            std::vector<PairCost> ps(wave.size());
             for (size_t q = 0; q < wave.size(); ++q) {
                 wc[q] = (double)wave[q].m * wave[q].n;
-                ps[q] = single_pair_seconds(wave[q].m, wave[q].n, sc);
+                ps[q] = single_pair_cost(wave[q].m, wave[q].n, sc);
             }
-            const std::vector<size_t> strag = pick_stragglers(wc, wc, ps);
+            const std::vector<size_t> strag = pick_stragglers(wc, wc, ps, ctx->sm_count);
             if (!strag.empty() && strag.size() < wave.size()) {
                 std::vector<char> routed(wave.size(), 0);
                 std::vector<BatchTask> st;
@@ -1198,7 +1222,7 @@ extern "C" int64_t nw_route_stragglers(const double *warp_cells, const double *f
                                        uint32_t *out) {
     if (n && (!warp_cells || !full_cells || !out)) return -NW_ERR_ARG;
     const std::vector<size_t> r = pick_stragglers(std::vector<double>(warp_cells, warp_cells + n),
-                                                  std::vector<double>(full_cells, full_cells + n), {});
+                                                  std::vector<double>(full_cells, full_cells + n), {}, 152);
     for (size_t k = 0; k < r.size(); ++k) out[k] = (uint32_t)r[k];
     return (int64_t)r.size();
 }
