@@ -267,6 +267,15 @@ static std::vector<size_t> pick_stragglers(const std::vector<double> &warp_cells
     return std::vector<size_t>(order.begin(), order.begin() + best_k);
 }
 
+// NW_BAND_KEEP=1 keeps every pair in the banded rounds (none leaves them for
+// scheduling), so that what the rounds certify measures the band widths
+// alone; small batches otherwise send wide-band pairs to the full-grid
+// single-pair kernel, which runs them together.
+static bool band_keep_all() {
+    const char *e = getenv("NW_BAND_KEEP");
+    return e && *e && *e != '0';
+}
+
 // Run one pair on the single-pair kernels, writing into the batch outputs.
 static int run_straggler(nw_ctx *ctx, const uint8_t *pool, uint64_t a_off, uint32_t m, uint64_t b_off, uint32_t n,
                          const nw_scoring &sc, uint32_t flags, int32_t *score, char *cigar, uint64_t cigar_cap,
@@ -429,7 +438,9 @@ static int bits_round(nw_ctx *ctx, const uint8_t *pool, const PlaneSet &planes, 
             fc[q] = (double)items[q].m * items[q].n;
             ps[q] = single_pair_cost(items[q].m, items[q].n, sc);
         }
-        const std::vector<size_t> strag = pick_stragglers(wc, fc, ps, ctx->sm_count, kWarpRate * 4.0 * ctx->sm_count);
+        const std::vector<size_t> strag = band_keep_all()
+                                              ? std::vector<size_t>()
+                                              : pick_stragglers(wc, fc, ps, ctx->sm_count, kWarpRate * 4.0 * ctx->sm_count);
         if (!strag.empty()) {
             std::vector<char> routed(items.size(), 0);
             for (size_t q : strag) {
@@ -646,7 +657,8 @@ static int band_rounds(nw_ctx *ctx, const uint8_t *pool, const uint64_t *a_off, 
                 fc[q] = (double)tasks[q].m * tasks[q].n;
                 ps[q] = single_pair_cost(tasks[q].m, tasks[q].n, sc);
             }
-            const std::vector<size_t> strag = pick_stragglers(wc, fc, ps, ctx->sm_count);
+            const std::vector<size_t> strag =
+                band_keep_all() ? std::vector<size_t>() : pick_stragglers(wc, fc, ps, ctx->sm_count);
             routed_full = strag.size();
             if (!strag.empty()) {
                 std::vector<char> routed(tasks.size(), 0);

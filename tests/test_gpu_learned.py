@@ -62,21 +62,30 @@ def test_learned_band_beats_fixed_start_and_full_grid():
     want = oracle.align_many(held_out)
     full_cells = sum(int(x) * int(y) for x, y in zip(al, bl))
 
-    # without the network: certified band from the fixed start (64)
-    c0 = nw.Context(0, torch.cuda.current_stream())
-    s0, g0 = nw.nw_align_batch(c0, pool, ao, al, bo, bl, (1, -1, -1), nw.NW_CIGAR | nw.NW_LEARNED_BAND)
-    st0 = nw.nw_ctx_band_stats(c0)
+    # every pair stays in the banded rounds (none is sent to the full-grid
+    # kernel for scheduling), so that the certificates measure the widths
+    os.environ["NW_BAND_KEEP"] = "1"
+    try:
+        # without the network: certified band from the fixed start (64)
+        c0 = nw.Context(0, torch.cuda.current_stream())
+        s0, g0 = nw.nw_align_batch(c0, pool, ao, al, bo, bl, (1, -1, -1), nw.NW_CIGAR | nw.NW_LEARNED_BAND)
+        st0 = nw.nw_ctx_band_stats(c0)
 
-    # with the network trained on the GPU
-    c1 = nw.Context(0, torch.cuda.current_stream())
-    first, last = _train(nw, c1)
-    assert last < 0.5 * first
-    s1, g1 = nw.nw_align_batch(c1, pool, ao, al, bo, bl, (1, -1, -1), nw.NW_CIGAR | nw.NW_LEARNED_BAND)
-    st1 = nw.nw_ctx_band_stats(c1)
+        # with the network trained on the GPU
+        c1 = nw.Context(0, torch.cuda.current_stream())
+        first, last = _train(nw, c1)
+        assert last < 0.5 * first
+        s1, g1 = nw.nw_align_batch(c1, pool, ao, al, bo, bl, (1, -1, -1), nw.NW_CIGAR | nw.NW_LEARNED_BAND)
+        st1 = nw.nw_ctx_band_stats(c1)
+    finally:
+        del os.environ["NW_BAND_KEEP"]
+    # with scheduling on, the same results whatever the rounds keep
+    s2, g2 = nw.nw_align_batch(c1, pool, ao, al, bo, bl, (1, -1, -1), nw.NW_CIGAR | nw.NW_LEARNED_BAND)
 
     for k, (s, ops) in enumerate(want):
         assert s0[k] == s and g0[k] == oracle.rle(ops)
         assert s1[k] == s and g1[k] == oracle.rle(ops)
+        assert s2[k] == s and g2[k] == oracle.rle(ops)
 
     def swept(st):
         # banded cells plus the full grid of every pair that fell back
