@@ -1,6 +1,6 @@
-"""The seeded synthetic inputs have the shapes the configs state (the input
-recipes of the design notes): lengths, mutation rates, arrival process, and
-every generated pair's transcript turns A into B."""
+"""The seeded synthetic inputs have the shapes the workloads state: lengths,
+mutation rates, arrival process, and every generated pair's transcript turns
+A into B."""
 import numpy as np
 
 import seqgen
