@@ -420,12 +420,15 @@ static int bits_round(nw_ctx *ctx, const uint8_t *pool, const PlaneSet &planes, 
     {
         // pairs that would take longer on their warp than the whole round
         // ideally takes (the GPU's 4 x 152 schedulers busy) spread their
-        // window over more lanes
+        // window over more lanes (NW_BBAND_FAST=0 keeps every pair on the
+        // throughput shape)
+        const char *fe = getenv("NW_BBAND_FAST");
+        const bool fast_on = !(fe && *fe == '0');
         double total = 0;
         for (const auto &it : items) total += band_bits_seconds(it.shape);
         const double ideal = total / (4.0 * ctx->sm_count);
         for (auto &it : items)
-            if (band_bits_seconds(it.shape) > ideal) band_bits_fast(&it.shape);
+            if (fast_on && band_bits_seconds(it.shape) > ideal) band_bits_fast(&it.shape);
     }
     {
         // one warp of this kernel runs its pair at about the scalar batch
@@ -611,6 +614,7 @@ static int band_rounds(nw_ctx *ctx, const uint8_t *pool, const uint64_t *a_off, 
             std::vector<BandBitsItem> items;
             std::vector<uint32_t> iw, keep_w;
             std::vector<BatchTask> keep;
+            const int max_q = band_bits_max_q();
             for (size_t q = 0; q < tasks.size(); ++q) {
                 const BatchTask &t = tasks[q];
                 BandBitsShape sh;
@@ -629,7 +633,7 @@ static int band_rounds(nw_ctx *ctx, const uint8_t *pool, const uint64_t *a_off, 
                     wq = cap;
                     band_task(tb, R, wq);
                 }
-                if (band_bits_shape(tb.m, tb.n, tb.lo, tb.hi, &sh)) {
+                if (band_bits_shape(tb.m, tb.n, tb.lo, tb.hi, &sh, max_q)) {
                     const uint32_t pq = pos_of[tb.out0];
                     items.push_back(BandBitsItem{tb.a_off, tb.b_off, 0, a_slot[pq], b_slot[pq], tb.m, tb.n, tb.out0, sh});
                     iw.push_back(wq);

@@ -169,9 +169,13 @@ struct BandBitsItem {
     uint32_t m, n, out0;
     BandBitsShape shape;
 };
-// The window of the band of diagonals [lo, hi]; false when it needs more
-// than 128 words (4,096 rows).
-bool band_bits_shape(uint32_t m, uint32_t n, int32_t lo, int32_t hi, BandBitsShape *s);
+// Most words per lane of the throughput shape: 4, or NW_BBAND_MAXQ (1..4)
+// when set (read on each call; a round reads it once).
+int band_bits_max_q();
+// The window of the band of diagonals [lo, hi] on the fewest lanes of at
+// most max_q words each; false when it needs more than 128 words (4,096
+// rows).
+bool band_bits_shape(uint32_t m, uint32_t n, int32_t lo, int32_t hi, BandBitsShape *s, int max_q);
 // The same window spread over as many lanes as it has words (up to 32):
 // fewer instructions per lane and step, so a shorter time for the pair.
 void band_bits_fast(BandBitsShape *s);

@@ -36,6 +36,7 @@
 // anti-diagonals: (L, Hb) of the first, (L, Hb) of the second.
 #include <algorithm>
 #include <cmath>
+#include <cstdlib>
 #include <vector>
 
 #include "nw_bits.cuh"
@@ -43,8 +44,9 @@
 namespace nw {
 
 // Words per lane: at most 4, so a pair's window holds up to 128 words (4,096
-// rows, bands up to ~8,190 diagonals) and a lane ~100 registers (wider Q
-// measured slower: fewer warps per SM to hide the update's dependency chain).
+// rows, bands up to ~8,190 diagonals).  Up to 8 words per lane (fewer lanes
+// per pair, the lane's fixed work per step shared by more words) measured
+// 1.5x slower on the band workload: 27.3 against 18.0 ms per fill.
 constexpr int kBandBitsMaxQ = 4;
 constexpr int kBandBitsMaxWords = 32 * kBandBitsMaxQ;
 constexpr int kWalkWarps = 4;
@@ -167,6 +169,8 @@ __device__ __forceinline__ void band_job(const BandBitsArgs &p, const BandBitsJo
                 }
                 fB0 <<= 1;
                 fB1 <<= 1;
+                // (these one-bit shifts as multiply-adds, on the other pipe,
+                // measured slower: 20.2 against 18.8 ms per fill)
 #pragma unroll
                 for (int v = Q - 1; v >= 0; --v) {
                     const int32_t W = (int32_t)gl * Q + v;
@@ -362,13 +366,20 @@ static uint32_t next_pow2(uint32_t x) {
     return p;
 }
 
-bool band_bits_shape(uint32_t m, uint32_t n, int32_t lo, int32_t hi, BandBitsShape *s) {
+int band_bits_max_q() {
+    const char *e = getenv("NW_BBAND_MAXQ");
+    const int q = e ? atoi(e) : 0;
+    return q >= 1 && q <= kBandBitsMaxQ ? q : kBandBitsMaxQ;
+}
+
+bool band_bits_shape(uint32_t m, uint32_t n, int32_t lo, int32_t hi, BandBitsShape *s, int max_q) {
     const int32_t hip = hi + (int32_t)(((int64_t)m + n - hi) & 1);
     const int64_t words = ((int64_t)hip - lo + 4 + 63) / 64;
     if (words > kBandBitsMaxWords) return false;
-    // throughput shape: the fewest lanes with at most kBandBitsMaxQ words
-    // each (a lane's fixed work per step is shared by more words)
-    s->g = std::min<uint32_t>(32, next_pow2((uint32_t)((words + kBandBitsMaxQ - 1) / kBandBitsMaxQ)));
+    // throughput shape: the fewest lanes with at most max_q words each (a
+    // lane's fixed work per step is shared by more words)
+    max_q = std::min(std::max(max_q, 1), kBandBitsMaxQ);
+    s->g = std::min<uint32_t>(32, next_pow2((uint32_t)((words + max_q - 1) / max_q)));
     s->Q = (uint32_t)((words + s->g - 1) / s->g);
     s->words = (uint32_t)words;
     s->hi = hip;

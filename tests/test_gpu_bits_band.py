@@ -80,14 +80,18 @@ def test_fixed_widths_exact(ctx, w):
     assert s_only.tolist() == list(scores)
 
 
-def test_every_window_shape(ctx):
-    """Bands from one word to 255 words: up to 128 words (32 lanes x 4 words)
-    on the window kernel, with every lane count 1..32 and word count 1..4,
-    wider ones on the scalar banded kernel."""
+@pytest.mark.parametrize("fast", ["1", "0"])
+def test_every_window_shape(ctx, fast):
+    """Bands from one word to 255 words: up to 128 words on the window
+    kernel, wider ones on the scalar banded kernel.  A batch this small puts
+    most pairs on the latency shape (one word per lane up to 32 lanes, then
+    32 lanes of up to 4 words); NW_BBAND_FAST=0 keeps them on the throughput
+    shape (the fewest lanes of up to 4 words: every word count 1..4 and lane
+    count 1..32)."""
     import paper_2412_21103_gb300 as nw
     rs = seqgen.Stream(610)
     pairs, ws = [], []
-    for words in [1, 2, 3, 5, 8, 9, 12, 16, 17, 24, 33, 40, 64, 65, 100, 128, 129, 200, 255]:
+    for words in [1, 2, 3, 4, 5, 6, 7, 8, 9, 12, 16, 17, 24, 30, 33, 40, 50, 64, 65, 100, 128, 129, 200, 255]:
         w = max(0, (64 * words - 8) // 2 - 2)
         m = int(rs.integers(max(200, w), 2 * w + 600, 1)[0])
         a = rs.bases(m)
@@ -95,8 +99,14 @@ def test_every_window_shape(ctx):
         pairs.append((a, b))
         ws.append(w)
     pool, ao, al, bo, bl = _pool(pairs)
-    scores, cigars = nw.nw_align_batch_banded(ctx, pool, ao, al, bo, bl, np.array(ws, np.uint32), (1, -1, -1),
-                                              nw.NW_CIGAR)
+    os.environ["NW_BBAND_FAST"] = fast
+    os.environ["NW_BAND_KEEP"] = "1"  # no pair leaves for the full grid
+    try:
+        scores, cigars = nw.nw_align_batch_banded(ctx, pool, ao, al, bo, bl, np.array(ws, np.uint32), (1, -1, -1),
+                                                  nw.NW_CIGAR)
+    finally:
+        del os.environ["NW_BBAND_FAST"]
+        del os.environ["NW_BAND_KEEP"]
     _check_exact(pairs, scores, cigars)
 
 
