@@ -6,6 +6,7 @@
 #include <chrono>
 #include <cstdlib>
 #include <cstring>
+#include <functional>
 #include <numeric>
 #include <vector>
 
@@ -518,12 +519,40 @@ static int bits_round(nw_ctx *ctx, const uint8_t *pool, const PlaneSet &planes, 
     return NW_OK;
 }
 
+// The planar copy of a call's sequences for the window kernel, with each
+// pair's two slots by pair id.  Its table (the distinct sequences and their
+// slots) is built on the host once per call: by the learned-band entry while
+// the feature and network kernels run, else by the rounds, which then
+// upload it and launch the copy.
+struct BandPlanes {
+    bool added = false;
+    PlaneSet planes;
+    std::vector<int64_t> a_slot, b_slot;  // by pair id
+};
+
+static void add_band_planes(nw_ctx *ctx, const uint64_t *a_off, const uint32_t *a_len, const uint64_t *b_off,
+                            const uint32_t *b_len, const std::vector<uint32_t> &ids, BandPlanes &bp) {
+    HostTimer htp(ctx, "bband_planes");
+    uint32_t cap = 0;
+    for (uint32_t id : ids) cap = std::max(cap, id + 1);
+    bp.planes.reserve(2 * ids.size());
+    bp.a_slot.assign(cap, 0);
+    bp.b_slot.assign(cap, 0);
+    for (uint32_t id : ids) {
+        bp.a_slot[id] = bp.planes.add(a_off[id], a_len[id]);
+        bp.b_slot[id] = bp.planes.add(b_off[id], b_len[id]);
+    }
+    bp.added = true;
+}
+
 // Banded rounds for the pairs in `ids` with starting half-widths w0[k]; the
-// pairs no round certifies are appended to `rest` for the full kernel.
+// pairs no round certifies are appended to `rest` for the full kernel.  `bp`
+// holds the planar copy of the pairs' sequences when the caller built it.
 static int band_rounds(nw_ctx *ctx, const uint8_t *pool, const uint64_t *a_off, const uint32_t *a_len,
                        const uint64_t *b_off, const uint32_t *b_len, const std::vector<uint32_t> &ids,
                        const std::vector<uint32_t> &w0, const nw_scoring &sc, uint32_t flags, int32_t *scores,
-                       char *cigar_pool, const uint64_t *cigar_off, uint64_t *cigar_len, std::vector<uint32_t> &rest) {
+                       char *cigar_pool, const uint64_t *cigar_off, uint64_t *cigar_len, std::vector<uint32_t> &rest,
+                       BandPlanes &bp) {
     HostTimer ht_all(ctx, "band_rounds");
     const Profile pf = make_profile(sc);
     const bool want = flags & NW_CIGAR;
@@ -551,25 +580,14 @@ static int band_rounds(nw_ctx *ctx, const uint8_t *pool, const uint64_t *a_off, 
     // NW_BAND_SCALAR=1 keeps every round on the scalar banded kernel (for
     // comparisons)
     const bool use_bits = sc.match - 2 * sc.gap == 3 && sc.mismatch - 2 * sc.gap == 1 && !getenv("NW_BAND_SCALAR");
-    PlaneSet planes;
-    std::vector<int64_t> a_slot, b_slot;  // by position in ids
     uint32_t score_cap_all = 0;
-    std::vector<uint32_t> pos_of;         // pair id -> position in ids
+    for (uint32_t id : ids) score_cap_all = std::max(score_cap_all, id + 1);
     if (use_bits) {
-        HostTimer htp(ctx, "bband_planes");
-        planes.reserve(2 * ids.size());
-        a_slot.resize(ids.size());
-        b_slot.resize(ids.size());
-        for (size_t q = 0; q < ids.size(); ++q) {
-            const uint32_t id = ids[q];
-            a_slot[q] = planes.add(a_off[id], a_len[id]);
-            b_slot[q] = planes.add(b_off[id], b_len[id]);
-            score_cap_all = std::max(score_cap_all, id + 1);
-        }
-        pos_of.assign(score_cap_all, 0u);
-        for (size_t q = 0; q < ids.size(); ++q) pos_of[ids[q]] = (uint32_t)q;
-        if ((rc = planes.launch(ctx, pool, "bband"))) return rc;
+        if (!bp.added) add_band_planes(ctx, a_off, a_len, b_off, b_len, ids, bp);
+        HostTimer htp(ctx, "bband_planes_copy");
+        if ((rc = bp.planes.launch(ctx, pool, "bband"))) return rc;
     }
+    const PlaneSet &planes = bp.planes;
     for (int round = 0; round < kRounds && !pending.empty(); ++round) {
         size_t routed_full = 0;
         // the previous round's pointer words are traced already (stream
@@ -634,8 +652,8 @@ static int band_rounds(nw_ctx *ctx, const uint8_t *pool, const uint64_t *a_off, 
                     band_task(tb, R, wq);
                 }
                 if (band_bits_shape(tb.m, tb.n, tb.lo, tb.hi, &sh, max_q)) {
-                    const uint32_t pq = pos_of[tb.out0];
-                    items.push_back(BandBitsItem{tb.a_off, tb.b_off, 0, a_slot[pq], b_slot[pq], tb.m, tb.n, tb.out0, sh});
+                    items.push_back(BandBitsItem{tb.a_off, tb.b_off, 0, bp.a_slot[tb.out0], bp.b_slot[tb.out0], tb.m,
+                                                 tb.n, tb.out0, sh});
                     iw.push_back(wq);
                 } else {
                     keep.push_back(t);
@@ -853,7 +871,7 @@ static int band_raw(nw_ctx *ctx, const uint8_t *pool, const uint64_t *a_off, con
 static int band_batch(nw_ctx *ctx, const uint8_t *pool, const uint64_t *a_off, const uint32_t *a_len,
                       const uint64_t *b_off, const uint32_t *b_len, uint32_t npairs, const uint32_t *w0,
                       const nw_scoring &sc, uint32_t flags, int32_t *scores, char *cigar_pool,
-                      const uint64_t *cigar_off, uint64_t *cigar_len) {
+                      const uint64_t *cigar_off, uint64_t *cigar_len, BandPlanes &bp) {
     std::vector<uint32_t> ids(npairs), width(npairs), rest;
     ctx->band_round.assign(npairs, 0);
     ctx->band_w_cert.assign(npairs, 0);
@@ -866,7 +884,7 @@ static int band_batch(nw_ctx *ctx, const uint8_t *pool, const uint64_t *a_off, c
         ctx->band_stats[7] += full_cells(t, 8);
     }
     int rc = band_rounds(ctx, pool, a_off, a_len, b_off, b_len, ids, width, sc, flags, scores, cigar_pool, cigar_off,
-                         cigar_len, rest);
+                         cigar_len, rest, bp);
     if (rc || rest.empty()) return rc;
     // the banded pointer words are dead now: hand their memory to the full
     // kernel's waves (it stays in the context's pool for the next call)
@@ -1176,7 +1194,8 @@ static int check_batch_args(nw_ctx *ctx, const nw_scoring &sc, const uint8_t *po
 }
 
 int learned_band_widths(nw_ctx *ctx, const uint8_t *pool, const uint64_t *a_off, const uint32_t *a_len,
-                        const uint64_t *b_off, const uint32_t *b_len, uint32_t npairs, std::vector<uint32_t> &w);
+                        const uint64_t *b_off, const uint32_t *b_len, uint32_t npairs, std::vector<uint32_t> &w,
+                        const std::function<int()> &overlap);
 
 extern "C" int nw_align_batch(nw_ctx *ctx, const uint8_t *pool2b, const uint64_t *a_off, const uint32_t *a_len,
                               const uint64_t *b_off, const uint32_t *b_len, uint32_t npairs, nw_scoring sc,
@@ -1195,14 +1214,24 @@ extern "C" int nw_align_batch(nw_ctx *ctx, const uint8_t *pool2b, const uint64_t
             return batch_device_impl(ctx, pool, a_off, a_len, b_off, b_len, nullptr, npairs, sc, fl, sc_out, cig,
                                      cigar_off, clen);
         std::vector<uint32_t> w;
+        BandPlanes bp;
         int r;
         {
+            // the table of the window kernel's planar copy is built on the
+            // host while the feature and network kernels run (the paper's
+            // scoring only)
             HostTimer ht(ctx, "band_widths");
-            r = learned_band_widths(ctx, pool, a_off, a_len, b_off, b_len, npairs, w);
+            const bool bits = sc.match - 2 * sc.gap == 3 && sc.mismatch - 2 * sc.gap == 1 && !getenv("NW_BAND_SCALAR");
+            std::vector<uint32_t> all(npairs);
+            for (uint32_t k = 0; k < npairs; ++k) all[k] = k;
+            r = learned_band_widths(ctx, pool, a_off, a_len, b_off, b_len, npairs, w, [&]() -> int {
+                if (bits) add_band_planes(ctx, a_off, a_len, b_off, b_len, all, bp);
+                return NW_OK;
+            });
         }
         if (r) return r;
         return band_batch(ctx, pool, a_off, a_len, b_off, b_len, npairs, w.data(), sc, fl, sc_out, cig, cigar_off,
-                          clen);
+                          clen, bp);
     };
     if (!(flags & NW_HOST_IO)) return body(pool2b, scores, cigar_pool, cigar_len);
     return with_host_io(ctx, pool2b, a_off, a_len, b_off, b_len, npairs, flags, scores, cigar_pool, cigar_off,
@@ -1226,8 +1255,9 @@ extern "C" int nw_align_batch_banded(nw_ctx *ctx, const uint8_t *pool2b, const u
     if ((flags & NW_BAND_RAW) && (flags & NW_CIGAR)) return fail(ctx, NW_ERR_ARG, "NW_BAND_RAW is score only");
     auto body = [&](const uint8_t *pool, int32_t *sc_out, char *cig, uint64_t *clen) -> int {
         if (flags & NW_BAND_RAW) return band_raw(ctx, pool, a_off, a_len, b_off, b_len, npairs, band_w, sc, sc_out);
+        BandPlanes bp;
         return band_batch(ctx, pool, a_off, a_len, b_off, b_len, npairs, band_w, sc, flags & ~NW_HOST_IO, sc_out, cig,
-                          cigar_off, clen);
+                          cigar_off, clen, bp);
     };
     if (!(flags & NW_HOST_IO)) return body(pool2b, scores, cigar_pool, cigar_len);
     return with_host_io(ctx, pool2b, a_off, a_len, b_off, b_len, npairs, flags, scores, cigar_pool, cigar_off,

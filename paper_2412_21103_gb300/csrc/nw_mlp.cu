@@ -22,6 +22,7 @@
 #include <cstdio>
 #include <cstdlib>
 #include <cstring>
+#include <functional>
 #include <vector>
 
 #include "nw_internal.cuh"
@@ -304,8 +305,13 @@ static int features_smem(nw_ctx *ctx, uint32_t maxn) {
 // Features -> network -> half-widths (with a safety factor), on the host.
 uint32_t band_start_width(float y, uint32_t m, uint32_t n, double margin, double probe_cap, bool skip);
 
+// `overlap` runs on the host once the feature and network kernels are
+// queued, before the copy of their output (a copy into pageable memory
+// returns only when it is done); not at all when the call keeps the fixed
+// start.
 int learned_band_widths(nw_ctx *ctx, const uint8_t *pool, const uint64_t *a_off, const uint32_t *a_len,
-                        const uint64_t *b_off, const uint32_t *b_len, uint32_t npairs, std::vector<uint32_t> &w) {
+                        const uint64_t *b_off, const uint32_t *b_len, uint32_t npairs, std::vector<uint32_t> &w,
+                        const std::function<int()> &overlap) {
     w.assign(npairs, 64u);
     BandModel *bm = nullptr;
     if (!ctx->band_model) return NW_OK;  // no model: fixed starting width 64
@@ -345,6 +351,7 @@ int learned_band_widths(nw_ctx *ctx, const uint8_t *pool, const uint64_t *a_off,
     if (const cudaError_t e = cudaGetLastError(); e != cudaSuccess) return cuda_fail(ctx, e, "features launch");
     Acts a;
     if ((rc = forward(ctx, bm, (const float *)f, npairs, a))) return rc;
+    if (overlap && (rc = overlap())) return rc;
     std::vector<float> y(npairs);
     cudaMemcpyAsync(y.data(), a.y, (size_t)npairs * 4, cudaMemcpyDeviceToHost, ctx->stream);
     if ((rc = nw_ctx_sync(ctx))) return rc;
