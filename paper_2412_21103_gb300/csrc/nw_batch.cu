@@ -13,6 +13,7 @@
 #include "nw_batch_kernel.cuh"
 #include "nw_bits.cuh"
 #include "nw_internal.cuh"
+#include "nw_order.h"
 
 namespace nw {
 
@@ -238,9 +239,10 @@ static PairCost single_pair_cost(uint32_t m, uint32_t n, const nw_scoring &sc) {
 static std::vector<size_t> pick_stragglers(const std::vector<double> &warp_cells, const std::vector<double> &full_cells,
                                            const std::vector<PairCost> &costs, int sms,
                                            double batch_rate = kBatchRate) {
-    std::vector<size_t> order(warp_cells.size());
-    std::iota(order.begin(), order.end(), (size_t)0);
-    std::sort(order.begin(), order.end(), [&](size_t x, size_t y) { return warp_cells[x] > warp_cells[y]; });
+    std::vector<uint64_t> keys(warp_cells.size());
+    for (size_t k = 0; k < keys.size(); ++k) keys[k] = order_key(warp_cells[k]);
+    const std::vector<uint32_t> ord = radix_order_desc(std::move(keys));  // largest first, index order among equals
+    const std::vector<size_t> order(ord.begin(), ord.end());
     double rest = 0;
     for (double c : warp_cells) rest += c;
     const double lanes = 6.0 * std::max(sms, 1);  // warps at full speed on the GPU's schedulers

@@ -40,6 +40,7 @@
 #include <vector>
 
 #include "nw_bits.cuh"
+#include "nw_order.h"
 
 namespace nw {
 
@@ -417,14 +418,13 @@ int band_bits_fill(nw_ctx *ctx, const PlaneSet &planes, const std::vector<BandBi
     HostTimer ht(ctx, "bband_fill_host");
     HostTimer htp(ctx, "bband_fill_prep");
     // jobs: pairs of equal shape (g, Q), similar lengths, 32/g per warp
-    std::vector<uint32_t> order(items.size());
-    for (uint32_t k = 0; k < order.size(); ++k) order[k] = k;
-    std::stable_sort(order.begin(), order.end(), [&](uint32_t x, uint32_t y) {
-        const BandBitsShape &a = items[x].shape, &b = items[y].shape;
-        if (a.Q != b.Q) return a.Q > b.Q;
-        if (a.g != b.g) return a.g > b.g;
-        return a.nchunks > b.nchunks;
-    });
+    // (Q, g, chunks), each descending, ties in item order
+    std::vector<uint64_t> keys(items.size());
+    for (size_t k = 0; k < items.size(); ++k) {
+        const BandBitsShape &sh = items[k].shape;
+        keys[k] = ((uint64_t)sh.Q << 40) | ((uint64_t)sh.g << 32) | sh.nchunks;
+    }
+    const std::vector<uint32_t> order = radix_order_desc(std::move(keys));
     std::vector<BandBitsTask> tasks(items.size());
     std::vector<uint32_t> task_item(items.size());
     std::vector<BandBitsJob> jobs;
@@ -450,10 +450,15 @@ int band_bits_fill(nw_ctx *ctx, const PlaneSet &planes, const std::vector<BandBi
         }
         jobs.push_back(j);
     }
-    // longest jobs first
-    std::stable_sort(jobs.begin(), jobs.end(), [](const BandBitsJob &x, const BandBitsJob &y) {
-        return (uint64_t)x.nchunks * (20 * x.Q + 14) > (uint64_t)y.nchunks * (20 * y.Q + 14);
-    });
+    // longest jobs first (ties in job order)
+    {
+        std::vector<uint64_t> jk(jobs.size());
+        for (size_t q = 0; q < jobs.size(); ++q) jk[q] = (uint64_t)jobs[q].nchunks * (20 * jobs[q].Q + 14);
+        const std::vector<uint32_t> jo = radix_order_desc(std::move(jk));
+        std::vector<BandBitsJob> sorted(jobs.size());
+        for (size_t q = 0; q < jobs.size(); ++q) sorted[q] = jobs[jo[q]];
+        jobs.swap(sorted);
+    }
     void *v = nullptr;
     if ((rc = scratch(ctx, "bband_tasks", tasks.size() * sizeof(BandBitsTask) + 16, &v))) return rc;
     BandBitsTask *dt = (BandBitsTask *)v;
@@ -524,10 +529,13 @@ int band_bits_walk(nw_ctx *ctx, const void *ptr, const std::vector<BandBitsItem>
     int rc;
     HostTimer ht(ctx, "bband_walk_host");
     // longest walks first: the kernel's warps take pairs in order
-    std::vector<uint32_t> order(which);
-    std::stable_sort(order.begin(), order.end(), [&](uint32_t x, uint32_t y) {
-        return (uint64_t)items[x].m + items[x].n > (uint64_t)items[y].m + items[y].n;
-    });
+    std::vector<uint32_t> order(which.size());
+    {
+        std::vector<uint64_t> wk(which.size());
+        for (size_t q = 0; q < which.size(); ++q) wk[q] = (uint64_t)items[which[q]].m + items[which[q]].n;
+        const std::vector<uint32_t> wo = radix_order_desc(std::move(wk));  // ties in `which` order
+        for (size_t q = 0; q < which.size(); ++q) order[q] = which[wo[q]];
+    }
     uint64_t mbytes = 0;
     for (uint32_t k : order) mbytes += (uint64_t)items[k].m + items[k].n + 16;
     void *mv = nullptr, *nm = nullptr, *v = nullptr;
