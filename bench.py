@@ -94,14 +94,34 @@ def code_only(text: str) -> str:
     return "\n".join(ln.rstrip() for ln in "".join(out).splitlines() if ln.strip())
 
 
-def sources_sha(files) -> str:
+def source_region(text: str, spec: str) -> str:
+    """The part of a source that a record covers: the whole text, or for a
+    spec `from..to` the lines from the first one holding `from` up to (not
+    including) the next one holding `to` (empty when either is missing)."""
+    if not spec:
+        return text
+    start, _, end = spec.partition("..")
+    lines = text.splitlines()
+    try:
+        i = next(k for k, ln in enumerate(lines) if start in ln)
+        j = next(k for k in range(i + 1, len(lines)) if end in lines[k])
+    except StopIteration:
+        return ""
+    return "\n".join(lines[i:j])
+
+
+def sources_sha(files, read=None) -> str:
     """First 16 hex digits of the sha256 over the code (comments removed) of
-    the given files, in name order."""
+    the given sources, in name order.  A source is a file path, or
+    `path#from..to` for one region of it (source_region); `read(path)` gives
+    a file's text (default: the file in this tree)."""
     import hashlib
+    read = read or (lambda f: open(os.path.join(HERE, f), encoding="utf-8").read())
     h = hashlib.sha256()
-    for f in sorted(files):
-        h.update(os.path.basename(f).encode())
-        h.update(code_only(open(os.path.join(HERE, f), encoding="utf-8").read()).encode())
+    for src in sorted(files):
+        f, _, spec = src.partition("#")
+        h.update(os.path.basename(src).encode())
+        h.update(code_only(source_region(read(f), spec)).encode())
     return h.hexdigest()[:16]
 
 

@@ -268,12 +268,21 @@ struct BitsWalkTask {
 };
 
 // One warp per pair: it stages 32 records (64 anti-diagonals) of the three
-// words around the walk's position into shared memory, then lane 0 walks
-// from (m, n) while the cells stay inside them; moves are written in walk
-// order (0 diagonal, 1 vertical, 2 horizontal), as the CIGAR assembly reads.
-// While lane 0 walks one block, the loads of the 32 records before it (the
+// words around the walk's position into shared memory, then walks from
+// (m, n) while the cells stay inside them; moves are written in walk order
+// (0 diagonal, 1 vertical, 2 horizontal), as the CIGAR assembly reads.
+// While the warp walks one block, the loads of the 32 records before it (the
 // same words) are in flight; they fill the second buffer, which the walk
 // continues in unless it left those words (then a new block is staged).
+//
+// RUNS: the whole warp walks, a run of diagonal moves at a time.  A
+// diagonal move keeps the cell's row in the window (same word and bit) and
+// goes one record row down, so lane t reads the cell t diagonal moves on;
+// a ballot of their L bits gives the run's length (its first lane whose
+// diagonal loses), the run's zero bytes are one store, and the cell that
+// ends it gives the vertical or horizontal move by its Hb bit.  Otherwise
+// lane 0 walks one move at a time.
+template <bool RUNS>
 __global__ void __launch_bounds__(kWalkWarps * 32) k_bits_walk(const uint4 *ptr, const BitsWalkTask *tasks,
                                                                uint32_t ntasks, uint8_t *moves, uint64_t *nmoves,
                                                                uint32_t *err) {
@@ -313,7 +322,48 @@ __global__ void __launch_bounds__(kWalkWarps * 32) k_bits_walk(const uint4 *ptr,
 #pragma unroll
             for (int x = 0; x < 3; ++x)
                 r[x] = (rec >= 0 && w_lo + x < gq) ? __ldcg(pp + (uint64_t)rec * gq + w_lo + x) : make_uint4(0, 0, 0, 0);
-            if (lane == 0) {
+            if (RUNS) {
+                // every pass makes a move or leaves the loop: at most m + n passes
+                const uint64_t k0 = k;
+                while (i > 0 && j > 0) {
+                    const int32_t a2 = i + j, rel = a2 - tk.a_first, x = (rel >> 1) - ds_lo, par = rel & 1;
+                    const int32_t P = i - ((a2 - tk.hi) >> 1), W2 = P >> 5, y = W2 - w_lo;
+                    if (x < 0 || x > 31 || y < 0 || y > 2 || W2 >= gq || P < 0) break;
+                    const uint32_t bit = (uint32_t)P & 31u;
+                    // lane t: the cell t diagonal moves on (record row x - t, same word and bit);
+                    // rows outside the block count as ending the run
+                    const int32_t xr = x - (int32_t)lane;
+                    uint32_t Lw = ~0u, Hw = 0u;
+                    if (xr >= 0 && ds_lo + xr >= 0) {
+                        const uint4 rc = tile[wb][cur][xr][y];
+                        Lw = par ? rc.z : rc.x;
+                        Hw = par ? rc.w : rc.y;
+                    }
+                    const uint32_t stop = __ballot_sync(kFull, (Lw >> bit) & 1u);
+                    const int32_t f = stop ? __ffs(stop) - 1 : 32;
+                    const int32_t run = min(f, min(i, j));
+                    if ((int32_t)lane < run) mv[k + lane] = 0;
+                    k += (uint64_t)run;
+                    i -= run;
+                    j -= run;
+                    const uint32_t hb = __shfl_sync(kFull, (Hw >> bit) & 1u, f & 31);
+                    if (run == f && f < 32 && x - f >= 0 && ds_lo + x - f >= 0 && i > 0 && j > 0) {
+                        const uint32_t mvc = hb ? 2u : 1u;
+                        if (lane == 0) mv[k] = (uint8_t)mvc;
+                        ++k;
+                        i -= mvc == 1u;
+                        j -= mvc == 2u;
+                    } else if (run == 0) {
+                        break;
+                    }
+                }
+                // a block staged at the walk's own cell: no progress means the
+                // walk left the window, which a certified band excludes
+                if (staged && k == k0) {
+                    if (lane == 0) raise_error(err, NW_ERR_ARG, 0x50000u + ti);
+                    ok = false;
+                }
+            } else if (lane == 0) {
                 uint32_t steps = 0;
                 while (i > 0 && j > 0) {
                     const int32_t a2 = i + j, rel = a2 - tk.a_first, d2 = rel >> 1;
@@ -581,8 +631,12 @@ int band_bits_walk(nw_ctx *ctx, const void *ptr, const std::vector<BandBitsItem>
         // 16 / 8 / 4 / 2 / 1 measured 8.6 / 9.3 / 10.1 / 14.9 / 24.2 ms per step
         // on config 4, against 8.3 ms uncapped)
         const uint32_t blocks = (uint32_t)std::min<size_t>((which.size() + kWalkWarps - 1) / kWalkWarps, 65535);
-        k_bits_walk<<<blocks, kWalkWarps * 32, 0, ctx->stream>>>((const uint4 *)ptr, dw, (uint32_t)which.size(),
-                                                                 (uint8_t *)mv, (uint64_t *)nm, ctx->d_err);
+        // runs of diagonal moves at a time; NW_BWALK_SERIAL=1 walks one move
+        // at a time on lane 0 (for comparisons)
+        const char *se = getenv("NW_BWALK_SERIAL");
+        auto walk = (se && *se == '1') ? k_bits_walk<false> : k_bits_walk<true>;
+        walk<<<blocks, kWalkWarps * 32, 0, ctx->stream>>>((const uint4 *)ptr, dw, (uint32_t)which.size(),
+                                                          (uint8_t *)mv, (uint64_t *)nm, ctx->d_err);
     }
     e = cudaGetLastError();
     if (e != cudaSuccess) return cuda_fail(ctx, e, "walk launch");

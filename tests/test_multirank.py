@@ -88,6 +88,27 @@ def test_traffic_records_ignore_comment_edits_only(tmp_path):
     assert bench.sources_sha([str(f)]) != h0
 
 
+def test_traffic_record_of_a_region_ignores_the_rest_of_its_file(tmp_path):
+    """A record that covers one kernel's region of a file (`path#from..to`)
+    keeps its hash when code outside the region changes and loses it when
+    the region's code changes or its markers are gone."""
+    sys.path.insert(0, ROOT)
+    import bench
+    f = tmp_path / "k.cu"
+    src = lambda fill, walk: (f"struct Args {{ int x; }};\n__global__ void fill(int *p) {{ p[0] = {fill}; }}\n"
+                              f"struct WalkTask {{ int y; }};\n__global__ void walk(int *p) {{ p[1] = {walk}; }}\n")
+    spec = [str(f) + "#struct Args {..struct WalkTask {"]
+    f.write_text(src(1, 1))
+    h0 = bench.sources_sha(spec)
+    f.write_text(src(1, 2))  # the walk changed: not in the region
+    assert bench.sources_sha(spec) == h0
+    f.write_text(src(2, 2))  # the fill changed
+    assert bench.sources_sha(spec) != h0
+    f.write_text(src(1, 1).replace("struct WalkTask", "struct Other"))
+    assert bench.sources_sha(spec) != h0
+    assert bench.source_region("a\nb\nc\n", "a..c") == "a\nb"
+
+
 def test_clock_summary_keeps_the_timed_window_and_reasons():
     """The bench's clock record: only samples inside the timed window count,
     the median SM clock and the active throttle reasons are reported."""
