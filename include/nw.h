@@ -251,11 +251,13 @@ int nw_align(nw_ctx *ctx, const uint8_t *a2b, uint64_t m, const uint8_t *b2b, ui
  * the process exits.  a2b, b2b and score are device pointers on the current
  * device; the kernel runs on `stream` (a cudaStream_t, NULL = legacy
  * default) and the call waits for that stream (cudaStreamSynchronize)
- * before returning, so a device-side timeout comes back as NW_ERR_TIMEOUT.
- * The first call on each device looks up the array's device address with
- * that device current and keeps it for later calls (make that first call
- * before any stream capture); a cudaDeviceReset while the library is
- * loaded is not supported, since the kept address would be stale.
+ * before returning, so a device-side timeout comes back as NW_ERR_TIMEOUT;
+ * because it waits for its stream, it may not be called while that stream
+ * (or the legacy default stream) is being captured into a CUDA graph.  The
+ * first call on each device looks up the array's device address with that
+ * device current and keeps it for later calls; a cudaDeviceReset while the
+ * library is loaded is not supported, since the kept address would be
+ * stale.
  * Sizes: ceil(m/512) <= 4096 and (ceil(m/512)-1) * 32*ceil((n+1)/32) <=
  * 3,141,568 words (for example m = n = 32,768 fits); larger inputs return
  * NW_ERR_ARG.  Calls share the array, so calls that overlap on the GPU
